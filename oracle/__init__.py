@@ -1,0 +1,195 @@
+"""FP64 CPU oracle for the ANI-2x-style NNP energy and forces.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package.  The
+product path (``paper_2201_08110_gb300``) never imports it and shares no code,
+table or constant with it.
+
+The arithmetic lives in ``ani_oracle.c`` (plain C, FP64, built with
+``-ffp-contract=off`` so every product and sum is rounded on its own); this
+module compiles it with gcc on first use and marshals numpy arrays.  What is
+computed is the NNP term V_NNP(Z, r) of the paper's Sec. 2 (Eqs. 2-3) and
+F = -grad V_NNP, with the ANI featurizer and ensemble of atomic networks the
+paper names in Sec. 1 and Sec. 2 ("Optimization").  The functional form is
+written out in the header of ``ani_oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ani_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD_DIR, "libani_oracle.so")
+
+NUM_FEATURES = 1008
+ELEMENTS_Z = (1, 6, 7, 8, 9, 16, 17)
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ani_oracle.c into a shared library (gcc, OpenMP, FP64)."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        lib.ani_oracle_weights_per_model.restype = ctypes.c_long
+        lib.ani_oracle_compute.restype = ctypes.c_int
+        lib.ani_oracle_compute.argtypes = [ctypes.c_int, P, P, P, P, ctypes.c_int, P,
+                                           ctypes.c_long, P, P, P, P, P, ctypes.c_int]
+        lib.ani_oracle_pairs.restype = ctypes.c_long
+        lib.ani_oracle_pairs.argtypes = [ctypes.c_int, P, P, ctypes.c_double, P, P, ctypes.c_long]
+        lib.ani_oracle_triples.restype = ctypes.c_long
+        lib.ani_oracle_triples.argtypes = [ctypes.c_int, P, P, ctypes.c_double, P, P, P,
+                                           ctypes.c_long]
+        lib.ani_oracle_aev.restype = ctypes.c_int
+        lib.ani_oracle_aev.argtypes = [ctypes.c_int, P, P, P, P]
+        lib.ani_oracle_aev_adjoint.restype = ctypes.c_int
+        lib.ani_oracle_aev_adjoint.argtypes = [ctypes.c_int, P, P, P, P, P]
+        lib.ani_oracle_hyper.restype = None
+        lib.ani_oracle_hyper.argtypes = [P]
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _box(box):
+    if box is None:
+        return None
+    b = np.ascontiguousarray(box, dtype=np.float64).reshape(3)
+    if not np.any(b):
+        return None
+    return b
+
+
+def weights_per_model() -> int:
+    return int(_load().ani_oracle_weights_per_model())
+
+
+def hyper() -> dict:
+    """The featurizer constants as the oracle uses them."""
+    out = np.zeros(33, dtype=np.float64)
+    _load().ani_oracle_hyper(_ptr(out))
+    return {"Rcr": out[0], "Rca": out[1], "EtaR": out[2], "EtaA": out[3], "Zeta": out[4],
+            "ShfR": out[5:21].copy(), "ShfA": out[21:29].copy(), "ShfZ": out[29:33].copy()}
+
+
+def compute(Z, pos, mol_off, weights, n_models, box=None, forces=True, aev=False,
+            atom_energies=False, dEdG=False, nthreads=0):
+    """Energies [n_mols] and (optionally) forces [N,3], features [N,1008],
+    per-atom energies [N] and dE/dG [N,1008] of a batch, all FP64.
+
+    pos may be float32 or float64; float32 values are promoted exactly.
+    """
+    lib = _load()
+    Z = np.ascontiguousarray(Z, dtype=np.int32)
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    mol_off = np.ascontiguousarray(mol_off, dtype=np.int32)
+    w = np.ascontiguousarray(weights, dtype=np.float32).reshape(-1)
+    n = int(mol_off[-1])
+    assert Z.shape[0] == n and pos.shape[0] == n
+    n_mols = mol_off.shape[0] - 1
+    E = np.zeros(n_mols, dtype=np.float64)
+    F = np.zeros((n, 3), dtype=np.float64) if (forces or dEdG) else None
+    G = np.zeros((n, NUM_FEATURES), dtype=np.float64) if aev else None
+    Ea = np.zeros(n, dtype=np.float64) if atom_energies else None
+    dG = np.zeros((n, NUM_FEATURES), dtype=np.float64) if dEdG else None
+    rc = lib.ani_oracle_compute(n_mols, _ptr(mol_off), _ptr(Z), _ptr(pos), _ptr(_box(box)),
+                                int(n_models), _ptr(w), int(w.size), _ptr(E), _ptr(F), _ptr(G),
+                                _ptr(Ea), _ptr(dG), int(nthreads))
+    if rc == -1:
+        raise ValueError("oracle: unsupported atomic number")
+    if rc != 0:
+        raise ValueError(f"oracle: bad arguments (code {rc})")
+    out = {"energy": E}
+    if forces:
+        out["forces"] = F
+    if aev:
+        out["aev"] = G
+    if atom_energies:
+        out["atom_energies"] = Ea
+    if dEdG:
+        out["dEdG"] = dG
+    return out
+
+
+def energy(Z, pos, weights, n_models, box=None):
+    """Energy of a single molecule (all atoms), FP64."""
+    n = len(Z)
+    return float(compute(Z, pos, np.array([0, n]), weights, n_models, box=box,
+                         forces=False)["energy"][0])
+
+
+def pairs(pos, rc, box=None):
+    """Ordered pairs (i, j), i != j, with d^2 < rc^2 (FP64 predicate)."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    n = pos.shape[0]
+    cap = max(1, n * (n - 1))
+    I = np.zeros(cap, dtype=np.int32)
+    J = np.zeros(cap, dtype=np.int32)
+    cnt = lib.ani_oracle_pairs(n, _ptr(pos), _ptr(_box(box)), float(rc), _ptr(I), _ptr(J), cap)
+    return np.stack([I[:cnt], J[:cnt]], axis=1)
+
+
+def triples(pos, rc, box=None):
+    """Triples (i, j, k), j < k, both within rc of centre i."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    n = pos.shape[0]
+    cap = max(1, n * (n - 1) * (n - 2) // 2)
+    I = np.zeros(cap, dtype=np.int32)
+    J = np.zeros(cap, dtype=np.int32)
+    K = np.zeros(cap, dtype=np.int32)
+    cnt = lib.ani_oracle_triples(n, _ptr(pos), _ptr(_box(box)), float(rc), _ptr(I), _ptr(J),
+                                 _ptr(K), cap)
+    return np.stack([I[:cnt], J[:cnt], K[:cnt]], axis=1)
+
+
+def aev(Z, pos, box=None):
+    """Feature vectors [n, 1008] of one molecule, FP64."""
+    lib = _load()
+    Z = np.ascontiguousarray(Z, dtype=np.int32)
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros((Z.shape[0], NUM_FEATURES), dtype=np.float64)
+    if lib.ani_oracle_aev(Z.shape[0], _ptr(Z), _ptr(pos), _ptr(_box(box)), _ptr(out)) != 0:
+        raise ValueError("oracle: unsupported atomic number")
+    return out
+
+
+def aev_adjoint(Z, pos, g, box=None):
+    """d(sum_i g_i . G_i)/dx for one molecule, FP64 [n, 3]."""
+    lib = _load()
+    Z = np.ascontiguousarray(Z, dtype=np.int32)
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    g = np.ascontiguousarray(g, dtype=np.float64).reshape(Z.shape[0], NUM_FEATURES)
+    out = np.zeros((Z.shape[0], 3), dtype=np.float64)
+    if lib.ani_oracle_aev_adjoint(Z.shape[0], _ptr(Z), _ptr(pos), _ptr(_box(box)), _ptr(g),
+                                  _ptr(out)) != 0:
+        raise ValueError("oracle: unsupported atomic number")
+    return out
