@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Throughput of NNP energy + force evaluation on GB300, in atom-evals/s.
+
+One step = one energy + force evaluation of a whole batch (neighbour lists,
+features, the 8-network ensemble forward and reverse, the featurizer's reverse
+pass to coordinates), i.e. every stage of the path.  Default workload: 512
+molecules with 20-120 atoms (H .45, C .35, N .08, O .08, F/S/Cl .04), random
+Xavier-normal ANI-2x-architecture weights, network products in BF16, replayed
+as one CUDA graph per step.  An atom-eval is one atom's share of E and F for
+the full ensemble.
+
+Also reported: the plain FP32 unbatched GPU path on a sample of the same
+molecules (one molecule per call, direct launches), the end-to-end number
+through the host-buffer entry point, per-stage times with the roofline of the
+dominant stage, and the FP64 CPU oracle on the host cores.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2201_08110_gb300 import workloads as W  # noqa: E402
+
+METRIC = "NNP energy+force atom-evals/s vs plain FP32 path on 1 GB300 at stated error"
+UNIT = "atom-evals/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--molecules", type=int, default=512)
+    ap.add_argument("--unbatched-sample", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers ----
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def rank_batch(n_mols: int, rank: int):
+    """Workload 3's batch on rank 0; other ranks draw their own molecules of the
+    same distribution (weak scaling: per-rank work is fixed)."""
+    b, w, M = W.config3(n_mols)
+    if rank == 0:
+        return b, w, M
+    sizes = np.random.Generator(np.random.PCG64(W.workload_seed(3) + 100 + rank)).integers(
+        20, 121, size=n_mols)
+    return W.batch(W.workload_seed(3) + 7919 * rank, sizes), w, M
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, n in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        loaded = [s for s in sm if s > 0.5 * (max(mx) if mx else 1)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d["hbm_gbs"], d["bf16_tflops"], d.get("bf16_tflops_sustained"), "measured", d.get("sm_max_mhz", 2070.0)
+    return 6800.0, 1900.0, 1700.0, "fallback", 2070.0
+
+
+# Algorithmic work per stage ("Algorithmic work").
+HID = W.HIDDEN
+
+
+def stage_work(Z, M: int, es: int):
+    """FLOPs of each matrix-product stage and HBM bytes of the featurizer
+    stages, from the element counts of the batch.  K of the first layer is the
+    1008 real features (padding excluded)."""
+    zs = list(W.ELEMENTS_Z)
+    cnt = [int(np.sum(Z == z)) for z in zs]
+    f = {"l1_fwd": 0.0, "l2_fwd": 0.0, "l3_fwd": 0.0, "l3_rev": 0.0, "l2_rev": 0.0, "l1_rev": 0.0}
+    for e, n in enumerate(cnt):
+        h1, h2, h3 = HID[e]
+        f["l1_fwd"] += 2.0 * n * M * h1 * 1008
+        f["l2_fwd"] += 2.0 * n * M * h1 * h2
+        f["l3_fwd"] += 2.0 * n * M * h2 * h3 + 2.0 * n * M * h3
+        f["l3_rev"] += 2.0 * n * M * h3 * h2
+        f["l2_rev"] += 2.0 * n * M * h2 * h1
+        f["l1_rev"] += 2.0 * n * M * h1 * 1008
+    N = len(Z)
+    # featurizer: positions in (16 B), features out (1008 * es); reverse: dE/dG in (1008 * 4)
+    # and forces out (24 B)
+    b = {"features": N * (16.0 + 1008 * es), "adjoint": N * (16.0 + 1008 * 4 + 24)}
+    return f, b
+
+
+def src_hash(*names):
+    h = hashlib.sha256()
+    for n in names:
+        h.update(open(os.path.join(ROOT, "paper_2201_08110_gb300", "csrc", n), "rb").read())
+    return h.hexdigest()[:12]
+
+
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
+# kernel, keyed by the kernel's source hash at capture time (profiles/ holds the
+# summaries); scaled to the bench workload by atoms.  Empty until captured.
+NCU_TRAFFIC = {}
+
+
+def cpu_oracle_rate(b, w, M, target_s: float = 12.0):
+    """The FP64 oracle as it stands, on all host cores, over a bounded sample
+    of the batch's molecules (atom-evals/s, sample description, cores)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    n_done = 0
+    atoms = 0
+    m = 0
+    chunk = max(1, cores)
+    while time.perf_counter() - t0 < target_s and m < b.n_mols:
+        hi = min(b.n_mols, m + chunk)
+        sub_off = b.mol_off[m:hi + 1] - b.mol_off[m]
+        a0, a1 = int(b.mol_off[m]), int(b.mol_off[hi])
+        oracle.compute(b.Z[a0:a1], b.pos[a0:a1], sub_off, w, M, nthreads=cores)
+        atoms += a1 - a0
+        n_done += hi - m
+        m = hi
+    dt = time.perf_counter() - t0
+    return atoms / dt, f"first {n_done} molecules ({atoms} atoms) of the batch, {dt:.1f} s", cores
+
+
+# ------------------------------------------------------------------ arms ----
+
+def run_reference(args):
+    """The oracle (FP64 C, OpenMP over molecules) timed on the host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    b, w, M = W.config3(args.molecules)
+    cores = os.cpu_count() or 1
+    per_step_mols = max(cores, 16)
+    sub = slice(0, per_step_mols)
+    a1 = int(b.mol_off[per_step_mols])
+    Z, pos, off = b.Z[:a1], b.pos[:a1], b.mol_off[:per_step_mols + 1]
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle.compute(Z, pos, off, w, M, nthreads=cores)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.compute(Z, pos, off, w, M, nthreads=cores)
+        ts.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(ts) / len(ts)
+    value = a1 / (ms / 1e3)
+    sample = f"{per_step_mols} molecules ({a1} atoms) of workload 3 per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "workload 3 batch (512 molecules, 20-120 atoms), 8 networks",
+                       "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    del sub
+    return 0
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2201_08110_gb300 import build, nnp
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+
+    b, w, M = rank_batch(args.molecules, rank)
+    # CPU baseline first (no CUDA work in flight; the oracle uses its own threads)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        rate, sample, cores = cpu_oracle_rate(b, w, M)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    model = nnp.NNP(b.Z, w, M, mol_off=b.mol_off, precision=args.precision, use_graph=True)
+    pos = torch.tensor(b.pos, device="cuda")
+    E = torch.empty(b.n_mols, dtype=torch.float64, device="cuda")
+    F = torch.empty(b.n_atoms, 3, dtype=torch.float64, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        model.compute(pos, E, F)
+    torch.cuda.synchronize()
+    model.status()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush, outside the timed events
+        starts[k].record(stream)
+        model.compute(pos, E, F)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    if dist is not None:
+        dist.barrier()
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    model.status()
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    n_atoms_all = torch.tensor([float(b.n_atoms)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n_atoms_all, op=dist.ReduceOp.SUM)
+    total_ms = float(t.item())
+    atoms_all = float(n_atoms_all.item())
+    ms_per_step = total_ms / args.steps
+    value = atoms_all * args.steps / (total_ms / 1e3)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- per-stage times and the roofline of the dominant stage ----
+    stage_runs = [model.compute_timed(pos, E, F) for _ in range(5)]
+    stages = {k: statistics.median(r[k] for r in stage_runs) for k in stage_runs[0]}
+    hbm, bf16, bf16_sus, peak_kind, sm_max = peaks()
+    es = 4 if args.precision == "fp32" else 2
+    flops, bytes_ = stage_work(b.Z, M, es)
+    dom = max(stages, key=stages.get)
+    if dom in flops:
+        achieved = flops[dom] / (stages[dom] * 1e-3) / 1e12
+        if args.precision == "fp32":
+            peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FFMA lanes x 2 x max clock
+            roof = {"bound": "alu", "unit": "TFLOP/s", "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+        else:
+            peak = bf16
+            roof = {"bound": "tensor", "unit": "TFLOP/s", "peak_note": f"{peak_kind} bf16 burst"}
+    else:
+        achieved = bytes_.get(dom, 0.0) / (stages[dom] * 1e-3) / 1e9
+        peak = hbm
+        roof = {"bound": "hbm", "unit": "GB/s", "peak_note": f"{peak_kind} copy bandwidth"}
+    kernel_key = {"features": "aev.cu", "adjoint": "aev.cu"}.get(dom, "mlp_tc.cu" if es == 2 else "mlp_simt.cu")
+    tr = NCU_TRAFFIC.get((dom, src_hash(kernel_key)))
+    roof.update({"stage": dom, "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                 "traffic": None if tr is None else tr * b.n_atoms})
+    stage_share = {k: v / max(sum(stages.values()), 1e-12) for k, v in stages.items()}
+
+    # ---- end to end through the host-buffer entry point (pinned buffers) ----
+    hpos = torch.from_numpy(b.pos.copy()).pin_memory()
+    hE = torch.empty(b.n_mols, dtype=torch.float64).pin_memory()
+    hF = torch.empty(b.n_atoms, 3, dtype=torch.float64).pin_memory()
+    lib = nnp.load_library()
+    for _ in range(2):
+        lib.nnp_compute_host(model._h, hpos.data_ptr(), hE.data_ptr(), hF.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rc = lib.nnp_compute_host(model._h, hpos.data_ptr(), hE.data_ptr(), hF.data_ptr(),
+                                  stream.cuda_stream)
+        assert rc == 0
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": b.n_atoms * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(hpos.numel() * 4),
+           "d2h_bytes_per_step": int(hE.numel() * 8 + hF.numel() * 8)}
+
+    # ---- the plain FP32 unbatched path on a sample of the same molecules ----
+    unb = None
+    if args.unbatched_sample > 0:
+        ids = np.random.Generator(np.random.PCG64(17)).choice(b.n_mols, min(args.unbatched_sample, b.n_mols), replace=False)
+        tot_ms, tot_atoms = 0.0, 0
+        for m in ids:
+            sub = b.molecule(int(m))
+            h1 = nnp.NNP(sub.Z, w, M, precision="fp32", use_graph=False)
+            p1 = torch.tensor(sub.pos, device="cuda")
+            e1 = torch.empty(1, dtype=torch.float64, device="cuda")
+            f1 = torch.empty(sub.n_atoms, 3, dtype=torch.float64, device="cuda")
+            for _ in range(3):
+                h1.compute(p1, e1, f1)
+            torch.cuda.synchronize()
+            reps = 10
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            for _ in range(reps):
+                h1.compute(p1, e1, f1)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            tot_ms += s0.elapsed_time(s1) / reps
+            tot_atoms += sub.n_atoms
+            h1.close()
+        unb = {"value": tot_atoms / (tot_ms / 1e3), "unit": UNIT,
+               "sample": f"{len(ids)} molecules of the batch, one per call, FP32 networks, direct launches",
+               "ms_per_molecule": tot_ms / len(ids)}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"{args.molecules} molecules, 20-120 atoms, 8-network ensemble "
+                                   f"(workload 3 batch; {args.precision} networks as workload 4)",
+                       "n_molecules": b.n_mols, "n_atoms_per_rank": b.n_atoms, "n_models": M,
+                       "precision": args.precision, "graph": True,
+                       "l2": "flushed (256 MB write) between timed steps, outside the timed events",
+                       "parallelism": f"replicas x{world}, no collective on the data path"},
+            "roofline": roof, "stages_ms": stages, "stage_share": stage_share,
+            "e2e": e2e, "gpu_launches": model.kernels_per_step(True) * args.steps,
+            "clocks": clocks}
+    if unb is not None:
+        line["fp32_unbatched"] = unb
+        line["speedup_vs_fp32_unbatched"] = value / world / unb["value"]
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

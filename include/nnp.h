@@ -1,0 +1,204 @@
+/*
+ * nnp.h -- C ABI of libnnp: energy and forces of an ANI-2x-style neural
+ * network potential on the NNP region, computed on one GB300 (sm_103a).
+ *
+ * What the library computes is the NNP term of the paper's Eq. 1,
+ * V_NNP(Z, r) (Eq. 2), together with the forces F = -grad V_NNP (Eq. 3), for
+ * neutral molecules (Sec. 1: "only neutral molecules"), with the ANI
+ * featurizer (Sec. 1: modified Behler-Parrinello symmetry functions, 5.1 A
+ * cutoff, elements H C N O F S Cl) and an ensemble of M atomic networks
+ * (Sec. 2 "Optimization": 8 networks, evaluated in parallel over networks
+ * and atoms).  An MD engine adds the returned energy and forces to its MM
+ * terms.  Positions, energies and forces stay on the GPU (Sec. 2
+ * "Optimization", first point); nnp_compute takes device pointers and a
+ * stream and never synchronises or allocates.
+ *
+ * Featurizer (per atom i, neighbours j, k of the same molecule / periodic
+ * region; the paper names it but prints no formula, this is the ANI form):
+ *   fc(r; Rc) = 0.5 cos(pi r / Rc) + 0.5 for r < Rc
+ *   radial  G_i[s, k] = sum_{s(j)=s, r_ij<Rcr} 1/4 exp(-EtaR (r_ij-ShfR_k)^2) fc(r_ij; Rcr)
+ *   angular G_i[p(s,t), a, z] = sum_{j<k in the Rca shell} 2 ((1 + cos(theta'-ShfZ_z))/2)^Zeta
+ *            exp(-EtaA ((r_ij+r_ik)/2 - ShfA_a)^2) fc(r_ij; Rca) fc(r_ik; Rca),
+ *            theta' = acos(0.95 cos angle_jik)
+ *   Rcr = 5.1 A, EtaR = 19.7, ShfR = 16 points 0.8..4.9 A; Rca = 3.5 A,
+ *   EtaA = 12.5, Zeta = 14.1, ShfA = 8 points 0.8..3.1 A, ShfZ = 4 points
+ *   0.39..2.75 rad; 1008 features = 7x16 radial + 28x8x4 angular.
+ * Networks (per element; CELU alpha 0.1):
+ *   H 1008-256-192-160-1, C 1008-224-192-160-1, N and O 1008-192-160-128-1,
+ *   F, S and Cl 1008-160-128-96-1.  E_mol = (1/M) sum_m sum_i y_m(i).
+ *
+ * Units: positions in Angstrom; energy in the units of the network output;
+ * forces are -dE/dx in energy units per Angstrom.
+ *
+ * Threading: a handle may be used by one host thread at a time.  Calls on
+ * different handles are independent.
+ */
+#ifndef NNP_H_
+#define NNP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nnp_ctx* nnp_handle;
+
+typedef enum {
+  NNP_OK = 0,
+  NNP_ERR_ARG = 1,        /* bad argument (null pointer, size, layout) */
+  NNP_ERR_SPECIES = 2,    /* atomic number outside {1, 6, 7, 8, 9, 16, 17} */
+  NNP_ERR_CHARGE = 3,     /* total charge != 0: the model handles neutral molecules only */
+  NNP_ERR_ALLOC = 4,      /* device or host allocation failed */
+  NNP_ERR_CUDA = 5,       /* a CUDA call failed; see nnp_last_error */
+  NNP_ERR_CAPACITY = 6,   /* device: a neighbour list exceeded its capacity */
+  NNP_ERR_NONFINITE = 7,  /* device: a position was NaN or infinite */
+  NNP_ERR_TIMEOUT = 8,    /* device: a bounded wait inside a kernel gave up */
+  NNP_ERR_UNSUPPORTED = 9 /* the requested mode is not available */
+} nnp_status;
+
+/* Arithmetic of the networks' matrix products.  The featurizer, the neighbour
+ * distances and the reverse pass to coordinates are always FP32; per-molecule
+ * energies and per-atom forces are accumulated in FP64. */
+typedef enum {
+  NNP_FP32 = 0, /* SIMT FP32 FMA */
+  NNP_BF16 = 1, /* tensor cores (tcgen05), BF16 operands, FP32 accumulation */
+  NNP_FP16 = 2  /* tensor cores (tcgen05), FP16 operands, FP32 accumulation */
+} nnp_precision;
+
+typedef struct {
+  int32_t n_models;       /* ensemble size M >= 1 (8 for ANI-2x) */
+  int32_t precision;      /* nnp_precision */
+  const float* weights;   /* HOST pointer, FP32, copied at create time.  Packed
+                             [model][element H,C,N,O,F,S,Cl][W1 b1 W2 b2 W3 b3 w4 b4],
+                             each W row-major [out][in] */
+  int64_t n_weights;      /* number of floats in weights; must equal
+                             n_models * nnp_weights_per_model() */
+  double box[3];          /* 0,0,0: non-periodic; else orthorhombic periodic box edges
+                             in Angstrom (each > 2 * 5.1), minimum-image convention */
+  int32_t total_charge;   /* must be 0 */
+  int32_t max_neighbors;  /* radial neighbour capacity per atom; 0 = automatic */
+  int32_t max_angular;    /* angular (3.5 A) neighbour capacity per atom; 0 = automatic */
+  int32_t use_graph;      /* 1: replay the step as one CUDA graph (captured on first use
+                             for a given set of buffer pointers) */
+  int32_t reserved[8];    /* must be zero */
+} nnp_params;
+
+/* Number of FP32 parameters of one ensemble member (1,713,223). */
+int64_t nnp_weights_per_model(void);
+
+/* Number of features per atom (1008). */
+int32_t nnp_num_features(void);
+
+/*
+ * Create a handle for one molecule / NNP region of n_atoms atoms with atomic
+ * numbers Z (HOST pointer, copied).  Equivalent to nnp_create_batch with one
+ * molecule.  Returns NNP_ERR_SPECIES, NNP_ERR_CHARGE, NNP_ERR_ARG or
+ * NNP_ERR_ALLOC synchronously; *out is set only on NNP_OK.  Allocates device
+ * memory on the current CUDA device and synchronises it.
+ */
+nnp_status nnp_create(const int32_t* Z, int32_t n_atoms, const nnp_params* params,
+                      nnp_handle* out);
+
+/*
+ * Create a handle for a batch of n_mols independent molecules (or MD
+ * replicas).  Z: HOST [N] atomic numbers, molecule-contiguous; mol_offsets:
+ * HOST [n_mols + 1], non-decreasing, mol_offsets[0] = 0, N = mol_offsets[n_mols].
+ * Atoms interact only within their molecule.  With a periodic box every
+ * molecule uses the same box.
+ */
+nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_t n_mols,
+                            const nnp_params* params, nnp_handle* out);
+
+/*
+ * One energy + force evaluation, enqueued on `stream` (a cudaStream_t, may be
+ * 0 for the legacy default stream).
+ *   positions_dev: DEVICE FP32 [N][3], Angstrom, in the atom order given at
+ *                  create time; read only.
+ *   energy_out_dev: DEVICE FP64 [n_mols]; written.
+ *   forces_out_dev: DEVICE FP64 [N][3] or NULL (energy only); written.
+ * The caller owns the three buffers.  No allocation, no host synchronisation.
+ * Device-side conditions (capacity overflow, non-finite positions, a bounded
+ * wait that gave up) are recorded in a status word read by nnp_get_status;
+ * the outputs of such a step are unspecified.  Returns NNP_ERR_ARG or
+ * NNP_ERR_CUDA synchronously.
+ */
+nnp_status nnp_compute(nnp_handle h, const float* positions_dev, double* energy_out_dev,
+                       double* forces_out_dev, void* stream);
+
+/*
+ * Same as nnp_compute with HOST buffers (pinned or pageable): copies the
+ * positions in, evaluates, copies energies and forces out, and synchronises
+ * `stream` before returning.  forces_out_host may be NULL.
+ */
+nnp_status nnp_compute_host(nnp_handle h, const float* positions_host, double* energy_out_host,
+                            double* forces_out_host, void* stream);
+
+/* Synchronises the handle's last stream and returns (then clears) the
+ * device-side status: NNP_ERR_TIMEOUT if a bounded wait gave up, else
+ * NNP_ERR_NONFINITE if a position was not finite, else NNP_ERR_CAPACITY if a
+ * neighbour list overflowed (entries beyond the capacity are dropped, never
+ * written), else NNP_OK. */
+nnp_status nnp_get_status(nnp_handle h);
+
+/* Text of the last error on this handle (static storage owned by the handle;
+ * "" if none).  With h == NULL: the last error of a failed create. */
+const char* nnp_last_error(nnp_handle h);
+
+/* Free everything the handle owns.  Synchronises the device.  NULL is a no-op. */
+void nnp_destroy(nnp_handle h);
+
+/* ---- inspection (diagnostics and parity tests) ------------------------------
+ * These read the intermediate results of the LAST nnp_compute on the handle,
+ * in the caller's atom order, into caller-owned DEVICE buffers, enqueued on
+ * `stream`.  Call after nnp_compute on the same stream. */
+
+/* Neighbour capacities in use (radial, angular). */
+nnp_status nnp_get_capacity(nnp_handle h, int32_t* max_radial, int32_t* max_angular);
+
+/* kind 0: radial (r < 5.1 A) neighbours, kind 1: angular (r < 3.5 A).
+ * counts_dev: DEVICE int32 [N]; lists_dev: DEVICE int32 [N][cap] (cap >= the
+ * handle's capacity for that kind); entries [i][0..counts[i]) are the caller
+ * indices of atom i's neighbours, ascending in the handle's internal order
+ * (not sorted by caller index); the rest is -1. */
+nnp_status nnp_get_neighbors(nnp_handle h, int32_t kind, int32_t* counts_dev, int32_t* lists_dev,
+                             int32_t cap, void* stream);
+
+/* Features as the networks consumed them, widened to FP32: DEVICE [N][1008]. */
+nnp_status nnp_get_features(nnp_handle h, float* features_dev, void* stream);
+
+/* Per-atom ensemble-mean energies: DEVICE FP64 [N]. */
+nnp_status nnp_get_atomic_energies(nnp_handle h, double* energies_dev, void* stream);
+
+/* ---- measurement -------------------------------------------------------------- */
+
+/* Stages of one evaluation, in launch order. */
+typedef enum {
+  NNP_STAGE_NEIGHBORS = 0, /* position gather + neighbour lists */
+  NNP_STAGE_FEATURES = 1,  /* radial + angular features */
+  NNP_STAGE_L1_FWD = 2,    /* first layer, all elements and networks */
+  NNP_STAGE_L2_FWD = 3,
+  NNP_STAGE_L3_FWD = 4,    /* third layer + output layer (energies, start of reverse pass) */
+  NNP_STAGE_ENERGY = 5,    /* ensemble mean, FP64 per-molecule sums */
+  NNP_STAGE_L3_REV = 6,
+  NNP_STAGE_L2_REV = 7,
+  NNP_STAGE_L1_REV = 8,    /* dE/dG */
+  NNP_STAGE_ADJOINT = 9,   /* featurizer reverse pass, FP64 force accumulation */
+  NNP_NUM_STAGES = 10
+} nnp_stage;
+
+/* nnp_compute with direct launches and a CUDA event after each stage; waits
+ * for the step and writes the stage durations in milliseconds to the HOST
+ * array stage_ms[n_stages >= NNP_NUM_STAGES] (stages not run read 0). */
+nnp_status nnp_compute_timed(nnp_handle h, const float* positions_dev, double* energy_out_dev,
+                             double* forces_out_dev, void* stream, float* stage_ms,
+                             int32_t n_stages);
+
+/* Number of kernels one nnp_compute launches (with or without forces). */
+int32_t nnp_kernels_per_step(nnp_handle h, int32_t with_forces);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NNP_H_ */

@@ -1,0 +1,840 @@
+// nnp_api.cu -- the C ABI of include/nnp.h: handle set-up (element sort,
+// weight packing, work lists, buffers), the step schedule (direct launches or
+// one CUDA graph replay) and the inspection exports.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/nnp.h"
+#include "nnp_internal.cuh"
+
+namespace nnp {
+void launch_gemm_tc(const GemmProblem* probs, const GemmTile* tiles, int n_tiles, Prec p, int layer,
+                    const void* maps, unsigned* status, cudaStream_t s);
+bool tc_available();
+}  // namespace nnp
+
+using namespace nnp;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Layer {
+  std::vector<GemmProblem> probs;
+  std::vector<GemmTile> tiles;
+  GemmProblem* d_probs = nullptr;
+  GemmTile* d_tiles = nullptr;
+};
+
+size_t elem_size(Prec p) { return p == Prec::F32 ? 4 : 2; }
+
+}  // namespace
+
+struct nnp_ctx {
+  int dev = 0;
+  int n_atoms = 0, n_mols = 0, n_models = 1;
+  Prec prec = Prec::F32;
+  int use_graph = 0;
+  AevConst aevc{};
+  int elem_count[kSpecies] = {0};
+  int elem_row0[kSpecies + 1] = {0};
+  int n_rows = 0;
+  int max_mol = 0;
+  long ldh1 = 0, ldh2 = 0, ldz3 = 0;
+
+  // device: layout
+  int *d_Z = nullptr, *d_mol_off = nullptr, *d_orig = nullptr, *d_row_of_int = nullptr,
+      *d_species_int = nullptr, *d_mol_start = nullptr, *d_mol_end = nullptr, *d_row_elem = nullptr;
+  float4* d_pos = nullptr;
+  NeighborLists nl{};
+  // device: activations
+  void *d_aev = nullptr, *d_h1 = nullptr, *d_h2 = nullptr, *d_z3 = nullptr;
+  float *d_y = nullptr, *d_dG = nullptr;
+  double* d_atom_e = nullptr;
+  unsigned* d_status = nullptr;
+  // device: weights
+  void* d_w = nullptr;
+  float* d_b = nullptr;
+  float *d_w4 = nullptr, *d_b4 = nullptr;
+  size_t w_off[6] = {0};  // W1, W2, W3, W3T, W2T, W1T element offsets in d_w
+  Layer L[6];              // 0 L1 fwd, 1 L2 fwd, 2 L3 fwd, 3 L3 rev, 4 L2 rev, 5 L1 rev
+  void* d_maps = nullptr;  // tensor-core path: TMA descriptors per layer
+  // reverse pass work list
+  int4* d_work = nullptr;
+  int n_work = 0;
+  int fwd_warps = 4, adj_warps = 4, smem_atoms_max = 0;
+  // host-buffer entry point
+  float* d_pos_in = nullptr;
+  double *d_E = nullptr, *d_F = nullptr;
+  // graph
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const float* g_pos = nullptr;
+  double *g_E = nullptr, *g_F = nullptr;
+  cudaStream_t last_stream = nullptr;
+  std::string err;
+
+  Geometry geometry() const {
+    Geometry g;
+    g.pos = d_pos;
+    g.mol_start = d_mol_start;
+    g.mol_end = d_mol_end;
+    g.species = d_species_int;
+    g.n_atoms = n_atoms;
+    return g;
+  }
+};
+
+namespace {
+
+nnp_status fail(nnp_ctx* h, nnp_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? NNP_ERR_ALLOC : NNP_ERR_CUDA,    \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+void init_aev_const(AevConst& c, const double box[3]) {
+  std::memset(&c, 0, sizeof(c));
+  c.Rcr = 5.1f;
+  c.Rca = 3.5f;
+  c.Rcr2 = c.Rcr * c.Rcr;
+  c.Rca2 = c.Rca * c.Rca;
+  c.Rcr2d = (double)c.Rcr * (double)c.Rcr;
+  c.Rca2d = (double)c.Rca * (double)c.Rca;
+  c.EtaR = 19.7f;
+  c.EtaA = 12.5f;
+  c.Zeta = 14.1f;
+  for (int k = 0; k < kShfR; ++k) c.ShfR[k] = (float)(0.8 + (4.9 - 0.8) * k / (kShfR - 1));
+  for (int k = 0; k < kShfA; ++k) c.ShfA[k] = (float)(0.8 + (3.1 - 0.8) * k / (kShfA - 1));
+  for (int k = 0; k < kShfZ; ++k) {
+    const double z = 0.39 + (2.75 - 0.39) * k / (kShfZ - 1);
+    c.cosZ[k] = (float)std::cos(z);
+    c.sinZ[k] = (float)std::sin(z);
+  }
+  int p = 0;
+  for (int s = 0; s < kSpecies; ++s)
+    for (int t = s; t < kSpecies; ++t) {
+      c.pair_index[s][t] = p;
+      c.pair_index[t][s] = p;
+      ++p;
+    }
+  c.periodic = (box[0] != 0.0 || box[1] != 0.0 || box[2] != 0.0) ? 1 : 0;
+  for (int k = 0; k < 3; ++k) {
+    c.boxd[k] = box[k];
+    c.box[k] = (float)box[k];
+  }
+}
+
+long element_params(int e) {
+  const long n0 = kFeatures, n1 = kHidden[e][0], n2 = kHidden[e][1], n3 = kHidden[e][2];
+  return n1 * n0 + n1 + n2 * n1 + n2 + n3 * n2 + n3 + n3 + 1;
+}
+
+long model_params() {
+  long s = 0;
+  for (int e = 0; e < kSpecies; ++e) s += element_params(e);
+  return s;
+}
+
+uint16_t f2bf(float f) {  // round to nearest even
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+uint16_t f2h(float f) {  // IEEE binary16, round to nearest even
+  uint32_t x;
+  std::memcpy(&x, &f, 4);
+  const uint32_t sign = (x >> 16) & 0x8000u;
+  int32_t exp = (int32_t)((x >> 23) & 0xff) - 127 + 15;
+  uint32_t man = x & 0x7fffffu;
+  if (((x >> 23) & 0xff) == 0xff) return (uint16_t)(sign | 0x7c00u | (man ? 0x200u : 0u));
+  if (exp >= 31) return (uint16_t)(sign | 0x7c00u);
+  if (exp <= 0) {
+    if (exp < -10) return (uint16_t)sign;
+    man |= 0x800000u;
+    const int shift = 14 - exp;
+    uint32_t h = man >> shift;
+    const uint32_t rem = man & ((1u << shift) - 1u), half = 1u << (shift - 1);
+    if (rem > half || (rem == half && (h & 1u))) ++h;
+    return (uint16_t)(sign | h);
+  }
+  uint32_t h = ((uint32_t)exp << 10) | (man >> 13);
+  const uint32_t rem = man & 0x1fffu;
+  if (rem > 0x1000u || (rem == 0x1000u && (h & 1u))) ++h;
+  return (uint16_t)(sign | h);
+}
+
+// Packs host FP32 values into the device element type.
+struct Packer {
+  Prec p;
+  std::vector<float> f32;
+  std::vector<uint16_t> f16;
+  void resize(size_t n) {
+    if (p == Prec::F32) f32.assign(n, 0.f);
+    else f16.assign(n, 0);
+  }
+  void set(size_t i, float v) {
+    if (p == Prec::F32) f32[i] = v;
+    else f16[i] = p == Prec::BF16 ? f2bf(v) : f2h(v);
+  }
+  const void* data() const { return p == Prec::F32 ? (const void*)f32.data() : (const void*)f16.data(); }
+};
+
+void add_tiles(Layer& L, int bm, int bn) {
+  const int pi = (int)L.probs.size() - 1;
+  const GemmProblem& P = L.probs.back();
+  for (int m0 = 0; m0 < P.M; m0 += bm)
+    for (int n0 = 0; n0 < P.N; n0 += bn) L.tiles.push_back(GemmTile{pi, m0, n0, 0});
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t nnp_weights_per_model(void) { return model_params(); }
+int32_t nnp_num_features(void) { return kFeatures; }
+
+const char* nnp_last_error(nnp_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void nnp_destroy(nnp_handle h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  void* ptrs[] = {h->d_Z, h->d_mol_off, h->d_orig, h->d_row_of_int, h->d_species_int,
+                  h->d_mol_start, h->d_mol_end, h->d_row_elem, h->d_pos, h->nl.cnt_r,
+                  h->nl.nbr_r, h->nl.cnt_a, h->nl.nbr_a, h->nl.slot_a, h->d_aev, h->d_h1,
+                  h->d_h2, h->d_z3, h->d_y, h->d_dG, h->d_atom_e, h->d_status, h->d_w, h->d_b,
+                  h->d_w4, h->d_b4, h->d_maps, h->d_work, h->d_pos_in, h->d_E, h->d_F};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (auto& L : h->L) {
+    if (L.d_probs) cudaFree(L.d_probs);
+    if (L.d_tiles) cudaFree(L.d_tiles);
+  }
+  delete h;
+}
+
+nnp_status nnp_create(const int32_t* Z, int32_t n_atoms, const nnp_params* params, nnp_handle* out) {
+  if (n_atoms < 0) return fail(nullptr, NNP_ERR_ARG, "n_atoms < 0");
+  const int32_t off[2] = {0, n_atoms};
+  return nnp_create_batch(Z, off, 1, params, out);
+}
+
+nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_t n_mols,
+                            const nnp_params* params, nnp_handle* out) {
+  nnp_ctx* h = nullptr;
+  if (!out || !params || !mol_offsets || n_mols < 0) return fail(nullptr, NNP_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (mol_offsets[0] != 0) return fail(nullptr, NNP_ERR_ARG, "mol_offsets[0] != 0");
+  for (int m = 0; m < n_mols; ++m)
+    if (mol_offsets[m + 1] < mol_offsets[m]) return fail(nullptr, NNP_ERR_ARG, "mol_offsets decreasing");
+  const int N = mol_offsets[n_mols];
+  if (N > 0 && !Z) return fail(nullptr, NNP_ERR_ARG, "Z is null");
+  if (params->total_charge != 0)
+    return fail(nullptr, NNP_ERR_CHARGE, "total charge must be 0 (neutral molecules only)");
+  if (params->n_models < 1 || params->n_models > kMaxModels)
+    return fail(nullptr, NNP_ERR_ARG, "n_models must be in [1, 16]");
+  if (params->precision < 0 || params->precision > 2) return fail(nullptr, NNP_ERR_ARG, "bad precision");
+  if (!params->weights || params->n_weights != model_params() * params->n_models)
+    return fail(nullptr, NNP_ERR_ARG, "weights: expected n_models * nnp_weights_per_model() floats");
+  for (int r = 0; r < 8; ++r)
+    if (params->reserved[r] != 0) return fail(nullptr, NNP_ERR_ARG, "reserved fields must be zero");
+  for (int i = 0; i < N; ++i) {
+    const int z = Z[i];
+    if (!(z == 1 || z == 6 || z == 7 || z == 8 || z == 9 || z == 16 || z == 17))
+      return fail(nullptr, NNP_ERR_SPECIES, "unsupported atomic number " + std::to_string(z) +
+                                                 " at atom " + std::to_string(i));
+  }
+  const bool periodic = params->box[0] != 0.0 || params->box[1] != 0.0 || params->box[2] != 0.0;
+  if (periodic)
+    for (int k = 0; k < 3; ++k)
+      if (!(params->box[k] > 2.0 * 5.1)) return fail(nullptr, NNP_ERR_ARG, "box edge must exceed 2 * 5.1 A");
+  if (params->max_neighbors < 0 || params->max_angular < 0)
+    return fail(nullptr, NNP_ERR_ARG, "negative capacity");
+
+  h = new (std::nothrow) nnp_ctx();
+  if (!h) return fail(nullptr, NNP_ERR_ALLOC, "host allocation failed");
+  struct Guard {
+    nnp_ctx*& h;
+    bool ok = false;
+    ~Guard() {
+      if (!ok && h) {
+        g_create_error = h->err;
+        nnp_destroy(h);
+      }
+    }
+  } guard{h};
+
+  cudaGetDevice(&h->dev);
+  h->n_atoms = N;
+  h->n_mols = n_mols;
+  h->n_models = params->n_models;
+  h->prec = (Prec)params->precision;
+  h->use_graph = params->use_graph;
+  init_aev_const(h->aevc, params->box);
+  for (int m = 0; m < n_mols; ++m) h->max_mol = std::max(h->max_mol, mol_offsets[m + 1] - mol_offsets[m]);
+  if (h->prec != Prec::F32 && !tc_available())
+    return fail(h, NNP_ERR_UNSUPPORTED, "tensor-core path needs an sm_103a device");
+
+  const int M = h->n_models;
+  cudaStream_t s0 = nullptr;
+  CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  s0 = h->cap_stream;
+
+  // ---- element sort on the device (a1) ----
+  int* d_species_caller = nullptr;
+  int* d_mol_count = nullptr;
+  CK(dalloc(&h->d_Z, N));
+  CK(dalloc(&h->d_mol_off, n_mols + 1));
+  CK(dalloc(&d_species_caller, N));
+  CK(dalloc(&d_mol_count, (size_t)n_mols * kSpecies));
+  CK(dalloc(&h->d_status, 1));
+  CK(cudaMemset(h->d_status, 0, sizeof(unsigned)));
+  if (N) CK(cudaMemcpy(h->d_Z, Z, sizeof(int) * N, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_mol_off, mol_offsets, sizeof(int) * (n_mols + 1), cudaMemcpyHostToDevice));
+  launch_species_setup(h->d_Z, h->d_mol_off, n_mols, N, d_species_caller, d_mol_count, h->d_status, s0);
+  CK(cudaGetLastError());
+  std::vector<int> mol_count((size_t)n_mols * kSpecies);
+  CK(cudaStreamSynchronize(s0));
+  if (n_mols)
+    CK(cudaMemcpy(mol_count.data(), d_mol_count, sizeof(int) * mol_count.size(), cudaMemcpyDeviceToHost));
+  // prefix sums (host, create time)
+  std::vector<int> mol_species_prefix((size_t)n_mols * kSpecies), elem_mol_prefix((size_t)kSpecies * n_mols);
+  for (int m = 0; m < n_mols; ++m) {
+    int acc = 0;
+    for (int s = 0; s < kSpecies; ++s) {
+      mol_species_prefix[(size_t)m * kSpecies + s] = acc;
+      acc += mol_count[(size_t)m * kSpecies + s];
+    }
+  }
+  for (int s = 0; s < kSpecies; ++s) {
+    int acc = 0;
+    for (int m = 0; m < n_mols; ++m) {
+      elem_mol_prefix[(size_t)s * n_mols + m] = acc;
+      acc += mol_count[(size_t)m * kSpecies + s];
+    }
+    h->elem_count[s] = acc;
+  }
+  h->elem_row0[0] = 0;
+  for (int s = 0; s < kSpecies; ++s)
+    h->elem_row0[s + 1] = h->elem_row0[s] + ((h->elem_count[s] + kRowAlign - 1) / kRowAlign) * kRowAlign;
+  h->n_rows = std::max(h->elem_row0[kSpecies], kRowAlign);
+
+  int *d_msp = nullptr, *d_emp = nullptr, *d_er0 = nullptr;
+  CK(dalloc(&d_msp, mol_species_prefix.size()));
+  CK(dalloc(&d_emp, elem_mol_prefix.size()));
+  CK(dalloc(&d_er0, kSpecies + 1));
+  if (!mol_species_prefix.empty()) {
+    CK(cudaMemcpy(d_msp, mol_species_prefix.data(), sizeof(int) * mol_species_prefix.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_emp, elem_mol_prefix.data(), sizeof(int) * elem_mol_prefix.size(), cudaMemcpyHostToDevice));
+  }
+  CK(cudaMemcpy(d_er0, h->elem_row0, sizeof(int) * (kSpecies + 1), cudaMemcpyHostToDevice));
+  CK(dalloc(&h->d_orig, N));
+  CK(dalloc(&h->d_row_of_int, N));
+  CK(dalloc(&h->d_species_int, N));
+  CK(dalloc(&h->d_mol_start, N));
+  CK(dalloc(&h->d_mol_end, N));
+  CK(dalloc(&h->d_row_elem, h->n_rows));
+  CK(cudaMemset(h->d_row_elem, 0xff, sizeof(int) * h->n_rows));
+  launch_species_place(d_species_caller, h->d_mol_off, n_mols, d_msp, d_emp, d_er0, h->d_orig,
+                       h->d_row_of_int, h->d_species_int, h->d_mol_start, h->d_mol_end,
+                       h->d_row_elem, s0);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s0));
+  cudaFree(d_species_caller);
+  cudaFree(d_mol_count);
+  cudaFree(d_msp);
+  cudaFree(d_emp);
+  cudaFree(d_er0);
+
+  // ---- neighbour lists ----
+  auto round32 = [](int x) { return ((x + 31) / 32) * 32; };
+  int cap_r = params->max_neighbors;
+  if (cap_r == 0) cap_r = std::min(std::max(round32(h->max_mol - 1), 32), 256);
+  int cap_a = params->max_angular;
+  if (cap_a == 0) cap_a = std::min(cap_r, 160);
+  cap_r = round32(cap_r);
+  cap_a = round32(std::min(cap_a, cap_r));
+  if (cap_a > 255) cap_a = 256;
+  h->nl.cap_r = cap_r;
+  h->nl.cap_a = cap_a;
+  CK(dalloc(&h->d_pos, N));
+  CK(dalloc(&h->nl.cnt_r, N));
+  CK(dalloc(&h->nl.cnt_a, N));
+  CK(dalloc(&h->nl.nbr_r, (size_t)N * cap_r));
+  CK(dalloc(&h->nl.nbr_a, (size_t)N * cap_a));
+  CK(dalloc(&h->nl.slot_a, (size_t)N * cap_a));
+
+  // ---- activations ----
+  const size_t es = elem_size(h->prec);
+  h->ldh1 = (long)M * kH1Max;
+  h->ldh2 = (long)M * kH2Max;
+  h->ldz3 = (long)M * kH3Max;
+  const size_t R = h->n_rows;
+  CK(cudaMalloc(&h->d_aev, R * kFeaturesPad * es));
+  CK(cudaMemset(h->d_aev, 0, R * kFeaturesPad * es));
+  CK(cudaMalloc(&h->d_h1, R * h->ldh1 * es));
+  CK(cudaMemset(h->d_h1, 0, R * h->ldh1 * es));
+  CK(cudaMalloc(&h->d_h2, R * h->ldh2 * es));
+  CK(cudaMemset(h->d_h2, 0, R * h->ldh2 * es));
+  CK(cudaMalloc(&h->d_z3, R * h->ldz3 * es));
+  CK(cudaMemset(h->d_z3, 0, R * h->ldz3 * es));
+  CK(dalloc(&h->d_y, R * M));
+  CK(dalloc(&h->d_dG, R * kFeaturesPad));
+  CK(cudaMemset(h->d_dG, 0, R * kFeaturesPad * sizeof(float)));
+  CK(dalloc(&h->d_atom_e, R));
+  CK(dalloc(&h->d_pos_in, (size_t)N * 3));
+  CK(dalloc(&h->d_E, n_mols));
+  CK(dalloc(&h->d_F, (size_t)N * 3));
+
+  // ---- weights: pack into the product layouts ----
+  // W1  [e]: rows m*h1+o, 1024 cols         W2  [e][m]: rows o, 256 cols
+  // W3  [e][m]: rows o, 192 cols            W3T [e][m]: rows (h2 index), 160 cols
+  // W2T [e][m]: rows (h1 index), 192 cols   W1T [e]: rows 1024 (feature), M*256 cols
+  const float* W = params->weights;
+  const long per_model = model_params();
+  long eoff[kSpecies];
+  {
+    long a = 0;
+    for (int e = 0; e < kSpecies; ++e) {
+      eoff[e] = a;
+      a += element_params(e);
+    }
+  }
+  size_t rows_w1 = 0, rows_w2 = 0, rows_w3 = 0, rows_w3t = 0, rows_w2t = 0;
+  for (int e = 0; e < kSpecies; ++e) {
+    rows_w1 += (size_t)M * kHidden[e][0];
+    rows_w2 += (size_t)M * kHidden[e][1];
+    rows_w3 += (size_t)M * kHidden[e][2];
+    rows_w3t += (size_t)M * kHidden[e][1];
+    rows_w2t += (size_t)M * kHidden[e][0];
+  }
+  const size_t ld_w1 = kFeaturesPad, ld_w2 = kH1Max, ld_w3 = kH2Max, ld_w3t = kH3Max,
+               ld_w2t = kH2Max, ld_w1t = (size_t)M * kH1Max;
+  h->w_off[0] = 0;
+  h->w_off[1] = h->w_off[0] + rows_w1 * ld_w1;
+  h->w_off[2] = h->w_off[1] + rows_w2 * ld_w2;
+  h->w_off[3] = h->w_off[2] + rows_w3 * ld_w3;
+  h->w_off[4] = h->w_off[3] + rows_w3t * ld_w3t;
+  h->w_off[5] = h->w_off[4] + rows_w2t * ld_w2t;
+  const size_t w_total = h->w_off[5] + (size_t)kSpecies * kFeaturesPad * ld_w1t;
+  Packer pk{h->prec};
+  pk.resize(w_total);
+  size_t b1_total = rows_w1, b2_total = rows_w2, b3_total = rows_w3;
+  std::vector<float> bias(b1_total + b2_total + b3_total, 0.f);
+  std::vector<float> w4((size_t)kSpecies * kMaxModels * kH3Max, 0.f), b4((size_t)kSpecies * kMaxModels, 0.f);
+  // per element/model row starts
+  size_t r1[kSpecies], r2[kSpecies][kMaxModels], r3[kSpecies][kMaxModels], r3t[kSpecies][kMaxModels],
+      r2t[kSpecies][kMaxModels];
+  {
+    size_t a1 = 0, a2 = 0, a3 = 0, a3t = 0, a2t = 0;
+    for (int e = 0; e < kSpecies; ++e) {
+      r1[e] = a1;
+      a1 += (size_t)M * kHidden[e][0];
+      for (int m = 0; m < M; ++m) {
+        r2[e][m] = a2;
+        a2 += kHidden[e][1];
+        r3[e][m] = a3;
+        a3 += kHidden[e][2];
+        r3t[e][m] = a3t;
+        a3t += kHidden[e][1];
+        r2t[e][m] = a2t;
+        a2t += kHidden[e][0];
+      }
+    }
+  }
+  for (int e = 0; e < kSpecies; ++e) {
+    const int n1 = kHidden[e][0], n2 = kHidden[e][1], n3 = kHidden[e][2];
+    for (int m = 0; m < M; ++m) {
+      const float* p = W + (size_t)m * per_model + eoff[e];
+      const float *W1 = p, *b1 = W1 + (size_t)n1 * kFeatures, *W2 = b1 + n1, *b2 = W2 + (size_t)n2 * n1,
+                  *W3 = b2 + n2, *b3 = W3 + (size_t)n3 * n2, *w4p = b3 + n3, *b4p = w4p + n3;
+      for (int o = 0; o < n1; ++o) {
+        for (int k = 0; k < kFeatures; ++k) {
+          const float v = W1[(size_t)o * kFeatures + k];
+          pk.set(h->w_off[0] + (r1[e] + (size_t)m * n1 + o) * ld_w1 + k, v);
+          pk.set(h->w_off[5] + ((size_t)e * kFeaturesPad + k) * ld_w1t + (size_t)m * n1 + o, v);
+        }
+        bias[r1[e] + (size_t)m * n1 + o] = b1[o];
+      }
+      for (int o = 0; o < n2; ++o) {
+        for (int k = 0; k < n1; ++k) {
+          const float v = W2[(size_t)o * n1 + k];
+          pk.set(h->w_off[1] + (r2[e][m] + o) * ld_w2 + k, v);
+          pk.set(h->w_off[4] + (r2t[e][m] + k) * ld_w2t + o, v);
+        }
+        bias[b1_total + r2[e][m] + o] = b2[o];
+      }
+      for (int o = 0; o < n3; ++o) {
+        for (int k = 0; k < n2; ++k) {
+          const float v = W3[(size_t)o * n2 + k];
+          pk.set(h->w_off[2] + (r3[e][m] + o) * ld_w3 + k, v);
+          pk.set(h->w_off[3] + (r3t[e][m] + k) * ld_w3t + o, v);
+        }
+        bias[b1_total + b2_total + r3[e][m] + o] = b3[o];
+        w4[((size_t)e * kMaxModels + m) * kH3Max + o] = w4p[o];
+      }
+      b4[(size_t)e * kMaxModels + m] = b4p[0];
+    }
+  }
+  CK(cudaMalloc(&h->d_w, w_total * es));
+  CK(cudaMemcpy(h->d_w, pk.data(), w_total * es, cudaMemcpyHostToDevice));
+  CK(dalloc(&h->d_b, bias.size()));
+  CK(cudaMemcpy(h->d_b, bias.data(), bias.size() * sizeof(float), cudaMemcpyHostToDevice));
+  CK(dalloc(&h->d_w4, w4.size()));
+  CK(cudaMemcpy(h->d_w4, w4.data(), w4.size() * sizeof(float), cudaMemcpyHostToDevice));
+  CK(dalloc(&h->d_b4, b4.size()));
+  CK(cudaMemcpy(h->d_b4, b4.data(), b4.size() * sizeof(float), cudaMemcpyHostToDevice));
+
+  // ---- problem lists of the six matrix-product layers ----
+  char* wb = static_cast<char*>(h->d_w);
+  char* aev = static_cast<char*>(h->d_aev);
+  char* H1 = static_cast<char*>(h->d_h1);
+  char* H2 = static_cast<char*>(h->d_h2);
+  char* Z3 = static_cast<char*>(h->d_z3);
+  const bool tc = false;  // tile shapes of the tensor-core kernel (not yet enabled)
+  const int bm = tc ? 128 : 64;
+  for (int e = 0; e < kSpecies; ++e) {
+    const int Me = h->elem_count[e];
+    if (Me == 0) continue;
+    const int n1 = kHidden[e][0], n2 = kHidden[e][1], n3 = kHidden[e][2];
+    const size_t row0 = h->elem_row0[e];
+    {  // layer 1 forward
+      GemmProblem P{};
+      P.A = aev + row0 * kFeaturesPad * es; P.lda = kFeaturesPad;
+      P.B = wb + (h->w_off[0] + r1[e] * ld_w1) * es; P.ldb = ld_w1;
+      P.D = H1 + row0 * h->ldh1 * es; P.ldd = h->ldh1;
+      P.bias = h->d_b + r1[e];
+      P.M = Me; P.N = M * n1; P.K = tc ? kFeaturesPad : kFeatures; P.epi = (int)Epi::BiasCelu;
+      P.a_row0 = (int)row0; P.b_row0 = (int)r1[e]; P.elem = e; P.model = -1;
+      h->L[0].probs.push_back(P);
+      add_tiles(h->L[0], bm, tc ? 256 : 64);
+    }
+    {  // layer 1 reverse: dE/dG = sum_m delta1_m W1_m
+      GemmProblem P{};
+      P.A = H1 + row0 * h->ldh1 * es; P.lda = h->ldh1;
+      P.B = wb + (h->w_off[5] + (size_t)e * kFeaturesPad * ld_w1t) * es; P.ldb = ld_w1t;
+      P.D = h->d_dG + row0 * kFeaturesPad; P.ldd = kFeaturesPad;
+      P.M = Me; P.N = tc ? kFeaturesPad : kFeatures; P.K = M * n1; P.epi = (int)Epi::Store;
+      P.a_row0 = (int)row0; P.b_row0 = e * kFeaturesPad; P.elem = e; P.model = -1;
+      h->L[5].probs.push_back(P);
+      add_tiles(h->L[5], bm, tc ? 256 : 64);
+    }
+    for (int m = 0; m < M; ++m) {
+      {  // layer 2 forward
+        GemmProblem P{};
+        P.A = H1 + (row0 * h->ldh1 + (size_t)m * n1) * es; P.lda = h->ldh1;
+        P.B = wb + (h->w_off[1] + r2[e][m] * ld_w2) * es; P.ldb = ld_w2;
+        P.D = H2 + (row0 * h->ldh2 + (size_t)m * n2) * es; P.ldd = h->ldh2;
+        P.bias = h->d_b + b1_total + r2[e][m];
+        P.M = Me; P.N = n2; P.K = n1; P.epi = (int)Epi::BiasCelu;
+        P.a_row0 = (int)row0; P.a_col0 = m * n1; P.b_row0 = (int)r2[e][m]; P.elem = e; P.model = m;
+        h->L[1].probs.push_back(P);
+        add_tiles(h->L[1], bm, tc ? n2 : 64);
+      }
+      {  // layer 3 forward (pre-activation)
+        GemmProblem P{};
+        P.A = H2 + (row0 * h->ldh2 + (size_t)m * n2) * es; P.lda = h->ldh2;
+        P.B = wb + (h->w_off[2] + r3[e][m] * ld_w3) * es; P.ldb = ld_w3;
+        P.D = Z3 + (row0 * h->ldz3 + (size_t)m * n3) * es; P.ldd = h->ldz3;
+        P.bias = h->d_b + b1_total + b2_total + r3[e][m];
+        P.M = Me; P.N = n3; P.K = n2; P.epi = (int)Epi::Bias;
+        P.a_row0 = (int)row0; P.a_col0 = m * n2; P.b_row0 = (int)r3[e][m]; P.elem = e; P.model = m;
+        h->L[2].probs.push_back(P);
+        add_tiles(h->L[2], bm, tc ? n3 : 64);
+      }
+      {  // layer 3 reverse: delta2 = (delta3 W3) * celu'(h2), in place over h2
+        GemmProblem P{};
+        P.A = Z3 + (row0 * h->ldz3 + (size_t)m * n3) * es; P.lda = h->ldz3;
+        P.B = wb + (h->w_off[3] + r3t[e][m] * ld_w3t) * es; P.ldb = ld_w3t;
+        P.D = H2 + (row0 * h->ldh2 + (size_t)m * n2) * es; P.ldd = h->ldh2;
+        P.M = Me; P.N = n2; P.K = n3; P.epi = (int)Epi::DCelu;
+        P.a_row0 = (int)row0; P.a_col0 = m * n3; P.b_row0 = (int)r3t[e][m]; P.elem = e; P.model = m;
+        h->L[3].probs.push_back(P);
+        add_tiles(h->L[3], bm, tc ? n2 : 64);
+      }
+      {  // layer 2 reverse: delta1 = (delta2 W2) * celu'(h1), in place over h1
+        GemmProblem P{};
+        P.A = H2 + (row0 * h->ldh2 + (size_t)m * n2) * es; P.lda = h->ldh2;
+        P.B = wb + (h->w_off[4] + r2t[e][m] * ld_w2t) * es; P.ldb = ld_w2t;
+        P.D = H1 + (row0 * h->ldh1 + (size_t)m * n1) * es; P.ldd = h->ldh1;
+        P.M = Me; P.N = n1; P.K = n2; P.epi = (int)Epi::DCelu;
+        P.a_row0 = (int)row0; P.a_col0 = m * n2; P.b_row0 = (int)r2t[e][m]; P.elem = e; P.model = m;
+        h->L[4].probs.push_back(P);
+        add_tiles(h->L[4], bm, tc ? n1 : 64);
+      }
+    }
+  }
+  for (auto& L : h->L) {
+    CK(dalloc(&L.d_probs, L.probs.size()));
+    CK(dalloc(&L.d_tiles, L.tiles.size()));
+    if (!L.probs.empty())
+      CK(cudaMemcpy(L.d_probs, L.probs.data(), sizeof(GemmProblem) * L.probs.size(), cudaMemcpyHostToDevice));
+    if (!L.tiles.empty())
+      CK(cudaMemcpy(L.d_tiles, L.tiles.data(), sizeof(GemmTile) * L.tiles.size(), cudaMemcpyHostToDevice));
+  }
+
+  // ---- reverse-pass work list (molecule, centre chunk), largest first ----
+  {
+    const size_t budget = 160 * 1024;
+    const int warps = h->adj_warps;
+    const size_t fixed = aev_adj_smem_bytes(cap_r, cap_a, warps, 0);
+    int smax = 0;
+    if (fixed < budget) smax = (int)std::min<size_t>((budget - fixed) / ((size_t)warps * 24), 1 << 20);
+    smax = std::min(smax, h->max_mol);
+    smax = (smax / 2) * 2;
+    h->smem_atoms_max = smax;
+    const int chunk = N >= 152 * 64 ? 8 * warps : warps;
+    std::vector<int4> work;
+    std::vector<long> cost;
+    for (int m = 0; m < n_mols; ++m) {
+      const int a0 = mol_offsets[m], n = mol_offsets[m + 1] - a0;
+      for (int c0 = 0; c0 < n; c0 += chunk) {
+        work.push_back(make_int4(a0, n, a0 + c0, a0 + std::min(n, c0 + chunk)));
+        cost.push_back((long)std::min(chunk, n - c0) * n);
+      }
+    }
+    std::vector<int> order(work.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<int4> sorted(work.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = work[order[i]];
+    h->n_work = (int)sorted.size();
+    CK(dalloc(&h->d_work, sorted.size()));
+    if (!sorted.empty())
+      CK(cudaMemcpy(h->d_work, sorted.data(), sizeof(int4) * sorted.size(), cudaMemcpyHostToDevice));
+  }
+  CK(aev_set_smem_limits(aev_fwd_smem_bytes(cap_a, h->fwd_warps),
+                         aev_adj_smem_bytes(cap_r, cap_a, h->adj_warps, h->smem_atoms_max)));
+  CK(cudaDeviceSynchronize());
+  guard.ok = true;
+  *out = h;
+  return NNP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+void run_gemm(nnp_ctx* h, int layer, cudaStream_t s) {
+  Layer& L = h->L[layer];
+  if (L.tiles.empty()) return;
+  if (h->prec == Prec::F32)
+    launch_gemm_simt(L.d_probs, L.d_tiles, (int)L.tiles.size(), s);
+  else
+    launch_gemm_tc(L.d_probs, L.d_tiles, (int)L.tiles.size(), h->prec, layer, h->d_maps,
+                   h->d_status, s);
+}
+
+// The whole step, enqueued on s.  With ev != nullptr an event is recorded
+// after each stage (ev[0] before the first); stage order is nnp_stage.
+int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_t s,
+                 cudaEvent_t* ev = nullptr) {
+  const Geometry g = h->geometry();
+  int kernels = 0;
+  auto mark = [&](int i) {
+    if (ev) cudaEventRecord(ev[i], s);
+  };
+  auto gemm = [&](int layer) {
+    if (!h->L[layer].tiles.empty()) ++kernels;
+    run_gemm(h, layer, s);
+  };
+  mark(0);
+  if (F && h->n_atoms) cudaMemsetAsync(F, 0, sizeof(double) * 3 * (size_t)h->n_atoms, s);
+  launch_gather_positions(pos, h->d_orig, h->d_pos, h->n_atoms, h->d_status, s);
+  launch_neighbors(g, h->nl, h->aevc, h->d_status, s);
+  kernels += 2;
+  mark(1);
+  launch_aev(g, h->nl, h->aevc, h->d_row_of_int, h->d_aev, h->prec, h->fwd_warps, s);
+  ++kernels;
+  mark(2);
+  gemm(0);
+  mark(3);
+  gemm(1);
+  mark(4);
+  gemm(2);
+  launch_head(h->d_z3, h->ldz3, h->prec, h->d_row_elem, h->d_w4, h->d_b4, nullptr, nullptr,
+              h->d_y, h->n_rows, h->n_models, 0, s);
+  ++kernels;
+  mark(5);
+  launch_energy(h->d_y, h->n_models, h->d_row_of_int, h->d_mol_off, h->n_mols, E, h->d_atom_e, s);
+  ++kernels;
+  mark(6);
+  if (!F) return kernels;
+  gemm(3);
+  mark(7);
+  gemm(4);
+  mark(8);
+  gemm(5);
+  mark(9);
+  launch_aev_adjoint(g, h->nl, h->aevc, h->d_row_of_int, h->d_dG, h->d_work, h->n_work, h->d_orig,
+                     F, h->adj_warps, h->smem_atoms_max, s);
+  ++kernels;
+  mark(10);
+  return kernels;
+}
+
+}  // namespace
+
+extern "C" {
+
+nnp_status nnp_compute(nnp_handle h, const float* pos, double* E, double* F, void* stream) {
+  if (!h) return NNP_ERR_ARG;
+  if ((!pos && h->n_atoms) || (!E && h->n_mols)) return fail(h, NNP_ERR_ARG, "null buffer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->last_stream = s;
+  if (h->use_graph) {
+    if (!h->gexec || h->g_pos != pos || h->g_E != E || h->g_F != F) {
+      if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+      }
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+      enqueue_step(h, pos, E, F, h->cap_stream);
+      const cudaError_t le = cudaGetLastError();
+      const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+      if (le != cudaSuccess || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(h, NNP_ERR_CUDA, std::string("graph capture: ") +
+                                         cudaGetErrorString(le != cudaSuccess ? le : ce));
+      }
+      const cudaError_t ie = cudaGraphInstantiate(&h->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) {
+        h->gexec = nullptr;
+        return fail(h, NNP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+      }
+      h->g_pos = pos;
+      h->g_E = E;
+      h->g_F = F;
+    }
+    CK(cudaGraphLaunch(h->gexec, s));
+    return NNP_OK;
+  }
+  enqueue_step(h, pos, E, F, s);
+  CK(cudaGetLastError());
+  return NNP_OK;
+}
+
+nnp_status nnp_compute_timed(nnp_handle h, const float* pos, double* E, double* F, void* stream,
+                              float* stage_ms, int32_t n_stages) {
+  if (!h || !stage_ms || n_stages < NNP_NUM_STAGES) return NNP_ERR_ARG;
+  if ((!pos && h->n_atoms) || (!E && h->n_mols)) return fail(h, NNP_ERR_ARG, "null buffer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->last_stream = s;
+  cudaEvent_t ev[NNP_NUM_STAGES + 1];
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  enqueue_step(h, pos, E, F, s, ev);
+  const int last = F ? NNP_NUM_STAGES : NNP_STAGE_ENERGY + 1;
+  cudaError_t err = cudaGetLastError();
+  if (err == cudaSuccess) err = cudaEventSynchronize(ev[last]);
+  for (int i = 0; i < NNP_NUM_STAGES; ++i) {
+    stage_ms[i] = 0.f;
+    if (err == cudaSuccess && i < last) cudaEventElapsedTime(&stage_ms[i], ev[i], ev[i + 1]);
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  CK(err);
+  return NNP_OK;
+}
+
+int32_t nnp_kernels_per_step(nnp_handle h, int32_t with_forces) {
+  if (!h) return -1;
+  int k = 2 + 1 + 1 + 1;  // gather, neighbours, features, head, energy
+  for (int l = 0; l < 3; ++l) k += h->L[l].tiles.empty() ? 0 : 1;
+  if (with_forces) {
+    k += 1;  // reverse pass to coordinates
+    for (int l = 3; l < 6; ++l) k += h->L[l].tiles.empty() ? 0 : 1;
+  }
+  return k;
+}
+
+nnp_status nnp_compute_host(nnp_handle h, const float* pos, double* E, double* F, void* stream) {
+  if (!h) return NNP_ERR_ARG;
+  if ((!pos && h->n_atoms) || (!E && h->n_mols)) return fail(h, NNP_ERR_ARG, "null buffer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t N = h->n_atoms;
+  if (N) CK(cudaMemcpyAsync(h->d_pos_in, pos, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, s));
+  const nnp_status st = nnp_compute(h, h->d_pos_in, h->d_E, F ? h->d_F : nullptr, stream);
+  if (st != NNP_OK) return st;
+  if (h->n_mols) CK(cudaMemcpyAsync(E, h->d_E, sizeof(double) * h->n_mols, cudaMemcpyDeviceToHost, s));
+  if (F && N) CK(cudaMemcpyAsync(F, h->d_F, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return NNP_OK;
+}
+
+nnp_status nnp_get_status(nnp_handle h) {
+  if (!h) return NNP_ERR_ARG;
+  CK(cudaStreamSynchronize(h->last_stream));
+  unsigned st = 0;
+  CK(cudaMemcpy(&st, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(h->d_status, 0, sizeof(unsigned)));
+  if (st & kStatTimeout) return fail(h, NNP_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
+  if (st & kStatNonFinite) return fail(h, NNP_ERR_NONFINITE, "non-finite position");
+  if (st & (kStatCapRadial | kStatCapAngular))
+    return fail(h, NNP_ERR_CAPACITY, (st & kStatCapRadial) ? "radial neighbour capacity exceeded"
+                                                           : "angular neighbour capacity exceeded");
+  return NNP_OK;
+}
+
+nnp_status nnp_get_capacity(nnp_handle h, int32_t* r, int32_t* a) {
+  if (!h || !r || !a) return NNP_ERR_ARG;
+  *r = h->nl.cap_r;
+  *a = h->nl.cap_a;
+  return NNP_OK;
+}
+
+nnp_status nnp_get_neighbors(nnp_handle h, int32_t kind, int32_t* counts, int32_t* lists, int32_t cap,
+                             void* stream) {
+  if (!h || (kind != 0 && kind != 1)) return NNP_ERR_ARG;
+  if (cap < (kind == 0 ? h->nl.cap_r : h->nl.cap_a)) return fail(h, NNP_ERR_ARG, "cap too small");
+  if (h->n_atoms && (!counts || !lists)) return fail(h, NNP_ERR_ARG, "null buffer");
+  launch_export_neighbors(h->nl, kind, h->d_orig, h->n_atoms, counts, lists, cap,
+                          static_cast<cudaStream_t>(stream));
+  CK(cudaGetLastError());
+  return NNP_OK;
+}
+
+nnp_status nnp_get_features(nnp_handle h, float* out, void* stream) {
+  if (!h) return NNP_ERR_ARG;
+  if (h->n_atoms && !out) return fail(h, NNP_ERR_ARG, "null buffer");
+  launch_export_features(h->d_aev, h->prec, h->d_row_of_int, h->d_orig, h->n_atoms, out,
+                         static_cast<cudaStream_t>(stream));
+  CK(cudaGetLastError());
+  return NNP_OK;
+}
+
+nnp_status nnp_get_atomic_energies(nnp_handle h, double* out, void* stream) {
+  if (!h) return NNP_ERR_ARG;
+  if (h->n_atoms && !out) return fail(h, NNP_ERR_ARG, "null buffer");
+  launch_export_atomic_energies(h->d_atom_e, h->d_row_of_int, h->d_orig, h->n_atoms, out,
+                                static_cast<cudaStream_t>(stream));
+  CK(cudaGetLastError());
+  return NNP_OK;
+}
+
+}  // extern "C"

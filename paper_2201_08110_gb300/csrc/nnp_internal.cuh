@@ -1,0 +1,155 @@
+// nnp_internal.cuh -- shared declarations of the libnnp CUDA translation units.
+//
+// Data layout in device memory (see the C ABI in include/nnp.h):
+//   * caller order: atoms as passed to nnp_create_batch, molecule-contiguous.
+//   * internal order ("A"): molecule-contiguous, atoms of a molecule sorted by
+//     element (stable).  Neighbour lists hold internal indices, so a list
+//     ascending in internal index is grouped by element.
+//   * row order ("B"): element-major (all H of the batch, then all C, ...),
+//     molecule order inside an element.  The features, the network
+//     activations and dE/dG are stored as rows in this order, so each
+//     element's atoms form one contiguous block for the matrix products.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+namespace nnp {
+
+constexpr int kSpecies = 7;
+constexpr int kShfR = 16;
+constexpr int kShfA = 8;
+constexpr int kShfZ = 4;
+constexpr int kRadial = kSpecies * kShfR;               // 112
+constexpr int kPairBlocks = kSpecies * (kSpecies + 1) / 2;  // 28
+constexpr int kAngPerBlock = kShfA * kShfZ;             // 32
+constexpr int kAngular = kPairBlocks * kAngPerBlock;    // 896
+constexpr int kFeatures = kRadial + kAngular;           // 1008
+constexpr int kFeaturesPad = 1024;                      // K of the first layer, padded
+constexpr int kMaxModels = 16;
+constexpr int kRowAlign = 128;                          // row padding of every element block
+
+// Device status bits (sticky until nnp_get_status reads them).
+constexpr unsigned kStatNonFinite = 1u << 0;
+constexpr unsigned kStatCapRadial = 1u << 1;
+constexpr unsigned kStatCapAngular = 1u << 2;
+constexpr unsigned kStatTimeout = 1u << 3;
+
+// Hidden widths per element (H, C, N, O, F, S, Cl).
+constexpr int kHidden[kSpecies][3] = {{256, 192, 160}, {224, 192, 160}, {192, 160, 128},
+                                      {192, 160, 128}, {160, 128, 96},  {160, 128, 96},
+                                      {160, 128, 96}};
+constexpr int kH1Max = 256, kH2Max = 192, kH3Max = 160;
+
+// kHidden for device code: width of hidden layer l (0..2) of element e.
+__host__ __device__ __forceinline__ int hidden_width(int e, int l) {
+  constexpr int w[3][4] = {{256, 224, 192, 160}, {192, 192, 160, 128}, {160, 160, 128, 96}};
+  const int g = e <= 1 ? e : (e <= 3 ? 2 : 3);  // H, C, {N, O}, {F, S, Cl}
+  return w[l][g];
+}
+
+// Featurizer constants in FP32, as the kernels use them.
+struct AevConst {
+  float Rcr, Rca, Rcr2, Rca2;  // cutoffs and squares (FP32)
+  double Rcr2d, Rca2d;         // FP64 squares of the FP32 cutoffs (exact predicate)
+  float EtaR, EtaA, Zeta;
+  float ShfR[kShfR], ShfA[kShfA], cosZ[kShfZ], sinZ[kShfZ];
+  int pair_index[kSpecies][kSpecies];
+  float box[3];
+  double boxd[3];
+  int periodic;
+};
+
+// Geometry of one step: what the featurizer and its reverse pass read.
+struct Geometry {
+  const float4* pos;      // [N] internal order
+  const int* mol_start;   // [N] first internal index of the atom's molecule
+  const int* mol_end;     // [N] one past the last
+  const int* species;     // [N] element index of internal atom
+  int n_atoms;
+};
+
+struct NeighborLists {
+  int* cnt_r;   // [N]
+  int* nbr_r;   // [N][cap_r] internal indices, ascending
+  int* cnt_a;   // [N]
+  int* nbr_a;   // [N][cap_a] internal indices, ascending (subset of the radial list)
+  int* slot_a;  // [N][cap_a] position of the angular neighbour in the radial list
+  int cap_r, cap_a;
+};
+
+// Element precision of the network activations and operands.
+enum class Prec { F32 = 0, BF16 = 1, F16 = 2 };
+
+// One matrix product D[M, N] = A[M, K] * B[N, K]^T (both K-major) with an
+// epilogue.  Rows are atoms, A and D share the row index.
+enum class Epi : int {
+  BiasCelu = 0,   // D = celu(acc + bias[n])           (forward hidden layer)
+  Bias = 1,       // D = acc + bias[n]                  (pre-activation)
+  DCelu = 2,      // D = acc * celu'(D_in-place)       (reverse through a hidden layer)
+  Store = 3       // D = acc (FP32 output)              (dE/dG)
+};
+
+struct GemmProblem {
+  const void* A;  long lda;   // element offset already applied
+  const void* B;  long ldb;
+  void* D;        long ldd;
+  const float* bias;
+  int M, N, K;
+  int epi;
+  int a_row0, b_row0, a_col0, b_col0, d_col0;  // used by the tensor-core path (TMA coordinates)
+  int elem, model;
+};
+
+// A tile of the flattened problem list.
+struct GemmTile {
+  int problem, m0, n0, pad;
+};
+
+// ---- kernels' host launchers ------------------------------------------------
+
+void launch_gather_positions(const float* pos_caller, const int* orig_of_int, float4* pos_int,
+                             int n, unsigned* status, cudaStream_t s);
+void launch_neighbors(const Geometry& g, const NeighborLists& nl, const AevConst& c,
+                      unsigned* status, cudaStream_t s);
+void launch_aev(const Geometry& g, const NeighborLists& nl, const AevConst& c,
+                const int* row_of_int, void* aev_out, Prec out_prec, int warps_per_cta,
+                cudaStream_t s);
+void launch_aev_adjoint(const Geometry& g, const NeighborLists& nl, const AevConst& c,
+                        const int* row_of_int, const float* dG, const int4* work, int n_work,
+                        const int* orig_of_int, double* forces_out, int warps_per_cta,
+                        int mol_atoms_smem_max, cudaStream_t s);
+void launch_head(const void* z3, long ldz, Prec prec, const int* row_elem, const float* w4,
+                 const float* b4, const float* b3, void* delta3, float* y, int n_rows,
+                 int n_models, int inv_models_scale, cudaStream_t s);
+void launch_energy(const float* y, int n_models, const int* row_of_int, const int* mol_off,
+                   int n_mols, double* energy_out, double* atom_energy_row, cudaStream_t s);
+void launch_gemm_simt(const GemmProblem* d_problems, const GemmTile* d_tiles, int n_tiles,
+                      cudaStream_t s);
+void launch_gemm_simt_typed(const GemmProblem* d_problems, const GemmTile* d_tiles, int n_tiles,
+                            Prec p, cudaStream_t s);
+size_t aev_fwd_smem_bytes(int cap_a, int warps);
+size_t aev_adj_smem_bytes(int cap_r, int cap_a, int warps, int mol_atoms_smem_max);
+cudaError_t aev_set_smem_limits(size_t fwd_bytes, size_t adj_bytes);
+
+// Inspection helpers.
+void launch_export_neighbors(const NeighborLists& nl, int kind, const int* orig_of_int, int n,
+                             int* counts_out, int* lists_out, int cap_out, cudaStream_t s);
+void launch_export_features(const void* aev, Prec prec, const int* row_of_int,
+                            const int* orig_of_int, int n, float* out, cudaStream_t s);
+void launch_export_atomic_energies(const double* atom_energy_row, const int* row_of_int,
+                                   const int* orig_of_int, int n, double* out, cudaStream_t s);
+
+// Setup kernels (create time).
+void launch_species_setup(const int* Z_caller, const int* mol_off, int n_mols, int n_atoms,
+                          int* species_caller, int* mol_species_count, unsigned* bad,
+                          cudaStream_t s);
+void launch_species_place(const int* species_caller, const int* mol_off, int n_mols,
+                          const int* mol_species_prefix, const int* elem_mol_prefix,
+                          const int* elem_row0, int* orig_of_int, int* row_of_int,
+                          int* species_int, int* mol_start, int* mol_end, int* row_elem,
+                          cudaStream_t s);
+
+}  // namespace nnp

@@ -1,0 +1,281 @@
+"""Python binding of libnnp (include/nnp.h): argument marshalling only.
+
+Every step of the energy/force evaluation runs in the library's CUDA kernels;
+this module passes device pointers (from torch tensors), sizes and the CUDA
+stream through the C ABI and turns status codes into exceptions.  If the
+library is not built the import of the binding fails loudly: there is no
+Python or CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libnnp.so")
+
+FP32, BF16, FP16 = 0, 1, 2
+_PREC = {"fp32": FP32, "bf16": BF16, "fp16": FP16}
+STATUS = {0: "NNP_OK", 1: "NNP_ERR_ARG", 2: "NNP_ERR_SPECIES", 3: "NNP_ERR_CHARGE",
+          4: "NNP_ERR_ALLOC", 5: "NNP_ERR_CUDA", 6: "NNP_ERR_CAPACITY", 7: "NNP_ERR_NONFINITE",
+          8: "NNP_ERR_TIMEOUT", 9: "NNP_ERR_UNSUPPORTED"}
+
+# Every entry point declared in include/nnp.h.
+EXPORTS = ("nnp_weights_per_model", "nnp_num_features", "nnp_create", "nnp_create_batch",
+           "nnp_compute", "nnp_compute_host", "nnp_get_status", "nnp_last_error", "nnp_destroy",
+           "nnp_get_capacity", "nnp_get_neighbors", "nnp_get_features",
+           "nnp_get_atomic_energies", "nnp_compute_timed", "nnp_kernels_per_step")
+STAGES = ("neighbors", "features", "l1_fwd", "l2_fwd", "l3_fwd", "energy", "l3_rev", "l2_rev",
+          "l1_rev", "adjoint")
+
+
+class NNPError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("n_models", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("weights", ctypes.c_void_p), ("n_weights", ctypes.c_int64),
+                ("box", ctypes.c_double * 3), ("total_charge", ctypes.c_int32),
+                ("max_neighbors", ctypes.c_int32), ("max_angular", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libnnp.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libnnp is not built ({path} missing): run "
+                          "`python -m paper_2201_08110_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.nnp_weights_per_model.restype = I64
+    lib.nnp_num_features.restype = I32
+    lib.nnp_create.argtypes = [P, I32, P, P]
+    lib.nnp_create.restype = ctypes.c_int
+    lib.nnp_create_batch.argtypes = [P, P, I32, P, P]
+    lib.nnp_create_batch.restype = ctypes.c_int
+    lib.nnp_compute.argtypes = [P, P, P, P, P]
+    lib.nnp_compute.restype = ctypes.c_int
+    lib.nnp_compute_host.argtypes = [P, P, P, P, P]
+    lib.nnp_compute_host.restype = ctypes.c_int
+    lib.nnp_get_status.argtypes = [P]
+    lib.nnp_get_status.restype = ctypes.c_int
+    lib.nnp_last_error.argtypes = [P]
+    lib.nnp_last_error.restype = ctypes.c_char_p
+    lib.nnp_destroy.argtypes = [P]
+    lib.nnp_destroy.restype = None
+    lib.nnp_get_capacity.argtypes = [P, P, P]
+    lib.nnp_get_capacity.restype = ctypes.c_int
+    lib.nnp_get_neighbors.argtypes = [P, I32, P, P, I32, P]
+    lib.nnp_get_neighbors.restype = ctypes.c_int
+    lib.nnp_get_features.argtypes = [P, P, P]
+    lib.nnp_get_features.restype = ctypes.c_int
+    lib.nnp_get_atomic_energies.argtypes = [P, P, P]
+    lib.nnp_get_atomic_energies.restype = ctypes.c_int
+    lib.nnp_compute_timed.argtypes = [P, P, P, P, P, P, I32]
+    lib.nnp_compute_timed.restype = ctypes.c_int
+    lib.nnp_kernels_per_step.argtypes = [P, I32]
+    lib.nnp_kernels_per_step.restype = I32
+    _lib = lib
+    return lib
+
+
+def weights_per_model() -> int:
+    return int(load_library().nnp_weights_per_model())
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else int(t.data_ptr())
+
+
+class NNP:
+    """A handle on libnnp for one batch layout (atomic numbers and molecule
+    boundaries fixed at construction; positions change every call)."""
+
+    def __init__(self, Z, weights, n_models: int, mol_off=None, precision: str = "fp32",
+                 box=None, max_neighbors: int = 0, max_angular: int = 0,
+                 use_graph: bool = False, total_charge: int = 0):
+        self._lib = load_library()
+        Z = np.ascontiguousarray(Z, dtype=np.int32)
+        if mol_off is None:
+            mol_off = np.array([0, Z.shape[0]], dtype=np.int32)
+        mol_off = np.ascontiguousarray(mol_off, dtype=np.int32)
+        w = np.ascontiguousarray(weights, dtype=np.float32).reshape(-1)
+        p = Params()
+        p.n_models = int(n_models)
+        p.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+        p.weights = w.ctypes.data
+        p.n_weights = w.size
+        b = np.zeros(3) if box is None else np.asarray(box, dtype=np.float64).reshape(3)
+        for k in range(3):
+            p.box[k] = float(b[k])
+        p.total_charge = int(total_charge)
+        p.max_neighbors = int(max_neighbors)
+        p.max_angular = int(max_angular)
+        p.use_graph = 1 if use_graph else 0
+        h = ctypes.c_void_p()
+        rc = self._lib.nnp_create_batch(Z.ctypes.data, mol_off.ctypes.data, mol_off.shape[0] - 1,
+                                        ctypes.byref(p), ctypes.byref(h))
+        if rc != 0:
+            raise NNPError(rc, self._lib.nnp_last_error(None).decode())
+        self._h = h
+        self.n_atoms = int(mol_off[-1])
+        self.n_mols = int(mol_off.shape[0] - 1)
+        self.n_models = int(n_models)
+        self.precision = precision
+        self.mol_off = mol_off
+        self.box = b
+
+    # -- lifetime --
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.nnp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise NNPError(rc, self._lib.nnp_last_error(self._h).decode())
+
+    # -- evaluation --
+    def compute(self, positions, energy_out=None, forces_out=None, forces: bool = True, stream=None):
+        """positions: CUDA float32 [N, 3].  Returns (energy [n_mols] float64,
+        forces [N, 3] float64 or None), enqueued on `stream` (default: torch's
+        current stream)."""
+        import torch
+        assert positions.is_cuda and positions.dtype == torch.float32 and positions.is_contiguous()
+        dev = positions.device
+        if energy_out is None:
+            energy_out = torch.empty(self.n_mols, dtype=torch.float64, device=dev)
+        if forces and forces_out is None:
+            forces_out = torch.empty(self.n_atoms, 3, dtype=torch.float64, device=dev)
+        if not forces:
+            forces_out = None
+        self._check(self._lib.nnp_compute(self._h, _ptr(positions), _ptr(energy_out),
+                                          _ptr(forces_out), _stream_ptr(stream)))
+        return energy_out, forces_out
+
+    def compute_host(self, positions: np.ndarray, forces: bool = True, stream=None):
+        """Host arrays in and out (copies inside, synchronises)."""
+        pos = np.ascontiguousarray(positions, dtype=np.float32)
+        E = np.zeros(self.n_mols, dtype=np.float64)
+        F = np.zeros((self.n_atoms, 3), dtype=np.float64) if forces else None
+        self._check(self._lib.nnp_compute_host(self._h, pos.ctypes.data, E.ctypes.data,
+                                               None if F is None else F.ctypes.data,
+                                               _stream_ptr(stream)))
+        return E, F
+
+    def compute_timed(self, positions, energy_out, forces_out=None, stream=None):
+        """One evaluation with direct launches; returns {stage: milliseconds}."""
+        ms = (ctypes.c_float * len(STAGES))()
+        self._check(self._lib.nnp_compute_timed(self._h, _ptr(positions), _ptr(energy_out),
+                                                _ptr(forces_out), _stream_ptr(stream), ms,
+                                                len(STAGES)))
+        return dict(zip(STAGES, list(ms)))
+
+    def kernels_per_step(self, forces: bool = True) -> int:
+        return int(self._lib.nnp_kernels_per_step(self._h, 1 if forces else 0))
+
+    def status(self):
+        """Raise NNPError if a device-side condition was recorded."""
+        self._check(self._lib.nnp_get_status(self._h))
+
+    # -- inspection --
+    def capacity(self):
+        r, a = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._lib.nnp_get_capacity(self._h, ctypes.byref(r), ctypes.byref(a)))
+        return r.value, a.value
+
+    def neighbors(self, kind: int = 0, stream=None):
+        import torch
+        cap = self.capacity()[kind]
+        counts = torch.empty(self.n_atoms, dtype=torch.int32, device="cuda")
+        lists = torch.empty(self.n_atoms, cap, dtype=torch.int32, device="cuda")
+        self._check(self._lib.nnp_get_neighbors(self._h, kind, _ptr(counts), _ptr(lists), cap,
+                                                _stream_ptr(stream)))
+        return counts, lists
+
+    def features(self, stream=None):
+        import torch
+        out = torch.empty(self.n_atoms, 1008, dtype=torch.float32, device="cuda")
+        self._check(self._lib.nnp_get_features(self._h, _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def atomic_energies(self, stream=None):
+        import torch
+        out = torch.empty(self.n_atoms, dtype=torch.float64, device="cuda")
+        self._check(self._lib.nnp_get_atomic_energies(self._h, _ptr(out), _stream_ptr(stream)))
+        return out
+
+
+def _autograd_function():
+    import torch
+
+    class NNPEnergy(torch.autograd.Function):
+        """E(positions) with forces from the library's hand-written reverse pass.
+
+        forward evaluates energies and forces in one call and keeps the forces;
+        with ``recompute=True`` it evaluates the energy only and the backward
+        re-runs the whole pass (nothing of the forward is kept), which is the
+        low-memory mode for large batches."""
+
+        @staticmethod
+        def forward(ctx, positions, model: NNP, recompute: bool = False):
+            pos = positions.detach().contiguous()
+            if recompute:
+                E, _ = model.compute(pos, forces=False)
+                ctx.save_for_backward(pos)
+            else:
+                E, F = model.compute(pos, forces=True)
+                ctx.save_for_backward(F)
+            ctx.model, ctx.recompute = model, recompute
+            return E
+
+        @staticmethod
+        def backward(ctx, gE):
+            model = ctx.model
+            if ctx.recompute:
+                (pos,) = ctx.saved_tensors
+                _, F = model.compute(pos, forces=True)
+            else:
+                (F,) = ctx.saved_tensors
+            counts = torch.as_tensor(np.diff(model.mol_off), device=F.device, dtype=torch.long)
+            g_atom = torch.repeat_interleave(gE.to(torch.float64), counts)
+            return (-(g_atom[:, None] * F)).to(torch.float32), None, None
+
+    return NNPEnergy
+
+
+_fn = None
+
+
+def energy(positions, model: NNP, recompute: bool = False):
+    """Differentiable energies [n_mols] (float64) of CUDA positions [N, 3]."""
+    global _fn
+    if _fn is None:
+        _fn = _autograd_function()
+    return _fn.apply(positions, model, recompute)

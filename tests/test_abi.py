@@ -1,0 +1,66 @@
+"""The C ABI library builds for sm_103a, loads without a GPU and exports every
+entry point include/nnp.h declares (no compute call is made here)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "nnp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nnp_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not shutil.which("nvcc") and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2201_08110_gb300 import build, nnp
+    build.build()
+    return nnp.load_library()
+
+
+def test_header_declarations_are_the_binding_exports():
+    from paper_2201_08110_gb300 import nnp
+    assert declared_functions() == sorted(nnp.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert isinstance(getattr(lib, name), ctypes._CFuncPtr), name
+
+
+def test_host_only_queries(lib):
+    from paper_2201_08110_gb300 import workloads as W
+    assert lib.nnp_weights_per_model() == W.weights_per_model() == 1713223
+    assert lib.nnp_num_features() == 1008
+
+
+def test_create_rejects_bad_arguments_before_touching_the_device(lib):
+    """Argument, species and charge errors are returned synchronously."""
+    from paper_2201_08110_gb300 import nnp
+    import numpy as np
+    p = nnp.Params()
+    p.n_models = 1
+    w = np.zeros(nnp.weights_per_model(), np.float32)
+    p.weights = w.ctypes.data
+    p.n_weights = w.size
+    h = ctypes.c_void_p()
+    Z = np.array([6, 5], np.int32)
+    assert lib.nnp_create(Z.ctypes.data, 2, ctypes.byref(p), ctypes.byref(h)) == 2  # species
+    assert b"atomic number 5" in lib.nnp_last_error(None)
+    Z = np.array([6, 1], np.int32)
+    p.total_charge = -1
+    assert lib.nnp_create(Z.ctypes.data, 2, ctypes.byref(p), ctypes.byref(h)) == 3  # charge
+    p.total_charge = 0
+    p.n_weights = w.size - 1
+    assert lib.nnp_create(Z.ctypes.data, 2, ctypes.byref(p), ctypes.byref(h)) == 1  # weights size
+    p.n_weights = w.size
+    p.box[0] = p.box[1] = p.box[2] = 9.0
+    assert lib.nnp_create(Z.ctypes.data, 2, ctypes.byref(p), ctypes.byref(h)) == 1  # box < 2 Rc
+    assert not h.value
