@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) k_gemm_simt(const GemmProblem* __restrict
           break;
         }
         case (int)Epi::Bias:
-          st_f(static_cast<T*>(P.D) + (size_t)m * P.ldd + n, v + P.bias[n]);
+          static_cast<float*>(P.D)[(size_t)m * P.ldd + n] = v + P.bias[n];
           break;
         case (int)Epi::DCelu: {
           T* d = static_cast<T*>(P.D) + (size_t)m * P.ldd + n;

@@ -53,7 +53,8 @@ struct nnp_ctx {
   float4* d_pos = nullptr;
   NeighborLists nl{};
   // device: activations
-  void *d_aev = nullptr, *d_h1 = nullptr, *d_h2 = nullptr, *d_z3 = nullptr;
+  void *d_aev = nullptr, *d_h1 = nullptr, *d_h2 = nullptr, *d_d3 = nullptr;
+  float* d_z3 = nullptr;  // third-layer pre-activation, FP32 (not a product operand)
   float *d_y = nullptr, *d_dG = nullptr;
   double* d_atom_e = nullptr;
   unsigned* d_status = nullptr;
@@ -227,7 +228,7 @@ void nnp_destroy(nnp_handle h) {
   void* ptrs[] = {h->d_Z, h->d_mol_off, h->d_orig, h->d_row_of_int, h->d_species_int,
                   h->d_mol_start, h->d_mol_end, h->d_row_elem, h->d_pos, h->nl.cnt_r,
                   h->nl.nbr_r, h->nl.cnt_a, h->nl.nbr_a, h->nl.slot_a, h->d_aev, h->d_h1,
-                  h->d_h2, h->d_z3, h->d_y, h->d_dG, h->d_atom_e, h->d_status, h->d_w, h->d_b,
+                  h->d_h2, h->d_z3, h->d_d3, h->d_y, h->d_dG, h->d_atom_e, h->d_status, h->d_w, h->d_b,
                   h->d_w4, h->d_b4, h->d_maps, h->d_work, h->d_pos_in, h->d_E, h->d_F};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -401,8 +402,10 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   CK(cudaMemset(h->d_h1, 0, R * h->ldh1 * es));
   CK(cudaMalloc(&h->d_h2, R * h->ldh2 * es));
   CK(cudaMemset(h->d_h2, 0, R * h->ldh2 * es));
-  CK(cudaMalloc(&h->d_z3, R * h->ldz3 * es));
-  CK(cudaMemset(h->d_z3, 0, R * h->ldz3 * es));
+  CK(dalloc(&h->d_z3, R * h->ldz3));
+  CK(cudaMemset(h->d_z3, 0, R * h->ldz3 * sizeof(float)));
+  CK(cudaMalloc(&h->d_d3, R * h->ldz3 * es));
+  CK(cudaMemset(h->d_d3, 0, R * h->ldz3 * es));
   CK(dalloc(&h->d_y, R * M));
   CK(dalloc(&h->d_dG, R * kFeaturesPad));
   CK(cudaMemset(h->d_dG, 0, R * kFeaturesPad * sizeof(float)));
@@ -515,7 +518,8 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   char* aev = static_cast<char*>(h->d_aev);
   char* H1 = static_cast<char*>(h->d_h1);
   char* H2 = static_cast<char*>(h->d_h2);
-  char* Z3 = static_cast<char*>(h->d_z3);
+  float* Z3 = h->d_z3;
+  char* D3 = static_cast<char*>(h->d_d3);
   const bool tc = false;  // tile shapes of the tensor-core kernel (not yet enabled)
   const int bm = tc ? 128 : 64;
   for (int e = 0; e < kSpecies; ++e) {
@@ -560,7 +564,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         GemmProblem P{};
         P.A = H2 + (row0 * h->ldh2 + (size_t)m * n2) * es; P.lda = h->ldh2;
         P.B = wb + (h->w_off[2] + r3[e][m] * ld_w3) * es; P.ldb = ld_w3;
-        P.D = Z3 + (row0 * h->ldz3 + (size_t)m * n3) * es; P.ldd = h->ldz3;
+        P.D = Z3 + (row0 * h->ldz3 + (size_t)m * n3); P.ldd = h->ldz3;
         P.bias = h->d_b + b1_total + b2_total + r3[e][m];
         P.M = Me; P.N = n3; P.K = n2; P.epi = (int)Epi::Bias;
         P.a_row0 = (int)row0; P.a_col0 = m * n2; P.b_row0 = (int)r3[e][m]; P.elem = e; P.model = m;
@@ -569,7 +573,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
       }
       {  // layer 3 reverse: delta2 = (delta3 W3) * celu'(h2), in place over h2
         GemmProblem P{};
-        P.A = Z3 + (row0 * h->ldz3 + (size_t)m * n3) * es; P.lda = h->ldz3;
+        P.A = D3 + (row0 * h->ldz3 + (size_t)m * n3) * es; P.lda = h->ldz3;
         P.B = wb + (h->w_off[3] + r3t[e][m] * ld_w3t) * es; P.ldb = ld_w3t;
         P.D = H2 + (row0 * h->ldh2 + (size_t)m * n2) * es; P.ldd = h->ldh2;
         P.M = Me; P.N = n2; P.K = n3; P.epi = (int)Epi::DCelu;
@@ -677,8 +681,8 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
   gemm(1);
   mark(4);
   gemm(2);
-  launch_head(h->d_z3, h->ldz3, h->prec, h->d_row_elem, h->d_w4, h->d_b4, nullptr, nullptr,
-              h->d_y, h->n_rows, h->n_models, 0, s);
+  launch_head(h->d_z3, h->ldz3, h->prec, h->d_row_elem, h->d_w4, h->d_b4, h->d_d3, h->d_y,
+              h->n_rows, h->n_models, s);
   ++kernels;
   mark(5);
   launch_energy(h->d_y, h->n_models, h->d_row_of_int, h->d_mol_off, h->n_mols, E, h->d_atom_e, s);

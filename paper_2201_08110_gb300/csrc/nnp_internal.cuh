@@ -87,7 +87,7 @@ enum class Prec { F32 = 0, BF16 = 1, F16 = 2 };
 // epilogue.  Rows are atoms, A and D share the row index.
 enum class Epi : int {
   BiasCelu = 0,   // D = celu(acc + bias[n])           (forward hidden layer)
-  Bias = 1,       // D = acc + bias[n]                  (pre-activation)
+  Bias = 1,       // D = acc + bias[n], FP32 output     (pre-activation of the last hidden layer)
   DCelu = 2,      // D = acc * celu'(D_in-place)       (reverse through a hidden layer)
   Store = 3       // D = acc (FP32 output)              (dE/dG)
 };
@@ -121,9 +121,9 @@ void launch_aev_adjoint(const Geometry& g, const NeighborLists& nl, const AevCon
                         const int* row_of_int, const float* dG, const int4* work, int n_work,
                         const int* orig_of_int, double* forces_out, int warps_per_cta,
                         int mol_atoms_smem_max, cudaStream_t s);
-void launch_head(const void* z3, long ldz, Prec prec, const int* row_elem, const float* w4,
-                 const float* b4, const float* b3, void* delta3, float* y, int n_rows,
-                 int n_models, int inv_models_scale, cudaStream_t s);
+void launch_head(const float* z3, long ldz, Prec prec, const int* row_elem, const float* w4,
+                 const float* b4, void* delta3, float* y, int n_rows, int n_models,
+                 cudaStream_t s);
 void launch_energy(const float* y, int n_models, const int* row_of_int, const int* mol_off,
                    int n_mols, double* energy_out, double* atom_energy_row, cudaStream_t s);
 void launch_gemm_simt(const GemmProblem* d_problems, const GemmTile* d_tiles, int n_tiles,

@@ -104,13 +104,14 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float
 template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
 
 // Output layer of every network: from the third layer's pre-activation z3
-// (bias included), h3 = celu(z3), y = w4 . h3 + b4, and the start of the
-// reverse pass delta3 = (1/M) w4 * celu'(z3), written over z3.
-// One warp per (row, model).
+// (FP32, bias included), h3 = celu(z3), y = w4 . h3 + b4, and the start of
+// the reverse pass delta3 = (1/M) w4 * celu'(z3) in the products' element
+// type.  One warp per (row, model).
 template <typename T>
-__global__ void k_head(T* __restrict__ z3, long ldz, const int* __restrict__ row_elem,
+__global__ void k_head(const float* __restrict__ z3, long ldz, const int* __restrict__ row_elem,
                        const float* __restrict__ w4, const float* __restrict__ b4,
-                       float* __restrict__ y, int n_rows, int n_models, float inv_m) {
+                       T* __restrict__ d3, float* __restrict__ y, int n_rows, int n_models,
+                       float inv_m) {
   const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= (long)n_rows * n_models) return;
@@ -121,16 +122,17 @@ __global__ void k_head(T* __restrict__ z3, long ldz, const int* __restrict__ row
     return;
   }
   const int h3 = hidden_width(e, 2);
-  T* zr = z3 + (size_t)row * ldz + (size_t)m * h3;
+  const float* zr = z3 + (size_t)row * ldz + (size_t)m * h3;
+  T* dr = d3 + (size_t)row * ldz + (size_t)m * h3;
   const float* w = w4 + ((size_t)e * kMaxModels + m) * kH3Max;
   float acc = 0.f;
   for (int c = lane; c < h3; c += 32) {
-    const float z = to_f(zr[c]);
+    const float z = zr[c];
     const float ex = expf(fminf(z, 0.f) * 10.f);  // exp(z / alpha), alpha = 0.1
     const float h = z > 0.f ? z : 0.1f * (ex - 1.f);
     const float dh = z > 0.f ? 1.f : ex;
     acc = fmaf(w[c], h, acc);
-    zr[c] = from_f<T>(w[c] * dh * inv_m);
+    dr[c] = from_f<T>(w[c] * dh * inv_m);
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -212,9 +214,8 @@ void launch_gather_positions(const float* pos, const int* orig, float4* out, int
   if (n > 0) k_gather_positions<<<(n + 255) / 256, 256, 0, s>>>(pos, orig, out, n, status);
 }
 
-void launch_head(const void* z3, long ldz, Prec prec, const int* row_elem, const float* w4,
-                 const float* b4, const float* /*b3*/, void* /*delta3*/, float* y, int n_rows,
-                 int n_models, int /*inv_models_scale*/, cudaStream_t s) {
+void launch_head(const float* z3, long ldz, Prec prec, const int* row_elem, const float* w4,
+                 const float* b4, void* d3, float* y, int n_rows, int n_models, cudaStream_t s) {
   const long warps = (long)n_rows * n_models;
   if (warps == 0) return;
   const int threads = 256;
@@ -222,15 +223,16 @@ void launch_head(const void* z3, long ldz, Prec prec, const int* row_elem, const
   const float inv_m = 1.0f / (float)n_models;
   switch (prec) {
     case Prec::F32:
-      k_head<float><<<blocks, threads, 0, s>>>((float*)z3, ldz, row_elem, w4, b4, y, n_rows,
+      k_head<float><<<blocks, threads, 0, s>>>(z3, ldz, row_elem, w4, b4, (float*)d3, y, n_rows,
                                                n_models, inv_m);
       break;
     case Prec::BF16:
-      k_head<__nv_bfloat16><<<blocks, threads, 0, s>>>((__nv_bfloat16*)z3, ldz, row_elem, w4, b4,
-                                                       y, n_rows, n_models, inv_m);
+      k_head<__nv_bfloat16><<<blocks, threads, 0, s>>>(z3, ldz, row_elem, w4, b4,
+                                                       (__nv_bfloat16*)d3, y, n_rows, n_models,
+                                                       inv_m);
       break;
     case Prec::F16:
-      k_head<__half><<<blocks, threads, 0, s>>>((__half*)z3, ldz, row_elem, w4, b4, y, n_rows,
+      k_head<__half><<<blocks, threads, 0, s>>>(z3, ldz, row_elem, w4, b4, (__half*)d3, y, n_rows,
                                                 n_models, inv_m);
       break;
   }
