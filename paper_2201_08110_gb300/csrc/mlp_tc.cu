@@ -1,14 +1,384 @@
-// mlp_tc.cu -- grouped matrix products of the atomic networks on the tensor
-// cores (BF16 / FP16 operands, FP32 accumulation).
+// mlp_tc.cu -- grouped matrix products of the atomic networks on the 5th-gen
+// tensor cores: BF16 or FP16 operands, FP32 accumulation in tensor memory.
+//
+// The networks of every element and ensemble member run as one launch per
+// layer (Sec. 2 "Optimization": the ensemble is evaluated in parallel over
+// networks and atoms).  Each CTA computes one 128 x N output tile (N <= 256,
+// set per tile in the instruction descriptor) of D = A * B^T, A and B K-major:
+//   * warp 0, one lane: TMA producer, 64-wide K blocks of A (128 rows) and B
+//     (256 rows) into a 4-stage ring of 128B-swizzled shared memory;
+//   * warp 1, one lane: issues tcgen05.mma (M = 128, K = 16 per instruction)
+//     into a 256-column FP32 accumulator in tensor memory and releases each
+//     stage with tcgen05.commit;
+//   * all 4 warps: epilogue, tcgen05.ld of the rows they own (warp w = lanes
+//     32w..32w+31), bias / CELU / CELU' fused, stores to global memory.
+// Every mbarrier wait is bounded; a wait that gives up sets the status word's
+// timeout bit and the CTA skips the rest of its work, frees its tensor
+// memory and returns.
+#include <cuda.h>
+
+#include <cstring>
+
 #include "nnp_internal.cuh"
 
 namespace nnp {
 
-bool tc_available() { return true; }
+namespace {
 
-void launch_gemm_tc(const GemmProblem* probs, const GemmTile* tiles, int n_tiles, Prec p, int /*layer*/,
-                    const void* /*maps*/, unsigned* /*status*/, cudaStream_t s) {
-  launch_gemm_simt_typed(probs, tiles, n_tiles, p, s);
+constexpr int kBM = 128;       // tile rows (atoms)
+constexpr int kBNMax = 256;    // tile columns, TMEM columns allocated
+constexpr int kBK = 64;        // K per stage (128 bytes of 16-bit elements)
+constexpr int kStages = 4;
+constexpr int kThreads = 128;
+constexpr uint32_t kABytes = kBM * kBK * 2;      // 16 KB
+constexpr uint32_t kBBytes = kBNMax * kBK * 2;   // 32 KB
+constexpr uint32_t kStageBytes = kABytes + kBBytes;
+constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+constexpr long long kSpinLimit = 1ll << 26;  // try_wait polls before giving up
+
+struct TcMaps {
+  CUtensorMap a;
+  CUtensorMap b;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long i = 0; i < kSpinLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void* p) {
+  const uint32_t addr = smem_u32(p);
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(16u >> 4) << 16;    // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;             // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;             // swizzle mode: 128 B
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, A/B both BF16 (fmt 1)
+// or both FP16 (fmt 0), K-major A and B, M = 128, N = n.
+__device__ __forceinline__ uint32_t instr_desc(uint32_t fmt, uint32_t n) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <typename T> struct Pack;
+template <> struct Pack<__nv_bfloat16> {
+  static __device__ __forceinline__ uint32_t two(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  static __device__ __forceinline__ float lo(uint32_t u) {
+    return __bfloat162float(__ushort_as_bfloat16((unsigned short)(u & 0xffffu)));
+  }
+  static __device__ __forceinline__ float hi(uint32_t u) {
+    return __bfloat162float(__ushort_as_bfloat16((unsigned short)(u >> 16)));
+  }
+  static constexpr uint32_t fmt = 1;
+};
+template <> struct Pack<__half> {
+  static __device__ __forceinline__ uint32_t two(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  static __device__ __forceinline__ float lo(uint32_t u) {
+    return __half2float(__ushort_as_half((unsigned short)(u & 0xffffu)));
+  }
+  static __device__ __forceinline__ float hi(uint32_t u) {
+    return __half2float(__ushort_as_half((unsigned short)(u >> 16)));
+  }
+  static constexpr uint32_t fmt = 0;
+};
+
+__device__ __forceinline__ float celu01(float z) {
+  return z > 0.f ? z : 0.1f * (expf(fminf(z, 0.f) * 10.f) - 1.f);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_tc(const __grid_constant__ TcMaps maps, const GemmProblem* __restrict__ probs,
+              const GemmTile* __restrict__ tiles, unsigned* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* accum = empty + kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmProblem P = probs[tl.problem];
+  const int n_tile = min(kBNMax, P.N - tl.n0);  // multiple of 16
+  const int nkb = (P.K + kBK - 1) / kBK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"((uint32_t)kBNMax));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ----
+    const int ay = P.a_row0 + tl.m0, by = P.b_row0 + tl.n0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % kStages;
+      if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1)) {
+        atomicOr(status, kStatTimeout);
+        atomicExch(abort_flag, 1);
+        break;
+      }
+      unsigned char* sa = smem + s * kStageBytes;
+      mbar_expect_tx(&full[s], kStageBytes);
+      tma_load_2d(sa, &maps.a, P.a_col0 + kb * kBK, ay, &full[s]);
+      tma_load_2d(sa + kABytes, &maps.b, P.b_col0 + kb * kBK, by, &full[s]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    const uint32_t idesc = instr_desc(Pack<T>::fmt, (uint32_t)n_tile);
+    bool ok = true;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % kStages;
+      if (!mbar_wait(&full[s], (kb / kStages) & 1)) {
+        atomicOr(status, kStatTimeout);
+        atomicExch(abort_flag, 1);
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const unsigned char* sa = smem + s * kStageBytes;
+      const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sa + kABytes);
+      const int ksteps = min(kBK, P.K - kb * kBK) / 16;
+      for (int j = 0; j < ksteps; ++j)  // +32 bytes per K step inside the swizzle atom
+        mma_f16(tmem, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc,
+                (kb > 0 || j > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+    }
+    if (ok) mma_commit(accum);
+  }
+  __syncwarp();
+
+  // ---- epilogue: all warps ----
+  const bool have = mbar_wait(accum, 0);
+  if (!have) atomicOr(status, kStatTimeout);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (have && !*(volatile int*)abort_flag) {
+    const int row = tl.m0 + warp * 32 + lane;
+    const bool row_ok = row < P.M;
+    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c = 0; c < n_tile; c += 16) {
+      float v[16];
+      tmem_ld16(tbase + (uint32_t)c, v);  // all lanes take part (sync.aligned)
+      if (!row_ok) continue;
+      const int n = tl.n0 + c;
+      switch (P.epi) {
+        case (int)Epi::BiasCelu: {
+          uint32_t o[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            o[i] = Pack<T>::two(celu01(v[2 * i] + P.bias[n + 2 * i]),
+                                celu01(v[2 * i + 1] + P.bias[n + 2 * i + 1]));
+          uint4* d = reinterpret_cast<uint4*>(static_cast<T*>(P.D) + (size_t)row * P.ldd + n);
+          d[0] = make_uint4(o[0], o[1], o[2], o[3]);
+          d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+          break;
+        }
+        case (int)Epi::Bias: {
+          float4* d = reinterpret_cast<float4*>(static_cast<float*>(P.D) + (size_t)row * P.ldd + n);
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            d[i] = make_float4(v[4 * i] + P.bias[n + 4 * i], v[4 * i + 1] + P.bias[n + 4 * i + 1],
+                               v[4 * i + 2] + P.bias[n + 4 * i + 2],
+                               v[4 * i + 3] + P.bias[n + 4 * i + 3]);
+          break;
+        }
+        case (int)Epi::DCelu: {
+          uint4* d = reinterpret_cast<uint4*>(static_cast<T*>(P.D) + (size_t)row * P.ldd + n);
+          const uint4 h0 = d[0], h1 = d[1];
+          const uint32_t hin[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+          uint32_t o[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float ha = Pack<T>::lo(hin[i]), hb = Pack<T>::hi(hin[i]);
+            const float ga = ha > 0.f ? 1.f : fmaf(10.f, ha, 1.f);  // celu' from celu, alpha 0.1
+            const float gb = hb > 0.f ? 1.f : fmaf(10.f, hb, 1.f);
+            o[i] = Pack<T>::two(v[2 * i] * ga, v[2 * i + 1] * gb);
+          }
+          d[0] = make_uint4(o[0], o[1], o[2], o[3]);
+          d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+          break;
+        }
+        default: {
+          float4* d = reinterpret_cast<float4*>(static_cast<float*>(P.D) + (size_t)row * P.ldd + n);
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            d[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+          break;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)kBNMax));
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+bool tc_available() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
+
+size_t tc_maps_bytes() { return sizeof(TcMaps); }
+
+// 2D tensor map over a row-major [rows][cols] array of 16-bit elements with a
+// 64-column x box_rows box and 128-byte swizzle.  Returns false on failure.
+bool tc_make_map(void* out_map, const void* base, Prec p, uint64_t rows, uint64_t cols,
+                 uint64_t row_stride_elems, uint32_t box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  CUtensorMap* m = static_cast<CUtensorMap*>(out_map);
+  std::memset(m, 0, sizeof(*m));
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {row_stride_elems * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(m, p == Prec::BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                        2, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+cudaError_t tc_set_smem() {
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<__nv_bfloat16>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_gemm_tc<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kSmemBytes);
+}
+
+// maps: HOST pointer to the layer's {A map, B map} pair (copied into the
+// launch's parameters).
+void launch_gemm_tc(const GemmProblem* probs, const GemmTile* tiles, int n_tiles, Prec p,
+                    int /*layer*/, const void* maps, unsigned* status, cudaStream_t s) {
+  if (n_tiles <= 0) return;
+  TcMaps m;
+  std::memcpy(&m, maps, sizeof(m));
+  if (p == Prec::BF16)
+    k_gemm_tc<__nv_bfloat16><<<n_tiles, kThreads, kSmemBytes, s>>>(m, probs, tiles, status);
+  else
+    k_gemm_tc<__half><<<n_tiles, kThreads, kSmemBytes, s>>>(m, probs, tiles, status);
 }
 
 }  // namespace nnp

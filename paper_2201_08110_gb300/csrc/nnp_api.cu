@@ -16,6 +16,10 @@ namespace nnp {
 void launch_gemm_tc(const GemmProblem* probs, const GemmTile* tiles, int n_tiles, Prec p, int layer,
                     const void* maps, unsigned* status, cudaStream_t s);
 bool tc_available();
+size_t tc_maps_bytes();
+bool tc_make_map(void* out_map, const void* base, Prec p, uint64_t rows, uint64_t cols,
+                 uint64_t row_stride_elems, uint32_t box_rows);
+cudaError_t tc_set_smem();
 }  // namespace nnp
 
 using namespace nnp;
@@ -64,7 +68,8 @@ struct nnp_ctx {
   float *d_w4 = nullptr, *d_b4 = nullptr;
   size_t w_off[6] = {0};  // W1, W2, W3, W3T, W2T, W1T element offsets in d_w
   Layer L[6];              // 0 L1 fwd, 1 L2 fwd, 2 L3 fwd, 3 L3 rev, 4 L2 rev, 5 L1 rev
-  void* d_maps = nullptr;  // tensor-core path: TMA descriptors per layer
+  void* d_maps = nullptr;
+  alignas(64) unsigned char tc_maps[6][256];  // tensor-core path: {A, B} TMA descriptors per layer
   // reverse pass work list
   int4* d_work = nullptr;
   int n_work = 0;
@@ -520,7 +525,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   char* H2 = static_cast<char*>(h->d_h2);
   float* Z3 = h->d_z3;
   char* D3 = static_cast<char*>(h->d_d3);
-  const bool tc = false;  // tile shapes of the tensor-core kernel (not yet enabled)
+  const bool tc = h->prec != Prec::F32;
   const int bm = tc ? 128 : 64;
   for (int e = 0; e < kSpecies; ++e) {
     const int Me = h->elem_count[e];
@@ -536,7 +541,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
       P.M = Me; P.N = M * n1; P.K = tc ? kFeaturesPad : kFeatures; P.epi = (int)Epi::BiasCelu;
       P.a_row0 = (int)row0; P.b_row0 = (int)r1[e]; P.elem = e; P.model = -1;
       h->L[0].probs.push_back(P);
-      add_tiles(h->L[0], bm, tc ? 256 : 64);
+      add_tiles(h->L[0], bm, tc ? 256 : 64);  // first layer forward
     }
     {  // layer 1 reverse: dE/dG = sum_m delta1_m W1_m
       GemmProblem P{};
@@ -558,7 +563,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         P.M = Me; P.N = n2; P.K = n1; P.epi = (int)Epi::BiasCelu;
         P.a_row0 = (int)row0; P.a_col0 = m * n1; P.b_row0 = (int)r2[e][m]; P.elem = e; P.model = m;
         h->L[1].probs.push_back(P);
-        add_tiles(h->L[1], bm, tc ? n2 : 64);
+        add_tiles(h->L[1], bm, tc ? 256 : 64);
       }
       {  // layer 3 forward (pre-activation)
         GemmProblem P{};
@@ -569,7 +574,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         P.M = Me; P.N = n3; P.K = n2; P.epi = (int)Epi::Bias;
         P.a_row0 = (int)row0; P.a_col0 = m * n2; P.b_row0 = (int)r3[e][m]; P.elem = e; P.model = m;
         h->L[2].probs.push_back(P);
-        add_tiles(h->L[2], bm, tc ? n3 : 64);
+        add_tiles(h->L[2], bm, tc ? 256 : 64);
       }
       {  // layer 3 reverse: delta2 = (delta3 W3) * celu'(h2), in place over h2
         GemmProblem P{};
@@ -579,7 +584,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         P.M = Me; P.N = n2; P.K = n3; P.epi = (int)Epi::DCelu;
         P.a_row0 = (int)row0; P.a_col0 = m * n3; P.b_row0 = (int)r3t[e][m]; P.elem = e; P.model = m;
         h->L[3].probs.push_back(P);
-        add_tiles(h->L[3], bm, tc ? n2 : 64);
+        add_tiles(h->L[3], bm, tc ? 256 : 64);
       }
       {  // layer 2 reverse: delta1 = (delta2 W2) * celu'(h1), in place over h1
         GemmProblem P{};
@@ -589,9 +594,36 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         P.M = Me; P.N = n1; P.K = n2; P.epi = (int)Epi::DCelu;
         P.a_row0 = (int)row0; P.a_col0 = m * n2; P.b_row0 = (int)r2t[e][m]; P.elem = e; P.model = m;
         h->L[4].probs.push_back(P);
-        add_tiles(h->L[4], bm, tc ? n1 : 64);
+        add_tiles(h->L[4], bm, tc ? 256 : 64);
       }
     }
+  }
+  if (tc) {
+    if (tc_maps_bytes() > sizeof(h->tc_maps[0])) return fail(h, NNP_ERR_UNSUPPORTED, "tensor map size");
+    const uint64_t R64 = (uint64_t)h->n_rows;
+    struct MapSpec {
+      const void* base;
+      uint64_t rows, cols;
+    };
+    const MapSpec A[6] = {{h->d_aev, R64, (uint64_t)kFeaturesPad},
+                          {h->d_h1, R64, (uint64_t)h->ldh1},
+                          {h->d_h2, R64, (uint64_t)h->ldh2},
+                          {h->d_d3, R64, (uint64_t)h->ldz3},
+                          {h->d_h2, R64, (uint64_t)h->ldh2},
+                          {h->d_h1, R64, (uint64_t)h->ldh1}};
+    const MapSpec B[6] = {{wb + h->w_off[0] * es, rows_w1, ld_w1},
+                          {wb + h->w_off[1] * es, rows_w2, ld_w2},
+                          {wb + h->w_off[2] * es, rows_w3, ld_w3},
+                          {wb + h->w_off[3] * es, rows_w3t, ld_w3t},
+                          {wb + h->w_off[4] * es, rows_w2t, ld_w2t},
+                          {wb + h->w_off[5] * es, (uint64_t)kSpecies * kFeaturesPad, ld_w1t}};
+    const size_t half = tc_maps_bytes() / 2;
+    for (int l = 0; l < 6; ++l) {
+      if (!tc_make_map(h->tc_maps[l], A[l].base, h->prec, A[l].rows, A[l].cols, A[l].cols, 128) ||
+          !tc_make_map(h->tc_maps[l] + half, B[l].base, h->prec, B[l].rows, B[l].cols, B[l].cols, 256))
+        return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for layer " + std::to_string(l));
+    }
+    CK(tc_set_smem());
   }
   for (auto& L : h->L) {
     CK(dalloc(&L.d_probs, L.probs.size()));
@@ -650,7 +682,7 @@ void run_gemm(nnp_ctx* h, int layer, cudaStream_t s) {
   if (h->prec == Prec::F32)
     launch_gemm_simt(L.d_probs, L.d_tiles, (int)L.tiles.size(), s);
   else
-    launch_gemm_tc(L.d_probs, L.d_tiles, (int)L.tiles.size(), h->prec, layer, h->d_maps,
+    launch_gemm_tc(L.d_probs, L.d_tiles, (int)L.tiles.size(), h->prec, layer, h->tc_maps[layer],
                    h->d_status, s);
 }
 

