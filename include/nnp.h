@@ -54,7 +54,8 @@ typedef enum {
   NNP_ERR_CAPACITY = 6,   /* device: a neighbour list exceeded its capacity */
   NNP_ERR_NONFINITE = 7,  /* device: a position was NaN or infinite */
   NNP_ERR_TIMEOUT = 8,    /* device: a bounded wait inside a kernel gave up */
-  NNP_ERR_UNSUPPORTED = 9 /* the requested mode is not available */
+  NNP_ERR_UNSUPPORTED = 9, /* the requested mode is not available */
+  NNP_ERR_TOO_LARGE = 10   /* nnp_features_static: more than NNP_STATIC_MAX_ATOMS atoms */
 } nnp_status;
 
 /* Arithmetic of the networks' matrix products.  The featurizer, the neighbour
@@ -196,6 +197,32 @@ nnp_status nnp_compute_timed(nnp_handle h, const float* positions_dev, double* e
 
 /* Number of kernels one nnp_compute launches (with or without forces). */
 int32_t nnp_kernels_per_step(nnp_handle h, int32_t with_forces);
+
+/* ---- allocation-free entry point -----------------------------------------------
+ * The paper has no counterpart: this serves callers that cannot let a library
+ * allocate device memory -- an MD engine capturing its whole time step into a
+ * CUDA graph (cudaMalloc cannot be captured and synchronises the device), or a
+ * host framework that owns the device memory budget and forbids raw
+ * cudaMalloc.  It needs no handle and allocates nothing.
+ *
+ * Features of ONE non-periodic molecule, the same quantities nnp_get_features
+ * returns after nnp_compute:
+ *   Z_dev:            DEVICE int32 [n_atoms] atomic numbers
+ *   positions_dev:    DEVICE FP32 [n_atoms][3], Angstrom
+ *   features_out_dev: DEVICE FP32 [n_atoms][1008], written (caller order)
+ * n_atoms > NNP_STATIC_MAX_ATOMS returns NNP_ERR_TOO_LARGE; nothing is enqueued.
+ * An atomic number outside {1,6,7,8,9,16,17} or a non-finite position makes
+ * every output feature NaN (there is no handle to carry a status).
+ * Intermediates live in one fixed scratch array of about 2 MB in device global
+ * memory that every GPU loading the library holds until the process exits;
+ * all calls on a device share it and it keeps the last call's contents, so
+ * calls that overlap on the GPU race: serialise them (one stream, or events).
+ * The first call on each device looks up the array's address (with that
+ * device current); make that first call before any stream capture.  Returns
+ * NNP_ERR_ARG for null buffers, NNP_ERR_CUDA if a launch failed. */
+#define NNP_STATIC_MAX_ATOMS 256
+nnp_status nnp_features_static(const int32_t* Z_dev, const float* positions_dev, int32_t n_atoms,
+                               float* features_out_dev, void* stream);
 
 #ifdef __cplusplus
 }

@@ -218,6 +218,11 @@ void add_tiles(Layer& L, int bm, int bn) {
 
 }  // namespace
 
+namespace nnp {
+// The featurizer constants, for other translation units of the library.
+void aev_constants(AevConst& c, const double box[3]) { init_aev_const(c, box); }
+}  // namespace nnp
+
 extern "C" {
 
 int64_t nnp_weights_per_model(void) { return model_params(); }

@@ -142,6 +142,9 @@ void launch_export_features(const void* aev, Prec prec, const int* row_of_int,
 void launch_export_atomic_energies(const double* atom_energy_row, const int* row_of_int,
                                    const int* orig_of_int, int n, double* out, cudaStream_t s);
 
+// Featurizer constants (cutoffs, shift grids, species-pair table, box).
+void aev_constants(AevConst& c, const double box[3]);
+
 // Setup kernels (create time).
 void launch_species_setup(const int* Z_caller, const int* mol_off, int n_mols, int n_atoms,
                           int* species_caller, int* mol_species_count, unsigned* bad,

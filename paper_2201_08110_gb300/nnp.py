@@ -21,13 +21,15 @@ FP32, BF16, FP16 = 0, 1, 2
 _PREC = {"fp32": FP32, "bf16": BF16, "fp16": FP16}
 STATUS = {0: "NNP_OK", 1: "NNP_ERR_ARG", 2: "NNP_ERR_SPECIES", 3: "NNP_ERR_CHARGE",
           4: "NNP_ERR_ALLOC", 5: "NNP_ERR_CUDA", 6: "NNP_ERR_CAPACITY", 7: "NNP_ERR_NONFINITE",
-          8: "NNP_ERR_TIMEOUT", 9: "NNP_ERR_UNSUPPORTED"}
+          8: "NNP_ERR_TIMEOUT", 9: "NNP_ERR_UNSUPPORTED", 10: "NNP_ERR_TOO_LARGE"}
 
 # Every entry point declared in include/nnp.h.
 EXPORTS = ("nnp_weights_per_model", "nnp_num_features", "nnp_create", "nnp_create_batch",
            "nnp_compute", "nnp_compute_host", "nnp_get_status", "nnp_last_error", "nnp_destroy",
            "nnp_get_capacity", "nnp_get_neighbors", "nnp_get_features",
-           "nnp_get_atomic_energies", "nnp_compute_timed", "nnp_kernels_per_step")
+           "nnp_get_atomic_energies", "nnp_compute_timed", "nnp_kernels_per_step",
+           "nnp_features_static")
+STATIC_MAX_ATOMS = 256
 STAGES = ("neighbors", "features", "l1_fwd", "l2_fwd", "l3_fwd", "energy", "l3_rev", "l2_rev",
           "l1_rev", "adjoint")
 
@@ -88,6 +90,8 @@ def load_library(path: str = LIB_PATH):
     lib.nnp_compute_timed.restype = ctypes.c_int
     lib.nnp_kernels_per_step.argtypes = [P, I32]
     lib.nnp_kernels_per_step.restype = I32
+    lib.nnp_features_static.argtypes = [P, P, I32, P, P]
+    lib.nnp_features_static.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -230,6 +234,22 @@ class NNP:
         out = torch.empty(self.n_atoms, dtype=torch.float64, device="cuda")
         self._check(self._lib.nnp_get_atomic_energies(self._h, _ptr(out), _stream_ptr(stream)))
         return out
+
+
+def features_static(Z, positions, out=None, stream=None):
+    """Features of one non-periodic molecule (CUDA int32 Z [n], CUDA float32
+    positions [n, 3]) through the allocation-free entry point; returns CUDA
+    float32 [n, 1008].  For callers that cannot let the library allocate
+    device memory (see nnp_features_static in include/nnp.h)."""
+    import torch
+    lib = load_library()
+    n = int(positions.shape[0])
+    if out is None:
+        out = torch.empty(n, 1008, dtype=torch.float32, device=positions.device)
+    rc = lib.nnp_features_static(_ptr(Z), _ptr(positions), n, _ptr(out), _stream_ptr(stream))
+    if rc != 0:
+        raise NNPError(rc, "nnp_features_static")
+    return out
 
 
 def _autograd_function():
