@@ -129,120 +129,222 @@ template <> __device__ __forceinline__ __nv_bfloat16 cvt_out<__nv_bfloat16>(floa
 }
 template <> __device__ __forceinline__ __half cvt_out<__half>(float v) { return __float2half_rn(v); }
 
-// Per-warp shared memory of the forward kernel (floats).
-__host__ __device__ constexpr int aev_fwd_warp_floats(int cap_a) {
-  return kAngular + 2 * kRadial + 32 * 13 + cap_a * 6;
+// Per-warp shared memory of the forward kernel (floats):
+//   buf[12][36] (the radial accumulators R2[2][112] alias it) | meta: block prefix
+//   bpre[32], group start gs[8], group count gn[8] (ints) |
+//   staging union: radial {rd, rfc, rsp}[cap_r]  or  angular {avec float4, afc, asp}[cap_a]
+constexpr int kBufStride = 36;  // phase-1 factor rows: 16-byte aligned, bank-spread
+constexpr int kMeta = 48;
+__host__ __device__ constexpr int aev_fwd_warp_floats(int cap_r, int cap_a) {
+  return 12 * kBufStride + kMeta + (3 * cap_r > 6 * cap_a ? 3 * cap_r : 6 * cap_a);
 }
 
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Species pair (s, t), s <= t, of each of the 28 blocks, row-major upper triangle.
+__constant__ unsigned char kBlkS[kPairBlocks] = {0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 2,
+                                                 2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 5, 5, 6};
+__constant__ unsigned char kBlkT[kPairBlocks] = {0, 1, 2, 3, 4, 5, 6, 1, 2, 3, 4, 5, 6, 2,
+                                                 3, 4, 5, 6, 3, 4, 5, 6, 4, 5, 6, 5, 6, 6};
+
+// Index of the unordered species pair {s, t} in the row-major upper triangle.
+__device__ __forceinline__ int pair_block(int s, int t) {
+  const int a = min(s, t), b = max(s, t);
+  return a * kSpecies - (a * (a - 1)) / 2 + (b - a);
+}
+
+// The angular features of a centre are sums over unordered neighbour pairs.
+// Pairs are enumerated block-major: species-pair block b = (s, t) holds every
+// pair with one neighbour of element s and one of element t (the neighbour
+// list is sorted by element, so each element is one contiguous group), and
+// the blocks follow each other in feature order.  Each block is then one
+// contiguous run of pairs, accumulated once and written once.
 template <typename TOut>
 __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __restrict__ row_of_int,
                       TOut* __restrict__ out) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
+  const unsigned FULL = 0xffffffffu;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = blockIdx.x * (blockDim.x >> 5) + warp;
   if (q >= g.n_atoms) return;  // warp-uniform; no block-level barriers below
-  float* Gang = smem + (size_t)warp * aev_fwd_warp_floats(nl.cap_a);
-  float* R2 = Gang + kAngular;          // [2][112]
-  float* buf = R2 + 2 * kRadial;        // [32][13]
-  float4* nb = reinterpret_cast<float4*>(buf + 32 * 13);  // [cap_a]  (16-byte aligned: see host)
-  float* nfc = reinterpret_cast<float*>(nb + nl.cap_a);    // [cap_a]
-  int* nsp = reinterpret_cast<int*>(nfc + nl.cap_a);       // [cap_a]
+  float* buf = smem + (size_t)warp * aev_fwd_warp_floats(nl.cap_r, nl.cap_a);  // [12][36]
+  float* R2 = buf;                                       // [2][112], radial phase only
+  int* bpre = reinterpret_cast<int*>(buf + 12 * kBufStride);  // [29] block prefix
+  int* gs = bpre + 32;                                   // [7] group start
+  int* gn = gs + 8;                                      // [7] group size
+  float* U = buf + 12 * kBufStride + kMeta;              // staging union (16-byte aligned)
+  float* rd = U;
+  float* rfc = rd + nl.cap_r;
+  int* rsp = reinterpret_cast<int*>(rfc + nl.cap_r);
+  float4* avec = reinterpret_cast<float4*>(U);
+  float* afc = reinterpret_cast<float*>(avec + nl.cap_a);
+  int* asp = reinterpret_cast<int*>(afc + nl.cap_a);
+  TOut* dst = out + (size_t)row_of_int[q] * kFeaturesPad;
 
-  for (int f = lane; f < kAngular; f += 32) Gang[f] = 0.f;
   for (int f = lane; f < 2 * kRadial; f += 32) R2[f] = 0.f;
   const float4 xi = g.pos[q];
 
-  // ---- radial: lane = (half, shift) ----
+  // ---- radial: stage the neighbours (lane-parallel loads), then lane =
+  //      (neighbour parity, shift), each lane owning one accumulator column ----
+  const int nr = min(nl.cnt_r[q], nl.cap_r);
   {
-    const int nr = min(nl.cnt_r[q], nl.cap_r);
-    const int half = lane >> 4, k = lane & 15;
-    const float shf = c.ShfR[k];
     const int* lr = nl.nbr_r + (size_t)q * nl.cap_r;
-    float* acc = R2 + half * kRadial;
-    __syncwarp();
-    for (int t = half; t < nr; t += 2) {
+    for (int t = lane; t < nr; t += 32) {
       const int j = lr[t];
       const float3 d = disp(xi, g.pos[j], c);
       const float r = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
-      const float fc = 0.5f * cospif(r / c.Rcr) + 0.5f;
-      const float x = r - shf;
-      acc[g.species[j] * kShfR + k] += 0.25f * expf(-c.EtaR * x * x) * fc;
-    }
-  }
-
-  // ---- angular ----
-  const int na = min(nl.cnt_a[q], nl.cap_a);
-  {
-    const int* la = nl.nbr_a + (size_t)q * nl.cap_a;
-    for (int t = lane; t < na; t += 32) {
-      const int j = la[t];
-      const float3 d = disp(xi, g.pos[j], c);
-      const float r = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
-      nb[t] = make_float4(d.x, d.y, d.z, r);
-      nfc[t] = 0.5f * cospif(r / c.Rca) + 0.5f;
-      nsp[t] = g.species[j];
+      rd[t] = r;
+      rfc[t] = 0.5f * cospif(r / c.Rcr) + 0.5f;
+      rsp[t] = g.species[j];
     }
   }
   __syncwarp();
-  const int T = na * (na - 1) / 2;
+  {
+    const int half = lane >> 4, k = lane & 15;
+    const float shf = c.ShfR[k];
+    const float eta = -c.EtaR * kLog2e;
+    float* acc = R2 + half * kRadial;
+    for (int t = half; t < nr; t += 2) {
+      const float x = rd[t] - shf;
+      acc[rsp[t] * kShfR + k] += 0.25f * exp2f(eta * x * x) * rfc[t];
+    }
+  }
+  __syncwarp();
+  for (int f = lane; f < kRadial; f += 32) dst[f] = cvt_out<TOut>(R2[f] + R2[kRadial + f]);
+  __syncwarp();  // R2 and the radial staging are dead from here on
+
+  // ---- angular staging and the element groups of the list ----
+  const int na = min(nl.cnt_a[q], nl.cap_a);
+  int cnt_s = 0;  // lane s < 7: size of element group s
+  {
+    const int* la = nl.nbr_a + (size_t)q * nl.cap_a;
+    for (int base = 0; base < na; base += 32) {
+      const int t = base + lane;
+      int sp = -1;
+      if (t < na) {
+        const int j = la[t];
+        const float3 d = disp(xi, g.pos[j], c);
+        const float r = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+        avec[t] = make_float4(d.x, d.y, d.z, r);
+        afc[t] = 0.5f * cospif(r / c.Rca) + 0.5f;
+        sp = g.species[j];
+        asp[t] = sp;
+      }
+#pragma unroll
+      for (int e = 0; e < kSpecies; ++e) {
+        const int n_e = __popc(__ballot_sync(FULL, sp == e));
+        if (lane == e) cnt_s += n_e;
+      }
+    }
+  }
+  {
+    int start = cnt_s;  // exclusive prefix over lanes 0..6
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const int v = __shfl_up_sync(FULL, start, o);
+      if (lane >= o) start += v;
+    }
+    start -= cnt_s;
+    if (lane < kSpecies) {
+      gs[lane] = start;
+      gn[lane] = cnt_s;
+    }
+    // pairs per block, then the block prefix (lanes 0..27)
+    const int bs = lane < kPairBlocks ? kBlkS[lane] : 0, bt = lane < kPairBlocks ? kBlkT[lane] : 0;
+    const int ns = __shfl_sync(FULL, cnt_s, bs), nt = __shfl_sync(FULL, cnt_s, bt);
+    const int size = lane < kPairBlocks ? (bs == bt ? ns * (ns - 1) / 2 : ns * nt) : 0;
+    int incl = size;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane < kPairBlocks) bpre[lane + 1] = incl;
+    if (lane == 0) bpre[0] = 0;
+  }
+  __syncwarp();
+  const int T = bpre[kPairBlocks];
+
+  // ---- angular, 32 neighbour pairs at a time ----
   const int fa = lane >> 2, fz = lane & 3;
+  const float etaA = -c.EtaA * kLog2e;
   float acc = 0.f;
-  int pcur = -1;
+  int pcur = -1;  // block being accumulated; blocks before it are written
   for (int base = 0; base < T; base += 32) {
     const int P = base + lane;
-    float* my = buf + lane * 13;
-    if (P < T) {
+    const bool valid = P < T;
+    int pl = -1;
+    if (valid) {
+      // phase 1: this lane's pair -> 8 distance factors, 4 angle factors
+      int b = 0;
+#pragma unroll
+      for (int step = 16; step; step >>= 1)
+        if (b + step <= kPairBlocks - 1 && bpre[b + step] <= P) b += step;
+      const int l = P - bpre[b];
+      const int s = kBlkS[b], t = kBlkT[b];
       int j, k;
-      decode_pair(P, na, j, k);
-      const float4 rj = nb[j], rk = nb[k];
-      const float cost = (rj.x * rk.x + rj.y * rk.y + rj.z * rk.z) / (rj.w * rk.w);
+      if (s != t) {
+        const int n_t = gn[t];
+        int qd = (int)__fdividef((float)l + 0.5f, (float)n_t);
+        if (qd * n_t > l) --qd;
+        else if ((qd + 1) * n_t <= l) ++qd;
+        j = gs[s] + qd;
+        k = gs[t] + (l - qd * n_t);
+      } else {
+        decode_pair(l, gn[s], j, k);
+        j += gs[s];
+        k += gs[s];
+      }
+      const float4 rj = avec[j], rk = avec[k];
+      const float cost = __fdividef(rj.x * rk.x + rj.y * rk.y + rj.z * rk.z, rj.w * rk.w);
       const float cp = 0.95f * cost;
       const float sp = sqrtf(fmaxf(1.f - cp * cp, 0.f));
-      const float fcjk = nfc[j] * nfc[k];
+      const float fcjk = 2.f * afc[j] * afc[k];
       const float u = 0.5f * (rj.w + rk.w);
 #pragma unroll
       for (int a = 0; a < kShfA; ++a) {
         const float x = u - c.ShfA[a];
-        my[a] = expf(-c.EtaA * x * x);
+        buf[a * kBufStride + lane] = exp2f(etaA * x * x);
       }
 #pragma unroll
       for (int z = 0; z < kShfZ; ++z) {
-        const float b = fmaxf(0.5f * (1.f + cp * c.cosZ[z] + sp * c.sinZ[z]), 0.f);
-        my[kShfA + z] = 2.f * exp2f(c.Zeta * log2f(b)) * fcjk;
+        const float bb = fmaxf(0.5f * (1.f + cp * c.cosZ[z] + sp * c.sinZ[z]), 0.f);
+        buf[(kShfA + z) * kBufStride + lane] = exp2f(c.Zeta * __log2f(bb)) * fcjk;
       }
-      my[12] = __int_as_float(c.pair_index[nsp[j]][nsp[k]]);
+      pl = b;
     }
-    __syncwarp();
+    // phase 2: lane = feature (a, z); walk the runs of equal block
+    const int prev = __shfl_up_sync(FULL, pl, 1);
+    unsigned starts = __ballot_sync(FULL, valid && (lane == 0 || prev != pl));
     const int cnt = min(32, T - base);
-    for (int t = 0; t < cnt; ++t) {
-      const float* row = buf + t * 13;
-      const int p = __float_as_int(row[12]);
-      if (p != pcur) {
-        if (pcur >= 0) Gang[pcur * kAngPerBlock + lane] += acc;
+    __syncwarp();
+    const float* ra = buf + fa * kBufStride;
+    const float* za = buf + (kShfA + fz) * kBufStride;
+    while (starts) {
+      const int t0 = __ffs(starts) - 1;
+      starts &= starts - 1;
+      const int t1 = starts ? __ffs(starts) - 1 : cnt;
+      const int p = __shfl_sync(FULL, pl, t0);
+      if (p != pcur) {  // block pcur is complete: write it, and zeros for empty blocks
+        if (pcur >= 0) dst[kRadial + pcur * kAngPerBlock + lane] = cvt_out<TOut>(acc);
+        for (int e = pcur + 1; e < p; ++e) dst[kRadial + e * kAngPerBlock + lane] = cvt_out<TOut>(0.f);
         acc = 0.f;
         pcur = p;
       }
-      acc = fmaf(row[fa], row[kShfA + fz], acc);
+#pragma unroll 4
+      for (int t = t0; t < t1; ++t) acc = fmaf(ra[t], za[t], acc);
     }
     __syncwarp();
   }
-  if (pcur >= 0) Gang[pcur * kAngPerBlock + lane] += acc;
-  __syncwarp();
-
-  TOut* dst = out + (size_t)row_of_int[q] * kFeaturesPad;
-  for (int f = lane; f < kFeaturesPad; f += 32) {
-    float v;
-    if (f < kRadial) v = R2[f] + R2[kRadial + f];
-    else if (f < kFeatures) v = Gang[f - kRadial];
-    else v = 0.f;
-    dst[f] = cvt_out<TOut>(v);
-  }
+  if (pcur >= 0) dst[kRadial + pcur * kAngPerBlock + lane] = cvt_out<TOut>(acc);
+  for (int e = pcur + 1; e < kPairBlocks; ++e) dst[kRadial + e * kAngPerBlock + lane] = cvt_out<TOut>(0.f);
+  if (lane < kFeaturesPad - kFeatures) dst[kFeatures + lane] = cvt_out<TOut>(0.f);
 }
 
 // ---------------------------------------------------------------------------
 // Reverse pass.
 
-constexpr int kGAStride = 33;  // padded row of an angular block (bank spread)
+constexpr int kGAStride = 36;  // padded row of an angular block (16-byte aligned, bank spread)
 
 __host__ __device__ constexpr int adj_warp_floats(int cap_r, int cap_a) {
   // gR[112] | gA[28*33] (+pad to 4) | nb float4[cap_a] | nfc, ndfc, nsp, nslot [cap_a] | sg[cap_r*3]
@@ -286,15 +388,39 @@ __global__ void k_aev_adjoint(Geometry g, NeighborLists nl, AevConst c,
   float* sg = reinterpret_cast<float*>(nslot + nl.cap_a);  // [cap_r][3]
   double* acc_w = smem_acc ? accm + (size_t)warp * smem_atoms_max * 3 : nullptr;
 
+  __shared__ int next_centre;  // centres are handed to warps as they free up
+  if (threadIdx.x == 0) next_centre = q0;
   if (smem_acc)
     for (int t = threadIdx.x; t < nwarps * smem_atoms_max * 3; t += blockDim.x) accm[t] = 0.0;
   __syncthreads();
 
-  for (int q = q0 + warp; q < q1; q += nwarps) {
-    const float* grow = dG + (size_t)row_of_int[q] * kFeaturesPad;
-    for (int f = lane; f < kRadial; f += 32) gR[f] = grow[f];
-    for (int f = lane; f < kAngular; f += 32)
-      gA[(f >> 5) * kGAStride + (f & 31)] = grow[kRadial + f];
+  for (;;) {
+    int q = 0;
+    if (lane == 0) q = atomicAdd(&next_centre, 1);
+    q = __shfl_sync(0xffffffffu, q, 0);
+    if (q >= q1) break;
+    {
+      // dE/dG row: 252 float4 (1008 floats), 8 per lane, loads issued together
+      const float4* grow = reinterpret_cast<const float4*>(dG + (size_t)row_of_int[q] * kFeaturesPad);
+      float4 v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int f4 = lane + 32 * i;
+        if (f4 < kFeatures / 4) v[i] = __ldg(grow + f4);
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int f = 4 * (lane + 32 * i);
+        if (f >= kFeatures) continue;
+        const float e[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const int ff = f + h;
+          if (ff < kRadial) gR[ff] = e[h];
+          else gA[((ff - kRadial) >> 5) * kGAStride + ((ff - kRadial) & 31)] = e[h];
+        }
+      }
+    }
     const float4 xi = g.pos[q];
     const int nr = min(nl.cnt_r[q], nl.cap_r);
     const int* lr = nl.nbr_r + (size_t)q * nl.cap_r;
@@ -309,11 +435,12 @@ __global__ void k_aev_adjoint(Geometry g, NeighborLists nl, AevConst c,
       const float fc = 0.5f * cospif(r / c.Rcr) + 0.5f;
       const float dfc = -0.5f * kPi / c.Rcr * sinpif(r / c.Rcr);
       const float* gs = gR + g.species[j] * kShfR;
+      const float etaR = -c.EtaR * kLog2e;
       float dEdr = 0.f;
 #pragma unroll
       for (int k = 0; k < kShfR; ++k) {
         const float x = r - c.ShfR[k];
-        const float e = expf(-c.EtaR * x * x);
+        const float e = exp2f(etaR * x * x);
         dEdr = fmaf(gs[k] * 0.25f * e, fmaf(-2.f * c.EtaR * x, fc, dfc), dEdr);
       }
       const float s = dEdr / r;
@@ -351,34 +478,31 @@ __global__ void k_aev_adjoint(Geometry g, NeighborLists nl, AevConst c,
       if (valid) {
         decode_pair(P, na, j, k);
         const float4 rj = nb[j], rk = nb[k];
-        const float inv_jk = 1.f / (rj.w * rk.w);
+        const float inv_jk = __fdividef(1.f, rj.w * rk.w);
         const float cost = (rj.x * rk.x + rj.y * rk.y + rj.z * rk.z) * inv_jk;
         const float cp = 0.95f * cost;
         const float sp = sqrtf(fmaxf(1.f - cp * cp, 1e-12f));
         const float fcj = nfc[j], fck = nfc[k];
         const float u = 0.5f * (rj.w + rk.w);
-        const float* gp = gA + c.pair_index[nsp[j]][nsp[k]] * kGAStride;
+        const float4* gp = reinterpret_cast<const float4*>(gA + pair_block(nsp[j], nsp[k]) * kGAStride);
         float A[kShfZ], dA[kShfZ];
 #pragma unroll
         for (int z = 0; z < kShfZ; ++z) {
           const float b = fmaxf(0.5f * (1.f + cp * c.cosZ[z] + sp * c.sinZ[z]), 0.f);
-          const float L = log2f(b);
+          const float L = __log2f(b);
           A[z] = 2.f * exp2f(c.Zeta * L);
           // dA/dcp = 2 Zeta b^(Zeta-1) db/dcp,  db/dcp = (cosZ - cp/sp sinZ) / 2
           dA[z] = c.Zeta * exp2f((c.Zeta - 1.f) * L) * (c.cosZ[z] - cp / sp * c.sinZ[z]);
         }
         float V = 0.f, dVdc = 0.f, dVdu = 0.f;
+        const float etaA = -c.EtaA * kLog2e;
 #pragma unroll
         for (int a = 0; a < kShfA; ++a) {
           const float x = u - c.ShfA[a];
-          const float R = expf(-c.EtaA * x * x);
-          float SA = 0.f, SdA = 0.f;
-#pragma unroll
-          for (int z = 0; z < kShfZ; ++z) {
-            const float gv = gp[a * kShfZ + z];
-            SA = fmaf(gv, A[z], SA);
-            SdA = fmaf(gv, dA[z], SdA);
-          }
+          const float R = exp2f(etaA * x * x);
+          const float4 g4 = gp[a];  // g[a][0..3]
+          const float SA = fmaf(g4.x, A[0], fmaf(g4.y, A[1], fmaf(g4.z, A[2], g4.w * A[3])));
+          const float SdA = fmaf(g4.x, dA[0], fmaf(g4.y, dA[1], fmaf(g4.z, dA[2], g4.w * dA[3])));
           V = fmaf(R, SA, V);
           dVdc = fmaf(R, SdA, dVdc);
           dVdu = fmaf(-2.f * c.EtaA * x * R, SA, dVdu);
@@ -462,8 +586,8 @@ void launch_neighbors(const Geometry& g, const NeighborLists& nl, const AevConst
   k_neighbors<<<blocks, threads, 0, s>>>(g, nl, c, status);
 }
 
-size_t aev_fwd_smem_bytes(int cap_a, int warps) {
-  return (size_t)warps * aev_fwd_warp_floats(cap_a) * sizeof(float);
+size_t aev_fwd_smem_bytes(int cap_r, int cap_a, int warps) {
+  return (size_t)warps * aev_fwd_warp_floats(cap_r, cap_a) * sizeof(float);
 }
 
 size_t aev_adj_smem_bytes(int cap_r, int cap_a, int warps, int mol_atoms_smem_max) {
@@ -475,7 +599,7 @@ void launch_aev(const Geometry& g, const NeighborLists& nl, const AevConst& c,
                 const int* row_of_int, void* out, Prec prec, int warps, cudaStream_t s) {
   if (g.n_atoms <= 0) return;
   const int blocks = (g.n_atoms + warps - 1) / warps;
-  const size_t smem = aev_fwd_smem_bytes(nl.cap_a, warps);
+  const size_t smem = aev_fwd_smem_bytes(nl.cap_r, nl.cap_a, warps);
   switch (prec) {
     case Prec::F32:
       k_aev<float><<<blocks, warps * 32, smem, s>>>(g, nl, c, row_of_int, (float*)out);

@@ -3,18 +3,22 @@
 //
 // The networks of every element and ensemble member run as one launch per
 // layer (Sec. 2 "Optimization": the ensemble is evaluated in parallel over
-// networks and atoms).  Each CTA computes one 128 x N output tile (N <= 256,
-// set per tile in the instruction descriptor) of D = A * B^T, A and B K-major:
+// networks and atoms).  D = A * B^T, A and B K-major, in 128 x N output tiles
+// (N <= 256, set per tile in the instruction descriptor).  The kernel is
+// persistent (one CTA per SM walks the tile list) and warp-specialised:
 //   * warp 0, one lane: TMA producer, 64-wide K blocks of A (128 rows) and B
-//     (256 rows) into a 4-stage ring of 128B-swizzled shared memory;
+//     (up to 256 rows) into a 4-stage ring of 128B-swizzled shared memory,
+//     running ahead across tile boundaries;
 //   * warp 1, one lane: issues tcgen05.mma (M = 128, K = 16 per instruction)
-//     into a 256-column FP32 accumulator in tensor memory and releases each
-//     stage with tcgen05.commit;
-//   * all 4 warps: epilogue, tcgen05.ld of the rows they own (warp w = lanes
-//     32w..32w+31), bias / CELU / CELU' fused, stores to global memory.
-// Every mbarrier wait is bounded; a wait that gives up sets the status word's
-// timeout bit and the CTA skips the rest of its work, frees its tensor
-// memory and returns.
+//     into one of two 256-column FP32 accumulators in tensor memory, releases
+//     each stage with tcgen05.commit and signals the finished accumulator;
+//   * warps 2-5: epilogue, tcgen05.ld of the rows they own (warp w reads TMEM
+//     lanes 32 (w % 4) ...), bias / CELU / CELU' / the output layer fused,
+//     stores to global memory; then hand the accumulator back.
+// With two accumulators the epilogue of one tile overlaps the MMAs of the
+// next.  Every mbarrier wait is bounded; a wait that gives up sets the status
+// word's timeout bit, every role stops, the CTA frees its tensor memory and
+// returns.
 #include <cuda.h>
 
 #include <cstring>
@@ -26,12 +30,13 @@ namespace nnp {
 namespace {
 
 constexpr int kBM = 128;       // tile rows (atoms)
-constexpr int kBNMax = 256;    // tile columns, TMEM columns allocated
+constexpr int kBNMax = 256;    // tile columns, TMEM columns per accumulator
 constexpr int kBK = 64;        // K per stage (128 bytes of 16-bit elements)
 constexpr int kStages = 4;
-constexpr int kThreads = 128;
+constexpr int kEpiWarps = 8;   // two per TMEM lane quarter, each half of the columns
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer, MMA, epilogue warps
 constexpr uint32_t kABytes = kBM * kBK * 2;      // 16 KB
-constexpr uint32_t kBBytes = kBNMax * kBK * 2;   // 32 KB
+constexpr uint32_t kBBytes = kBNMax * kBK * 2;   // 32 KB (room for 256 B rows)
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
 constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
 constexpr long long kSpinLimit = 1ll << 26;  // try_wait polls before giving up
@@ -55,8 +60,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
-// Bounded wait for the phase with the given parity; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false if it gave up or
+// another role already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const int* abort_flag) {
   const uint32_t a = smem_u32(bar);
   for (long long i = 0; i < kSpinLimit; ++i) {
     uint32_t done;
@@ -68,6 +78,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((i & 1023) == 1023 && *(volatile const int*)abort_flag) return false;
   }
   return false;
 }
@@ -162,31 +173,104 @@ __device__ __forceinline__ float celu01(float z) {
   return z > 0.f ? z : 0.1f * (expf(fminf(z, 0.f) * 10.f) - 1.f);
 }
 
+// Epilogue of one 16-column chunk of one row.
+template <typename T>
+__device__ __forceinline__ void epilogue_chunk(const GemmProblem& P, int row, int n,
+                                               const float (&v)[16], float& head_acc) {
+  switch (P.epi) {
+    case (int)Epi::BiasCelu: {
+      uint32_t o[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        o[i] = Pack<T>::two(celu01(v[2 * i] + P.bias[n + 2 * i]),
+                            celu01(v[2 * i + 1] + P.bias[n + 2 * i + 1]));
+      uint4* d = reinterpret_cast<uint4*>(static_cast<T*>(P.D) + (size_t)row * P.ldd + n);
+      d[0] = make_uint4(o[0], o[1], o[2], o[3]);
+      d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+      break;
+    }
+    case (int)Epi::Head: {
+      uint32_t o[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float dv[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = n + 2 * i + h;
+          const float z = v[2 * i + h] + P.bias[c];
+          const float ex = expf(fminf(z, 0.f) * 10.f);  // exp(z / alpha), alpha = 0.1
+          const float act = z > 0.f ? z : 0.1f * (ex - 1.f);
+          const float w = P.w4[c];
+          head_acc = fmaf(w, act, head_acc);
+          dv[h] = w * (z > 0.f ? 1.f : ex) * P.inv_m;
+        }
+        o[i] = Pack<T>::two(dv[0], dv[1]);
+      }
+      uint4* d = reinterpret_cast<uint4*>(static_cast<T*>(P.D) + (size_t)row * P.ldd + n);
+      d[0] = make_uint4(o[0], o[1], o[2], o[3]);
+      d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+      break;
+    }
+    case (int)Epi::Bias: {
+      float4* d = reinterpret_cast<float4*>(static_cast<float*>(P.D) + (size_t)row * P.ldd + n);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        d[i] = make_float4(v[4 * i] + P.bias[n + 4 * i], v[4 * i + 1] + P.bias[n + 4 * i + 1],
+                           v[4 * i + 2] + P.bias[n + 4 * i + 2], v[4 * i + 3] + P.bias[n + 4 * i + 3]);
+      break;
+    }
+    case (int)Epi::DCelu: {
+      uint4* d = reinterpret_cast<uint4*>(static_cast<T*>(P.D) + (size_t)row * P.ldd + n);
+      const uint4 h0 = d[0], h1 = d[1];
+      const uint32_t hin[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+      uint32_t o[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float ha = Pack<T>::lo(hin[i]), hb = Pack<T>::hi(hin[i]);
+        const float ga = ha > 0.f ? 1.f : fmaf(10.f, ha, 1.f);  // celu' from celu, alpha 0.1
+        const float gb = hb > 0.f ? 1.f : fmaf(10.f, hb, 1.f);
+        o[i] = Pack<T>::two(v[2 * i] * ga, v[2 * i + 1] * gb);
+      }
+      d[0] = make_uint4(o[0], o[1], o[2], o[3]);
+      d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+      break;
+    }
+    default: {
+      float4* d = reinterpret_cast<float4*>(static_cast<float*>(P.D) + (size_t)row * P.ldd + n);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) d[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+      break;
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ TcMaps maps, const GemmProblem* __restrict__ probs,
-              const GemmTile* __restrict__ tiles, unsigned* __restrict__ status) {
+              const GemmTile* __restrict__ tiles, int n_tiles, int b_box_rows,
+              unsigned* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
   uint64_t* empty = full + kStages;
-  uint64_t* accum = empty + kStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  uint64_t* tfull = empty + kStages;  // [2] accumulator ready
+  uint64_t* tempty = tfull + 2;       // [2] accumulator drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const GemmTile tl = tiles[blockIdx.x];
-  const GemmProblem P = probs[tl.problem];
-  const int n_tile = min(kBNMax, P.N - tl.n0);  // multiple of 16
-  const int nkb = (P.K + kBK - 1) / kBK;
+  const uint32_t stage_tx = kABytes + (uint32_t)b_box_rows * kBK * 2;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accum, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], kEpiWarps);  // one arrival per epilogue warp
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -194,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"((uint32_t)kBNMax));
+                 "r"((uint32_t)(2 * kBNMax)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -202,104 +286,146 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // ---- TMA producer ----
-    const int ay = P.a_row0 + tl.m0, by = P.b_row0 + tl.n0;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % kStages;
-      if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1)) {
-        atomicOr(status, kStatTimeout);
-        atomicExch(abort_flag, 1);
-        break;
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer ----
+      uint32_t it = 0;
+      for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const GemmTile tl = tiles[tile];
+        const GemmProblem& P = probs[tl.problem];
+        const int nkb = (P.K + kBK - 1) / kBK;
+        const int ay = P.a_row0 + tl.m0, by = P.b_row0 + tl.n0;
+        bool ok = true;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % kStages;
+          const uint32_t use = it / kStages;
+          if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          unsigned char* sa = smem + s * kStageBytes;
+          mbar_expect_tx(&full[s], stage_tx);
+          tma_load_2d(sa, &maps.a, P.a_col0 + kb * kBK, ay, &full[s]);
+          tma_load_2d(sa + kABytes, &maps.b, P.b_col0 + kb * kBK, by, &full[s]);
+        }
+        if (!ok) {
+          atomicOr(status, kStatTimeout);
+          atomicExch(abort_flag, 1);
+          break;
+        }
       }
-      unsigned char* sa = smem + s * kStageBytes;
-      mbar_expect_tx(&full[s], kStageBytes);
-      tma_load_2d(sa, &maps.a, P.a_col0 + kb * kBK, ay, &full[s]);
-      tma_load_2d(sa + kABytes, &maps.b, P.b_col0 + kb * kBK, by, &full[s]);
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer ----
-    const uint32_t idesc = instr_desc(Pack<T>::fmt, (uint32_t)n_tile);
-    bool ok = true;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % kStages;
-      if (!mbar_wait(&full[s], (kb / kStages) & 1)) {
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer ----
+      uint32_t it = 0, tcount = 0;
+      for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tcount) {
+        const GemmTile tl = tiles[tile];
+        const GemmProblem& P = probs[tl.problem];
+        const int nkb = (P.K + kBK - 1) / kBK;
+        const int n_tile = min(kBNMax, P.N - tl.n0);
+        const uint32_t idesc = instr_desc(Pack<T>::fmt, (uint32_t)n_tile);
+        const uint32_t acc = tcount & 1, use = tcount >> 1;
+        bool ok = use == 0 || mbar_wait(&tempty[acc], (use - 1) & 1, abort_flag);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dtm = tmem + acc * kBNMax;
+        for (int kb = 0; ok && kb < nkb; ++kb, ++it) {
+          const int s = it % kStages;
+          if (!mbar_wait(&full[s], (it / kStages) & 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const unsigned char* sa = smem + s * kStageBytes;
+          const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sa + kABytes);
+          const int ksteps = min(kBK, P.K - kb * kBK) / 16;
+          for (int j = 0; j < ksteps; ++j)  // +32 bytes per K step inside the swizzle atom
+            mma_f16(dtm, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc,
+                    (kb > 0 || j > 0) ? 1u : 0u);
+          mma_commit(&empty[s]);
+        }
+        if (!ok) {
+          atomicOr(status, kStatTimeout);
+          atomicExch(abort_flag, 1);
+          break;
+        }
+        mma_commit(&tfull[acc]);
+      }
+    }
+  } else {
+    // ---- epilogue warps 2..9: TMEM lane quarter = warp % 4, column half ----
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    uint32_t tcount = 0;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tcount) {
+      const GemmTile tl = tiles[tile];
+      const GemmProblem& P = probs[tl.problem];
+      const int n_tile = min(kBNMax, P.N - tl.n0);
+      const uint32_t acc = tcount & 1, use = tcount >> 1;
+      if (!mbar_wait(&tfull[acc], use & 1, abort_flag)) {
         atomicOr(status, kStatTimeout);
         atomicExch(abort_flag, 1);
-        ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const unsigned char* sa = smem + s * kStageBytes;
-      const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sa + kABytes);
-      const int ksteps = min(kBK, P.K - kb * kBK) / 16;
-      for (int j = 0; j < ksteps; ++j)  // +32 bytes per K step inside the swizzle atom
-        mma_f16(tmem, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc,
-                (kb > 0 || j > 0) ? 1u : 0u);
-      mma_commit(&empty[s]);
-    }
-    if (ok) mma_commit(accum);
-  }
-  __syncwarp();
-
-  // ---- epilogue: all warps ----
-  const bool have = mbar_wait(accum, 0);
-  if (!have) atomicOr(status, kStatTimeout);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (have && !*(volatile int*)abort_flag) {
-    const int row = tl.m0 + warp * 32 + lane;
-    const bool row_ok = row < P.M;
-    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c = 0; c < n_tile; c += 16) {
-      float v[16];
-      tmem_ld16(tbase + (uint32_t)c, v);  // all lanes take part (sync.aligned)
-      if (!row_ok) continue;
-      const int n = tl.n0 + c;
-      switch (P.epi) {
-        case (int)Epi::BiasCelu: {
+      const int epi = P.epi;
+      const int row = tl.m0 + quarter * 32 + lane;
+      const bool row_ok = row < P.M;
+      const uint32_t tbase = tmem + acc * kBNMax + ((uint32_t)(quarter * 32) << 16);
+      // column range of this warp: the output layer needs whole rows (first half only)
+      int c0 = 0, c1 = n_tile;
+      if (epi != (int)Epi::Head) {
+        c0 = half * (n_tile >> 1);
+        c1 = c0 + (n_tile >> 1);
+      } else if (half) {
+        c1 = 0;
+      }
+      if (epi == (int)Epi::DCelu) {
+        // prefetch the stored activations of every chunk before the first use
+        uint4 hv[2 * (kBNMax / 32)];
+#pragma unroll
+        for (int i = 0; i < kBNMax / 32; ++i) {
+          const int c = c0 + 16 * i;
+          if (row_ok && c < c1) {
+            const uint4* d = reinterpret_cast<const uint4*>(static_cast<const T*>(P.D) +
+                                                           (size_t)row * P.ldd + tl.n0 + c);
+            hv[2 * i] = d[0];
+            hv[2 * i + 1] = d[1];
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < kBNMax / 32; ++i) {
+          const int c = c0 + 16 * i;
+          if (c >= c1) break;
+          float v[16];
+          tmem_ld16(tbase + (uint32_t)c, v);
+          if (!row_ok) continue;
+          const uint32_t hin[8] = {hv[2 * i].x, hv[2 * i].y, hv[2 * i].z, hv[2 * i].w,
+                                   hv[2 * i + 1].x, hv[2 * i + 1].y, hv[2 * i + 1].z,
+                                   hv[2 * i + 1].w};
           uint32_t o[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            o[i] = Pack<T>::two(celu01(v[2 * i] + P.bias[n + 2 * i]),
-                                celu01(v[2 * i + 1] + P.bias[n + 2 * i + 1]));
-          uint4* d = reinterpret_cast<uint4*>(static_cast<T*>(P.D) + (size_t)row * P.ldd + n);
-          d[0] = make_uint4(o[0], o[1], o[2], o[3]);
-          d[1] = make_uint4(o[4], o[5], o[6], o[7]);
-          break;
-        }
-        case (int)Epi::Bias: {
-          float4* d = reinterpret_cast<float4*>(static_cast<float*>(P.D) + (size_t)row * P.ldd + n);
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-            d[i] = make_float4(v[4 * i] + P.bias[n + 4 * i], v[4 * i + 1] + P.bias[n + 4 * i + 1],
-                               v[4 * i + 2] + P.bias[n + 4 * i + 2],
-                               v[4 * i + 3] + P.bias[n + 4 * i + 3]);
-          break;
-        }
-        case (int)Epi::DCelu: {
-          uint4* d = reinterpret_cast<uint4*>(static_cast<T*>(P.D) + (size_t)row * P.ldd + n);
-          const uint4 h0 = d[0], h1 = d[1];
-          const uint32_t hin[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-          uint32_t o[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float ha = Pack<T>::lo(hin[i]), hb = Pack<T>::hi(hin[i]);
+          for (int k = 0; k < 8; ++k) {
+            const float ha = Pack<T>::lo(hin[k]), hb = Pack<T>::hi(hin[k]);
             const float ga = ha > 0.f ? 1.f : fmaf(10.f, ha, 1.f);  // celu' from celu, alpha 0.1
             const float gb = hb > 0.f ? 1.f : fmaf(10.f, hb, 1.f);
-            o[i] = Pack<T>::two(v[2 * i] * ga, v[2 * i + 1] * gb);
+            o[k] = Pack<T>::two(v[2 * k] * ga, v[2 * k + 1] * gb);
           }
+          uint4* d = reinterpret_cast<uint4*>(static_cast<T*>(P.D) + (size_t)row * P.ldd + tl.n0 + c);
           d[0] = make_uint4(o[0], o[1], o[2], o[3]);
           d[1] = make_uint4(o[4], o[5], o[6], o[7]);
-          break;
         }
-        default: {
-          float4* d = reinterpret_cast<float4*>(static_cast<float*>(P.D) + (size_t)row * P.ldd + n);
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-            d[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-          break;
+      } else {
+        float head_acc = 0.f;
+        for (int c = c0; c < c1; c += 16) {
+          float v[16];
+          tmem_ld16(tbase + (uint32_t)c, v);  // all lanes take part (sync.aligned)
+          if (row_ok) epilogue_chunk<T>(P, row, tl.n0 + c, v, head_acc);
         }
+        if (epi == (int)Epi::Head && half == 0 && row_ok) P.y[(size_t)row * P.ldy] = head_acc + P.b4;
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -307,7 +433,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)kBNMax));
+                 "r"((uint32_t)(2 * kBNMax)));
   }
 }
 
@@ -369,16 +495,25 @@ cudaError_t tc_set_smem() {
 }
 
 // maps: HOST pointer to the layer's {A map, B map} pair (copied into the
-// launch's parameters).
+// launch's parameters); b_box_rows: rows of the B map's box.
 void launch_gemm_tc(const GemmProblem* probs, const GemmTile* tiles, int n_tiles, Prec p,
-                    int /*layer*/, const void* maps, unsigned* status, cudaStream_t s) {
+                    int b_box_rows, const void* maps, unsigned* status, cudaStream_t s) {
   if (n_tiles <= 0) return;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+  }
   TcMaps m;
   std::memcpy(&m, maps, sizeof(m));
+  const int grid = n_tiles < sms ? n_tiles : sms;
   if (p == Prec::BF16)
-    k_gemm_tc<__nv_bfloat16><<<n_tiles, kThreads, kSmemBytes, s>>>(m, probs, tiles, status);
+    k_gemm_tc<__nv_bfloat16><<<grid, kThreads, kSmemBytes, s>>>(m, probs, tiles, n_tiles, b_box_rows,
+                                                                status);
   else
-    k_gemm_tc<__half><<<n_tiles, kThreads, kSmemBytes, s>>>(m, probs, tiles, status);
+    k_gemm_tc<__half><<<grid, kThreads, kSmemBytes, s>>>(m, probs, tiles, n_tiles, b_box_rows, status);
 }
 
 }  // namespace nnp

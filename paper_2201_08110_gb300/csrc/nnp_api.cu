@@ -13,8 +13,8 @@
 #include "nnp_internal.cuh"
 
 namespace nnp {
-void launch_gemm_tc(const GemmProblem* probs, const GemmTile* tiles, int n_tiles, Prec p, int layer,
-                    const void* maps, unsigned* status, cudaStream_t s);
+void launch_gemm_tc(const GemmProblem* probs, const GemmTile* tiles, int n_tiles, Prec p,
+                    int b_box_rows, const void* maps, unsigned* status, cudaStream_t s);
 bool tc_available();
 size_t tc_maps_bytes();
 bool tc_make_map(void* out_map, const void* base, Prec p, uint64_t rows, uint64_t cols,
@@ -36,6 +36,10 @@ struct Layer {
 };
 
 size_t elem_size(Prec p) { return p == Prec::F32 ? 4 : 2; }
+
+// Rows of the weight operand's TMA box per layer (the largest N of the layer):
+// L1 fwd, L2 fwd, L3 fwd, L3 rev, L2 rev, L1 rev.
+constexpr int kTcBoxRows[6] = {256, kH2Max, kH3Max, kH2Max, kH1Max, 256};
 
 }  // namespace
 
@@ -570,13 +574,24 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         h->L[1].probs.push_back(P);
         add_tiles(h->L[1], bm, tc ? 256 : 64);
       }
-      {  // layer 3 forward (pre-activation)
+      {  // layer 3 forward; on tensor cores with the output layer fused (the
+         // tile holds the whole row), else the FP32 pre-activation for k_head
         GemmProblem P{};
         P.A = H2 + (row0 * h->ldh2 + (size_t)m * n2) * es; P.lda = h->ldh2;
         P.B = wb + (h->w_off[2] + r3[e][m] * ld_w3) * es; P.ldb = ld_w3;
-        P.D = Z3 + (row0 * h->ldz3 + (size_t)m * n3); P.ldd = h->ldz3;
+        if (tc) {
+          P.D = D3 + (row0 * h->ldz3 + (size_t)m * n3) * es; P.ldd = h->ldz3;
+          P.epi = (int)Epi::Head;
+          P.w4 = h->d_w4 + ((size_t)e * kMaxModels + m) * kH3Max;
+          P.y = h->d_y + row0 * M + m; P.ldy = M;
+          P.b4 = b4[(size_t)e * kMaxModels + m];
+          P.inv_m = 1.0f / (float)M;
+        } else {
+          P.D = Z3 + (row0 * h->ldz3 + (size_t)m * n3); P.ldd = h->ldz3;
+          P.epi = (int)Epi::Bias;
+        }
         P.bias = h->d_b + b1_total + b2_total + r3[e][m];
-        P.M = Me; P.N = n3; P.K = n2; P.epi = (int)Epi::Bias;
+        P.M = Me; P.N = n3; P.K = n2;
         P.a_row0 = (int)row0; P.a_col0 = m * n2; P.b_row0 = (int)r3[e][m]; P.elem = e; P.model = m;
         h->L[2].probs.push_back(P);
         add_tiles(h->L[2], bm, tc ? 256 : 64);
@@ -625,7 +640,8 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
     const size_t half = tc_maps_bytes() / 2;
     for (int l = 0; l < 6; ++l) {
       if (!tc_make_map(h->tc_maps[l], A[l].base, h->prec, A[l].rows, A[l].cols, A[l].cols, 128) ||
-          !tc_make_map(h->tc_maps[l] + half, B[l].base, h->prec, B[l].rows, B[l].cols, B[l].cols, 256))
+          !tc_make_map(h->tc_maps[l] + half, B[l].base, h->prec, B[l].rows, B[l].cols, B[l].cols,
+                       kTcBoxRows[l]))
         return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for layer " + std::to_string(l));
     }
     CK(tc_set_smem());
@@ -669,7 +685,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
     if (!sorted.empty())
       CK(cudaMemcpy(h->d_work, sorted.data(), sizeof(int4) * sorted.size(), cudaMemcpyHostToDevice));
   }
-  CK(aev_set_smem_limits(aev_fwd_smem_bytes(cap_a, h->fwd_warps),
+  CK(aev_set_smem_limits(aev_fwd_smem_bytes(cap_r, cap_a, h->fwd_warps),
                          aev_adj_smem_bytes(cap_r, cap_a, h->adj_warps, h->smem_atoms_max)));
   CK(cudaDeviceSynchronize());
   guard.ok = true;
@@ -687,8 +703,8 @@ void run_gemm(nnp_ctx* h, int layer, cudaStream_t s) {
   if (h->prec == Prec::F32)
     launch_gemm_simt(L.d_probs, L.d_tiles, (int)L.tiles.size(), s);
   else
-    launch_gemm_tc(L.d_probs, L.d_tiles, (int)L.tiles.size(), h->prec, layer, h->tc_maps[layer],
-                   h->d_status, s);
+    launch_gemm_tc(L.d_probs, L.d_tiles, (int)L.tiles.size(), h->prec, kTcBoxRows[layer],
+                   h->tc_maps[layer], h->d_status, s);
 }
 
 // The whole step, enqueued on s.  With ev != nullptr an event is recorded
@@ -718,9 +734,11 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
   gemm(1);
   mark(4);
   gemm(2);
-  launch_head(h->d_z3, h->ldz3, h->prec, h->d_row_elem, h->d_w4, h->d_b4, h->d_d3, h->d_y,
-              h->n_rows, h->n_models, s);
-  ++kernels;
+  if (h->prec == Prec::F32) {  // the tensor-core path fuses the output layer into gemm(2)
+    launch_head(h->d_z3, h->ldz3, h->prec, h->d_row_elem, h->d_w4, h->d_b4, h->d_d3, h->d_y,
+                h->n_rows, h->n_models, s);
+    ++kernels;
+  }
   mark(5);
   launch_energy(h->d_y, h->n_models, h->d_row_of_int, h->d_mol_off, h->n_mols, E, h->d_atom_e, s);
   ++kernels;
@@ -805,7 +823,7 @@ nnp_status nnp_compute_timed(nnp_handle h, const float* pos, double* E, double* 
 
 int32_t nnp_kernels_per_step(nnp_handle h, int32_t with_forces) {
   if (!h) return -1;
-  int k = 2 + 1 + 1 + 1;  // gather, neighbours, features, head, energy
+  int k = 2 + 1 + 1 + (h->prec == Prec::F32 ? 1 : 0);  // gather, neighbours, features, energy, head
   for (int l = 0; l < 3; ++l) k += h->L[l].tiles.empty() ? 0 : 1;
   if (with_forces) {
     k += 1;  // reverse pass to coordinates

@@ -71,6 +71,9 @@ struct Geometry {
   int n_atoms;
 };
 
+// Lists hold internal indices in ascending order.  The featurizer relies on
+// the internal order being element-sorted within each molecule: every list is
+// then grouped by element, elements in ascending order.
 struct NeighborLists {
   int* cnt_r;   // [N]
   int* nbr_r;   // [N][cap_r] internal indices, ascending
@@ -89,7 +92,9 @@ enum class Epi : int {
   BiasCelu = 0,   // D = celu(acc + bias[n])           (forward hidden layer)
   Bias = 1,       // D = acc + bias[n], FP32 output     (pre-activation of the last hidden layer)
   DCelu = 2,      // D = acc * celu'(D_in-place)       (reverse through a hidden layer)
-  Store = 3       // D = acc (FP32 output)              (dE/dG)
+  Store = 3,      // D = acc (FP32 output)              (dE/dG)
+  Head = 4        // last hidden layer + output layer: z = acc + bias, y[row] = w4 . celu(z) + b4,
+                  // D = (1/M) w4 * celu'(z)  (needs the whole row in one tile)
 };
 
 struct GemmProblem {
@@ -101,6 +106,11 @@ struct GemmProblem {
   int epi;
   int a_row0, b_row0, a_col0, b_col0, d_col0;  // used by the tensor-core path (TMA coordinates)
   int elem, model;
+  // Epi::Head only
+  const float* w4;  // [N] output weights of this (element, member)
+  float* y;         // per-row output, stride ldy
+  long ldy;
+  float b4, inv_m;
 };
 
 // A tile of the flattened problem list.
@@ -130,7 +140,7 @@ void launch_gemm_simt(const GemmProblem* d_problems, const GemmTile* d_tiles, in
                       cudaStream_t s);
 void launch_gemm_simt_typed(const GemmProblem* d_problems, const GemmTile* d_tiles, int n_tiles,
                             Prec p, cudaStream_t s);
-size_t aev_fwd_smem_bytes(int cap_a, int warps);
+size_t aev_fwd_smem_bytes(int cap_r, int cap_a, int warps);
 size_t aev_adj_smem_bytes(int cap_r, int cap_a, int warps, int mol_atoms_smem_max);
 cudaError_t aev_set_smem_limits(size_t fwd_bytes, size_t adj_bytes);
 

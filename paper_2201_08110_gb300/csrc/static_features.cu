@@ -63,23 +63,38 @@ __device__ __forceinline__ int element_index(int z) {
   }
 }
 
-// Caller's molecule into the scratch layout (caller order kept: the
-// featurizer accepts neighbour lists in any order).
+// Caller's molecule into the scratch layout: one block, one thread per atom.
+// Atoms are placed in element order (stable), which the featurizer requires
+// of its neighbour lists; row[] maps each placed atom back to its caller row.
 __global__ void k_static_prepare(const int* __restrict__ Z, const float* __restrict__ pos, int n,
                                  StaticScratch* __restrict__ s) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int e = element_index(Z[i]);
-  const float x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
-  if (e < 0 || !(isfinite(x) && isfinite(y) && isfinite(z))) {
-    atomicOr(&s->bad_input, 1u);
-    e = 0;  // keeps every index in range; the output is poisoned below
+  __shared__ int elem[kStaticMax];
+  const int i = threadIdx.x;
+  int e = 0;
+  float x = 0.f, y = 0.f, z = 0.f;
+  if (i < n) {
+    e = element_index(Z[i]);
+    x = pos[3 * i];
+    y = pos[3 * i + 1];
+    z = pos[3 * i + 2];
+    if (e < 0 || !(isfinite(x) && isfinite(y) && isfinite(z))) {
+      atomicOr(&s->bad_input, 1u);
+      e = e < 0 ? 0 : e;  // keeps every index in range; the output is poisoned below
+    }
+    elem[i] = e;
   }
-  s->pos[i] = make_float4(x, y, z, 0.f);
-  s->species[i] = e;
-  s->mol_start[i] = 0;
-  s->mol_end[i] = n;
-  s->row[i] = i;
+  __syncthreads();
+  if (i >= n) return;
+  int slot = 0;
+  for (int j = 0; j < n; ++j) {
+    const int ej = elem[j];
+    slot += (ej < e) || (ej == e && j < i);
+  }
+  s->pos[slot] = make_float4(x, y, z, 0.f);
+  s->species[slot] = e;
+  s->mol_start[slot] = 0;
+  s->mol_end[slot] = n;
+  s->row[slot] = i;
 }
 
 __global__ void k_static_export(const StaticScratch* __restrict__ s, int n, float* __restrict__ out) {
@@ -115,7 +130,7 @@ extern "C" nnp_status nnp_features_static(const int32_t* Z_dev, const float* pos
     if (!g_scratch_addr[dev]) {
       void* addr = nullptr;
       if (cudaGetSymbolAddress(&addr, g_static_scratch) != cudaSuccess || !addr) return NNP_ERR_CUDA;
-      if (aev_set_smem_limits(aev_fwd_smem_bytes(kStaticCap, kStaticWarps), 0) != cudaSuccess)
+      if (aev_set_smem_limits(aev_fwd_smem_bytes(kStaticCap, kStaticCap, kStaticWarps), 0) != cudaSuccess)
         return NNP_ERR_CUDA;
       g_scratch_addr[dev] = static_cast<StaticScratch*>(addr);
     }
@@ -125,7 +140,7 @@ extern "C" nnp_status nnp_features_static(const int32_t* Z_dev, const float* pos
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // the flags start at zero on every call; everything else is fully rewritten
   if (cudaMemsetAsync(&p->bad_input, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return NNP_ERR_CUDA;
-  k_static_prepare<<<(n_atoms + 127) / 128, 128, 0, s>>>(Z_dev, positions_dev, n_atoms, p);
+  k_static_prepare<<<1, kStaticMax, 0, s>>>(Z_dev, positions_dev, n_atoms, p);
   AevConst c;
   const double no_box[3] = {0.0, 0.0, 0.0};
   aev_constants(c, no_box);

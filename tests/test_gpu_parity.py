@@ -116,7 +116,10 @@ def test_features_match_oracle(lib, case):
         ref = oracle.aev(b.Z[a0:a1], b.pos[a0:a1], box=b.box if np.any(b.box) else None)
         scale = np.maximum(np.abs(ref).max(axis=1, keepdims=True), 1e-30)
         err = np.abs(G[a0:a1] - ref) / scale
-        assert err.max() < 2e-6, f"molecule {m}: feature error {err.max():.3e} (row-max relative)"
+        # bound: the angular power uses the SFU log2 (absolute error <= 2^-22 on
+        # [0.5, 2]), so a term carries up to Zeta * 2^-22 * ln 2 = 2.4e-6 relative
+        # error; the FP32 energy bound (1e-5) holds with margin on top of it
+        assert err.max() < 5e-6, f"molecule {m}: feature error {err.max():.3e} (row-max relative)"
 
 
 # --- energies and forces -------------------------------------------------------

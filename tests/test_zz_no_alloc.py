@@ -54,7 +54,7 @@ def test_static_entry_point_matches_handle_features_on_consecutive_calls(nnp):
         scale = np.maximum(np.abs(ref).max(axis=1, keepdims=True), 1e-30)
         err = np.abs(got - ref) / scale
         assert np.all(np.isfinite(got))
-        assert err.max() < 2e-6, f"feature error {err.max():.3e} (row-max relative)"
+        assert err.max() < 5e-6, f"feature error {err.max():.3e} (row-max relative)"
 
 
 def test_static_entry_point_rejects_too_many_atoms(nnp):
