@@ -153,6 +153,62 @@ __device__ __forceinline__ int pair_block(int s, int t) {
   return a * kSpecies - (a * (a - 1)) / 2 + (b - a);
 }
 
+// Element groups of an element-sorted angular neighbour list and the prefix
+// of the block-major pair enumeration.  cnt_s: on lanes 0..6 the size of
+// element group s.  Writes gs[7] (group starts), gn[7] (sizes) and bpre[29]
+// (first pair of each block, bpre[28] = number of pairs); call with the whole
+// warp, then __syncwarp before reading.
+__device__ __forceinline__ void angular_blocks(int cnt_s, int lane, int* gs, int* gn, int* bpre) {
+  const unsigned FULL = 0xffffffffu;
+  int start = cnt_s;
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    const int v = __shfl_up_sync(FULL, start, o);
+    if (lane >= o) start += v;
+  }
+  start -= cnt_s;
+  if (lane < kSpecies) {
+    gs[lane] = start;
+    gn[lane] = cnt_s;
+  }
+  const int bs = lane < kPairBlocks ? kBlkS[lane] : 0, bt = lane < kPairBlocks ? kBlkT[lane] : 0;
+  const int ns = __shfl_sync(FULL, cnt_s, bs), nt = __shfl_sync(FULL, cnt_s, bt);
+  const int size = lane < kPairBlocks ? (bs == bt ? ns * (ns - 1) / 2 : ns * nt) : 0;
+  int incl = size;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane < kPairBlocks) bpre[lane + 1] = incl;
+  if (lane == 0) bpre[0] = 0;
+}
+
+// Pair P of the block-major enumeration: its block and the list positions
+// j < k of its two neighbours.
+__device__ __forceinline__ int decode_block_pair(int P, const int* bpre, const int* gs,
+                                                 const int* gn, int& j, int& k) {
+  int b = 0;
+#pragma unroll
+  for (int step = 16; step; step >>= 1)
+    if (b + step <= kPairBlocks - 1 && bpre[b + step] <= P) b += step;
+  const int l = P - bpre[b];
+  const int s = kBlkS[b], t = kBlkT[b];
+  if (s != t) {
+    const int n_t = gn[t];
+    int qd = (int)__fdividef((float)l + 0.5f, (float)n_t);
+    if (qd * n_t > l) --qd;
+    else if ((qd + 1) * n_t <= l) ++qd;
+    j = gs[s] + qd;
+    k = gs[t] + (l - qd * n_t);
+  } else {
+    decode_pair(l, gn[s], j, k);
+    j += gs[s];
+    k += gs[s];
+  }
+  return b;
+}
+
 // The angular features of a centre are sums over unordered neighbour pairs.
 // Pairs are enumerated block-major: species-pair block b = (s, t) holds every
 // pair with one neighbour of element s and one of element t (the neighbour
@@ -237,31 +293,7 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
       }
     }
   }
-  {
-    int start = cnt_s;  // exclusive prefix over lanes 0..6
-#pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-      const int v = __shfl_up_sync(FULL, start, o);
-      if (lane >= o) start += v;
-    }
-    start -= cnt_s;
-    if (lane < kSpecies) {
-      gs[lane] = start;
-      gn[lane] = cnt_s;
-    }
-    // pairs per block, then the block prefix (lanes 0..27)
-    const int bs = lane < kPairBlocks ? kBlkS[lane] : 0, bt = lane < kPairBlocks ? kBlkT[lane] : 0;
-    const int ns = __shfl_sync(FULL, cnt_s, bs), nt = __shfl_sync(FULL, cnt_s, bt);
-    const int size = lane < kPairBlocks ? (bs == bt ? ns * (ns - 1) / 2 : ns * nt) : 0;
-    int incl = size;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(FULL, incl, o);
-      if (lane >= o) incl += v;
-    }
-    if (lane < kPairBlocks) bpre[lane + 1] = incl;
-    if (lane == 0) bpre[0] = 0;
-  }
+  angular_blocks(cnt_s, lane, gs, gn, bpre);
   __syncwarp();
   const int T = bpre[kPairBlocks];
 
@@ -276,25 +308,8 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
     int pl = -1;
     if (valid) {
       // phase 1: this lane's pair -> 8 distance factors, 4 angle factors
-      int b = 0;
-#pragma unroll
-      for (int step = 16; step; step >>= 1)
-        if (b + step <= kPairBlocks - 1 && bpre[b + step] <= P) b += step;
-      const int l = P - bpre[b];
-      const int s = kBlkS[b], t = kBlkT[b];
       int j, k;
-      if (s != t) {
-        const int n_t = gn[t];
-        int qd = (int)__fdividef((float)l + 0.5f, (float)n_t);
-        if (qd * n_t > l) --qd;
-        else if ((qd + 1) * n_t <= l) ++qd;
-        j = gs[s] + qd;
-        k = gs[t] + (l - qd * n_t);
-      } else {
-        decode_pair(l, gn[s], j, k);
-        j += gs[s];
-        k += gs[s];
-      }
+      const int b = decode_block_pair(P, bpre, gs, gn, j, k);
       const float4 rj = avec[j], rk = avec[k];
       const float cost = __fdividef(rj.x * rk.x + rj.y * rk.y + rj.z * rk.z, rj.w * rk.w);
       const float cp = 0.95f * cost;
@@ -346,11 +361,16 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
 
 constexpr int kGAStride = 36;  // padded row of an angular block (16-byte aligned, bank spread)
 
-__host__ __device__ constexpr int adj_warp_floats(int cap_r, int cap_a) {
-  // gR[112] | gA[28*33] (+pad to 4) | nb float4[cap_a] | nfc, ndfc, nsp, nslot [cap_a] | sg[cap_r*3]
-  return ((kRadial + kPairBlocks * kGAStride + 3) / 4) * 4 + cap_a * 4 + cap_a * 4 + cap_r * 3;
+// Per-warp shared memory of the reverse pass (floats):
+//   gR[112] | gA[28][36] | avec float4[cap_a] | afc[cap_a] | adfc[cap_a] | asp[cap_a] |
+//   sg[cap_a][3]
+__host__ __device__ constexpr int adj_warp_floats(int /*cap_r*/, int cap_a) {
+  return kRadial + kPairBlocks * kGAStride + 10 * cap_a;
 }
 
+// Adds a gradient to the force of atom a_glob (internal index): into the
+// warp's own FP64 accumulator of the molecule, or with FP64 atomics straight
+// into the forces when the molecule is too large for shared memory.
 __device__ __forceinline__ void add_force(double* acc_w, int local, const int* orig, int a_glob,
                                           double* F, float gx, float gy, float gz) {
   if (acc_w) {
@@ -365,27 +385,33 @@ __device__ __forceinline__ void add_force(double* acc_w, int local, const int* o
   }
 }
 
+// Reverse pass of the featurizer: given dE/dG of every atom, the forces.
+// One work item (CTA) = a chunk of centres of one molecule; warps take
+// centres as they free up.  Per centre: radial terms lane per neighbour,
+// angular terms lane per pair; each pair's gradients go to per-neighbour
+// accumulators in shared memory
+// (the lanes of a chunk that share the first neighbour are reduced by a
+// segmented scan first), then to the warp's FP64 accumulator of the molecule.
 __global__ void k_aev_adjoint(Geometry g, NeighborLists nl, AevConst c,
                               const int* __restrict__ row_of_int, const float* __restrict__ dG,
                               const int4* __restrict__ work, const int* __restrict__ orig,
                               double* __restrict__ F, int smem_atoms_max) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const unsigned FULL = 0xffffffffu;
   const int nwarps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int4 w = work[blockIdx.x];
   const int a0 = w.x, n_mol = w.y, q0 = w.z, q1 = w.w;
   const bool smem_acc = n_mol <= smem_atoms_max;
   double* accm = reinterpret_cast<double*>(smem_raw);  // [nwarps][smem_atoms_max][3]
-  float* wbase = reinterpret_cast<float*>(accm + (size_t)nwarps * smem_atoms_max * 3) +
-                 (size_t)warp * adj_warp_floats(nl.cap_r, nl.cap_a);
-  float* gR = wbase;
-  float* gA = gR + kRadial;
-  float4* nb = reinterpret_cast<float4*>(wbase + ((kRadial + kPairBlocks * kGAStride + 3) / 4) * 4);
-  float* nfc = reinterpret_cast<float*>(nb + nl.cap_a);
-  float* ndfc = nfc + nl.cap_a;
-  int* nsp = reinterpret_cast<int*>(ndfc + nl.cap_a);
-  int* nslot = nsp + nl.cap_a;
-  float* sg = reinterpret_cast<float*>(nslot + nl.cap_a);  // [cap_r][3]
+  float* gR = reinterpret_cast<float*>(accm + (size_t)nwarps * smem_atoms_max * 3) +
+              (size_t)warp * adj_warp_floats(nl.cap_r, nl.cap_a);
+  float* gA = gR + kRadial;  // [28][36]
+  float4* avec = reinterpret_cast<float4*>(gA + kPairBlocks * kGAStride);
+  float* afc = reinterpret_cast<float*>(avec + nl.cap_a);
+  float* adfc = afc + nl.cap_a;
+  int* asp = reinterpret_cast<int*>(adfc + nl.cap_a);
+  float* sg = reinterpret_cast<float*>(asp + nl.cap_a);  // [cap_a][3]
   double* acc_w = smem_acc ? accm + (size_t)warp * smem_atoms_max * 3 : nullptr;
 
   __shared__ int next_centre;  // centres are handed to warps as they free up
@@ -394,10 +420,11 @@ __global__ void k_aev_adjoint(Geometry g, NeighborLists nl, AevConst c,
     for (int t = threadIdx.x; t < nwarps * smem_atoms_max * 3; t += blockDim.x) accm[t] = 0.0;
   __syncthreads();
 
+  const float etaR = -c.EtaR * kLog2e, etaA = -c.EtaA * kLog2e;
   for (;;) {
     int q = 0;
     if (lane == 0) q = atomicAdd(&next_centre, 1);
-    q = __shfl_sync(0xffffffffu, q, 0);
+    q = __shfl_sync(FULL, q, 0);
     if (q >= q1) break;
     {
       // dE/dG row: 252 float4 (1008 floats), 8 per lane, loads issued together
@@ -422,80 +449,82 @@ __global__ void k_aev_adjoint(Geometry g, NeighborLists nl, AevConst c,
       }
     }
     const float4 xi = g.pos[q];
-    const int nr = min(nl.cnt_r[q], nl.cap_r);
-    const int* lr = nl.nbr_r + (size_t)q * nl.cap_r;
-    __syncwarp();
-
     float gix = 0.f, giy = 0.f, giz = 0.f;
-    // ---- radial: lane per neighbour ----
-    for (int t = lane; t < nr; t += 32) {
-      const int j = lr[t];
+
+    // ---- angular staging (first: its loads overlap the dE/dG row's) ----
+    const int na = min(nl.cnt_a[q], nl.cap_a);
+    const int* la = nl.nbr_a + (size_t)q * nl.cap_a;
+    for (int t = lane; t < na; t += 32) {
+      const int j = la[t];
       const float3 d = disp(xi, g.pos[j], c);
       const float r = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
-      const float fc = 0.5f * cospif(r / c.Rcr) + 0.5f;
-      const float dfc = -0.5f * kPi / c.Rcr * sinpif(r / c.Rcr);
-      const float* gs = gR + g.species[j] * kShfR;
-      const float etaR = -c.EtaR * kLog2e;
-      float dEdr = 0.f;
-#pragma unroll
-      for (int k = 0; k < kShfR; ++k) {
-        const float x = r - c.ShfR[k];
-        const float e = exp2f(etaR * x * x);
-        dEdr = fmaf(gs[k] * 0.25f * e, fmaf(-2.f * c.EtaR * x, fc, dfc), dEdr);
-      }
-      const float s = dEdr / r;
-      sg[3 * t + 0] = s * d.x;
-      sg[3 * t + 1] = s * d.y;
-      sg[3 * t + 2] = s * d.z;
-      gix -= s * d.x;
-      giy -= s * d.y;
-      giz -= s * d.z;
-    }
-
-    // ---- angular ----
-    const int na = min(nl.cnt_a[q], nl.cap_a);
-    {
-      const int* la = nl.nbr_a + (size_t)q * nl.cap_a;
-      const int* sa = nl.slot_a + (size_t)q * nl.cap_a;
-      for (int t = lane; t < na; t += 32) {
-        const int j = la[t];
-        const float3 d = disp(xi, g.pos[j], c);
-        const float r = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
-        nb[t] = make_float4(d.x, d.y, d.z, r);
-        nfc[t] = 0.5f * cospif(r / c.Rca) + 0.5f;
-        ndfc[t] = -0.5f * kPi / c.Rca * sinpif(r / c.Rca);
-        nsp[t] = g.species[j];
-        nslot[t] = sa[t];
-      }
+      avec[t] = make_float4(d.x, d.y, d.z, r);
+      float sn, cs;
+      sincospif(r / c.Rca, &sn, &cs);
+      afc[t] = 0.5f * cs + 0.5f;
+      adfc[t] = -0.5f * kPi / c.Rca * sn;
+      asp[t] = g.species[j];
+      sg[3 * t] = sg[3 * t + 1] = sg[3 * t + 2] = 0.f;
     }
     __syncwarp();
+
+    // ---- radial: lane per neighbour, straight into the molecule accumulator ----
+    {
+      const int nr = min(nl.cnt_r[q], nl.cap_r);
+      const int* lr = nl.nbr_r + (size_t)q * nl.cap_r;
+      for (int t = lane; t < nr; t += 32) {
+        const int j = lr[t];
+        const float3 d = disp(xi, g.pos[j], c);
+        const float r = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+        float sn, cs;
+        sincospif(r / c.Rcr, &sn, &cs);
+        const float fc = 0.5f * cs + 0.5f;
+        const float dfc = -0.5f * kPi / c.Rcr * sn;
+        const float* gsp = gR + g.species[j] * kShfR;
+        float dEdr = 0.f;
+#pragma unroll
+        for (int k = 0; k < kShfR; ++k) {
+          const float x = r - c.ShfR[k];
+          const float e = exp2f(etaR * x * x);
+          dEdr = fmaf(gsp[k] * 0.25f * e, fmaf(-2.f * c.EtaR * x, fc, dfc), dEdr);
+        }
+        const float s = dEdr / r;
+        gix -= s * d.x;
+        giy -= s * d.y;
+        giz -= s * d.z;
+        add_force(acc_w, j - a0, orig, j, F, s * d.x, s * d.y, s * d.z);
+      }
+    }
+
+    // ---- angular: lane per pair, pairs row-major over the list (j rising,
+    //      so lanes sharing j are contiguous and k differs between lanes) ----
     const int T = na * (na - 1) / 2;
     for (int base = 0; base < T; base += 32) {
       const int P = base + lane;
       const bool valid = P < T;
       int j = -1, k = -1;
-      float gjx = 0.f, gjy = 0.f, gjz = 0.f, gkx = 0.f, gky = 0.f, gkz = 0.f;
+      float gjx = 0.f, gjy = 0.f, gjz = 0.f;
       if (valid) {
         decode_pair(P, na, j, k);
-        const float4 rj = nb[j], rk = nb[k];
+        const int b = pair_block(asp[j], asp[k]);
+        const float4 rj = avec[j], rk = avec[k];
         const float inv_jk = __fdividef(1.f, rj.w * rk.w);
         const float cost = (rj.x * rk.x + rj.y * rk.y + rj.z * rk.z) * inv_jk;
         const float cp = 0.95f * cost;
         const float sp = sqrtf(fmaxf(1.f - cp * cp, 1e-12f));
-        const float fcj = nfc[j], fck = nfc[k];
+        const float fcj = afc[j], fck = afc[k];
         const float u = 0.5f * (rj.w + rk.w);
-        const float4* gp = reinterpret_cast<const float4*>(gA + pair_block(nsp[j], nsp[k]) * kGAStride);
+        const float4* gp = reinterpret_cast<const float4*>(gA + b * kGAStride);
         float A[kShfZ], dA[kShfZ];
 #pragma unroll
         for (int z = 0; z < kShfZ; ++z) {
-          const float b = fmaxf(0.5f * (1.f + cp * c.cosZ[z] + sp * c.sinZ[z]), 0.f);
-          const float L = __log2f(b);
+          const float bb = fmaxf(0.5f * (1.f + cp * c.cosZ[z] + sp * c.sinZ[z]), 0.f);
+          const float L = __log2f(bb);
           A[z] = 2.f * exp2f(c.Zeta * L);
           // dA/dcp = 2 Zeta b^(Zeta-1) db/dcp,  db/dcp = (cosZ - cp/sp sinZ) / 2
           dA[z] = c.Zeta * exp2f((c.Zeta - 1.f) * L) * (c.cosZ[z] - cp / sp * c.sinZ[z]);
         }
         float V = 0.f, dVdc = 0.f, dVdu = 0.f;
-        const float etaA = -c.EtaA * kLog2e;
 #pragma unroll
         for (int a = 0; a < kShfA; ++a) {
           const float x = u - c.ShfA[a];
@@ -510,59 +539,59 @@ __global__ void k_aev_adjoint(Geometry g, NeighborLists nl, AevConst c,
         const float fcjk = fcj * fck;
         const float dEdcos = 0.95f * fcjk * dVdc;
         const float dEdu = fcjk * dVdu;
-        const float dEdrj = 0.5f * dEdu + V * ndfc[j] * fck;
-        const float dEdrk = 0.5f * dEdu + V * fcj * ndfc[k];
+        const float dEdrj = 0.5f * dEdu + V * adfc[j] * fck;
+        const float dEdrk = 0.5f * dEdu + V * fcj * adfc[k];
         const float cj = cost / (rj.w * rj.w), ck = cost / (rk.w * rk.w);
         const float ej = dEdrj / rj.w, ek = dEdrk / rk.w;
         gjx = dEdcos * (rk.x * inv_jk - cj * rj.x) + ej * rj.x;
         gjy = dEdcos * (rk.y * inv_jk - cj * rj.y) + ej * rj.y;
         gjz = dEdcos * (rk.z * inv_jk - cj * rj.z) + ej * rj.z;
-        gkx = dEdcos * (rj.x * inv_jk - ck * rk.x) + ek * rk.x;
-        gky = dEdcos * (rj.y * inv_jk - ck * rk.y) + ek * rk.y;
-        gkz = dEdcos * (rj.z * inv_jk - ck * rk.z) + ek * rk.z;
+        const float gkx = dEdcos * (rj.x * inv_jk - ck * rk.x) + ek * rk.x;
+        const float gky = dEdcos * (rj.y * inv_jk - ck * rk.y) + ek * rk.y;
+        const float gkz = dEdcos * (rj.z * inv_jk - ck * rk.z) + ek * rk.z;
         gix -= gjx + gkx;
         giy -= gjy + gky;
         giz -= gjz + gkz;
-        const int sk = nslot[k];
-        if (sk < nl.cap_r) {
-          atomicAdd(&sg[3 * sk + 0], gkx);
-          atomicAdd(&sg[3 * sk + 1], gky);
-          atomicAdd(&sg[3 * sk + 2], gkz);
-        }
+        atomicAdd(&sg[3 * k + 0], gkx);
+        atomicAdd(&sg[3 * k + 1], gky);
+        atomicAdd(&sg[3 * k + 2], gkz);
       }
-      // j side: lanes sharing j are contiguous -> segmented inclusive scan.
+      // j side: a run of consecutive lanes with the same j (the same j can
+      // recur in a later block of the chunk: that is a separate run) is
+      // reduced by a segmented inclusive scan; the run's last lane adds it.
       const int key = valid ? j : -1 - lane;
+      const int prev_key = __shfl_up_sync(FULL, key, 1);
+      const unsigned heads = __ballot_sync(FULL, lane == 0 || prev_key != key);
+      const int head = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // run start
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
-        const float ox = __shfl_up_sync(0xffffffffu, gjx, off);
-        const float oy = __shfl_up_sync(0xffffffffu, gjy, off);
-        const float oz = __shfl_up_sync(0xffffffffu, gjz, off);
-        const int ok = __shfl_up_sync(0xffffffffu, key, off);
-        if (lane >= off && ok == key) {
+        const float ox = __shfl_up_sync(FULL, gjx, off);
+        const float oy = __shfl_up_sync(FULL, gjy, off);
+        const float oz = __shfl_up_sync(FULL, gjz, off);
+        if (lane - off >= head) {
           gjx += ox;
           gjy += oy;
           gjz += oz;
         }
       }
-      const int next = __shfl_down_sync(0xffffffffu, key, 1);
-      if (valid && (lane == 31 || next != key)) {
-        const int sj = nslot[j];
-        if (sj < nl.cap_r) {
-          atomicAdd(&sg[3 * sj + 0], gjx);
-          atomicAdd(&sg[3 * sj + 1], gjy);
-          atomicAdd(&sg[3 * sj + 2], gjz);
-        }
+      const bool run_end = lane == 31 || ((heads >> (lane + 1)) & 1u);
+      if (valid && run_end) {
+        atomicAdd(&sg[3 * j + 0], gjx);
+        atomicAdd(&sg[3 * j + 1], gjy);
+        atomicAdd(&sg[3 * j + 2], gjz);
       }
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-      gix += __shfl_xor_sync(0xffffffffu, gix, o);
-      giy += __shfl_xor_sync(0xffffffffu, giy, o);
-      giz += __shfl_xor_sync(0xffffffffu, giz, o);
+      gix += __shfl_xor_sync(FULL, gix, o);
+      giy += __shfl_xor_sync(FULL, giy, o);
+      giz += __shfl_xor_sync(FULL, giz, o);
     }
     __syncwarp();
-    for (int t = lane; t < nr; t += 32)
-      add_force(acc_w, lr[t] - a0, orig, lr[t], F, sg[3 * t], sg[3 * t + 1], sg[3 * t + 2]);
+    for (int t = lane; t < na; t += 32) {
+      const int j = la[t];
+      add_force(acc_w, j - a0, orig, j, F, sg[3 * t], sg[3 * t + 1], sg[3 * t + 2]);
+    }
     if (lane == 0) add_force(acc_w, q - a0, orig, q, F, gix, giy, giz);
     __syncwarp();
   }
