@@ -24,10 +24,13 @@
 #include <cstring>
 
 #include "nnp_internal.cuh"
+#include "tc_common.cuh"
 
 namespace nnp {
 
 namespace {
+
+using namespace tc;
 
 constexpr int kBM = 128;       // tile rows (atoms)
 constexpr int kBNMax = 256;    // tile columns, TMEM columns per accumulator
@@ -39,139 +42,11 @@ constexpr uint32_t kABytes = kBM * kBK * 2;      // 16 KB
 constexpr uint32_t kBBytes = kBNMax * kBK * 2;   // 32 KB (room for 256 B rows)
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
 constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
-constexpr long long kSpinLimit = 1ll << 26;  // try_wait polls before giving up
 
 struct TcMaps {
   CUtensorMap a;
   CUtensorMap b;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Bounded wait for the phase with the given parity; false if it gave up or
-// another role already aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const int* abort_flag) {
-  const uint32_t a = smem_u32(bar);
-  for (long long i = 0; i < kSpinLimit; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if ((i & 1023) == 1023 && *(volatile const int*)abort_flag) return false;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc_sw128(const void* p) {
-  const uint32_t addr = smem_u32(p);
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-  d |= (uint64_t)(16u >> 4) << 16;    // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset: 8 rows x 128 B
-  d |= (uint64_t)1 << 46;             // descriptor version (sm_100 family)
-  d |= (uint64_t)2 << 61;             // swizzle mode: 128 B
-  return d;
-}
-
-// Instruction descriptor of kind::f16: FP32 accumulator, A/B both BF16 (fmt 1)
-// or both FP16 (fmt 0), K-major A and B, M = 128, N = n.
-__device__ __forceinline__ uint32_t instr_desc(uint32_t fmt, uint32_t n) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((n >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
-                                        uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-template <typename T> struct Pack;
-template <> struct Pack<__nv_bfloat16> {
-  static __device__ __forceinline__ uint32_t two(float a, float b) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<uint32_t*>(&h);
-  }
-  static __device__ __forceinline__ float lo(uint32_t u) {
-    return __bfloat162float(__ushort_as_bfloat16((unsigned short)(u & 0xffffu)));
-  }
-  static __device__ __forceinline__ float hi(uint32_t u) {
-    return __bfloat162float(__ushort_as_bfloat16((unsigned short)(u >> 16)));
-  }
-  static constexpr uint32_t fmt = 1;
-};
-template <> struct Pack<__half> {
-  static __device__ __forceinline__ uint32_t two(float a, float b) {
-    __half2 h = __floats2half2_rn(a, b);
-    return *reinterpret_cast<uint32_t*>(&h);
-  }
-  static __device__ __forceinline__ float lo(uint32_t u) {
-    return __half2float(__ushort_as_half((unsigned short)(u & 0xffffu)));
-  }
-  static __device__ __forceinline__ float hi(uint32_t u) {
-    return __half2float(__ushort_as_half((unsigned short)(u >> 16)));
-  }
-  static constexpr uint32_t fmt = 0;
-};
-
-__device__ __forceinline__ float celu01(float z) {
-  return z > 0.f ? z : 0.1f * (expf(fminf(z, 0.f) * 10.f) - 1.f);
-}
 
 // Epilogue of one 16-column chunk of one row.
 template <typename T>
@@ -292,7 +167,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t it = 0;
       for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const GemmTile tl = tiles[tile];
-        const GemmProblem& P = probs[tl.problem];
+        const GemmProblem P = probs[tl.problem];  // by value: asm memory clobbers force reloads of references
         const int nkb = (P.K + kBK - 1) / kBK;
         const int ay = P.a_row0 + tl.m0, by = P.b_row0 + tl.n0;
         bool ok = true;
@@ -321,7 +196,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t it = 0, tcount = 0;
       for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tcount) {
         const GemmTile tl = tiles[tile];
-        const GemmProblem& P = probs[tl.problem];
+        const GemmProblem P = probs[tl.problem];  // by value: asm memory clobbers force reloads of references
         const int nkb = (P.K + kBK - 1) / kBK;
         const int n_tile = min(kBNMax, P.N - tl.n0);
         const uint32_t idesc = instr_desc(Pack<T>::fmt, (uint32_t)n_tile);
@@ -358,10 +233,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t tcount = 0;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tcount) {
       const GemmTile tl = tiles[tile];
-      const GemmProblem& P = probs[tl.problem];
+      const GemmProblem P = probs[tl.problem];  // by value: asm memory clobbers force reloads of references
       const int n_tile = min(kBNMax, P.N - tl.n0);
       const uint32_t acc = tcount & 1, use = tcount >> 1;
-      if (!mbar_wait(&tfull[acc], use & 1, abort_flag)) {
+      const bool got = mbar_wait(&tfull[acc], use & 1, abort_flag);
+      if (!__all_sync(0xffffffffu, got)) {  // the warp leaves together (tcgen05.ld is .sync.aligned)
         atomicOr(status, kStatTimeout);
         atomicExch(abort_flag, 1);
         break;

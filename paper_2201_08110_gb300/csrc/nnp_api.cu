@@ -74,6 +74,11 @@ struct nnp_ctx {
   Layer L[6];              // 0 L1 fwd, 1 L2 fwd, 2 L3 fwd, 3 L3 rev, 4 L2 rev, 5 L1 rev
   void* d_maps = nullptr;
   alignas(64) unsigned char tc_maps[6][256];  // tensor-core path: {A, B} TMA descriptors per layer
+  alignas(64) unsigned char tail_maps[5 * 128];  // fused tail: h1, w2, w3, w3t, w2t
+  std::vector<TailProblem> tail_probs;
+  std::vector<GemmTile> tail_tiles;
+  TailProblem* d_tail_probs = nullptr;
+  GemmTile* d_tail_tiles = nullptr;
   // reverse pass work list
   int4* d_work = nullptr;
   int n_work = 0;
@@ -250,6 +255,8 @@ void nnp_destroy(nnp_handle h) {
     if (L.d_probs) cudaFree(L.d_probs);
     if (L.d_tiles) cudaFree(L.d_tiles);
   }
+  if (h->d_tail_probs) cudaFree(h->d_tail_probs);
+  if (h->d_tail_tiles) cudaFree(h->d_tail_tiles);
   delete h;
 }
 
@@ -645,6 +652,53 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for layer " + std::to_string(l));
     }
     CK(tc_set_smem());
+    // fused tail: one problem per (element, member), tiles of 128 rows
+    for (int e = 0; e < kSpecies; ++e) {
+      const int Me = h->elem_count[e];
+      if (Me == 0) continue;
+      for (int m = 0; m < M; ++m) {
+        TailProblem T{};
+        T.Me = Me;
+        T.row0 = h->elem_row0[e];
+        T.h1 = kHidden[e][0];
+        T.h2 = kHidden[e][1];
+        T.h3 = kHidden[e][2];
+        T.a_col0 = m * T.h1;
+        T.w2_row0 = (int)r2[e][m];
+        T.w3_row0 = (int)r3[e][m];
+        T.w3t_row0 = (int)r3t[e][m];
+        T.w2t_row0 = (int)r2t[e][m];
+        T.b2 = h->d_b + b1_total + r2[e][m];
+        T.b3 = h->d_b + b1_total + b2_total + r3[e][m];
+        T.w4 = h->d_w4 + ((size_t)e * kMaxModels + m) * kH3Max;
+        T.b4 = b4[(size_t)e * kMaxModels + m];
+        T.inv_m = 1.0f / (float)M;
+        T.y = h->d_y + (size_t)T.row0 * M + m;
+        T.ldy = M;
+        T.h1g = H1 + ((size_t)T.row0 * h->ldh1 + (size_t)m * T.h1) * es;
+        T.ldh1 = h->ldh1;
+        const int pi = (int)h->tail_probs.size();
+        h->tail_probs.push_back(T);
+        for (int m0 = 0; m0 < Me; m0 += 128) h->tail_tiles.push_back(GemmTile{pi, m0, 0, 0});
+      }
+    }
+    if (tail_maps_bytes() > sizeof(h->tail_maps)) return fail(h, NNP_ERR_UNSUPPORTED, "tail map size");
+    const MapSpec TW[4] = {B[1], B[2], B[3], B[4]};  // w2, w3, w3t, w2t
+    if (!tc_make_map(h->tail_maps, h->d_h1, h->prec, R64, (uint64_t)h->ldh1, (uint64_t)h->ldh1, 128))
+      return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the fused tail");
+    for (int i = 0; i < 4; ++i)
+      if (!tc_make_map(h->tail_maps + 128 * (i + 1), TW[i].base, h->prec, TW[i].rows, TW[i].cols,
+                       TW[i].cols, (uint32_t)tail_weight_box(i)))
+        return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the fused tail");
+    CK(tail_set_smem());
+    CK(dalloc(&h->d_tail_probs, h->tail_probs.size()));
+    CK(dalloc(&h->d_tail_tiles, h->tail_tiles.size()));
+    if (!h->tail_probs.empty()) {
+      CK(cudaMemcpy(h->d_tail_probs, h->tail_probs.data(), sizeof(TailProblem) * h->tail_probs.size(),
+                    cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(h->d_tail_tiles, h->tail_tiles.data(), sizeof(GemmTile) * h->tail_tiles.size(),
+                    cudaMemcpyHostToDevice));
+    }
   }
   for (auto& L : h->L) {
     CK(dalloc(&L.d_probs, L.probs.size()));
@@ -731,23 +785,38 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
   mark(2);
   gemm(0);
   mark(3);
-  gemm(1);
-  mark(4);
-  gemm(2);
-  if (h->prec == Prec::F32) {  // the tensor-core path fuses the output layer into gemm(2)
+  if (h->prec != Prec::F32) {
+    // tensor cores: L2 fwd, L3 fwd + output layer, L3 rev, L2 rev in one kernel
+    if (!h->tail_tiles.empty()) {
+      launch_mlp_tail(h->d_tail_probs, h->d_tail_tiles, (int)h->tail_tiles.size(), h->prec,
+                      h->tail_maps, F ? 1 : 0, h->d_status, s);
+      ++kernels;
+    }
+    mark(4);
+    mark(5);
+    launch_energy(h->d_y, h->n_models, h->d_row_of_int, h->d_mol_off, h->n_mols, E, h->d_atom_e, s);
+    ++kernels;
+    mark(6);
+    if (!F) return kernels;
+    mark(7);
+    mark(8);
+  } else {
+    gemm(1);
+    mark(4);
+    gemm(2);
     launch_head(h->d_z3, h->ldz3, h->prec, h->d_row_elem, h->d_w4, h->d_b4, h->d_d3, h->d_y,
                 h->n_rows, h->n_models, s);
     ++kernels;
+    mark(5);
+    launch_energy(h->d_y, h->n_models, h->d_row_of_int, h->d_mol_off, h->n_mols, E, h->d_atom_e, s);
+    ++kernels;
+    mark(6);
+    if (!F) return kernels;
+    gemm(3);
+    mark(7);
+    gemm(4);
+    mark(8);
   }
-  mark(5);
-  launch_energy(h->d_y, h->n_models, h->d_row_of_int, h->d_mol_off, h->n_mols, E, h->d_atom_e, s);
-  ++kernels;
-  mark(6);
-  if (!F) return kernels;
-  gemm(3);
-  mark(7);
-  gemm(4);
-  mark(8);
   gemm(5);
   mark(9);
   launch_aev_adjoint(g, h->nl, h->aevc, h->d_row_of_int, h->d_dG, h->d_work, h->n_work, h->d_orig,
@@ -823,12 +892,17 @@ nnp_status nnp_compute_timed(nnp_handle h, const float* pos, double* E, double* 
 
 int32_t nnp_kernels_per_step(nnp_handle h, int32_t with_forces) {
   if (!h) return -1;
-  int k = 2 + 1 + 1 + (h->prec == Prec::F32 ? 1 : 0);  // gather, neighbours, features, energy, head
-  for (int l = 0; l < 3; ++l) k += h->L[l].tiles.empty() ? 0 : 1;
-  if (with_forces) {
-    k += 1;  // reverse pass to coordinates
-    for (int l = 3; l < 6; ++l) k += h->L[l].tiles.empty() ? 0 : 1;
+  int k = 2 + 1 + 1;  // gather, neighbours, features, energy
+  k += h->L[0].tiles.empty() ? 0 : 1;
+  if (h->prec == Prec::F32) {
+    k += 1;  // head
+    for (int l = 1; l < 3; ++l) k += h->L[l].tiles.empty() ? 0 : 1;
+    if (with_forces)
+      for (int l = 3; l < 5; ++l) k += h->L[l].tiles.empty() ? 0 : 1;
+  } else {
+    k += h->tail_tiles.empty() ? 0 : 1;
   }
+  if (with_forces) k += 1 + (h->L[5].tiles.empty() ? 0 : 1);  // L1 reverse, featurizer reverse
   return k;
 }
 

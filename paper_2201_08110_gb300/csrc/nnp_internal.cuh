@@ -113,6 +113,24 @@ struct GemmProblem {
   float b4, inv_m;
 };
 
+// The fused tail of one (element, ensemble member): second and third hidden
+// layers, output layer and their reverse pass (tensor-core path).
+struct TailProblem {
+  int Me;       // atoms of the element
+  int row0;     // first row of the element block
+  int h1, h2, h3;
+  int a_col0;   // first column of this member in the h1 activations
+  int w2_row0, w3_row0, w3t_row0, w2t_row0;  // rows in the stacked weight arrays
+  const float* b2;
+  const float* b3;
+  const float* w4;
+  float b4, inv_m;
+  float* y;     // y + row0 * M + member, stride ldy
+  long ldy;
+  void* h1g;    // h1 (then d1) of row0, column a_col0; row stride ldh1 elements
+  long ldh1;
+};
+
 // A tile of the flattened problem list.
 struct GemmTile {
   int problem, m0, n0, pad;
@@ -151,6 +169,12 @@ void launch_export_features(const void* aev, Prec prec, const int* row_of_int,
                             const int* orig_of_int, int n, float* out, cudaStream_t s);
 void launch_export_atomic_energies(const double* atom_energy_row, const int* row_of_int,
                                    const int* orig_of_int, int n, double* out, cudaStream_t s);
+
+size_t tail_maps_bytes();
+int tail_weight_box(int which);  // box rows of the w2, w3, w3t, w2t maps
+cudaError_t tail_set_smem();
+void launch_mlp_tail(const TailProblem* probs, const GemmTile* tiles, int n_tiles, Prec p,
+                     const void* maps, int reverse, unsigned* status, cudaStream_t s);
 
 // Featurizer constants (cutoffs, shift grids, species-pair table, box).
 void aev_constants(AevConst& c, const double box[3]);
