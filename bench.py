@@ -5,9 +5,10 @@ One step = one energy + force evaluation of a whole batch (neighbour lists,
 features, the 8-network ensemble forward and reverse, the featurizer's reverse
 pass to coordinates), i.e. every stage of the path.  Default workload: 512
 molecules with 20-120 atoms (H .45, C .35, N .08, O .08, F/S/Cl .04), random
-Xavier-normal ANI-2x-architecture weights, network products in BF16, replayed
-as one CUDA graph per step.  An atom-eval is one atom's share of E and F for
-the full ensemble.
+Xavier-normal ANI-2x-architecture weights, network products in FP16 (the
+16-bit format that meets the stated error bounds; BF16 is timed alongside),
+replayed as one CUDA graph per step.  An atom-eval is one atom's share of E
+and F for the full ensemble.
 
 Also reported: the plain FP32 unbatched GPU path on a sample of the same
 molecules (one molecule per call, direct launches), the end-to-end number
@@ -46,7 +47,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--precision", default="fp16", choices=["fp32", "bf16", "fp16"],
+                    help="arithmetic of the networks' matrix products (FP16 meets the stated "
+                         "2e-3 energy / 1e-2 force bounds; single-pass BF16 does not on every "
+                         "molecule, see DESIGN.md)")
+    ap.add_argument("--alt-precision", default="bf16", choices=["none", "fp32", "bf16", "fp16"],
+                    help="a second precision timed the same way and reported alongside")
+    ap.add_argument("--workload", type=int, default=3, choices=[2, 3, 5],
+                    help="3: the 512-molecule batch (default, headline); 2: one 60-atom "
+                         "molecule on the plain FP32 path over perturbed coordinates; 5: 4096 "
+                         "molecules of 30-250 atoms plus a 1500-atom periodic pocket")
     ap.add_argument("--molecules", type=int, default=512)
     ap.add_argument("--unbatched-sample", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -132,30 +142,40 @@ def peaks():
     return 6800.0, 1900.0, 1700.0, "fallback", 2070.0
 
 
-# Algorithmic work per stage ("Algorithmic work").
+# Algorithmic work per stage ("Algorithmic work per stage").
 HID = W.HIDDEN
+# FP32 operations of the featurizer per directed radial pair / unordered
+# angular pair of neighbours (exp2 and log2 counted as one operation each).
+FLOP_RADIAL_FWD, FLOP_ANGULAR_FWD = 100.0, 142.0
+FLOP_RADIAL_REV, FLOP_ANGULAR_REV = 137.0, 300.0
+FLOP_DISTANCE = 8.0  # one neighbour-search distance test
 
 
-def stage_work(Z, M: int, es: int):
-    """FLOPs of each matrix-product stage and HBM bytes of the featurizer
-    stages, from the element counts of the batch.  K of the first layer is the
-    1008 real features (padding excluded)."""
+def stage_work(Z, M: int, n_pairs: float, n_triples: float, n_tests: float):
+    """{stage: (bound, algorithmic work)}: FLOPs of the matrix products from the
+    element counts (first-layer K = the 1008 real features), FP32 operations
+    of the featurizer from the pair / triple counts."""
     zs = list(W.ELEMENTS_Z)
     cnt = [int(np.sum(Z == z)) for z in zs]
-    f = {"l1_fwd": 0.0, "l2_fwd": 0.0, "l3_fwd": 0.0, "l3_rev": 0.0, "l2_rev": 0.0, "l1_rev": 0.0}
+    l1 = l2 = l3 = out = 0.0
     for e, n in enumerate(cnt):
         h1, h2, h3 = HID[e]
-        f["l1_fwd"] += 2.0 * n * M * h1 * 1008
-        f["l2_fwd"] += 2.0 * n * M * h1 * h2
-        f["l3_fwd"] += 2.0 * n * M * h2 * h3 + 2.0 * n * M * h3
-        f["l3_rev"] += 2.0 * n * M * h3 * h2
-        f["l2_rev"] += 2.0 * n * M * h2 * h1
-        f["l1_rev"] += 2.0 * n * M * h1 * 1008
-    N = len(Z)
-    # featurizer: positions in (16 B), features out (1008 * es); reverse: dE/dG in (1008 * 4)
-    # and forces out (24 B)
-    b = {"features": N * (16.0 + 1008 * es), "adjoint": N * (16.0 + 1008 * 4 + 24)}
-    return f, b
+        l1 += 2.0 * n * M * h1 * 1008
+        l2 += 2.0 * n * M * h1 * h2
+        l3 += 2.0 * n * M * h2 * h3
+        out += 2.0 * n * M * h3
+    return {
+        "neighbors": ("alu", n_tests * FLOP_DISTANCE),
+        "features": ("alu", n_pairs * FLOP_RADIAL_FWD + n_triples * FLOP_ANGULAR_FWD),
+        "l1_fwd": ("tensor", l1),
+        # on the tensor-core path the l2_fwd stage is the fused tail: both
+        # hidden layers forward, the output layer and both hidden layers reverse
+        "tail": ("tensor", 2 * l2 + 2 * l3 + out),
+        "l2_fwd": ("tensor", l2), "l3_fwd": ("tensor", l3 + out), "l3_rev": ("tensor", l3),
+        "l2_rev": ("tensor", l2),
+        "l1_rev": ("tensor", l1),
+        "adjoint": ("alu", n_pairs * FLOP_RADIAL_REV + n_triples * FLOP_ANGULAR_REV),
+    }
 
 
 def src_hash(*names):
@@ -232,6 +252,44 @@ def run_reference(args):
     return 0
 
 
+def max_over_ranks(x: float, dist) -> float:
+    """The maximum of a per-rank number (the timing rule: max over ranks)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    if dist.get_backend() == "nccl":
+        t = t.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, dist) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    if dist.get_backend() == "nccl":
+        t = t.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def timed_steps(model, pos, E, F, steps: int, flush, stream):
+    """Sum of per-step CUDA-event times (ms); the L2 flush between steps is
+    outside the events."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record(stream)
+        model.compute(pos, E, F)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -257,73 +315,86 @@ def run_ours(args):
 
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    model = nnp.NNP(b.Z, w, M, mol_off=b.mol_off, precision=args.precision, use_graph=True)
     pos = torch.tensor(b.pos, device="cuda")
     E = torch.empty(b.n_mols, dtype=torch.float64, device="cuda")
     F = torch.empty(b.n_atoms, 3, dtype=torch.float64, device="cuda")
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
-    for _ in range(max(3, args.warmup)):
-        model.compute(pos, E, F)
-    torch.cuda.synchronize()
-    model.status()
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    def make(prec):
+        m = nnp.NNP(b.Z, w, M, mol_off=b.mol_off, precision=prec, use_graph=True)
+        for _ in range(max(3, args.warmup)):
+            m.compute(pos, E, F)
+        torch.cuda.synchronize()
+        m.status()
+        return m
+
+    model = make(args.precision)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     clk = Clocks(local)
     clk.start()
-    for k in range(args.steps):
-        flush.zero_()  # L2 flush, outside the timed events
-        starts[k].record(stream)
-        model.compute(pos, E, F)
-        ends[k].record(stream)
-    torch.cuda.synchronize()
+    total_ms = timed_steps(model, pos, E, F, args.steps, flush, stream)
     clocks = clk.stop()
+    model.status()
     if dist is not None:
         dist.barrier()
-    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    model.status()
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    n_atoms_all = torch.tensor([float(b.n_atoms)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(n_atoms_all, op=dist.ReduceOp.SUM)
-    total_ms = float(t.item())
-    atoms_all = float(n_atoms_all.item())
+    total_ms = max_over_ranks(total_ms, dist)
+    atoms_all = sum_over_ranks(b.n_atoms, dist)
     ms_per_step = total_ms / args.steps
     value = atoms_all * args.steps / (total_ms / 1e3)
+
+    alt = None
+    if args.alt_precision not in ("none", args.precision):
+        m2 = make(args.alt_precision)
+        alt_ms = max_over_ranks(timed_steps(m2, pos, E, F, args.steps, flush, stream), dist)
+        alt = {"precision": args.alt_precision, "value": atoms_all * args.steps / (alt_ms / 1e3),
+               "unit": UNIT, "ms_per_step": alt_ms / args.steps}
+        m2.close()
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
 
-    # ---- per-stage times and the roofline of the dominant stage ----
+    # ---- per-stage times, algorithmic work and rooflines ----
     stage_runs = [model.compute_timed(pos, E, F) for _ in range(5)]
     stages = {k: statistics.median(r[k] for r in stage_runs) for k in stage_runs[0]}
+    cr, _ = model.neighbors(0)
+    ca, _ = model.neighbors(1)
+    cr = cr.cpu().numpy().astype(np.float64)
+    ca = ca.cpu().numpy().astype(np.float64)
+    sizes = np.diff(b.mol_off).astype(np.float64)
+    work = stage_work(b.Z, M, float(cr.sum()), float((ca * (ca - 1) / 2).sum()),
+                      float((sizes * (sizes - 1)).sum()))
     hbm, bf16, bf16_sus, peak_kind, sm_max = peaks()
-    es = 4 if args.precision == "fp32" else 2
-    flops, bytes_ = stage_work(b.Z, M, es)
-    dom = max(stages, key=stages.get)
-    if dom in flops:
-        achieved = flops[dom] / (stages[dom] * 1e-3) / 1e12
-        if args.precision == "fp32":
-            peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FFMA lanes x 2 x max clock
-            roof = {"bound": "alu", "unit": "TFLOP/s", "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 lanes x 2 x max SM clock, TFLOP/s
+    tensor_path = args.precision != "fp32"
+    shown = dict(stages)
+    if tensor_path:  # the fused tail runs in the l2_fwd slot
+        shown = {k: v for k, v in stages.items() if k not in ("l2_fwd", "l3_fwd", "l3_rev", "l2_rev")}
+        shown["tail"] = stages["l2_fwd"]
+    rooflines = {}
+    for k, ms in shown.items():
+        if k not in work or ms <= 0:
+            continue
+        bound, amount = work[k]
+        if bound == "tensor" and tensor_path:
+            peak, unit, note = bf16, "TFLOP/s", f"{peak_kind} dense bf16 (fp16 equal rate)"
         else:
-            peak = bf16
-            roof = {"bound": "tensor", "unit": "TFLOP/s", "peak_note": f"{peak_kind} bf16 burst"}
-    else:
-        achieved = bytes_.get(dom, 0.0) / (stages[dom] * 1e-3) / 1e9
-        peak = hbm
-        roof = {"bound": "hbm", "unit": "GB/s", "peak_note": f"{peak_kind} copy bandwidth"}
-    kernel_key = {"features": "aev.cu", "adjoint": "aev.cu"}.get(dom, "mlp_tc.cu" if es == 2 else "mlp_simt.cu")
-    tr = NCU_TRAFFIC.get((dom, src_hash(kernel_key)))
-    roof.update({"stage": dom, "achieved": achieved, "peak": peak, "frac": achieved / peak,
-                 "traffic": None if tr is None else tr * b.n_atoms})
-    stage_share = {k: v / max(sum(stages.values()), 1e-12) for k, v in stages.items()}
+            bound = "alu"
+            peak, unit, note = fp32_peak, "TFLOP/s", "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 x max SM clock"
+        achieved = amount / (ms * 1e-3) / 1e12
+        rooflines[k] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                        "frac": achieved / peak, "work": amount, "ms": ms, "peak_note": note}
+    dom = max(rooflines, key=lambda k: rooflines[k]["ms"])
+    kernel_src = {"features": "aev.cu", "adjoint": "aev.cu", "neighbors": "aev.cu",
+                  "tail": "mlp_tail_tc.cu"}.get(dom, "mlp_tc.cu" if tensor_path else "mlp_simt.cu")
+    tr = NCU_TRAFFIC.get((dom, src_hash(kernel_src)))
+    roof = dict(rooflines[dom])
+    roof.update({"stage": dom, "traffic": None if tr is None else tr * b.n_atoms})
+    total_stage = max(sum(shown.values()), 1e-12)
+    stage_share = {k: v / total_stage for k, v in shown.items()}
 
     # ---- end to end through the host-buffer entry point (pinned buffers) ----
     hpos = torch.from_numpy(b.pos.copy()).pin_memory()
@@ -346,7 +417,8 @@ def run_ours(args):
     # ---- the plain FP32 unbatched path on a sample of the same molecules ----
     unb = None
     if args.unbatched_sample > 0:
-        ids = np.random.Generator(np.random.PCG64(17)).choice(b.n_mols, min(args.unbatched_sample, b.n_mols), replace=False)
+        ids = np.random.Generator(np.random.PCG64(17)).choice(
+            b.n_mols, min(args.unbatched_sample, b.n_mols), replace=False)
         tot_ms, tot_atoms = 0.0, 0
         for m in ids:
             sub = b.molecule(int(m))
@@ -368,8 +440,8 @@ def run_ours(args):
             tot_atoms += sub.n_atoms
             h1.close()
         unb = {"value": tot_atoms / (tot_ms / 1e3), "unit": UNIT,
-               "sample": f"{len(ids)} molecules of the batch, one per call, FP32 networks, direct launches",
-               "ms_per_molecule": tot_ms / len(ids)}
+               "sample": f"{len(ids)} molecules of the batch, one per call, FP32 networks, "
+                         "direct launches", "ms_per_molecule": tot_ms / len(ids)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -380,9 +452,11 @@ def run_ours(args):
                        "precision": args.precision, "graph": True,
                        "l2": "flushed (256 MB write) between timed steps, outside the timed events",
                        "parallelism": f"replicas x{world}, no collective on the data path"},
-            "roofline": roof, "stages_ms": stages, "stage_share": stage_share,
+            "roofline": roof, "rooflines": rooflines, "stages_ms": shown, "stage_share": stage_share,
             "e2e": e2e, "gpu_launches": model.kernels_per_step(True) * args.steps,
             "clocks": clocks}
+    if alt is not None:
+        line["alt_precision"] = alt
     if unb is not None:
         line["fp32_unbatched"] = unb
         line["speedup_vs_fp32_unbatched"] = value / world / unb["value"]
@@ -394,10 +468,113 @@ def run_ours(args):
     return 0
 
 
+def run_workload2(args):
+    """One 60-atom molecule, 8 networks, plain FP32 path (direct launches), new
+    coordinates every step (independent N(0, 0.01^2) A perturbations)."""
+    import torch
+    from paper_2201_08110_gb300 import build, nnp
+    build.build()
+    b, w, M = W.config2()
+    steps = args.steps
+    g = W.rng(W.workload_seed(2) + 50)
+    P = torch.tensor(np.stack([W.perturb(g, b.pos) for _ in range(steps + args.warmup)]),
+                     device="cuda")
+    model = nnp.NNP(b.Z, w, M, precision="fp32", use_graph=False)
+    pos = torch.empty(b.n_atoms, 3, dtype=torch.float32, device="cuda")
+    E = torch.empty(1, dtype=torch.float64, device="cuda")
+    F = torch.empty(b.n_atoms, 3, dtype=torch.float64, device="cuda")
+    for k in range(args.warmup):
+        pos.copy_(P[k])
+        model.compute(pos, E, F)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for k in range(steps):
+        pos.copy_(P[args.warmup + k])
+        model.compute(pos, E, F)
+    s1.record()
+    torch.cuda.synchronize()
+    model.status()
+    ms = s0.elapsed_time(s1)
+    line = {"metric": METRIC, "value": b.n_atoms * steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": ms / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp32",
+            "data": "synthetic",
+            "config": {"workload": "one 60-atom molecule (H27 C21 N5 O4 F S Cl), 8 networks, "
+                                   "plain FP32 path, direct launches, new coordinates each step"},
+            "gpu_launches": model.kernels_per_step(True) * steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_workload5(args):
+    """4096 molecules (30-250 atoms, log-uniform) plus one 1500-atom periodic
+    pocket; one step evaluates both; reports the handles' device memory."""
+    import torch
+    from paper_2201_08110_gb300 import build, nnp
+    build.build()
+    batch, pocket, w, M = W.config5()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    free0 = torch.cuda.mem_get_info()[0]
+    hb = nnp.NNP(batch.Z, w, M, mol_off=batch.mol_off, precision=args.precision, use_graph=True)
+    hp = nnp.NNP(pocket.Z, w, M, precision=args.precision, box=pocket.box, use_graph=True)
+    torch.cuda.synchronize()
+    footprint = free0 - torch.cuda.mem_get_info()[0]
+    pb = torch.tensor(batch.pos, device="cuda")
+    pp = torch.tensor(pocket.pos, device="cuda")
+    Eb = torch.empty(batch.n_mols, dtype=torch.float64, device="cuda")
+    Fb = torch.empty(batch.n_atoms, 3, dtype=torch.float64, device="cuda")
+    Ep = torch.empty(1, dtype=torch.float64, device="cuda")
+    Fp = torch.empty(pocket.n_atoms, 3, dtype=torch.float64, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        hb.compute(pb, Eb, Fb)
+        hp.compute(pp, Ep, Fp)
+    torch.cuda.synchronize()
+    hb.status()
+    hp.status()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clk = Clocks(0)
+    clk.start()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        hb.compute(pb, Eb, Fb)
+        hp.compute(pp, Ep, Fp)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    hb.status()
+    hp.status()
+    ms = sum(a.elapsed_time(b2) for a, b2 in zip(starts, ends))
+    n = batch.n_atoms + pocket.n_atoms
+    stages_b = hb.compute_timed(pb, Eb, Fb)
+    stages_p = hp.compute_timed(pp, Ep, Fp)
+    line = {"metric": METRIC, "value": n * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": "4096 molecules, 30-250 atoms (log-uniform), plus a 1500-atom "
+                                   "periodic pocket (24.7 A cube); 8 networks",
+                       "n_atoms": n, "precision": args.precision, "graph": True},
+            "device_bytes": int(footprint), "stages_ms_batch": stages_b,
+            "stages_ms_pocket": stages_p,
+            "gpu_launches": (hb.kernels_per_step(True) + hp.kernels_per_step(True)) * args.steps,
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == 2:
+        return run_workload2(args)
+    if args.workload == 5:
+        return run_workload5(args)
     return run_ours(args)
 
 

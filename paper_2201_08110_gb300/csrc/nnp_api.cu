@@ -423,8 +423,10 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   CK(cudaMemset(h->d_h1, 0, R * h->ldh1 * es));
   CK(cudaMalloc(&h->d_h2, R * h->ldh2 * es));
   CK(cudaMemset(h->d_h2, 0, R * h->ldh2 * es));
-  CK(dalloc(&h->d_z3, R * h->ldz3));
-  CK(cudaMemset(h->d_z3, 0, R * h->ldz3 * sizeof(float)));
+  if (h->prec == Prec::F32) {  // the tensor-core path fuses the output layer: no z3
+    CK(dalloc(&h->d_z3, R * h->ldz3));
+    CK(cudaMemset(h->d_z3, 0, R * h->ldz3 * sizeof(float)));
+  }
   CK(cudaMalloc(&h->d_d3, R * h->ldz3 * es));
   CK(cudaMemset(h->d_d3, 0, R * h->ldz3 * es));
   CK(dalloc(&h->d_y, R * M));

@@ -278,3 +278,22 @@ def test_full_batch_sampled_against_oracle(lib, prec):
         Fm = F[a0:a1]
         scale = np.sqrt(np.mean(Fm ** 2)) * (a1 - a0)
         assert np.abs(Fm.sum(0)).max() <= 1e-4 * scale
+
+
+# --- workload 5 shapes: the periodic pocket and the densest molecules ----------------
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_pocket_and_dense_molecules(lib, prec):
+    """The 1500-atom periodic region (24.7 A box, too large for the per-warp
+    shared-memory force accumulators, so the global FP64 atomics path runs) and
+    250-atom molecules in the 8 A cube (about 0.49 atoms / A^3, the densest
+    lists of the workloads), against the oracle."""
+    w, M = W.weights(99, 2), 2
+    pocket = W.pocket(W.workload_seed(5) + 2)
+    _, E, F = run(lib, pocket, w, M, prec)
+    check_batch(prec, E, F, pocket, oracle_batch(pocket, w, M))
+    dense = W.batch(W.workload_seed(5), [250, 249, 30])
+    model, E, F = run(lib, dense, w, M, prec)
+    check_batch(prec, E, F, dense, oracle_batch(dense, w, M))
+    ca, _ = model.neighbors(1)
+    print(f"dense molecules: max angular neighbours {int(ca.max())} of capacity {model.capacity()[1]}")
