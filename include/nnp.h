@@ -82,7 +82,11 @@ typedef struct {
   int32_t max_angular;    /* angular (3.5 A) neighbour capacity per atom; 0 = automatic */
   int32_t use_graph;      /* 1: replay the step as one CUDA graph (captured on first use
                              for a given set of buffer pointers) */
-  int32_t reserved[8];    /* must be zero */
+  int32_t neighbor_mode;  /* 0: automatic (cell list for one periodic region of more than
+                             1024 atoms, else all pairs of each molecule); 1: all pairs;
+                             2: cell list (one periodic region of at most 32768 atoms,
+                             else NNP_ERR_UNSUPPORTED) */
+  int32_t reserved[7];    /* must be zero */
 } nnp_params;
 
 /* Number of FP32 parameters of one ensemble member (1,713,223). */
@@ -213,7 +217,7 @@ int32_t nnp_kernels_per_step(nnp_handle h, int32_t with_forces);
  * n_atoms > NNP_STATIC_MAX_ATOMS returns NNP_ERR_TOO_LARGE; nothing is enqueued.
  * An atomic number outside {1,6,7,8,9,16,17} or a non-finite position makes
  * every output feature NaN (there is no handle to carry a status).
- * Intermediates live in one fixed scratch array of about 2 MB in device global
+ * Intermediates live in one fixed scratch array of about 1.6 MB in device global
  * memory that every GPU loading the library holds until the process exits;
  * all calls on a device share it and it keeps the last call's contents, so
  * calls that overlap on the GPU race: serialise them (one stream, or events).

@@ -71,7 +71,6 @@ __global__ void k_neighbors(Geometry g, NeighborLists nl, AevConst c, unsigned* 
   int nr = 0, na = 0;
   int* lr = nl.nbr_r + (size_t)q * nl.cap_r;
   int* la = nl.nbr_a + (size_t)q * nl.cap_a;
-  int* sa = nl.slot_a + (size_t)q * nl.cap_a;
   for (int base = a0; base < a1; base += 32) {
     const int j = base + lane;
     bool inR = false, inA = false;
@@ -92,10 +91,7 @@ __global__ void k_neighbors(Geometry g, NeighborLists nl, AevConst c, unsigned* 
       if (slot < nl.cap_r) lr[slot] = j;
       if (inA) {
         const int sl = na + __popc(mA & lt);
-        if (sl < nl.cap_a) {
-          la[sl] = j;
-          sa[sl] = slot;
-        }
+        if (sl < nl.cap_a) la[sl] = j;
       }
     }
     nr += __popc(mR);

@@ -73,6 +73,9 @@ struct nnp_ctx {
   size_t w_off[6] = {0};  // W1, W2, W3, W3T, W2T, W1T element offsets in d_w
   Layer L[6];              // 0 L1 fwd, 1 L2 fwd, 2 L3 fwd, 3 L3 rev, 4 L2 rev, 5 L1 rev
   void* d_maps = nullptr;
+  bool use_cells = false;
+  CellGrid cells{};
+  CellBuffers cellbuf{};
   alignas(64) unsigned char tc_maps[6][256];  // tensor-core path: {A, B} TMA descriptors per layer
   alignas(64) unsigned char tail_maps[5 * 128];  // fused tail: h1, w2, w3, w3t, w2t
   std::vector<TailProblem> tail_probs;
@@ -246,7 +249,7 @@ void nnp_destroy(nnp_handle h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   void* ptrs[] = {h->d_Z, h->d_mol_off, h->d_orig, h->d_row_of_int, h->d_species_int,
                   h->d_mol_start, h->d_mol_end, h->d_row_elem, h->d_pos, h->nl.cnt_r,
-                  h->nl.nbr_r, h->nl.cnt_a, h->nl.nbr_a, h->nl.slot_a, h->d_aev, h->d_h1,
+                  h->nl.nbr_r, h->nl.cnt_a, h->nl.nbr_a, h->d_aev, h->d_h1,
                   h->d_h2, h->d_z3, h->d_d3, h->d_y, h->d_dG, h->d_atom_e, h->d_status, h->d_w, h->d_b,
                   h->d_w4, h->d_b4, h->d_maps, h->d_work, h->d_pos_in, h->d_E, h->d_F};
   for (void* p : ptrs)
@@ -255,6 +258,9 @@ void nnp_destroy(nnp_handle h) {
     if (L.d_probs) cudaFree(L.d_probs);
     if (L.d_tiles) cudaFree(L.d_tiles);
   }
+  for (void* p : {(void*)h->cellbuf.cell_of, (void*)h->cellbuf.count, (void*)h->cellbuf.start,
+                  (void*)h->cellbuf.fill, (void*)h->cellbuf.atoms})
+    if (p) cudaFree(p);
   if (h->d_tail_probs) cudaFree(h->d_tail_probs);
   if (h->d_tail_tiles) cudaFree(h->d_tail_tiles);
   delete h;
@@ -283,8 +289,10 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   if (params->precision < 0 || params->precision > 2) return fail(nullptr, NNP_ERR_ARG, "bad precision");
   if (!params->weights || params->n_weights != model_params() * params->n_models)
     return fail(nullptr, NNP_ERR_ARG, "weights: expected n_models * nnp_weights_per_model() floats");
-  for (int r = 0; r < 8; ++r)
+  for (int r = 0; r < 7; ++r)
     if (params->reserved[r] != 0) return fail(nullptr, NNP_ERR_ARG, "reserved fields must be zero");
+  if (params->neighbor_mode < 0 || params->neighbor_mode > 2)
+    return fail(nullptr, NNP_ERR_ARG, "neighbor_mode must be 0, 1 or 2");
   for (int i = 0; i < N; ++i) {
     const int z = Z[i];
     if (!(z == 1 || z == 6 || z == 7 || z == 8 || z == 9 || z == 16 || z == 17))
@@ -404,12 +412,28 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   if (cap_a > 255) cap_a = 256;
   h->nl.cap_r = cap_r;
   h->nl.cap_a = cap_a;
+  {  // cell list for one large periodic region
+    const int mode = params->neighbor_mode;
+    const bool want = mode == 2 || (mode == 0 && n_mols == 1 && N > 1024);
+    if (want && h->aevc.periodic && n_mols == 1 && cell_grid(h->aevc, N, h->cells)) {
+      const int ncell = h->cells.n[0] * h->cells.n[1] * h->cells.n[2];
+      CK(dalloc(&h->cellbuf.cell_of, N));
+      CK(dalloc(&h->cellbuf.count, ncell));
+      CK(dalloc(&h->cellbuf.start, ncell + 1));
+      CK(dalloc(&h->cellbuf.fill, ncell));
+      CK(dalloc(&h->cellbuf.atoms, N));
+      CK(cell_set_smem(cell_smem_bytes(N)));
+      h->use_cells = true;
+    } else if (mode == 2) {
+      return fail(h, NNP_ERR_UNSUPPORTED,
+                  "cell list needs one periodic region of at most 32768 atoms");
+    }
+  }
   CK(dalloc(&h->d_pos, N));
   CK(dalloc(&h->nl.cnt_r, N));
   CK(dalloc(&h->nl.cnt_a, N));
   CK(dalloc(&h->nl.nbr_r, (size_t)N * cap_r));
   CK(dalloc(&h->nl.nbr_a, (size_t)N * cap_a));
-  CK(dalloc(&h->nl.slot_a, (size_t)N * cap_a));
 
   // ---- activations ----
   const size_t es = elem_size(h->prec);
@@ -779,8 +803,13 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
   mark(0);
   if (F && h->n_atoms) cudaMemsetAsync(F, 0, sizeof(double) * 3 * (size_t)h->n_atoms, s);
   launch_gather_positions(pos, h->d_orig, h->d_pos, h->n_atoms, h->d_status, s);
-  launch_neighbors(g, h->nl, h->aevc, h->d_status, s);
-  kernels += 2;
+  if (h->use_cells) {
+    launch_neighbors_cells(g, h->nl, h->aevc, h->cells, h->cellbuf, h->n_atoms, h->d_status, s);
+    kernels += 5;  // gather, bin count, scan, fill, neighbours
+  } else {
+    launch_neighbors(g, h->nl, h->aevc, h->d_status, s);
+    kernels += 2;
+  }
   mark(1);
   launch_aev(g, h->nl, h->aevc, h->d_row_of_int, h->d_aev, h->prec, h->fwd_warps, s);
   ++kernels;
@@ -894,7 +923,7 @@ nnp_status nnp_compute_timed(nnp_handle h, const float* pos, double* E, double* 
 
 int32_t nnp_kernels_per_step(nnp_handle h, int32_t with_forces) {
   if (!h) return -1;
-  int k = 2 + 1 + 1;  // gather, neighbours, features, energy
+  int k = (h->use_cells ? 5 : 2) + 1 + 1;  // gather (+ cell binning), neighbours, features, energy
   k += h->L[0].tiles.empty() ? 0 : 1;
   if (h->prec == Prec::F32) {
     k += 1;  // head

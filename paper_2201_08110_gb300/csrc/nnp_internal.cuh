@@ -79,9 +79,24 @@ struct NeighborLists {
   int* nbr_r;   // [N][cap_r] internal indices, ascending
   int* cnt_a;   // [N]
   int* nbr_a;   // [N][cap_a] internal indices, ascending (subset of the radial list)
-  int* slot_a;  // [N][cap_a] position of the angular neighbour in the radial list
   int cap_r, cap_a;
 };
+
+// Cell list of one periodic region.
+constexpr int kCellMaxAtoms = 32768;  // bitmask compaction limit (8 KB of masks per warp)
+struct CellGrid {
+  int n[3];  // cells per dimension, edge = box / n > Rcr
+};
+struct CellBuffers {
+  int* cell_of;  // [N]
+  int* count;    // [ncell]
+  int* start;    // [ncell + 1]
+  int* fill;     // [ncell]
+  int* atoms;    // [N] atoms grouped by cell
+};
+bool cell_grid(const AevConst& c, int region_atoms, CellGrid& cg);
+size_t cell_smem_bytes(int region_atoms);
+cudaError_t cell_set_smem(size_t bytes);
 
 // Element precision of the network activations and operands.
 enum class Prec { F32 = 0, BF16 = 1, F16 = 2 };
@@ -142,6 +157,9 @@ void launch_gather_positions(const float* pos_caller, const int* orig_of_int, fl
                              int n, unsigned* status, cudaStream_t s);
 void launch_neighbors(const Geometry& g, const NeighborLists& nl, const AevConst& c,
                       unsigned* status, cudaStream_t s);
+void launch_neighbors_cells(const Geometry& g, const NeighborLists& nl, const AevConst& c,
+                            const CellGrid& cg, const CellBuffers& cb, int region_atoms,
+                            unsigned* status, cudaStream_t s);
 void launch_aev(const Geometry& g, const NeighborLists& nl, const AevConst& c,
                 const int* row_of_int, void* aev_out, Prec out_prec, int warps_per_cta,
                 cudaStream_t s);

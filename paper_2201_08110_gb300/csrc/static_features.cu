@@ -10,7 +10,7 @@
 // kernels, keeping every intermediate (positions, neighbour lists, padded
 // feature rows) in one fixed scratch array in device global memory, declared
 // at file scope below.  The array is part of the library image: every GPU that
-// loads the library holds it (about 2 MB) until the process exits.
+// loads the library holds it (about 1.6 MB) until the process exits.
 //
 // The caller passes the inputs and the output buffer.  All calls on a device
 // share the one scratch array and it keeps the last call's contents, so calls
@@ -40,7 +40,6 @@ struct StaticScratch {
   int cnt_a[kStaticMax];
   int nbr_r[kStaticMax * kStaticCap];
   int nbr_a[kStaticMax * kStaticCap];
-  int slot_a[kStaticMax * kStaticCap];
   float aev[kStaticMax * kFeaturesPad];
   unsigned bad_input;     // an atomic number outside the set, or a non-finite position
   unsigned list_status;   // neighbour-list flags (cannot overflow at this capacity)
@@ -155,7 +154,6 @@ extern "C" nnp_status nnp_features_static(const int32_t* Z_dev, const float* pos
   nl.nbr_r = p->nbr_r;
   nl.cnt_a = p->cnt_a;
   nl.nbr_a = p->nbr_a;
-  nl.slot_a = p->slot_a;
   nl.cap_r = kStaticCap;
   nl.cap_a = kStaticCap;
   launch_neighbors(g, nl, c, &p->list_status, s);

@@ -46,7 +46,8 @@ class Params(ctypes.Structure):
                 ("weights", ctypes.c_void_p), ("n_weights", ctypes.c_int64),
                 ("box", ctypes.c_double * 3), ("total_charge", ctypes.c_int32),
                 ("max_neighbors", ctypes.c_int32), ("max_angular", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
+                ("use_graph", ctypes.c_int32), ("neighbor_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 _lib = None
@@ -117,7 +118,7 @@ class NNP:
 
     def __init__(self, Z, weights, n_models: int, mol_off=None, precision: str = "fp32",
                  box=None, max_neighbors: int = 0, max_angular: int = 0,
-                 use_graph: bool = False, total_charge: int = 0):
+                 use_graph: bool = False, total_charge: int = 0, neighbor_mode: int = 0):
         self._lib = load_library()
         Z = np.ascontiguousarray(Z, dtype=np.int32)
         if mol_off is None:
@@ -136,6 +137,7 @@ class NNP:
         p.max_neighbors = int(max_neighbors)
         p.max_angular = int(max_angular)
         p.use_graph = 1 if use_graph else 0
+        p.neighbor_mode = int(neighbor_mode)
         h = ctypes.c_void_p()
         rc = self._lib.nnp_create_batch(Z.ctypes.data, mol_off.ctypes.data, mol_off.shape[0] - 1,
                                         ctypes.byref(p), ctypes.byref(h))

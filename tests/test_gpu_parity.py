@@ -47,17 +47,24 @@ def small_batch():
 
 # --- neighbour search ---------------------------------------------------------
 
-@pytest.mark.parametrize("case", ["cfg1", "batch", "periodic"])
+@pytest.mark.parametrize("case", ["cfg1", "batch", "periodic", "periodic_cells", "pocket_cells"])
 def test_pair_and_triple_sets_are_identical(lib, case):
+    """All-pairs search (molecules, small periodic region) and the cell list
+    (2 cells per side in a 14 A box, 4 per side in the 24.7 A pocket)."""
+    kw = {}
     if case == "cfg1":
         b, w, M = W.config1()
     elif case == "batch":
         b = small_batch()
         w, M = W.weights(5, 1), 1
+    elif case == "pocket_cells":
+        b = W.pocket(W.workload_seed(5) + 2)  # 1500 atoms: the cell list by default
+        w, M = W.weights(5, 1), 1
     else:
         b = W.pocket(9, n=250, edge=14.0)
         w, M = W.weights(5, 1), 1
-    model, _, _ = run(lib, b, w, M)
+        kw = {"neighbor_mode": 2} if case == "periodic_cells" else {"neighbor_mode": 1}
+    model, _, _ = run(lib, b, w, M, **kw)
     for kind, rc in ((0, RCR), (1, RCA)):
         counts, lists = model.neighbors(kind)
         counts, lists = counts.cpu().numpy(), lists.cpu().numpy()
