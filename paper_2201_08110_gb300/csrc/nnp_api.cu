@@ -37,9 +37,6 @@ struct Layer {
 
 size_t elem_size(Prec p) { return p == Prec::F32 ? 4 : 2; }
 
-// Rows of the weight operand's TMA box per layer (the largest N of the layer):
-// L1 fwd, L2 fwd, L3 fwd, L3 rev, L2 rev, L1 rev.
-constexpr int kTcBoxRows[6] = {256, kH2Max, kH3Max, kH2Max, kH1Max, 256};
 
 }  // namespace
 
@@ -85,7 +82,12 @@ struct nnp_ctx {
   // reverse pass work list
   int4* d_work = nullptr;
   int n_work = 0;
-  int fwd_warps = 4, adj_warps = 4, smem_atoms_max = 0;
+  int fwd_warps = 4, adj_warps = 4, adj_chunk = 0, smem_atoms_max = 0;
+  int l1_bn = 256;                  // N tile of the first layer's products (tensor cores)
+  int tc_box[6] = {256, kH2Max, kH3Max, kH2Max, kH1Max, 256};  // weight-box rows per layer
+  std::vector<int> mol_off_h;
+  const void* l1_b_base[2] = {nullptr, nullptr};  // W1, W1T (tensor-core maps of layers 0, 5)
+  uint64_t l1_b_rows[2] = {0, 0}, l1_b_cols[2] = {0, 0};
   // host-buffer entry point
   float* d_pos_in = nullptr;
   double *d_E = nullptr, *d_F = nullptr;
@@ -234,6 +236,73 @@ namespace nnp {
 // The featurizer constants, for other translation units of the library.
 void aev_constants(AevConst& c, const double box[3]) { init_aev_const(c, box); }
 }  // namespace nnp
+
+namespace {
+
+// Reverse-pass work list: (molecule, chunk of centres) items, largest first,
+// and the per-warp shared-memory accumulator limit for the given warps per CTA.
+nnp_status build_work_list(nnp_ctx* h, int warps, int chunk) {
+  const size_t budget = 160 * 1024;
+  const size_t fixed = aev_adj_smem_bytes(h->nl.cap_r, h->nl.cap_a, warps, 0);
+  int smax = 0;
+  if (fixed < budget) smax = (int)std::min<size_t>((budget - fixed) / ((size_t)warps * 24), 1 << 20);
+  smax = std::min(smax, h->max_mol);
+  smax = (smax / 2) * 2;
+  std::vector<int4> work;
+  std::vector<long> cost;
+  const int n_mols = h->n_mols;
+  for (int m = 0; m < n_mols; ++m) {
+    const int a0 = h->mol_off_h[m], n = h->mol_off_h[m + 1] - a0;
+    for (int c0 = 0; c0 < n; c0 += chunk) {
+      work.push_back(make_int4(a0, n, a0 + c0, a0 + std::min(n, c0 + chunk)));
+      cost.push_back((long)std::min(chunk, n - c0) * n);
+    }
+  }
+  std::vector<int> order(work.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<int4> sorted(work.size());
+  for (size_t i = 0; i < order.size(); ++i) sorted[i] = work[order[i]];
+  if (h->d_work) cudaFree(h->d_work);
+  h->d_work = nullptr;
+  CK(dalloc(&h->d_work, sorted.size()));
+  if (!sorted.empty())
+    CK(cudaMemcpy(h->d_work, sorted.data(), sizeof(int4) * sorted.size(), cudaMemcpyHostToDevice));
+  h->n_work = (int)sorted.size();
+  h->smem_atoms_max = smax;
+  h->adj_warps = warps;
+  h->adj_chunk = chunk;
+  CK(aev_set_smem_limits(0, aev_adj_smem_bytes(h->nl.cap_r, h->nl.cap_a, warps, smax)));
+  return NNP_OK;
+}
+
+// Tiles (and, on tensor cores, the weight maps) of the first layer's two
+// products for an N tile of bn columns.
+nnp_status set_l1_tiles(nnp_ctx* h, int bn) {
+  for (int layer : {0, 5}) {
+    Layer& L = h->L[layer];
+    L.tiles.clear();
+    for (int pi = 0; pi < (int)L.probs.size(); ++pi) {
+      const GemmProblem& P = L.probs[pi];
+      for (int m0 = 0; m0 < P.M; m0 += 128)
+        for (int n0 = 0; n0 < P.N; n0 += bn) L.tiles.push_back(GemmTile{pi, m0, n0, 0});
+    }
+    if (L.d_tiles) cudaFree(L.d_tiles);
+    L.d_tiles = nullptr;
+    CK(dalloc(&L.d_tiles, L.tiles.size()));
+    if (!L.tiles.empty())
+      CK(cudaMemcpy(L.d_tiles, L.tiles.data(), sizeof(GemmTile) * L.tiles.size(), cudaMemcpyHostToDevice));
+    const int i = layer == 0 ? 0 : 1;
+    if (!tc_make_map(h->tc_maps[layer] + tc_maps_bytes() / 2, h->l1_b_base[i], h->prec, h->l1_b_rows[i],
+                     h->l1_b_cols[i], h->l1_b_cols[i], (uint32_t)bn))
+      return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the first layer");
+    h->tc_box[layer] = bn;
+  }
+  h->l1_bn = bn;
+  return NNP_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -671,10 +740,16 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
                           {wb + h->w_off[4] * es, rows_w2t, ld_w2t},
                           {wb + h->w_off[5] * es, (uint64_t)kSpecies * kFeaturesPad, ld_w1t}};
     const size_t half = tc_maps_bytes() / 2;
+    h->l1_b_base[0] = B[0].base;
+    h->l1_b_rows[0] = B[0].rows;
+    h->l1_b_cols[0] = B[0].cols;
+    h->l1_b_base[1] = B[5].base;
+    h->l1_b_rows[1] = B[5].rows;
+    h->l1_b_cols[1] = B[5].cols;
     for (int l = 0; l < 6; ++l) {
       if (!tc_make_map(h->tc_maps[l], A[l].base, h->prec, A[l].rows, A[l].cols, A[l].cols, 128) ||
           !tc_make_map(h->tc_maps[l] + half, B[l].base, h->prec, B[l].rows, B[l].cols, B[l].cols,
-                       kTcBoxRows[l]))
+                       (uint32_t)h->tc_box[l]))
         return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for layer " + std::to_string(l));
     }
     CK(tc_set_smem());
@@ -735,38 +810,13 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
       CK(cudaMemcpy(L.d_tiles, L.tiles.data(), sizeof(GemmTile) * L.tiles.size(), cudaMemcpyHostToDevice));
   }
 
-  // ---- reverse-pass work list (molecule, centre chunk), largest first ----
+  h->mol_off_h.assign(mol_offsets, mol_offsets + n_mols + 1);
+  h->adj_chunk = N >= 152 * 64 ? 8 * h->adj_warps : h->adj_warps;
   {
-    const size_t budget = 160 * 1024;
-    const int warps = h->adj_warps;
-    const size_t fixed = aev_adj_smem_bytes(cap_r, cap_a, warps, 0);
-    int smax = 0;
-    if (fixed < budget) smax = (int)std::min<size_t>((budget - fixed) / ((size_t)warps * 24), 1 << 20);
-    smax = std::min(smax, h->max_mol);
-    smax = (smax / 2) * 2;
-    h->smem_atoms_max = smax;
-    const int chunk = N >= 152 * 64 ? 8 * warps : warps;
-    std::vector<int4> work;
-    std::vector<long> cost;
-    for (int m = 0; m < n_mols; ++m) {
-      const int a0 = mol_offsets[m], n = mol_offsets[m + 1] - a0;
-      for (int c0 = 0; c0 < n; c0 += chunk) {
-        work.push_back(make_int4(a0, n, a0 + c0, a0 + std::min(n, c0 + chunk)));
-        cost.push_back((long)std::min(chunk, n - c0) * n);
-      }
-    }
-    std::vector<int> order(work.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-    std::vector<int4> sorted(work.size());
-    for (size_t i = 0; i < order.size(); ++i) sorted[i] = work[order[i]];
-    h->n_work = (int)sorted.size();
-    CK(dalloc(&h->d_work, sorted.size()));
-    if (!sorted.empty())
-      CK(cudaMemcpy(h->d_work, sorted.data(), sizeof(int4) * sorted.size(), cudaMemcpyHostToDevice));
+    const nnp_status st = build_work_list(h, h->adj_warps, h->adj_chunk);
+    if (st != NNP_OK) return st;
   }
-  CK(aev_set_smem_limits(aev_fwd_smem_bytes(cap_r, cap_a, h->fwd_warps),
-                         aev_adj_smem_bytes(cap_r, cap_a, h->adj_warps, h->smem_atoms_max)));
+  CK(aev_set_smem_limits(aev_fwd_smem_bytes(cap_r, cap_a, h->fwd_warps), 0));
   CK(cudaDeviceSynchronize());
   guard.ok = true;
   *out = h;
@@ -783,7 +833,7 @@ void run_gemm(nnp_ctx* h, int layer, cudaStream_t s) {
   if (h->prec == Prec::F32)
     launch_gemm_simt(L.d_probs, L.d_tiles, (int)L.tiles.size(), s);
   else
-    launch_gemm_tc(L.d_probs, L.d_tiles, (int)L.tiles.size(), h->prec, kTcBoxRows[layer],
+    launch_gemm_tc(L.d_probs, L.d_tiles, (int)L.tiles.size(), h->prec, h->tc_box[layer],
                    h->tc_maps[layer], h->d_status, s);
 }
 
@@ -935,6 +985,88 @@ int32_t nnp_kernels_per_step(nnp_handle h, int32_t with_forces) {
   }
   if (with_forces) k += 1 + (h->L[5].tiles.empty() ? 0 : 1);  // L1 reverse, featurizer reverse
   return k;
+}
+
+nnp_status nnp_autotune(nnp_handle h, const float* pos, void* stream, int32_t* chosen) {
+  if (!h || (!pos && h->n_atoms)) return NNP_ERR_ARG;
+  if (h->n_atoms == 0) return NNP_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* dE = nullptr;
+  double* dF = nullptr;
+  CK(dalloc(&dE, h->n_mols));
+  CK(dalloc(&dF, 3 * (size_t)h->n_atoms));
+  float ms[NNP_NUM_STAGES];
+  auto time_stages = [&](int a, int b) -> float {  // median of 3 of stages [a, b]
+    float t[3];
+    for (int r = 0; r < 3; ++r) {
+      if (nnp_compute_timed(h, pos, dE, dF, stream, ms, NNP_NUM_STAGES) != NNP_OK) return 1e30f;
+      t[r] = 0.f;
+      for (int k = a; k <= b; ++k) t[r] += ms[k];
+    }
+    std::sort(t, t + 3);
+    return t[1];
+  };
+  nnp_status st = NNP_OK;
+  // featurizer: atoms (warps) per CTA
+  {
+    int best = h->fwd_warps;
+    float best_t = 1e30f;
+    for (int w : {2, 4, 8}) {
+      if (aev_set_smem_limits(aev_fwd_smem_bytes(h->nl.cap_r, h->nl.cap_a, w), 0) != cudaSuccess) continue;
+      h->fwd_warps = w;
+      const float t = time_stages(NNP_STAGE_FEATURES, NNP_STAGE_FEATURES);
+      if (t < best_t) {
+        best_t = t;
+        best = w;
+      }
+    }
+    h->fwd_warps = best;
+  }
+  // reverse pass: warps per CTA and centres per work item
+  {
+    int bw = h->adj_warps, bc = h->adj_chunk;
+    float best_t = 1e30f;
+    for (int w : {2, 4, 8})
+      for (int mult : {1, 4, 8}) {
+        if (build_work_list(h, w, mult * w) != NNP_OK) continue;
+        const float t = time_stages(NNP_STAGE_ADJOINT, NNP_STAGE_ADJOINT);
+        if (t < best_t) {
+          best_t = t;
+          bw = w;
+          bc = mult * w;
+        }
+      }
+    st = build_work_list(h, bw, bc);
+  }
+  // first layer: N tile of the tensor-core products
+  if (st == NNP_OK && h->prec != Prec::F32) {
+    int best = h->l1_bn;
+    float best_t = 1e30f;
+    for (int bn : {256, 128}) {
+      if (set_l1_tiles(h, bn) != NNP_OK) continue;
+      const float t = time_stages(NNP_STAGE_L1_FWD, NNP_STAGE_L1_FWD) +
+                      time_stages(NNP_STAGE_L1_REV, NNP_STAGE_L1_REV);
+      if (t < best_t) {
+        best_t = t;
+        best = bn;
+      }
+    }
+    st = set_l1_tiles(h, best);
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(dE);
+  cudaFree(dF);
+  if (h->gexec) {  // the schedule changed: capture again on next use
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  if (chosen) {
+    chosen[0] = h->fwd_warps;
+    chosen[1] = h->adj_warps;
+    chosen[2] = h->adj_chunk;
+    chosen[3] = h->l1_bn;
+  }
+  return st;
 }
 
 nnp_status nnp_compute_host(nnp_handle h, const float* pos, double* E, double* F, void* stream) {

@@ -139,27 +139,36 @@ __global__ void k_head(const float* __restrict__ z3, long ldz, const int* __rest
   if (lane == 0) y[(size_t)row * n_models + m] = acc + b4[e * kMaxModels + m];
 }
 
-// E_mol = sum over the molecule's atoms of (1/M) sum_m y_m, FP64.
-// One warp per molecule; also stores the per-atom ensemble means.
-__global__ void k_energy(const float* __restrict__ y, int n_models, const int* __restrict__ row_of_int,
-                         const int* __restrict__ mol_off, int n_mols, double* __restrict__ E,
-                         double* __restrict__ atom_e) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= n_mols) return;
-  const int a0 = mol_off[warp], a1 = mol_off[warp + 1];
+// E_mol = sum over the molecule's atoms of (1/M) sum_m y_m, FP64.  One CTA
+// per molecule, fixed reduction order (deterministic); also stores the
+// per-atom ensemble means.
+constexpr int kEnergyThreads = 128;
+__global__ void __launch_bounds__(kEnergyThreads)
+    k_energy(const float* __restrict__ y, int n_models, const int* __restrict__ row_of_int,
+             const int* __restrict__ mol_off, int n_mols, double* __restrict__ E,
+             double* __restrict__ atom_e) {
+  __shared__ double part[kEnergyThreads / 32];
+  const int m = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int a0 = mol_off[m], a1 = mol_off[m + 1];
   double sum = 0.0;
-  for (int q = a0 + lane; q < a1; q += 32) {
+  for (int q = a0 + threadIdx.x; q < a1; q += kEnergyThreads) {
     const int row = row_of_int[q];
     double e = 0.0;
-    for (int m = 0; m < n_models; ++m) e += (double)y[(size_t)row * n_models + m];
+    for (int k = 0; k < n_models; ++k) e += (double)y[(size_t)row * n_models + k];
     e /= n_models;
     if (atom_e) atom_e[row] = e;
     sum += e;
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-  if (lane == 0) E[warp] = sum;
+  if (lane == 0) part[warp] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kEnergyThreads / 32; ++w) t += part[w];
+    E[m] = t;
+  }
 }
 
 __global__ void k_export_neighbors(const int* __restrict__ cnt, const int* __restrict__ nbr, int cap,
@@ -241,8 +250,7 @@ void launch_head(const float* z3, long ldz, Prec prec, const int* row_elem, cons
 void launch_energy(const float* y, int n_models, const int* row_of_int, const int* mol_off,
                    int n_mols, double* E, double* atom_e, cudaStream_t s) {
   if (n_mols <= 0) return;
-  const int threads = 128, blocks = (n_mols * 32 + threads - 1) / threads;
-  k_energy<<<blocks, threads, 0, s>>>(y, n_models, row_of_int, mol_off, n_mols, E, atom_e);
+  k_energy<<<n_mols, kEnergyThreads, 0, s>>>(y, n_models, row_of_int, mol_off, n_mols, E, atom_e);
 }
 
 void launch_export_neighbors(const NeighborLists& nl, int kind, const int* orig, int n,

@@ -28,7 +28,7 @@ EXPORTS = ("nnp_weights_per_model", "nnp_num_features", "nnp_create", "nnp_creat
            "nnp_compute", "nnp_compute_host", "nnp_get_status", "nnp_last_error", "nnp_destroy",
            "nnp_get_capacity", "nnp_get_neighbors", "nnp_get_features",
            "nnp_get_atomic_energies", "nnp_compute_timed", "nnp_kernels_per_step",
-           "nnp_features_static")
+           "nnp_features_static", "nnp_autotune")
 STATIC_MAX_ATOMS = 256
 STAGES = ("neighbors", "features", "l1_fwd", "l2_fwd", "l3_fwd", "energy", "l3_rev", "l2_rev",
           "l1_rev", "adjoint")
@@ -91,6 +91,8 @@ def load_library(path: str = LIB_PATH):
     lib.nnp_compute_timed.restype = ctypes.c_int
     lib.nnp_kernels_per_step.argtypes = [P, I32]
     lib.nnp_kernels_per_step.restype = I32
+    lib.nnp_autotune.argtypes = [P, P, P, P]
+    lib.nnp_autotune.restype = ctypes.c_int
     lib.nnp_features_static.argtypes = [P, P, I32, P, P]
     lib.nnp_features_static.restype = ctypes.c_int
     _lib = lib
@@ -202,6 +204,13 @@ class NNP:
                                                 _ptr(forces_out), _stream_ptr(stream), ms,
                                                 len(STAGES)))
         return dict(zip(STAGES, list(ms)))
+
+    def autotune(self, positions, stream=None) -> dict:
+        """Time candidate schedules on these positions and keep the fastest."""
+        out = (ctypes.c_int32 * 4)()
+        self._check(self._lib.nnp_autotune(self._h, _ptr(positions), _stream_ptr(stream), out))
+        return {"featurizer_warps": out[0], "reverse_warps": out[1],
+                "reverse_centres_per_item": out[2], "first_layer_n_tile": out[3]}
 
     def kernels_per_step(self, forces: bool = True) -> int:
         return int(self._lib.nnp_kernels_per_step(self._h, 1 if forces else 0))

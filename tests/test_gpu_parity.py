@@ -304,3 +304,18 @@ def test_pocket_and_dense_molecules(lib, prec):
     check_batch(prec, E, F, dense, oracle_batch(dense, w, M))
     ca, _ = model.neighbors(1)
     print(f"dense molecules: max angular neighbours {int(ca.max())} of capacity {model.capacity()[1]}")
+
+
+def test_autotuner_keeps_results_and_picks_valid_schedule(lib):
+    b, w, M = small_batch(), W.weights(6, 8), 8
+    for prec in ("fp32", "fp16"):
+        model, E0, F0 = run(lib, b, w, M, prec, use_graph=True)
+        pos = torch.tensor(b.pos, device="cuda")
+        chosen = model.autotune(pos)
+        assert chosen["featurizer_warps"] in (2, 4, 8) and chosen["reverse_warps"] in (2, 4, 8)
+        assert chosen["first_layer_n_tile"] in (128, 256)
+        E, F = model.compute(pos)
+        torch.cuda.synchronize()
+        model.status()
+        np.testing.assert_allclose(E.cpu().numpy(), E0, rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(F.cpu().numpy(), F0, rtol=1e-6, atol=1e-9)
