@@ -204,12 +204,13 @@ int32_t nnp_kernels_per_step(nnp_handle h, int32_t with_forces);
 
 /* Autotuner: times candidate schedules on the given DEVICE positions (as for
  * nnp_compute) and keeps the fastest: atoms (warps) per CTA of the featurizer
- * {2, 4, 8}; warps per CTA {2, 4, 8} and centres per work item of the
- * featurizer's reverse pass; the N tile {256, 128} of the first layer's
- * tensor-core products.  Synchronises `stream`, allocates and frees scratch
- * for the outputs, and drops a captured graph (captured again on next use).
- * chosen: HOST int32[4] or NULL, receives (featurizer warps, reverse warps,
- * reverse centres per item, first-layer N tile). */
+ * {2, 4, 8}; warps per CTA {2, 4}, centres per work item and force
+ * accumulation (FP64 in shared memory per molecule, or FP64 atomics in global
+ * memory) of the featurizer's reverse pass; the N tile {256, 128} of the first
+ * layer's tensor-core products.  Synchronises `stream`, allocates and frees
+ * scratch for the outputs, and drops a captured graph (captured again on next
+ * use).  chosen: HOST int32[5] or NULL, receives (featurizer warps, reverse
+ * warps, reverse centres per item, first-layer N tile, shared accumulators). */
 nnp_status nnp_autotune(nnp_handle h, const float* positions_dev, void* stream, int32_t* chosen);
 
 /* ---- allocation-free entry point -----------------------------------------------

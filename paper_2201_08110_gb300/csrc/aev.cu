@@ -388,7 +388,7 @@ __device__ __forceinline__ void add_force(double* acc_w, int local, const int* o
 // accumulators in shared memory
 // (the lanes of a chunk that share the first neighbour are reduced by a
 // segmented scan first), then to the warp's FP64 accumulator of the molecule.
-__global__ void k_aev_adjoint(Geometry g, NeighborLists nl, AevConst c,
+__global__ void __launch_bounds__(128, 6) k_aev_adjoint(Geometry g, NeighborLists nl, AevConst c,
                               const int* __restrict__ row_of_int, const float* __restrict__ dG,
                               const int4* __restrict__ work, const int* __restrict__ orig,
                               double* __restrict__ F, int smem_atoms_max) {

@@ -82,7 +82,7 @@ struct nnp_ctx {
   // reverse pass work list
   int4* d_work = nullptr;
   int n_work = 0;
-  int fwd_warps = 4, adj_warps = 4, adj_chunk = 0, smem_atoms_max = 0;
+  int fwd_warps = 4, adj_warps = 4, adj_chunk = 0, adj_shared_acc = 1, smem_atoms_max = 0;
   int l1_bn = 256;                  // N tile of the first layer's products (tensor cores)
   int tc_box[6] = {256, kH2Max, kH3Max, kH2Max, kH1Max, 256};  // weight-box rows per layer
   std::vector<int> mol_off_h;
@@ -241,13 +241,17 @@ namespace {
 
 // Reverse-pass work list: (molecule, chunk of centres) items, largest first,
 // and the per-warp shared-memory accumulator limit for the given warps per CTA.
-nnp_status build_work_list(nnp_ctx* h, int warps, int chunk) {
+// shared_acc: 1 = per-warp FP64 accumulators of the molecule in shared
+// memory (molecules that fit), 0 = FP64 atomics straight into the forces.
+nnp_status build_work_list(nnp_ctx* h, int warps, int chunk, int shared_acc = 1) {
   const size_t budget = 160 * 1024;
   const size_t fixed = aev_adj_smem_bytes(h->nl.cap_r, h->nl.cap_a, warps, 0);
   int smax = 0;
-  if (fixed < budget) smax = (int)std::min<size_t>((budget - fixed) / ((size_t)warps * 24), 1 << 20);
+  if (shared_acc && fixed < budget)
+    smax = (int)std::min<size_t>((budget - fixed) / ((size_t)warps * 24), 1 << 20);
   smax = std::min(smax, h->max_mol);
   smax = (smax / 2) * 2;
+  h->adj_shared_acc = shared_acc;
   std::vector<int4> work;
   std::vector<long> cost;
   const int n_mols = h->n_mols;
@@ -1024,19 +1028,21 @@ nnp_status nnp_autotune(nnp_handle h, const float* pos, void* stream, int32_t* c
   }
   // reverse pass: warps per CTA and centres per work item
   {
-    int bw = h->adj_warps, bc = h->adj_chunk;
+    int bw = h->adj_warps, bc = h->adj_chunk, bs = h->adj_shared_acc;
     float best_t = 1e30f;
-    for (int w : {2, 4, 8})
-      for (int mult : {1, 4, 8}) {
-        if (build_work_list(h, w, mult * w) != NNP_OK) continue;
-        const float t = time_stages(NNP_STAGE_ADJOINT, NNP_STAGE_ADJOINT);
-        if (t < best_t) {
-          best_t = t;
-          bw = w;
-          bc = mult * w;
+    for (int sh : {1, 0})
+      for (int w : {2, 4})
+        for (int mult : {1, 4, 8}) {
+          if (build_work_list(h, w, mult * w, sh) != NNP_OK) continue;
+          const float t = time_stages(NNP_STAGE_ADJOINT, NNP_STAGE_ADJOINT);
+          if (t < best_t) {
+            best_t = t;
+            bw = w;
+            bc = mult * w;
+            bs = sh;
+          }
         }
-      }
-    st = build_work_list(h, bw, bc);
+    st = build_work_list(h, bw, bc, bs);
   }
   // first layer: N tile of the tensor-core products
   if (st == NNP_OK && h->prec != Prec::F32) {
@@ -1065,6 +1071,7 @@ nnp_status nnp_autotune(nnp_handle h, const float* pos, void* stream, int32_t* c
     chosen[1] = h->adj_warps;
     chosen[2] = h->adj_chunk;
     chosen[3] = h->l1_bn;
+    chosen[4] = h->adj_shared_acc;
   }
   return st;
 }

@@ -207,10 +207,11 @@ class NNP:
 
     def autotune(self, positions, stream=None) -> dict:
         """Time candidate schedules on these positions and keep the fastest."""
-        out = (ctypes.c_int32 * 4)()
+        out = (ctypes.c_int32 * 5)()
         self._check(self._lib.nnp_autotune(self._h, _ptr(positions), _stream_ptr(stream), out))
         return {"featurizer_warps": out[0], "reverse_warps": out[1],
-                "reverse_centres_per_item": out[2], "first_layer_n_tile": out[3]}
+                "reverse_centres_per_item": out[2], "first_layer_n_tile": out[3],
+                "reverse_shared_accumulators": out[4]}
 
     def kernels_per_step(self, forces: bool = True) -> int:
         return int(self._lib.nnp_kernels_per_step(self._h, 1 if forces else 0))
