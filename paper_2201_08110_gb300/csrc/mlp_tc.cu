@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const GemmTile tl = tiles[tile];
         const GemmProblem P = probs[tl.problem];  // by value: asm memory clobbers force reloads of references
         const int nkb = (P.K + kBK - 1) / kBK;
-        const int n_tile = min(kBNMax, P.N - tl.n0);
+        const int n_tile = min(b_box_rows, P.N - tl.n0);  // tile width = weight-box rows
         const uint32_t idesc = instr_desc(Pack<T>::fmt, (uint32_t)n_tile);
         const uint32_t acc = tcount & 1, use = tcount >> 1;
         bool ok = use == 0 || mbar_wait(&tempty[acc], (use - 1) & 1, abort_flag);
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tcount) {
       const GemmTile tl = tiles[tile];
       const GemmProblem P = probs[tl.problem];  // by value: asm memory clobbers force reloads of references
-      const int n_tile = min(kBNMax, P.N - tl.n0);
+      const int n_tile = min(b_box_rows, P.N - tl.n0);  // tile width = weight-box rows
       const uint32_t acc = tcount & 1, use = tcount >> 1;
       const bool got = mbar_wait(&tfull[acc], use & 1, abort_flag);
       if (!__all_sync(0xffffffffu, got)) {  // the warp leaves together (tcgen05.ld is .sync.aligned)
