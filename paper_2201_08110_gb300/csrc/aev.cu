@@ -137,6 +137,19 @@ __host__ __device__ constexpr int aev_fwd_warp_floats(int cap_r, int cap_a) {
 
 constexpr float kLog2e = 1.4426950408889634f;
 
+// The SFU base-2 exponential and logarithm, denormals flushed to zero (values
+// below 2^-126 only ever multiply other factors here).
+__device__ __forceinline__ float ex2_ftz(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_ftz(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Species pair (s, t), s <= t, of each of the 28 blocks, row-major upper triangle.
 __constant__ unsigned char kBlkS[kPairBlocks] = {0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 2,
                                                  2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 5, 5, 6};
@@ -258,7 +271,7 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
     float* acc = R2 + half * kRadial;
     for (int t = half; t < nr; t += 2) {
       const float x = rd[t] - shf;
-      acc[rsp[t] * kShfR + k] += 0.25f * exp2f(eta * x * x) * rfc[t];
+      acc[rsp[t] * kShfR + k] += 0.25f * ex2_ftz(eta * x * x) * rfc[t];
     }
   }
   __syncwarp();
@@ -315,12 +328,12 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
 #pragma unroll
       for (int a = 0; a < kShfA; ++a) {
         const float x = u - c.ShfA[a];
-        buf[a * kBufStride + lane] = exp2f(etaA * x * x);
+        buf[a * kBufStride + lane] = ex2_ftz(etaA * x * x);
       }
 #pragma unroll
       for (int z = 0; z < kShfZ; ++z) {
         const float bb = fmaxf(0.5f * (1.f + cp * c.cosZ[z] + sp * c.sinZ[z]), 0.f);
-        buf[(kShfA + z) * kBufStride + lane] = exp2f(c.Zeta * __log2f(bb)) * fcjk;
+        buf[(kShfA + z) * kBufStride + lane] = ex2_ftz(c.Zeta * lg2_ftz(bb)) * fcjk;
       }
       pl = b;
     }
@@ -342,8 +355,18 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
         acc = 0.f;
         pcur = p;
       }
-#pragma unroll 4
-      for (int t = t0; t < t1; ++t) acc = fmaf(ra[t], za[t], acc);
+      // 16-byte loads over the aligned middle of the run
+      int t = t0;
+      for (; t < t1 && (t & 3); ++t) acc = fmaf(ra[t], za[t], acc);
+      for (; t + 4 <= t1; t += 4) {
+        const float4 r4 = *reinterpret_cast<const float4*>(ra + t);
+        const float4 z4 = *reinterpret_cast<const float4*>(za + t);
+        acc = fmaf(r4.x, z4.x, acc);
+        acc = fmaf(r4.y, z4.y, acc);
+        acc = fmaf(r4.z, z4.z, acc);
+        acc = fmaf(r4.w, z4.w, acc);
+      }
+      for (; t < t1; ++t) acc = fmaf(ra[t], za[t], acc);
     }
     __syncwarp();
   }
@@ -481,7 +504,7 @@ __global__ void __launch_bounds__(128, 6) k_aev_adjoint(Geometry g, NeighborList
 #pragma unroll
         for (int k = 0; k < kShfR; ++k) {
           const float x = r - c.ShfR[k];
-          const float e = exp2f(etaR * x * x);
+          const float e = ex2_ftz(etaR * x * x);
           dEdr = fmaf(gsp[k] * 0.25f * e, fmaf(-2.f * c.EtaR * x, fc, dfc), dEdr);
         }
         const float s = dEdr / r;
@@ -515,16 +538,16 @@ __global__ void __launch_bounds__(128, 6) k_aev_adjoint(Geometry g, NeighborList
 #pragma unroll
         for (int z = 0; z < kShfZ; ++z) {
           const float bb = fmaxf(0.5f * (1.f + cp * c.cosZ[z] + sp * c.sinZ[z]), 0.f);
-          const float L = __log2f(bb);
-          A[z] = 2.f * exp2f(c.Zeta * L);
+          const float L = lg2_ftz(bb);
+          A[z] = 2.f * ex2_ftz(c.Zeta * L);
           // dA/dcp = 2 Zeta b^(Zeta-1) db/dcp,  db/dcp = (cosZ - cp/sp sinZ) / 2
-          dA[z] = c.Zeta * exp2f((c.Zeta - 1.f) * L) * (c.cosZ[z] - cp / sp * c.sinZ[z]);
+          dA[z] = c.Zeta * ex2_ftz((c.Zeta - 1.f) * L) * (c.cosZ[z] - cp / sp * c.sinZ[z]);
         }
         float V = 0.f, dVdc = 0.f, dVdu = 0.f;
 #pragma unroll
         for (int a = 0; a < kShfA; ++a) {
           const float x = u - c.ShfA[a];
-          const float R = exp2f(etaA * x * x);
+          const float R = ex2_ftz(etaA * x * x);
           const float4 g4 = gp[a];  // g[a][0..3]
           const float SA = fmaf(g4.x, A[0], fmaf(g4.y, A[1], fmaf(g4.z, A[2], g4.w * A[3])));
           const float SdA = fmaf(g4.x, dA[0], fmaf(g4.y, dA[1], fmaf(g4.z, dA[2], g4.w * dA[3])));
