@@ -16,8 +16,12 @@
 //
 // Roles (persistent CTA per SM over the tile list):
 //   warp 0, one lane: TMA producer (h1 tile, then W2, W3, W3^T, W2^T blocks);
-//   warp 1, one lane: tcgen05.mma issuer, one accumulator, four phases/tile;
-//   warps 2-5: epilogue of each phase (TMEM lane quarter = warp % 4).
+//   warp 1, one lane: tcgen05.mma issuer; the four phases of a tile alternate
+//     between two 256-column accumulators, and K block b of a phase waits
+//     only until the epilogue has written block b of its A operand, so a
+//     phase's MMAs overlap the previous phase's epilogue;
+//   warps 2-9: epilogue, 64 columns at a time (TMEM lane quarter = warp % 4,
+//     32 columns per warp), signalling each finished block.
 // Waits are bounded: one that gives up sets the timeout status bit, the CTA
 // stops, frees its tensor memory and returns.
 #include <cstring>
@@ -39,10 +43,10 @@ constexpr int kA1Blocks = 4;                 // h1 (<= 256 columns); d3 reuses i
 constexpr int kA2Blocks = 3;                 // h2, then d2 (<= 192 columns)
 constexpr int kEpiWarps = 8;   // two per TMEM lane quarter, each half of the columns
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr int kTmemCols = 256;
+constexpr int kTmemCols = 512;  // two accumulators of 256 columns
 constexpr size_t kSmemBytes =
     (size_t)(kA1Blocks + kA2Blocks) * kBlk + (size_t)kRing * kRingBytes + 1024 + 256 +
-    (kH2Max + 2 * kH3Max + 128) * sizeof(float);
+    (kH2Max + 3 * kH3Max + 128) * sizeof(float);
 
 struct TailMaps {
   CUtensorMap h1;   // activations [rows][M*256], box 64 x 128
@@ -70,27 +74,6 @@ __device__ __forceinline__ bool produce_weights(const CUtensorMap* map, int row0
   return true;
 }
 
-// One layer's MMAs: D[128][n] (+)= A[128][k] * B[n][k]^T, A in smem blocks at
-// a_base (16 KB per 64 columns), B from the ring.
-__device__ __forceinline__ bool issue_layer(uint32_t tmem, const unsigned char* a_base, int k, int n,
-                                            uint32_t fmt, unsigned char* ring, uint64_t* full,
-                                            uint64_t* empty, uint32_t& it, const int* abort_flag) {
-  const uint32_t idesc = instr_desc(fmt, (uint32_t)n);
-  const int n_kb = nblocks(k);
-  for (int kb = 0; kb < n_kb; ++kb, ++it) {
-    const int s = it % kRing;
-    if (!mbar_wait(&full[s], (it / kRing) & 1, abort_flag)) return false;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint64_t da = smem_desc_sw128(a_base + (size_t)kb * kBlk);
-    const uint64_t db = smem_desc_sw128(ring + (size_t)s * kRingBytes);
-    const int ksteps = min(kBK, k - kb * kBK) / 16;
-    for (int j = 0; j < ksteps; ++j)
-      mma_f16(tmem, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc, (kb > 0 || j > 0) ? 1u : 0u);
-    mma_commit(&empty[s]);
-  }
-  return true;
-}
-
 __device__ __forceinline__ void st_shared_v4(unsigned char* base, uint32_t off, uint4 v) {
   *reinterpret_cast<uint4*>(base + off) = v;
 }
@@ -113,9 +96,20 @@ __device__ __forceinline__ void get16(const unsigned char* blocks, int r, int c,
   o[4] = y.x; o[5] = y.y; o[6] = y.z; o[7] = y.w;
 }
 
-template <typename T>
-__device__ __forceinline__ float dcelu_from_act(float h) {  // celu'(z) = 1 + h/alpha for z <= 0
-  return h > 0.f ? 1.f : fmaf(10.f, h, 1.f);
+// celu'(z) from h = celu(z), alpha = 0.1: 1 + h / alpha for z <= 0, where it
+// is at most 1, and 1 for z > 0, where 1 + h / alpha exceeds 1.
+__device__ __forceinline__ float dcelu_from_act(float h) { return fminf(fmaf(10.f, h, 1.f), 1.f); }
+
+// 16 consecutive floats of shared memory (64-byte aligned).
+__device__ __forceinline__ void ld_shared16(const float* p, float (&v)[16]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float4 q = reinterpret_cast<const float4*>(p)[i];
+    v[4 * i] = q.x;
+    v[4 * i + 1] = q.y;
+    v[4 * i + 2] = q.z;
+    v[4 * i + 3] = q.w;
+  }
 }
 
 template <typename T>
@@ -124,8 +118,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                const GemmTile* __restrict__ tiles, int n_tiles, int reverse,
                unsigned* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // rounded up to 1024 bytes by pointer arithmetic, so that accesses through
+  // it stay shared-memory accesses
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* A1 = smem;                              // h1, later d3
   unsigned char* A2 = A1 + kA1Blocks * kBlk;             // h2, later d2
   unsigned char* ring = A2 + kA2Blocks * kBlk;
@@ -133,14 +128,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* empty = full + kRing;
   uint64_t* a1_full = empty + kRing;
   uint64_t* a1_free = a1_full + 1;
-  uint64_t* acc_ready = a1_free + 1;
-  uint64_t* epi_done = acc_ready + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(epi_done + 1);
+  uint64_t* acc_ready = a1_free + 1;  // [2] MMA -> epilogue, per accumulator
+  uint64_t* acc_free = acc_ready + 2;  // [2] epilogue -> MMA: accumulator drained
+  uint64_t* blk_done = acc_free + 2;   // [4] epilogue -> MMA: 64-column block of the next A written
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(blk_done + 4);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   float* sb2 = reinterpret_cast<float*>(smem + (kA1Blocks + kA2Blocks) * kBlk + kRing * kRingBytes + 256);
-  float* sb3 = sb2 + kH2Max;   // per-tile copies of b2, b3, w4
+  float* sb3 = sb2 + kH2Max;   // per-tile copies of b2, b3, w4 and w4 / M
   float* sw4 = sb3 + kH3Max;
-  float* ypart = sw4 + kH3Max;  // [128] second half of each row's output-layer dot
+  float* sw4m = sw4 + kH3Max;
+  float* ypart = sw4m + kH3Max;  // [128] second half of each row's output-layer dot
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t fmt = Pack<T>::fmt;
@@ -152,8 +149,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     mbar_init(a1_full, 1);
     mbar_init(a1_free, 1);
-    mbar_init(acc_ready, 1);
-    mbar_init(epi_done, kEpiWarps);  // one arrival per epilogue warp
+    for (int x = 0; x < 2; ++x) {
+      mbar_init(&acc_ready[x], 1);
+      mbar_init(&acc_free[x], kEpiWarps);
+    }
+    for (int b = 0; b < 4; ++b) mbar_init(&blk_done[b], kEpiWarps);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x, ++tcount) {
         const GemmTile tl = tiles[tile];
-        const TailProblem P = probs[tl.problem];  // by value: asm memory clobbers force reloads of references
+        const TailProblem P = probs[tl.problem];
         if (tcount > 0 && !mbar_wait(a1_free, (tcount - 1) & 1, abort_flag)) {
           ok = false;
           break;
@@ -198,43 +198,62 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // ---- MMA issuer ----
-      uint32_t it = 0, tcount = 0, u_epi = 0;
+      // ---- MMA issuer: phases alternate between the two accumulators; a
+      // phase's K block b waits only for block b of its A operand ----
+      uint32_t it = 0, tcount = 0;
+      uint32_t used[2] = {0, 0};       // phases issued per accumulator
+      uint32_t blk_waits[4] = {0, 0, 0, 0};
       bool ok = true;
-      auto wait_epi = [&]() {
-        if (ok && !mbar_wait(epi_done, u_epi & 1, abort_flag)) ok = false;
-        ++u_epi;
+      auto phase = [&](int x, const unsigned char* a_base, int k, int n, bool wait_blocks) {
+        if (!ok) return;
+        if (used[x] > 0 && !mbar_wait(&acc_free[x], (used[x] - 1) & 1, abort_flag)) {
+          ok = false;
+          return;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t idesc = instr_desc(fmt, (uint32_t)n);
+        const uint32_t d = tmem + (uint32_t)(x * kTmemCols / 2);
+        const int n_kb = nblocks(k);
+        for (int kb = 0; kb < n_kb; ++kb, ++it) {
+          if (wait_blocks) {
+            if (!mbar_wait(&blk_done[kb], blk_waits[kb] & 1, abort_flag)) {
+              ok = false;
+              return;
+            }
+            ++blk_waits[kb];
+          }
+          const int s = it % kRing;
+          if (!mbar_wait(&full[s], (it / kRing) & 1, abort_flag)) {
+            ok = false;
+            return;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t da = smem_desc_sw128(a_base + (size_t)kb * kBlk);
+          const uint64_t db = smem_desc_sw128(ring + (size_t)s * kRingBytes);
+          const int ksteps = min(kBK, k - kb * kBK) / 16;
+          for (int j = 0; j < ksteps; ++j)
+            mma_f16(d, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc, (kb > 0 || j > 0) ? 1u : 0u);
+          mma_commit(&empty[s]);
+        }
+        mma_commit(&acc_ready[x]);
+        ++used[x];
       };
       for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x, ++tcount) {
         const GemmTile tl = tiles[tile];
-        const TailProblem P = probs[tl.problem];  // by value: asm memory clobbers force reloads of references
+        const TailProblem P = probs[tl.problem];
         if (!mbar_wait(a1_full, tcount & 1, abort_flag)) {
           ok = false;
           break;
         }
-        if (tcount > 0) wait_epi();  // previous tile's last epilogue: TMEM free
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        ok = ok && issue_layer(tmem, A1, P.h1, P.h2, fmt, ring, full, empty, it, abort_flag);
-        if (!ok) break;
-        mma_commit(acc_ready);  // L2 forward
-        wait_epi();             // h2 in A2
-        ok = ok && issue_layer(tmem, A2, P.h2, P.h3, fmt, ring, full, empty, it, abort_flag);
-        if (!ok) break;
-        mma_commit(acc_ready);  // L3 forward
+        phase(0, A1, P.h1, P.h2, false);  // L2 forward
+        phase(1, A2, P.h2, P.h3, true);   // L3 forward, block by block of h2
         if (!reverse) {
-          mma_commit(a1_free);
+          if (ok) mma_commit(a1_free);
           continue;
         }
-        wait_epi();  // d3 in A1
-        ok = ok && issue_layer(tmem, A1, P.h3, P.h2, fmt, ring, full, empty, it, abort_flag);
-        if (!ok) break;
-        mma_commit(acc_ready);  // L3 reverse
-        mma_commit(a1_free);
-        wait_epi();  // d2 in A2
-        ok = ok && issue_layer(tmem, A2, P.h2, P.h1, fmt, ring, full, empty, it, abort_flag);
-        if (!ok) break;
-        mma_commit(acc_ready);  // L2 reverse
+        phase(0, A1, P.h3, P.h2, true);  // L3 reverse, block by block of d3
+        if (ok) mma_commit(a1_free);     // d3 (over h1) consumed once these MMAs finish
+        phase(1, A2, P.h2, P.h1, true);  // L2 reverse, block by block of d2
       }
       if (!ok) {
         atomicOr(status, kStatTimeout);
@@ -246,30 +265,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int quarter = warp & 3, half = (warp - 2) >> 2;
     const int et = threadIdx.x - 64;  // 0..255 over the epilogue warps
     const int r = quarter * 32 + lane;  // tile row = TMEM lane
-    const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16);
-    uint32_t u_acc = 0;
+    const uint32_t tq = (uint32_t)(quarter * 32) << 16;
+    uint32_t ready_waits[2] = {0, 0};
     bool ok = true;
-    auto wait_acc = [&]() -> bool {
-      if (ok && !mbar_wait(acc_ready, u_acc & 1, abort_flag)) {
+    auto wait_acc = [&](int x) -> uint32_t {  // TMEM address of accumulator x for this warp
+      if (ok && !mbar_wait(&acc_ready[x], ready_waits[x] & 1, abort_flag)) {
         atomicOr(status, kStatTimeout);
         atomicExch(abort_flag, 1);
         ok = false;
       }
       ok = __all_sync(0xffffffffu, ok);  // the warp's tcgen05.ld calls stay converged
-      ++u_acc;
+      ++ready_waits[x];
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      return ok;
+      return tmem + (uint32_t)(x * kTmemCols / 2) + tq;
     };
-    auto done = [&]() {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // smem writes -> tensor cores
+    auto arrive = [&](uint64_t* bar) {  // after shared-memory writes and TMEM reads
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(epi_done);
+      if (lane == 0) mbar_arrive(bar);
     };
     auto epi_sync = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory"); };
-    // barrier of the epilogue warps that also agrees on stopping: true if any
-    // of them failed a wait or another role aborted (no warp ever leaves the
-    // tile loop between two barriers, so none is left waiting at one)
     auto epi_stop = [&]() -> bool {
       const int in = (!ok || *(volatile int*)abort_flag) ? 1 : 0;
       int res;
@@ -281,11 +297,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           : "memory");
       return res != 0;
     };
-    // the two warps of a quarter (named barriers 2..5, 64 threads)
     auto pair_sync = [&]() { asm volatile("bar.sync %0, 64;" ::"r"(2 + quarter) : "memory"); };
+    // columns of block b handled by this warp: [b*64 + half*32, ... + 32) clipped to n
+    auto my_cols = [&](int b, int n, int& c0, int& c1) {
+      c0 = b * kBK + half * 32;
+      c1 = min(c0 + 32, n);
+    };
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
       const GemmTile tl = tiles[tile];
-      const TailProblem P = probs[tl.problem];  // by value: asm memory clobbers force reloads of references
+      const TailProblem P = probs[tl.problem];
       const int row = tl.m0 + r;
       const bool row_ok = row < P.Me;
       if (epi_stop()) break;  // also: previous tile's readers of sb2/sb3/sw4/ypart are done
@@ -293,79 +313,96 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int i = et; i < P.h3; i += 32 * kEpiWarps) {
         sb3[i] = P.b3[i];
         sw4[i] = P.w4[i];
+        sw4m[i] = P.w4[i] * P.inv_m;
       }
       epi_sync();
 
-      // L2 forward: h2 = celu(acc + b2) -> A2
+      // phase 1, L2 forward (accumulator 0): h2 = celu(acc + b2) -> A2, block by block
       {
-        const int n2 = P.h2 >> 1, c0 = half * n2;
-        wait_acc();
-        for (int c = c0; ok && c < c0 + n2; c += 16) {
-          float v[16];
-          tmem_ld16(tbase + (uint32_t)c, v);
-          uint32_t o[8];
+        const uint32_t t = wait_acc(0);
+        for (int b = 0; b < nblocks(P.h2); ++b) {
+          int c0, c1;
+          my_cols(b, P.h2, c0, c1);
+          for (int c = c0; ok && c < c1; c += 16) {
+            float v[16];
+            tmem_ld16(t + (uint32_t)c, v);
+            float bias[16];
+            ld_shared16(sb2 + c, bias);
+            uint32_t o[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            o[i] = Pack<T>::two(celu01_fast(v[2 * i] + sb2[c + 2 * i]),
-                                celu01_fast(v[2 * i + 1] + sb2[c + 2 * i + 1]));
-          put16(A2, r, c, o);
+            for (int i = 0; i < 8; ++i)
+              o[i] = Pack<T>::two(celu01_fast(v[2 * i] + bias[2 * i]),
+                                  celu01_fast(v[2 * i + 1] + bias[2 * i + 1]));
+            put16(A2, r, c, o);
+          }
+          arrive(&blk_done[b]);
         }
-        done();
+        arrive(&acc_free[0]);
       }
 
-      // L3 forward + output layer: y, d3 -> A1
+      // phase 2, L3 forward + output layer (accumulator 1): y, d3 -> A1
       {
-        const int n3 = P.h3 >> 1, c0 = half * n3;
-        wait_acc();
+        const uint32_t t = wait_acc(1);
         float yacc = 0.f;
-        for (int c = c0; ok && c < c0 + n3; c += 16) {
-          float v[16];
-          tmem_ld16(tbase + (uint32_t)c, v);
-          uint32_t o[8];
+        for (int b = 0; b < nblocks(P.h3); ++b) {
+          int c0, c1;
+          my_cols(b, P.h3, c0, c1);
+          for (int c = c0; ok && c < c1; c += 16) {
+            float v[16];
+            tmem_ld16(t + (uint32_t)c, v);
+            float b3[16], w4[16], w4m[16];
+            ld_shared16(sb3 + c, b3);
+            ld_shared16(sw4 + c, w4);
+            ld_shared16(sw4m + c, w4m);
+            uint32_t o[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            float dv[2];
+            for (int i = 0; i < 8; ++i) {
+              float dv[2];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int cc = c + 2 * i + h;
-              const float z = v[2 * i + h] + sb3[cc];
-              const float ex = expf(fminf(z, 0.f) * 10.f);  // exp(z / alpha), alpha = 0.1
-              const float act = z > 0.f ? z : 0.1f * (ex - 1.f);
-              const float w = sw4[cc];
-              yacc = fmaf(w, act, yacc);
-              dv[h] = w * (z > 0.f ? 1.f : ex) * P.inv_m;
+              for (int h = 0; h < 2; ++h) {
+                const int k = 2 * i + h;
+                const float z = v[k] + b3[k];
+                const float ex = celu01_exp(z);  // celu'(z): 1 above zero
+                yacc = fmaf(w4[k], fmaxf(z, fmaf(0.1f, ex, -0.1f)), yacc);
+                dv[h] = w4m[k] * ex;
+              }
+              o[i] = Pack<T>::two(dv[0], dv[1]);
             }
-            o[i] = Pack<T>::two(dv[0], dv[1]);
+            if (reverse) put16(A1, r, c, o);
           }
-          if (reverse) put16(A1, r, c, o);
+          if (reverse) arrive(&blk_done[b]);
         }
         if (half) ypart[r] = yacc;
         pair_sync();
         if (ok && !half && row_ok) P.y[(size_t)row * P.ldy] = yacc + ypart[r] + P.b4;
-        done();
+        arrive(&acc_free[1]);
       }
       if (!reverse) continue;
 
-      // L3 reverse: d2 = acc * celu'(h2), in place in A2
+      // phase 3, L3 reverse (accumulator 0): d2 = acc * celu'(h2), in place in A2
       {
-        const int n2 = P.h2 >> 1, c0 = half * n2;
-        wait_acc();
-        for (int c = c0; ok && c < c0 + n2; c += 16) {
-          float v[16];
-          tmem_ld16(tbase + (uint32_t)c, v);
-          uint32_t hin[8], o[8];
-          get16(A2, r, c, hin);
+        const uint32_t t = wait_acc(0);
+        for (int b = 0; b < nblocks(P.h2); ++b) {
+          int c0, c1;
+          my_cols(b, P.h2, c0, c1);
+          for (int c = c0; ok && c < c1; c += 16) {
+            float v[16];
+            tmem_ld16(t + (uint32_t)c, v);
+            uint32_t hin[8], o[8];
+            get16(A2, r, c, hin);
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            o[i] = Pack<T>::two(v[2 * i] * dcelu_from_act<T>(Pack<T>::lo(hin[i])),
-                                v[2 * i + 1] * dcelu_from_act<T>(Pack<T>::hi(hin[i])));
-          put16(A2, r, c, o);
+            for (int i = 0; i < 8; ++i)
+              o[i] = Pack<T>::two(v[2 * i] * dcelu_from_act(Pack<T>::lo(hin[i])),
+                                  v[2 * i + 1] * dcelu_from_act(Pack<T>::hi(hin[i])));
+            put16(A2, r, c, o);
+          }
+          arrive(&blk_done[b]);
         }
-        done();
+        arrive(&acc_free[0]);
       }
 
-      // L2 reverse: d1 = acc * celu'(h1) -> global, over h1 (h1 prefetched
-      // before the wait, while the last MMAs run)
+      // phase 4, L2 reverse (accumulator 1): d1 = acc * celu'(h1) -> global, over
+      // h1 (this warp's half of the columns, prefetched before the wait)
       {
         const int n1 = P.h1 >> 1, c0 = half * n1;  // <= 128 columns: 8 chunks
         T* hrow = static_cast<T*>(P.h1g) + (size_t)row * P.ldh1;
@@ -379,26 +416,26 @@ __global__ void __launch_bounds__(kThreads, 1)
             hv[2 * i + 1] = src[1];
           }
         }
-        wait_acc();
+        const uint32_t t = wait_acc(1);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int c = c0 + 16 * i;
           if (!ok || c >= c0 + n1) break;
           float v[16];
-          tmem_ld16(tbase + (uint32_t)c, v);
+          tmem_ld16(t + (uint32_t)c, v);
           if (!row_ok) continue;
           const uint32_t hin[8] = {hv[2 * i].x, hv[2 * i].y, hv[2 * i].z, hv[2 * i].w,
                                    hv[2 * i + 1].x, hv[2 * i + 1].y, hv[2 * i + 1].z, hv[2 * i + 1].w};
           uint32_t o[8];
 #pragma unroll
           for (int k = 0; k < 8; ++k)
-            o[k] = Pack<T>::two(v[2 * k] * dcelu_from_act<T>(Pack<T>::lo(hin[k])),
-                                v[2 * k + 1] * dcelu_from_act<T>(Pack<T>::hi(hin[k])));
+            o[k] = Pack<T>::two(v[2 * k] * dcelu_from_act(Pack<T>::lo(hin[k])),
+                                v[2 * k + 1] * dcelu_from_act(Pack<T>::hi(hin[k])));
           uint4* dst = reinterpret_cast<uint4*>(hrow + c);
           dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
           dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
         }
-        done();
+        arrive(&acc_free[1]);
       }
     }
   }

@@ -54,11 +54,12 @@ __device__ __forceinline__ void epilogue_chunk(const GemmProblem& P, int row, in
                                                const float (&v)[16], float& head_acc) {
   switch (P.epi) {
     case (int)Epi::BiasCelu: {
+      float b[16];
+      ldg16(P.bias + n, b);
       uint32_t o[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i)
-        o[i] = Pack<T>::two(celu01(v[2 * i] + P.bias[n + 2 * i]),
-                            celu01(v[2 * i + 1] + P.bias[n + 2 * i + 1]));
+        o[i] = Pack<T>::two(celu01_fast(v[2 * i] + b[2 * i]), celu01_fast(v[2 * i + 1] + b[2 * i + 1]));
       uint4* d = reinterpret_cast<uint4*>(static_cast<T*>(P.D) + (size_t)row * P.ldd + n);
       d[0] = make_uint4(o[0], o[1], o[2], o[3]);
       d[1] = make_uint4(o[4], o[5], o[6], o[7]);
@@ -73,11 +74,10 @@ __device__ __forceinline__ void epilogue_chunk(const GemmProblem& P, int row, in
         for (int h = 0; h < 2; ++h) {
           const int c = n + 2 * i + h;
           const float z = v[2 * i + h] + P.bias[c];
-          const float ex = expf(fminf(z, 0.f) * 10.f);  // exp(z / alpha), alpha = 0.1
-          const float act = z > 0.f ? z : 0.1f * (ex - 1.f);
+          const float ex = celu01_exp(z);  // celu'(z): 1 above zero
           const float w = P.w4[c];
-          head_acc = fmaf(w, act, head_acc);
-          dv[h] = w * (z > 0.f ? 1.f : ex) * P.inv_m;
+          head_acc = fmaf(w, fmaxf(z, fmaf(0.1f, ex, -0.1f)), head_acc);
+          dv[h] = w * ex * P.inv_m;
         }
         o[i] = Pack<T>::two(dv[0], dv[1]);
       }
@@ -102,8 +102,9 @@ __device__ __forceinline__ void epilogue_chunk(const GemmProblem& P, int row, in
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const float ha = Pack<T>::lo(hin[i]), hb = Pack<T>::hi(hin[i]);
-        const float ga = ha > 0.f ? 1.f : fmaf(10.f, ha, 1.f);  // celu' from celu, alpha 0.1
-        const float gb = hb > 0.f ? 1.f : fmaf(10.f, hb, 1.f);
+        // celu' from celu (alpha 0.1): 1 + h / alpha below zero, where it is <= 1
+        const float ga = fminf(fmaf(10.f, ha, 1.f), 1.f);
+        const float gb = fminf(fmaf(10.f, hb, 1.f), 1.f);
         o[i] = Pack<T>::two(v[2 * i] * ga, v[2 * i + 1] * gb);
       }
       d[0] = make_uint4(o[0], o[1], o[2], o[3]);
@@ -282,8 +283,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
             const float ha = Pack<T>::lo(hin[k]), hb = Pack<T>::hi(hin[k]);
-            const float ga = ha > 0.f ? 1.f : fmaf(10.f, ha, 1.f);  // celu' from celu, alpha 0.1
-            const float gb = hb > 0.f ? 1.f : fmaf(10.f, hb, 1.f);
+            const float ga = fminf(fmaf(10.f, ha, 1.f), 1.f);  // celu' from celu, alpha 0.1
+            const float gb = fminf(fmaf(10.f, hb, 1.f), 1.f);
             o[k] = Pack<T>::two(v[2 * k] * ga, v[2 * k + 1] * gb);
           }
           uint4* d = reinterpret_cast<uint4*>(static_cast<T*>(P.D) + (size_t)row * P.ldd + tl.n0 + c);

@@ -137,10 +137,6 @@ template <> struct Pack<__half> {
   static constexpr uint32_t fmt = 0;
 };
 
-__device__ __forceinline__ float celu01(float z) {
-  return z > 0.f ? z : 0.1f * (expf(fminf(z, 0.f) * 10.f) - 1.f);
-}
-
 
 // 32 consecutive FP32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
@@ -160,9 +156,35 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// CELU (alpha = 0.1) with the SFU exponential, for results rounded to 16 bits.
+// 16 consecutive floats of global memory, read-only for the kernel's lifetime
+// (64-byte aligned: every bias and output-layer weight vector starts at a
+// multiple of 16 floats).
+__device__ __forceinline__ void ldg16(const float* p, float (&v)[16]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p) + i);
+    v[4 * i] = q.x;
+    v[4 * i + 1] = q.y;
+    v[4 * i + 2] = q.z;
+    v[4 * i + 3] = q.w;
+  }
+}
+
+// exp(min(z, 0) / alpha), alpha = 0.1, on the SFU base-2 exponential with
+// denormals flushed to zero (relative error near 2^-22, far below the 16-bit
+// rounding of every value it feeds).  It is CELU's slope for z <= 0 and 1
+// for z > 0.
+__device__ __forceinline__ float celu01_exp(float z) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(fminf(z, 0.f) * 14.426950408889634f));
+  return y;
+}
+
+// CELU (alpha = 0.1) without a branch: max(z, alpha (exp(min(z, 0) / alpha) - 1)).
+// For z > 0 the exponential is ex2(0) = 1 and the second term 0; for z <= 0,
+// alpha (exp(z / alpha) - 1) >= z since exp(u) >= 1 + u.
 __device__ __forceinline__ float celu01_fast(float z) {
-  return z > 0.f ? z : 0.1f * (__expf(fminf(z, 0.f) * 10.f) - 1.f);
+  return fmaxf(z, fmaf(0.1f, celu01_exp(z), -0.1f));
 }
 
 // Byte offset of element (r, c) of a [128 rows][64 cols] block of 16-bit
