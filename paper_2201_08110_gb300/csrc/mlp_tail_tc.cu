@@ -44,9 +44,13 @@ constexpr int kA2Blocks = 3;                 // h2, then d2 (<= 192 columns)
 constexpr int kEpiWarps = 8;   // two per TMEM lane quarter, each half of the columns
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kTmemCols = 512;  // two accumulators of 256 columns
-constexpr size_t kSmemBytes =
-    (size_t)(kA1Blocks + kA2Blocks) * kBlk + (size_t)kRing * kRingBytes + 1024 + 256 +
-    (kH2Max + 3 * kH3Max + 128) * sizeof(float);
+// Phase 4 stages h1 in and d1 out through [kP4Boxes][128 rows][32 cols] boxes
+// (64-byte swizzle) over A2 and the 16 KB after it.
+constexpr uint32_t kP4Box = 128 * 32 * 2;
+constexpr int kP4Boxes = kH1Max / 32;
+static_assert((size_t)kP4Boxes * kP4Box <= (size_t)(kA2Blocks + 1) * kBlk, "phase-4 staging");
+constexpr size_t kSmemBytes = (size_t)(kA1Blocks + kA2Blocks + 1) * kBlk + (size_t)kRing * kRingBytes +
+                              1024 + 256 + 128 * sizeof(float);
 
 struct TailMaps {
   CUtensorMap h1;   // activations [rows][M*256], box 64 x 128
@@ -54,6 +58,7 @@ struct TailMaps {
   CUtensorMap w3;   // [sum h3 rows][192], box 64 x 160
   CUtensorMap w3t;  // [sum h2 rows][160], box 64 x 192
   CUtensorMap w2t;  // [sum h1 rows][192], box 64 x 256
+  CUtensorMap h1s;  // activations again, box 32 x 128, 64-byte swizzle (phase 4 in and out)
 };
 constexpr int kBoxW2 = kH2Max, kBoxW3 = kH3Max, kBoxW3T = kH2Max, kBoxW2T = kH1Max;
 
@@ -100,16 +105,25 @@ __device__ __forceinline__ void get16(const unsigned char* blocks, int r, int c,
 // is at most 1, and 1 for z > 0, where 1 + h / alpha exceeds 1.
 __device__ __forceinline__ float dcelu_from_act(float h) { return fminf(fmaf(10.f, h, 1.f), 1.f); }
 
-// 16 consecutive floats of shared memory (64-byte aligned).
-__device__ __forceinline__ void ld_shared16(const float* p, float (&v)[16]) {
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float4 q = reinterpret_cast<const float4*>(p)[i];
-    v[4 * i] = q.x;
-    v[4 * i + 1] = q.y;
-    v[4 * i + 2] = q.z;
-    v[4 * i + 3] = q.w;
-  }
+// Row r, columns c..c+15 (c a multiple of 16) of the phase-4 tile: box c / 32,
+// 64-byte rows whose 16-byte chunk k sits at position k ^ ((r / 2) % 4), the
+// layout of a TMA box with 64-byte swizzle.
+__device__ __forceinline__ uint32_t p4_offset(int r, int c) {
+  return (uint32_t)(c >> 5) * kP4Box + (uint32_t)(r * 64);
+}
+__device__ __forceinline__ uint32_t p4_chunk(int r, int k) { return (uint32_t)(((k ^ (r >> 1)) & 3) << 4); }
+__device__ __forceinline__ void get16_p4(const unsigned char* p4, int r, int c, uint32_t (&o)[8]) {
+  const unsigned char* b = p4 + p4_offset(r, c);
+  const int k = (c & 31) >> 3;
+  const uint4 x = ld_shared_v4(b, p4_chunk(r, k)), y = ld_shared_v4(b, p4_chunk(r, k + 1));
+  o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
+  o[4] = y.x; o[5] = y.y; o[6] = y.z; o[7] = y.w;
+}
+__device__ __forceinline__ void put16_p4(unsigned char* p4, int r, int c, const uint32_t (&o)[8]) {
+  unsigned char* b = p4 + p4_offset(r, c);
+  const int k = (c & 31) >> 3;
+  st_shared_v4(b, p4_chunk(r, k), make_uint4(o[0], o[1], o[2], o[3]));
+  st_shared_v4(b, p4_chunk(r, k + 1), make_uint4(o[4], o[5], o[6], o[7]));
 }
 
 template <typename T>
@@ -123,7 +137,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* A1 = smem;                              // h1, later d3
   unsigned char* A2 = A1 + kA1Blocks * kBlk;             // h2, later d2
-  unsigned char* ring = A2 + kA2Blocks * kBlk;
+  unsigned char* P4 = A2;  // phase 4: h1 in, d1 out, over A2 and the next 16 KB
+  unsigned char* ring = A2 + (kA2Blocks + 1) * kBlk;
   uint64_t* full = reinterpret_cast<uint64_t*>(ring + kRing * kRingBytes);
   uint64_t* empty = full + kRing;
   uint64_t* a1_full = empty + kRing;
@@ -131,13 +146,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* acc_ready = a1_free + 1;  // [2] MMA -> epilogue, per accumulator
   uint64_t* acc_free = acc_ready + 2;  // [2] epilogue -> MMA: accumulator drained
   uint64_t* blk_done = acc_free + 2;   // [4] epilogue -> MMA: 64-column block of the next A written
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(blk_done + 4);
+  uint64_t* p4_full = blk_done + 4;    // producer -> epilogue: the tile's h1 is in P4
+  uint64_t* a2_free = p4_full + 1;     // MMA -> producer: phase-4 MMAs are done with A2
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(a2_free + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
-  float* sb2 = reinterpret_cast<float*>(smem + (kA1Blocks + kA2Blocks) * kBlk + kRing * kRingBytes + 256);
-  float* sb3 = sb2 + kH2Max;   // per-tile copies of b2, b3, w4 and w4 / M
-  float* sw4 = sb3 + kH3Max;
-  float* sw4m = sw4 + kH3Max;
-  float* ypart = sw4m + kH3Max;  // [128] second half of each row's output-layer dot
+  float* ypart = reinterpret_cast<float*>(ring + kRing * kRingBytes + 256);  // [128] second
+  // half of each row's output-layer dot
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t fmt = Pack<T>::fmt;
@@ -154,6 +168,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&acc_free[x], kEpiWarps);
     }
     for (int b = 0; b < 4; ++b) mbar_init(&blk_done[b], kEpiWarps);
+    mbar_init(p4_full, 1);
+    mbar_init(a2_free, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -174,6 +190,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ---- TMA producer ----
       uint32_t it = 0, tcount = 0;
       bool ok = true;
+      int prev_h1 = 0, prev_col = 0, prev_row = 0;
+      // h1 of this CTA's k-th tile into P4, once its phase-4 MMAs are done with A2
+      auto load_p4 = [&](uint32_t k) -> bool {
+        if (!mbar_wait(a2_free, k & 1, abort_flag)) return false;
+        const int nbox = prev_h1 / 32;
+        mbar_expect_tx(p4_full, (uint32_t)nbox * kP4Box);
+        for (int j = 0; j < nbox; ++j)
+          tma_load_2d(P4 + (size_t)j * kP4Box, &maps.h1s, prev_col + 32 * j, prev_row, p4_full);
+        return true;
+      };
       for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x, ++tcount) {
         const GemmTile tl = tiles[tile];
         const TailProblem P = probs[tl.problem];
@@ -185,12 +211,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_expect_tx(a1_full, (uint32_t)nb1 * kBlk);
         for (int kb = 0; kb < nb1; ++kb)
           tma_load_2d(A1 + (size_t)kb * kBlk, &maps.h1, P.a_col0 + kb * kBK, P.row0 + tl.m0, a1_full);
+        if (reverse && tcount > 0 && !load_p4(tcount - 1)) {
+          ok = false;
+          break;
+        }
+        prev_h1 = P.h1;
+        prev_col = P.a_col0;
+        prev_row = P.row0 + tl.m0;
         ok = produce_weights(&maps.w2, P.w2_row0, nblocks(P.h1), kBoxW2, ring, full, empty, it, abort_flag) &&
              produce_weights(&maps.w3, P.w3_row0, nblocks(P.h2), kBoxW3, ring, full, empty, it, abort_flag);
         if (ok && reverse)
           ok = produce_weights(&maps.w3t, P.w3t_row0, nblocks(P.h3), kBoxW3T, ring, full, empty, it, abort_flag) &&
                produce_weights(&maps.w2t, P.w2t_row0, nblocks(P.h2), kBoxW2T, ring, full, empty, it, abort_flag);
       }
+      if (ok && reverse && tcount > 0) ok = load_p4(tcount - 1);
       if (!ok) {
         atomicOr(status, kStatTimeout);
         atomicExch(abort_flag, 1);
@@ -254,6 +288,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         phase(0, A1, P.h3, P.h2, true);  // L3 reverse, block by block of d3
         if (ok) mma_commit(a1_free);     // d3 (over h1) consumed once these MMAs finish
         phase(1, A2, P.h2, P.h1, true);  // L2 reverse, block by block of d2
+        if (ok) mma_commit(a2_free);     // d2 (A2) consumed once these MMAs finish
       }
       if (!ok) {
         atomicOr(status, kStatTimeout);
@@ -266,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int et = threadIdx.x - 64;  // 0..255 over the epilogue warps
     const int r = quarter * 32 + lane;  // tile row = TMEM lane
     const uint32_t tq = (uint32_t)(quarter * 32) << 16;
-    uint32_t ready_waits[2] = {0, 0};
+    uint32_t ready_waits[2] = {0, 0}, p4_waits = 0;
     bool ok = true;
     auto wait_acc = [&](int x) -> uint32_t {  // TMEM address of accumulator x for this warp
       if (ok && !mbar_wait(&acc_ready[x], ready_waits[x] & 1, abort_flag)) {
@@ -279,8 +314,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       return tmem + (uint32_t)(x * kTmemCols / 2) + tq;
     };
-    auto arrive = [&](uint64_t* bar) {  // after shared-memory writes and TMEM reads
+    // block b of the next A operand written: publish it to the tensor cores
+    auto arrive = [&](uint64_t* bar) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar);
+    };
+    // accumulator drained: order the TMEM loads before the next MMA into it
+    // (no shared-memory hand-off, hence no proxy fence, which would also wait
+    // for this warp's global stores)
+    auto release = [&](uint64_t* bar) {
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(bar);
@@ -308,14 +352,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       const TailProblem P = probs[tl.problem];
       const int row = tl.m0 + r;
       const bool row_ok = row < P.Me;
-      if (epi_stop()) break;  // also: previous tile's readers of sb2/sb3/sw4/ypart are done
-      for (int i = et; i < P.h2; i += 32 * kEpiWarps) sb2[i] = P.b2[i];
-      for (int i = et; i < P.h3; i += 32 * kEpiWarps) {
-        sb3[i] = P.b3[i];
-        sw4[i] = P.w4[i];
-        sw4m[i] = P.w4[i] * P.inv_m;
-      }
-      epi_sync();
+      // the previous tile's d1 store has read P4 (which overlaps A2) before
+      // anyone writes h2 there; the barrier also ends the readers of ypart
+      if (et == 0) bulk_wait_read();
+      if (epi_stop()) break;
 
       // phase 1, L2 forward (accumulator 0): h2 = celu(acc + b2) -> A2, block by block
       {
@@ -327,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             float v[16];
             tmem_ld16(t + (uint32_t)c, v);
             float bias[16];
-            ld_shared16(sb2 + c, bias);
+            ldg16(P.b2 + c, bias);
             uint32_t o[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
@@ -337,7 +377,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           arrive(&blk_done[b]);
         }
-        arrive(&acc_free[0]);
+        release(&acc_free[0]);
       }
 
       // phase 2, L3 forward + output layer (accumulator 1): y, d3 -> A1
@@ -350,10 +390,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int c = c0; ok && c < c1; c += 16) {
             float v[16];
             tmem_ld16(t + (uint32_t)c, v);
-            float b3[16], w4[16], w4m[16];
-            ld_shared16(sb3 + c, b3);
-            ld_shared16(sw4 + c, w4);
-            ld_shared16(sw4m + c, w4m);
+            float b3[16], w4[16];
+            ldg16(P.b3 + c, b3);
+            ldg16(P.w4 + c, w4);
             uint32_t o[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -364,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const float z = v[k] + b3[k];
                 const float ex = celu01_exp(z);  // celu'(z): 1 above zero
                 yacc = fmaf(w4[k], fmaxf(z, fmaf(0.1f, ex, -0.1f)), yacc);
-                dv[h] = w4m[k] * ex;
+                dv[h] = w4[k] * P.inv_m * ex;
               }
               o[i] = Pack<T>::two(dv[0], dv[1]);
             }
@@ -375,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (half) ypart[r] = yacc;
         pair_sync();
         if (ok && !half && row_ok) P.y[(size_t)row * P.ldy] = yacc + ypart[r] + P.b4;
-        arrive(&acc_free[1]);
+        release(&acc_free[1]);
       }
       if (!reverse) continue;
 
@@ -398,46 +437,45 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           arrive(&blk_done[b]);
         }
-        arrive(&acc_free[0]);
+        release(&acc_free[0]);
       }
 
-      // phase 4, L2 reverse (accumulator 1): d1 = acc * celu'(h1) -> global, over
-      // h1 (this warp's half of the columns, prefetched before the wait)
+      // phase 4, L2 reverse (accumulator 1): d1 = acc * celu'(h1), h1 staged in
+      // P4 by TMA and overwritten there by d1, which one thread then stores
+      // with TMA (this warp: half of the columns of its 32 rows)
       {
-        const int n1 = P.h1 >> 1, c0 = half * n1;  // <= 128 columns: 8 chunks
-        T* hrow = static_cast<T*>(P.h1g) + (size_t)row * P.ldh1;
-        uint4 hv[16];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int c = c0 + 16 * i;
-          if (row_ok && c < c0 + n1) {
-            const uint4* src = reinterpret_cast<const uint4*>(hrow + c);
-            hv[2 * i] = src[0];
-            hv[2 * i + 1] = src[1];
-          }
-        }
         const uint32_t t = wait_acc(1);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int c = c0 + 16 * i;
-          if (!ok || c >= c0 + n1) break;
+        if (ok && !mbar_wait(p4_full, p4_waits & 1, abort_flag)) {
+          atomicOr(status, kStatTimeout);
+          atomicExch(abort_flag, 1);
+          ok = false;
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        ++p4_waits;
+        const int n1 = P.h1 >> 1, c0 = half * n1;  // <= 128 columns: 8 chunks
+#pragma unroll 2
+        for (int c = c0; ok && c < c0 + n1; c += 16) {
           float v[16];
           tmem_ld16(t + (uint32_t)c, v);
-          if (!row_ok) continue;
-          const uint32_t hin[8] = {hv[2 * i].x, hv[2 * i].y, hv[2 * i].z, hv[2 * i].w,
-                                   hv[2 * i + 1].x, hv[2 * i + 1].y, hv[2 * i + 1].z, hv[2 * i + 1].w};
-          uint32_t o[8];
+          uint32_t hin[8], o[8];
+          get16_p4(P4, r, c, hin);
 #pragma unroll
           for (int k = 0; k < 8; ++k)
             o[k] = Pack<T>::two(v[2 * k] * dcelu_from_act(Pack<T>::lo(hin[k])),
                                 v[2 * k + 1] * dcelu_from_act(Pack<T>::hi(hin[k])));
-          uint4* dst = reinterpret_cast<uint4*>(hrow + c);
-          dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
-          dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+          put16_p4(P4, r, c, o);
         }
-        arrive(&acc_free[1]);
+        release(&acc_free[1]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        epi_sync();
+        if (et == 0 && ok) {
+          for (int j = 0; j < P.h1 / 32; ++j)
+            tma_store_2d(&maps.h1s, P4 + (size_t)j * kP4Box, P.a_col0 + 32 * j, P.row0 + tl.m0);
+          bulk_commit();
+        }
       }
     }
+    if (et == 0) bulk_wait_all();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();

@@ -347,18 +347,19 @@ size_t tc_maps_bytes() { return sizeof(TcMaps); }
 // 2D tensor map over a row-major [rows][cols] array of 16-bit elements with a
 // 64-column x box_rows box and 128-byte swizzle.  Returns false on failure.
 bool tc_make_map(void* out_map, const void* base, Prec p, uint64_t rows, uint64_t cols,
-                 uint64_t row_stride_elems, uint32_t box_rows) {
+                 uint64_t row_stride_elems, uint32_t box_rows, uint32_t box_cols, bool swizzle64) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   CUtensorMap* m = static_cast<CUtensorMap*>(out_map);
   std::memset(m, 0, sizeof(*m));
   const cuuint64_t dims[2] = {cols, rows};
   const cuuint64_t strides[1] = {row_stride_elems * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)kBK, box_rows};
+  const cuuint32_t box[2] = {box_cols, box_rows};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = fn(m, p == Prec::BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
                         2, const_cast<void*>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        swizzle64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }

@@ -17,8 +17,11 @@ void launch_gemm_tc(const GemmProblem* probs, const GemmTile* tiles, int n_tiles
                     int b_box_rows, const void* maps, unsigned* status, cudaStream_t s);
 bool tc_available();
 size_t tc_maps_bytes();
+// box_cols x box_rows boxes of a [rows][cols] 16-bit matrix; 128-byte swizzle
+// (64-column boxes), or 64-byte swizzle for 32-column boxes
 bool tc_make_map(void* out_map, const void* base, Prec p, uint64_t rows, uint64_t cols,
-                 uint64_t row_stride_elems, uint32_t box_rows);
+                 uint64_t row_stride_elems, uint32_t box_rows, uint32_t box_cols = 64,
+                 bool swizzle64 = false);
 cudaError_t tc_set_smem();
 }  // namespace nnp
 
@@ -74,7 +77,7 @@ struct nnp_ctx {
   CellGrid cells{};
   CellBuffers cellbuf{};
   alignas(64) unsigned char tc_maps[6][256];  // tensor-core path: {A, B} TMA descriptors per layer
-  alignas(64) unsigned char tail_maps[5 * 128];  // fused tail: h1, w2, w3, w3t, w2t
+  alignas(64) unsigned char tail_maps[6 * 128];  // fused tail: h1, w2, w3, w3t, w2t, h1 (32-col boxes)
   std::vector<TailProblem> tail_probs;
   std::vector<GemmTile> tail_tiles;
   TailProblem* d_tail_probs = nullptr;
@@ -780,8 +783,6 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         T.inv_m = 1.0f / (float)M;
         T.y = h->d_y + (size_t)T.row0 * M + m;
         T.ldy = M;
-        T.h1g = H1 + ((size_t)T.row0 * h->ldh1 + (size_t)m * T.h1) * es;
-        T.ldh1 = h->ldh1;
         const int pi = (int)h->tail_probs.size();
         h->tail_probs.push_back(T);
         for (int m0 = 0; m0 < Me; m0 += 128) h->tail_tiles.push_back(GemmTile{pi, m0, 0, 0});
@@ -795,6 +796,9 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
       if (!tc_make_map(h->tail_maps + 128 * (i + 1), TW[i].base, h->prec, TW[i].rows, TW[i].cols,
                        TW[i].cols, (uint32_t)tail_weight_box(i)))
         return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the fused tail");
+    if (!tc_make_map(h->tail_maps + 5 * 128, h->d_h1, h->prec, R64, (uint64_t)h->ldh1, (uint64_t)h->ldh1,
+                     128, 32, true))
+      return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the fused tail");
     CK(tail_set_smem());
     CK(dalloc(&h->d_tail_probs, h->tail_probs.size()));
     CK(dalloc(&h->d_tail_tiles, h->tail_tiles.size()));

@@ -142,8 +142,6 @@ struct TailProblem {
   float b4, inv_m;
   float* y;     // y + row0 * M + member, stride ldy
   long ldy;
-  void* h1g;    // h1 (then d1) of row0, column a_col0; row stride ldh1 elements
-  long ldh1;
 };
 
 // A tile of the flattened problem list.

@@ -11,7 +11,9 @@
 namespace nnp {
 namespace tc {
 
-constexpr long long kSpinLimit = 1ll << 26;  // try_wait polls before a wait gives up
+// A wait gives up after kWaitLimitNs of device time (or kPollLimit polls).
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+constexpr long long kPollLimit = 1ll << 26;
 constexpr int kBM = 128;                     // MMA rows (atoms)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -32,12 +34,27 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Bounded wait for the phase with the given parity; false if it gave up or
 // another role already aborted.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const int* abort_flag) {
   const uint32_t a = smem_u32(bar);
-  for (long long i = 0; i < kSpinLimit; ++i) {
-    uint32_t done;
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(a), "r"(parity)
+      : "memory");
+  if (done) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (long long i = 0; i < kPollLimit; ++i) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -46,7 +63,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const 
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
-    if ((i & 1023) == 1023 && *(volatile const int*)abort_flag) return false;
+    if ((i & 255) == 255 &&
+        (*(volatile const int*)abort_flag || globaltimer_ns() - t0 > kWaitLimitNs))
+      return false;
   }
   return false;
 }
@@ -186,6 +205,22 @@ __device__ __forceinline__ float celu01_exp(float z) {
 __device__ __forceinline__ float celu01_fast(float z) {
   return fmaxf(z, fmaf(0.1f, celu01_exp(z), -0.1f));
 }
+
+// TMA tile store from shared memory (bulk-group completion) and the waits on
+// this thread's committed stores.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the committed stores have finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// the committed stores are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Byte offset of element (r, c) of a [128 rows][64 cols] block of 16-bit
 // values in the 128-byte-swizzled K-major layout (what a TMA load with
