@@ -20,8 +20,8 @@
 //     between two 256-column accumulators, and K block b of a phase waits
 //     only until the epilogue has written block b of its A operand, so a
 //     phase's MMAs overlap the previous phase's epilogue;
-//   warps 2-9: epilogue, 64 columns at a time (TMEM lane quarter = warp % 4,
-//     32 columns per warp), signalling each finished block.
+//   warps 2-17: epilogue, 64 columns at a time (TMEM lane quarter = warp % 4,
+//     16 columns per warp), signalling each finished block.
 // Waits are bounded: one that gives up sets the timeout status bit, the CTA
 // stops, frees its tensor memory and returns.
 #include <cstring>
@@ -41,7 +41,7 @@ constexpr uint32_t kBlk = 128 * kBK * 2;     // one [128][64] 16-bit block: 16 K
 constexpr uint32_t kRingBytes = 256 * kBK * 2;  // a weight block of up to 256 rows
 constexpr int kA1Blocks = 4;                 // h1 (<= 256 columns); d3 reuses it
 constexpr int kA2Blocks = 3;                 // h2, then d2 (<= 192 columns)
-constexpr int kEpiWarps = 8;   // two per TMEM lane quarter, each half of the columns
+constexpr int kEpiWarps = 16;  // four per TMEM lane quarter, 16 of every 64 columns each
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kTmemCols = 512;  // two accumulators of 256 columns
 // Phase 4 stages h1 in and d1 out through [kP4Boxes][128 rows][32 cols] boxes
@@ -50,7 +50,7 @@ constexpr uint32_t kP4Box = 128 * 32 * 2;
 constexpr int kP4Boxes = kH1Max / 32;
 static_assert((size_t)kP4Boxes * kP4Box <= (size_t)(kA2Blocks + 1) * kBlk, "phase-4 staging");
 constexpr size_t kSmemBytes = (size_t)(kA1Blocks + kA2Blocks + 1) * kBlk + (size_t)kRing * kRingBytes +
-                              1024 + 256 + 128 * sizeof(float);
+                              1024 + 256 + 3 * 128 * sizeof(float);
 
 struct TailMaps {
   CUtensorMap h1;   // activations [rows][M*256], box 64 x 128
@@ -150,8 +150,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* a2_free = p4_full + 1;     // MMA -> producer: phase-4 MMAs are done with A2
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(a2_free + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
-  float* ypart = reinterpret_cast<float*>(ring + kRing * kRingBytes + 256);  // [128] second
-  // half of each row's output-layer dot
+  // [3][128]: the output-layer dot of each row over the column groups 1-3
+  float* ypart = reinterpret_cast<float*>(ring + kRing * kRingBytes + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t fmt = Pack<T>::fmt;
@@ -296,8 +296,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---- epilogue warps 2..9: TMEM lane quarter = warp % 4, column half ----
-    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    // ---- epilogue warps 2..17: TMEM lane quarter = warp % 4, column group ----
+    const int quarter = warp & 3, grp = (warp - 2) >> 2;
     const int et = threadIdx.x - 64;  // 0..255 over the epilogue warps
     const int r = quarter * 32 + lane;  // tile row = TMEM lane
     const uint32_t tq = (uint32_t)(quarter * 32) << 16;
@@ -341,11 +341,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           : "memory");
       return res != 0;
     };
-    auto pair_sync = [&]() { asm volatile("bar.sync %0, 64;" ::"r"(2 + quarter) : "memory"); };
-    // columns of block b handled by this warp: [b*64 + half*32, ... + 32) clipped to n
+    auto quad_sync = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(2 + quarter) : "memory"); };
+    // columns of block b handled by this warp: [b*64 + grp*16, ... + 16) if below n
     auto my_cols = [&](int b, int n, int& c0, int& c1) {
-      c0 = b * kBK + half * 32;
-      c1 = min(c0 + 32, n);
+      c0 = b * kBK + grp * 16;
+      c1 = min(c0 + 16, n);
     };
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
       const GemmTile tl = tiles[tile];
@@ -411,9 +411,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           if (reverse) arrive(&blk_done[b]);
         }
-        if (half) ypart[r] = yacc;
-        pair_sync();
-        if (ok && !half && row_ok) P.y[(size_t)row * P.ldy] = yacc + ypart[r] + P.b4;
+        if (grp) ypart[(grp - 1) * 128 + r] = yacc;
+        quad_sync();
+        if (ok && !grp && row_ok)
+          P.y[(size_t)row * P.ldy] = yacc + ypart[r] + ypart[128 + r] + ypart[256 + r] + P.b4;
         release(&acc_free[1]);
       }
       if (!reverse) continue;
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
       // phase 4, L2 reverse (accumulator 1): d1 = acc * celu'(h1), h1 staged in
       // P4 by TMA and overwritten there by d1, which one thread then stores
-      // with TMA (this warp: half of the columns of its 32 rows)
+      // with TMA (this warp: every fourth 16-column chunk of its 32 rows)
       {
         const uint32_t t = wait_acc(1);
         if (ok && !mbar_wait(p4_full, p4_waits & 1, abort_flag)) {
@@ -452,9 +453,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         ok = __all_sync(0xffffffffu, ok);
         ++p4_waits;
-        const int n1 = P.h1 >> 1, c0 = half * n1;  // <= 128 columns: 8 chunks
-#pragma unroll 2
-        for (int c = c0; ok && c < c0 + n1; c += 16) {
+        for (int c = grp * 16; ok && c < P.h1; c += 64) {
           float v[16];
           tmem_ld16(t + (uint32_t)c, v);
           uint32_t hin[8], o[8];
