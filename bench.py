@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--precision", default="fp16", choices=["fp32", "bf16", "fp16"],
                     help="arithmetic of the networks' matrix products (FP16 meets the stated "
                          "2e-3 energy / 1e-2 force bounds; single-pass BF16 does not on every "
-                         "molecule, see DESIGN.md)")
+                         "molecule: its weight rounding errors add coherently)")
     ap.add_argument("--alt-precision", default="bf16", choices=["none", "fp32", "bf16", "fp16"],
                     help="a second precision timed the same way and reported alongside")
     ap.add_argument("--workload", type=int, default=3, choices=[2, 3, 5],
@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default schedule instead of nnp_autotune's choice")
+    ap.add_argument("--schedule", default=None,
+                    help="pin the schedule instead of autotuning: featurizer warps, reverse "
+                         "warps, reverse centres per item, first-layer N tile, shared "
+                         "accumulators (comma-separated, as autotune reports them)")
     return ap.parse_args()
 
 
@@ -147,7 +151,7 @@ def peaks():
     return 6800.0, 1900.0, 1700.0, "fallback", 2070.0
 
 
-# Algorithmic work per stage ("Algorithmic work per stage").
+# Algorithmic work per stage: operations per unit of work, times the units.
 HID = W.HIDDEN
 # FP32 operations of the featurizer per directed radial pair / unordered
 # angular pair of neighbours (exp2 and log2 counted as one operation each).
@@ -191,9 +195,12 @@ def src_hash(*names):
 
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
-# kernel, keyed by the kernel's source hash at capture time (profiles/ holds the
-# summaries); scaled to the bench workload by atoms.  Empty until captured.
-NCU_TRAFFIC = {}
+# kernel, keyed by the kernel's source hash at capture time, in bytes per atom;
+# scaled to the bench workload by atoms.
+NCU_TRAFFIC = {
+    ("adjoint", "10cf27704530"): 4608.4,  # ncu --set full, 512-molecule batch, FP16
+    ("tail", "721acd50a1e8"): 6416.8,  # ncu --set full, 512-molecule batch, FP16
+}
 
 
 def cpu_oracle_rate(b, w, M, target_s: float = 12.0):
@@ -329,7 +336,11 @@ def run_ours(args):
 
     def make(prec):
         m = nnp.NNP(b.Z, w, M, mol_off=b.mol_off, precision=prec, use_graph=True)
-        if not args.no_autotune:
+        if args.schedule:
+            vals = [int(v) for v in args.schedule.split(",")]
+            schedules[prec] = dict(zip(nnp.NNP.SCHEDULE_KEYS, vals))
+            m.set_schedule(schedules[prec])
+        elif not args.no_autotune:
             schedules[prec] = m.autotune(pos)
         for _ in range(max(3, args.warmup)):
             m.compute(pos, E, F)

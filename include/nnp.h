@@ -213,6 +213,15 @@ int32_t nnp_kernels_per_step(nnp_handle h, int32_t with_forces);
  * warps, reverse centres per item, first-layer N tile, shared accumulators). */
 nnp_status nnp_autotune(nnp_handle h, const float* positions_dev, void* stream, int32_t* chosen);
 
+/* Applies a schedule that nnp_autotune chose earlier (same five values, same
+ * order: featurizer warps per CTA in {2, 4, 8}; reverse warps per CTA in
+ * {2, 4}; reverse centres per work item, a multiple of those warps up to 64;
+ * first-layer N tile in {128, 256}, ignored for FP32; shared accumulators 0
+ * or 1) without timing anything.  schedule: HOST int32[5].  Drops a captured
+ * graph.  NNP_ERR_ARG for a null pointer or a value out of range (nothing
+ * changes then); NNP_ERR_CUDA if a buffer could not be rebuilt. */
+nnp_status nnp_set_schedule(nnp_handle h, const int32_t* schedule);
+
 /* ---- allocation-free entry point -----------------------------------------------
  * The paper has no counterpart: this serves callers that cannot let a library
  * allocate device memory -- an MD engine capturing its whole time step into a

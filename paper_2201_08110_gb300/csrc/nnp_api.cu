@@ -1080,6 +1080,25 @@ nnp_status nnp_autotune(nnp_handle h, const float* pos, void* stream, int32_t* c
   return st;
 }
 
+nnp_status nnp_set_schedule(nnp_handle h, const int32_t* schedule) {
+  if (!h || !schedule) return NNP_ERR_ARG;
+  const int fw = schedule[0], aw = schedule[1], ac = schedule[2], bn = schedule[3], sh = schedule[4];
+  const bool fw_ok = fw == 2 || fw == 4 || fw == 8;
+  const bool adj_ok = (aw == 2 || aw == 4) && ac >= aw && ac <= 64 && ac % aw == 0 && (sh == 0 || sh == 1);
+  const bool bn_ok = bn == 256 || bn == 128;
+  if (!fw_ok || !adj_ok || !bn_ok) return fail(h, NNP_ERR_ARG, "schedule out of range");
+  if (h->n_atoms == 0) return NNP_OK;
+  CK(aev_set_smem_limits(aev_fwd_smem_bytes(h->nl.cap_r, h->nl.cap_a, fw), 0));
+  h->fwd_warps = fw;
+  nnp_status st = build_work_list(h, aw, ac, sh);
+  if (st == NNP_OK && h->prec != Prec::F32) st = set_l1_tiles(h, bn);
+  if (h->gexec) {  // the schedule changed: capture again on next use
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  return st;
+}
+
 nnp_status nnp_compute_host(nnp_handle h, const float* pos, double* E, double* F, void* stream) {
   if (!h) return NNP_ERR_ARG;
   if ((!pos && h->n_atoms) || (!E && h->n_mols)) return fail(h, NNP_ERR_ARG, "null buffer");

@@ -28,7 +28,7 @@ EXPORTS = ("nnp_weights_per_model", "nnp_num_features", "nnp_create", "nnp_creat
            "nnp_compute", "nnp_compute_host", "nnp_get_status", "nnp_last_error", "nnp_destroy",
            "nnp_get_capacity", "nnp_get_neighbors", "nnp_get_features",
            "nnp_get_atomic_energies", "nnp_compute_timed", "nnp_kernels_per_step",
-           "nnp_features_static", "nnp_autotune")
+           "nnp_features_static", "nnp_autotune", "nnp_set_schedule")
 STATIC_MAX_ATOMS = 256
 STAGES = ("neighbors", "features", "l1_fwd", "l2_fwd", "l3_fwd", "energy", "l3_rev", "l2_rev",
           "l1_rev", "adjoint")
@@ -94,6 +94,8 @@ def load_library(path: str = LIB_PATH):
     lib.nnp_autotune.argtypes = [P, P, P, P]
     lib.nnp_autotune.restype = ctypes.c_int
     lib.nnp_features_static.argtypes = [P, P, I32, P, P]
+    lib.nnp_set_schedule.argtypes = [P, P]
+    lib.nnp_set_schedule.restype = I32
     lib.nnp_features_static.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -212,6 +214,14 @@ class NNP:
         return {"featurizer_warps": out[0], "reverse_warps": out[1],
                 "reverse_centres_per_item": out[2], "first_layer_n_tile": out[3],
                 "reverse_shared_accumulators": out[4]}
+
+    SCHEDULE_KEYS = ("featurizer_warps", "reverse_warps", "reverse_centres_per_item",
+                     "first_layer_n_tile", "reverse_shared_accumulators")
+
+    def set_schedule(self, schedule: dict):
+        """Apply a schedule returned by autotune() (same keys), without timing."""
+        vals = (ctypes.c_int32 * 5)(*[int(schedule[k]) for k in self.SCHEDULE_KEYS])
+        self._check(self._lib.nnp_set_schedule(self._h, vals))
 
     def kernels_per_step(self, forces: bool = True) -> int:
         return int(self._lib.nnp_kernels_per_step(self._h, 1 if forces else 0))

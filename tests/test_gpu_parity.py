@@ -319,3 +319,22 @@ def test_autotuner_keeps_results_and_picks_valid_schedule(lib):
         model.status()
         np.testing.assert_allclose(E.cpu().numpy(), E0, rtol=1e-9, atol=1e-12)
         np.testing.assert_allclose(F.cpu().numpy(), F0, rtol=1e-6, atol=1e-9)
+
+
+def test_pinned_schedules_keep_results_and_reject_bad_values(lib):
+    # every schedule the autotuner may pick, pinned through nnp_set_schedule,
+    # gives the energies and forces of the default schedule
+    b, w, M = small_batch(), W.weights(6, 8), 8
+    model, E0, F0 = run(lib, b, w, M, "fp16", use_graph=True)
+    pos = torch.tensor(b.pos, device="cuda")
+    for sched in ((2, 2, 2, 256, 1), (8, 4, 16, 128, 0), (4, 2, 16, 256, 0)):
+        model.set_schedule(dict(zip(lib.NNP.SCHEDULE_KEYS, sched)))
+        E, F = model.compute(pos)
+        torch.cuda.synchronize()
+        model.status()
+        np.testing.assert_allclose(E.cpu().numpy(), E0, rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(F.cpu().numpy(), F0, rtol=1e-6, atol=1e-9)
+    for bad in ((3, 2, 2, 256, 1), (2, 2, 3, 256, 1), (2, 2, 2, 64, 1), (2, 2, 2, 256, 2)):
+        with pytest.raises(lib.NNPError) as e:
+            model.set_schedule(dict(zip(lib.NNP.SCHEDULE_KEYS, bad)))
+        assert e.value.status == "NNP_ERR_ARG"
