@@ -163,10 +163,11 @@ __device__ __forceinline__ int pair_block(int s, int t) {
 }
 
 // Element groups of an element-sorted angular neighbour list and the prefix
-// of the block-major pair enumeration.  cnt_s: on lanes 0..6 the size of
-// element group s.  Writes gs[7] (group starts), gn[7] (sizes) and bpre[29]
-// (first pair of each block, bpre[28] = number of pairs); call with the whole
-// warp, then __syncwarp before reading.
+// of the block-major pair enumeration, each block padded to a multiple of 4
+// pairs (the padding pairs contribute zero).  cnt_s: on lanes 0..6 the size
+// of element group s.  Writes gs[7] (group starts), gn[7] (sizes) and
+// bpre[29] (first pair of each block, bpre[28] = padded number of pairs);
+// call with the whole warp, then __syncwarp before reading.
 __device__ __forceinline__ void angular_blocks(int cnt_s, int lane, int* gs, int* gn, int* bpre) {
   const unsigned FULL = 0xffffffffu;
   int start = cnt_s;
@@ -183,7 +184,7 @@ __device__ __forceinline__ void angular_blocks(int cnt_s, int lane, int* gs, int
   const int bs = lane < kPairBlocks ? kBlkS[lane] : 0, bt = lane < kPairBlocks ? kBlkT[lane] : 0;
   const int ns = __shfl_sync(FULL, cnt_s, bs), nt = __shfl_sync(FULL, cnt_s, bt);
   const int size = lane < kPairBlocks ? (bs == bt ? ns * (ns - 1) / 2 : ns * nt) : 0;
-  int incl = size;
+  int incl = (size + 3) & ~3;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int v = __shfl_up_sync(FULL, incl, o);
@@ -193,8 +194,8 @@ __device__ __forceinline__ void angular_blocks(int cnt_s, int lane, int* gs, int
   if (lane == 0) bpre[0] = 0;
 }
 
-// Pair P of the block-major enumeration: its block and the list positions
-// j < k of its two neighbours.
+// Pair P of the (padded) block-major enumeration: its block and the list
+// positions j < k of its two neighbours, or j = -1 for a padding pair.
 __device__ __forceinline__ int decode_block_pair(int P, const int* bpre, const int* gs,
                                                  const int* gn, int& j, int& k) {
   int b = 0;
@@ -203,7 +204,10 @@ __device__ __forceinline__ int decode_block_pair(int P, const int* bpre, const i
     if (b + step <= kPairBlocks - 1 && bpre[b + step] <= P) b += step;
   const int l = P - bpre[b];
   const int s = kBlkS[b], t = kBlkT[b];
-  if (s != t) {
+  const int size = s == t ? gn[s] * (gn[s] - 1) / 2 : gn[s] * gn[t];
+  if (l >= size) {
+    j = k = -1;
+  } else if (s != t) {
     const int n_t = gn[t];
     int qd = (int)__fdividef((float)l + 0.5f, (float)n_t);
     if (qd * n_t > l) --qd;
@@ -223,7 +227,8 @@ __device__ __forceinline__ int decode_block_pair(int P, const int* bpre, const i
 // pair with one neighbour of element s and one of element t (the neighbour
 // list is sorted by element, so each element is one contiguous group), and
 // the blocks follow each other in feature order.  Each block is then one
-// contiguous run of pairs, accumulated once and written once.
+// contiguous run of pairs, accumulated once and written once; padded to a
+// multiple of 4 pairs, every run starts 16-byte aligned in the factor rows.
 template <typename TOut>
 __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __restrict__ row_of_int,
                       TOut* __restrict__ out) {
@@ -319,54 +324,56 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
       // phase 1: this lane's pair -> 8 distance factors, 4 angle factors
       int j, k;
       const int b = decode_block_pair(P, bpre, gs, gn, j, k);
-      const float4 rj = avec[j], rk = avec[k];
-      const float cost = __fdividef(rj.x * rk.x + rj.y * rk.y + rj.z * rk.z, rj.w * rk.w);
-      const float cp = 0.95f * cost;
-      const float sp = sqrtf(fmaxf(1.f - cp * cp, 0.f));
-      const float fcjk = 2.f * afc[j] * afc[k];
-      const float u = 0.5f * (rj.w + rk.w);
+      if (j >= 0) {
+        const float4 rj = avec[j], rk = avec[k];
+        const float cost = __fdividef(rj.x * rk.x + rj.y * rk.y + rj.z * rk.z, rj.w * rk.w);
+        const float cp = 0.95f * cost;
+        const float sp = sqrtf(fmaxf(1.f - cp * cp, 0.f));
+        const float fcjk = 2.f * afc[j] * afc[k];
+        const float u = 0.5f * (rj.w + rk.w);
 #pragma unroll
-      for (int a = 0; a < kShfA; ++a) {
-        const float x = u - c.ShfA[a];
-        buf[a * kBufStride + lane] = ex2_ftz(etaA * x * x);
-      }
+        for (int a = 0; a < kShfA; ++a) {
+          const float x = u - c.ShfA[a];
+          buf[a * kBufStride + lane] = ex2_ftz(etaA * x * x);
+        }
 #pragma unroll
-      for (int z = 0; z < kShfZ; ++z) {
-        const float bb = fmaxf(0.5f * (1.f + cp * c.cosZ[z] + sp * c.sinZ[z]), 0.f);
-        buf[(kShfA + z) * kBufStride + lane] = ex2_ftz(c.Zeta * lg2_ftz(bb)) * fcjk;
+        for (int z = 0; z < kShfZ; ++z) {
+          const float bb = fmaxf(0.5f * (1.f + cp * c.cosZ[z] + sp * c.sinZ[z]), 0.f);
+          buf[(kShfA + z) * kBufStride + lane] = ex2_ftz(c.Zeta * lg2_ftz(bb)) * fcjk;
+        }
+      } else {  // padding pair: zero factors
+#pragma unroll
+        for (int f = 0; f < kShfA + kShfZ; ++f) buf[f * kBufStride + lane] = 0.f;
       }
       pl = b;
     }
-    // phase 2: lane = feature (a, z); walk the runs of equal block
+    // phase 2: lane = feature (a, z).  Blocks are padded to multiples of 4
+    // pairs, so each group of 4 pairs lies in one block: walk the 8 groups,
+    // writing the accumulated block where the next one starts.
     const int prev = __shfl_up_sync(FULL, pl, 1);
-    unsigned starts = __ballot_sync(FULL, valid && (lane == 0 || prev != pl));
-    const int cnt = min(32, T - base);
+    const unsigned starts = __ballot_sync(FULL, valid && (lane == 0 || prev != pl));
+    const int ng = min(32, T - base) >> 2;
     __syncwarp();
-    const float* ra = buf + fa * kBufStride;
-    const float* za = buf + (kShfA + fz) * kBufStride;
-    while (starts) {
-      const int t0 = __ffs(starts) - 1;
-      starts &= starts - 1;
-      const int t1 = starts ? __ffs(starts) - 1 : cnt;
-      const int p = __shfl_sync(FULL, pl, t0);
-      if (p != pcur) {  // block pcur is complete: write it, and zeros for empty blocks
-        if (pcur >= 0) dst[kRadial + pcur * kAngPerBlock + lane] = cvt_out<TOut>(acc);
-        for (int e = pcur + 1; e < p; ++e) dst[kRadial + e * kAngPerBlock + lane] = cvt_out<TOut>(0.f);
-        acc = 0.f;
-        pcur = p;
-      }
-      // 16-byte loads over the aligned middle of the run
-      int t = t0;
-      for (; t < t1 && (t & 3); ++t) acc = fmaf(ra[t], za[t], acc);
-      for (; t + 4 <= t1; t += 4) {
-        const float4 r4 = *reinterpret_cast<const float4*>(ra + t);
-        const float4 z4 = *reinterpret_cast<const float4*>(za + t);
+    const float4* ra4 = reinterpret_cast<const float4*>(buf + fa * kBufStride);
+    const float4* za4 = reinterpret_cast<const float4*>(buf + (kShfA + fz) * kBufStride);
+#pragma unroll
+    for (int gi = 0; gi < 8; ++gi) {
+      if (gi < ng) {
+        if ((starts >> (4 * gi)) & 1u) {
+          const int p = __shfl_sync(FULL, pl, 4 * gi);
+          if (p != pcur) {  // block pcur is complete: write it, and zeros for empty blocks
+            if (pcur >= 0) dst[kRadial + pcur * kAngPerBlock + lane] = cvt_out<TOut>(acc);
+            for (int e = pcur + 1; e < p; ++e) dst[kRadial + e * kAngPerBlock + lane] = cvt_out<TOut>(0.f);
+            acc = 0.f;
+            pcur = p;
+          }
+        }
+        const float4 r4 = ra4[gi], z4 = za4[gi];
         acc = fmaf(r4.x, z4.x, acc);
         acc = fmaf(r4.y, z4.y, acc);
         acc = fmaf(r4.z, z4.z, acc);
         acc = fmaf(r4.w, z4.w, acc);
       }
-      for (; t < t1; ++t) acc = fmaf(ra[t], za[t], acc);
     }
     __syncwarp();
   }
@@ -381,10 +388,10 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
 constexpr int kGAStride = 36;  // padded row of an angular block (16-byte aligned, bank spread)
 
 // Per-warp shared memory of the reverse pass (floats):
-//   gR[112] | gA[28][36] | avec float4[cap_a] | afc[cap_a] | adfc[cap_a] | asp[cap_a] |
-//   sg[cap_a][3]
+//   gR[112] | gA[28][36] | avec float4[cap_a] (unit vector, distance) | afc[cap_a] |
+//   adfc[cap_a] | ainv[cap_a] (1 / distance) | asp[cap_a] | sg[cap_a][3]
 __host__ __device__ constexpr int adj_warp_floats(int /*cap_r*/, int cap_a) {
-  return kRadial + kPairBlocks * kGAStride + 10 * cap_a;
+  return kRadial + kPairBlocks * kGAStride + 11 * cap_a;
 }
 
 // Adds a gradient to the force of atom a_glob (internal index): into the
@@ -429,7 +436,8 @@ __global__ void __launch_bounds__(128, 6) k_aev_adjoint(Geometry g, NeighborList
   float4* avec = reinterpret_cast<float4*>(gA + kPairBlocks * kGAStride);
   float* afc = reinterpret_cast<float*>(avec + nl.cap_a);
   float* adfc = afc + nl.cap_a;
-  int* asp = reinterpret_cast<int*>(adfc + nl.cap_a);
+  float* ainv = adfc + nl.cap_a;
+  int* asp = reinterpret_cast<int*>(ainv + nl.cap_a);
   float* sg = reinterpret_cast<float*>(asp + nl.cap_a);  // [cap_a][3]
   double* acc_w = smem_acc ? accm + (size_t)warp * smem_atoms_max * 3 : nullptr;
 
@@ -440,6 +448,9 @@ __global__ void __launch_bounds__(128, 6) k_aev_adjoint(Geometry g, NeighborList
   __syncthreads();
 
   const float etaR = -c.EtaR * kLog2e, etaA = -c.EtaA * kLog2e;
+  const float inv_rcr = 1.f / c.Rcr, inv_rca = 1.f / c.Rca;
+  const float dfc_r = -0.5f * kPi * inv_rcr, dfc_a = -0.5f * kPi * inv_rca;  // d fc / dr = dfc_x sin(pi r / Rc)
+  const float m2etaR = -2.f * c.EtaR, m2etaA = -2.f * c.EtaA;
   for (;;) {
     int q = 0;
     if (lane == 0) q = atomicAdd(&next_centre, 1);
@@ -476,12 +487,14 @@ __global__ void __launch_bounds__(128, 6) k_aev_adjoint(Geometry g, NeighborList
     for (int t = lane; t < na; t += 32) {
       const int j = la[t];
       const float3 d = disp(xi, g.pos[j], c);
-      const float r = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
-      avec[t] = make_float4(d.x, d.y, d.z, r);
+      const float ir = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+      const float r = (d.x * d.x + d.y * d.y + d.z * d.z) * ir;
+      avec[t] = make_float4(d.x * ir, d.y * ir, d.z * ir, r);
+      ainv[t] = ir;
       float sn, cs;
-      sincospif(r / c.Rca, &sn, &cs);
+      sincospif(r * inv_rca, &sn, &cs);
       afc[t] = 0.5f * cs + 0.5f;
-      adfc[t] = -0.5f * kPi / c.Rca * sn;
+      adfc[t] = dfc_a * sn;
       asp[t] = g.species[j];
       sg[3 * t] = sg[3 * t + 1] = sg[3 * t + 2] = 0.f;
     }
@@ -494,20 +507,21 @@ __global__ void __launch_bounds__(128, 6) k_aev_adjoint(Geometry g, NeighborList
       for (int t = lane; t < nr; t += 32) {
         const int j = lr[t];
         const float3 d = disp(xi, g.pos[j], c);
-        const float r = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+        const float ir = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+        const float r = (d.x * d.x + d.y * d.y + d.z * d.z) * ir;
         float sn, cs;
-        sincospif(r / c.Rcr, &sn, &cs);
+        sincospif(r * inv_rcr, &sn, &cs);
         const float fc = 0.5f * cs + 0.5f;
-        const float dfc = -0.5f * kPi / c.Rcr * sn;
+        const float dfc = dfc_r * sn;
         const float* gsp = gR + g.species[j] * kShfR;
         float dEdr = 0.f;
 #pragma unroll
         for (int k = 0; k < kShfR; ++k) {
           const float x = r - c.ShfR[k];
           const float e = ex2_ftz(etaR * x * x);
-          dEdr = fmaf(gsp[k] * 0.25f * e, fmaf(-2.f * c.EtaR * x, fc, dfc), dEdr);
+          dEdr = fmaf(gsp[k] * e, fmaf(m2etaR * x, fc, dfc), dEdr);
         }
-        const float s = dEdr / r;
+        const float s = 0.25f * dEdr * ir;
         gix -= s * d.x;
         giy -= s * d.y;
         giz -= s * d.z;
@@ -526,22 +540,23 @@ __global__ void __launch_bounds__(128, 6) k_aev_adjoint(Geometry g, NeighborList
       if (valid) {
         decode_pair(P, na, j, k);
         const int b = pair_block(asp[j], asp[k]);
-        const float4 rj = avec[j], rk = avec[k];
-        const float inv_jk = __fdividef(1.f, rj.w * rk.w);
-        const float cost = (rj.x * rk.x + rj.y * rk.y + rj.z * rk.z) * inv_jk;
+        const float4 uj = avec[j], uk = avec[k];  // unit vectors, distances
+        const float cost = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
         const float cp = 0.95f * cost;
         const float sp = sqrtf(fmaxf(1.f - cp * cp, 1e-12f));
+        const float qs = __fdividef(cp, sp);
         const float fcj = afc[j], fck = afc[k];
-        const float u = 0.5f * (rj.w + rk.w);
+        const float u = 0.5f * (uj.w + uk.w);
         const float4* gp = reinterpret_cast<const float4*>(gA + b * kGAStride);
         float A[kShfZ], dA[kShfZ];
 #pragma unroll
         for (int z = 0; z < kShfZ; ++z) {
           const float bb = fmaxf(0.5f * (1.f + cp * c.cosZ[z] + sp * c.sinZ[z]), 0.f);
-          const float L = lg2_ftz(bb);
-          A[z] = 2.f * ex2_ftz(c.Zeta * L);
-          // dA/dcp = 2 Zeta b^(Zeta-1) db/dcp,  db/dcp = (cosZ - cp/sp sinZ) / 2
-          dA[z] = c.Zeta * ex2_ftz((c.Zeta - 1.f) * L) * (c.cosZ[z] - cp / sp * c.sinZ[z]);
+          // A = 2 b^Zeta = 2 b b^(Zeta-1);  dA/dcp = 2 Zeta b^(Zeta-1) db/dcp,
+          // db/dcp = (cosZ - cp/sp sinZ) / 2
+          const float pz = ex2_ftz((c.Zeta - 1.f) * lg2_ftz(bb));
+          A[z] = 2.f * bb * pz;
+          dA[z] = c.Zeta * pz * fmaf(-qs, c.sinZ[z], c.cosZ[z]);
         }
         float V = 0.f, dVdc = 0.f, dVdu = 0.f;
 #pragma unroll
@@ -553,21 +568,21 @@ __global__ void __launch_bounds__(128, 6) k_aev_adjoint(Geometry g, NeighborList
           const float SdA = fmaf(g4.x, dA[0], fmaf(g4.y, dA[1], fmaf(g4.z, dA[2], g4.w * dA[3])));
           V = fmaf(R, SA, V);
           dVdc = fmaf(R, SdA, dVdc);
-          dVdu = fmaf(-2.f * c.EtaA * x * R, SA, dVdu);
+          dVdu = fmaf(m2etaA * x * R, SA, dVdu);
         }
         const float fcjk = fcj * fck;
         const float dEdcos = 0.95f * fcjk * dVdc;
         const float dEdu = fcjk * dVdu;
         const float dEdrj = 0.5f * dEdu + V * adfc[j] * fck;
         const float dEdrk = 0.5f * dEdu + V * fcj * adfc[k];
-        const float cj = cost / (rj.w * rj.w), ck = cost / (rk.w * rk.w);
-        const float ej = dEdrj / rj.w, ek = dEdrk / rk.w;
-        gjx = dEdcos * (rk.x * inv_jk - cj * rj.x) + ej * rj.x;
-        gjy = dEdcos * (rk.y * inv_jk - cj * rj.y) + ej * rj.y;
-        gjz = dEdcos * (rk.z * inv_jk - cj * rj.z) + ej * rj.z;
-        const float gkx = dEdcos * (rj.x * inv_jk - ck * rk.x) + ek * rk.x;
-        const float gky = dEdcos * (rj.y * inv_jk - ck * rk.y) + ek * rk.y;
-        const float gkz = dEdcos * (rj.z * inv_jk - ck * rk.z) + ek * rk.z;
+        // d cos / d r_j = (u_k - cos u_j) / |r_j|,  d |r_j| / d r_j = u_j
+        const float aj = dEdcos * ainv[j], ak = dEdcos * ainv[k];
+        gjx = fmaf(aj, fmaf(-cost, uj.x, uk.x), dEdrj * uj.x);
+        gjy = fmaf(aj, fmaf(-cost, uj.y, uk.y), dEdrj * uj.y);
+        gjz = fmaf(aj, fmaf(-cost, uj.z, uk.z), dEdrj * uj.z);
+        const float gkx = fmaf(ak, fmaf(-cost, uk.x, uj.x), dEdrk * uk.x);
+        const float gky = fmaf(ak, fmaf(-cost, uk.y, uj.y), dEdrk * uk.y);
+        const float gkz = fmaf(ak, fmaf(-cost, uk.z, uj.z), dEdrk * uk.z);
         gix -= gjx + gkx;
         giy -= gjy + gky;
         giz -= gjz + gkz;
