@@ -12,9 +12,11 @@
 //   * warp 1, one lane: issues tcgen05.mma (M = 128, K = 16 per instruction)
 //     into one of two 256-column FP32 accumulators in tensor memory, releases
 //     each stage with tcgen05.commit and signals the finished accumulator;
-//   * warps 2-5: epilogue, tcgen05.ld of the rows they own (warp w reads TMEM
-//     lanes 32 (w % 4) ...), bias / CELU / CELU' / the output layer fused,
-//     stores to global memory; then hand the accumulator back.
+//   * warps 2-9: epilogue, tcgen05.ld of the rows they own (warp w reads TMEM
+//     lanes 32 (w % 4) ...), bias + CELU fused (forward) or plain FP32
+//     (reverse), written into a 128B-swizzled staging box in shared memory
+//     that one thread stores with TMA; the two halves of the epilogue warps
+//     take alternate boxes, each with its own staging buffer.
 // With two accumulators the epilogue of one tile overlaps the MMAs of the
 // next.  Every mbarrier wait is bounded; a wait that gives up sets the status
 // word's timeout bit, every role stops, the CTA frees its tensor memory and
@@ -41,82 +43,25 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer, MMA, epilogue warps
 constexpr uint32_t kABytes = kBM * kBK * 2;      // 16 KB
 constexpr uint32_t kBBytes = kBNMax * kBK * 2;   // 32 KB (room for 256 B rows)
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
-constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+constexpr uint32_t kStgBytes = 128 * 128;        // one output box: 128 rows x 128 bytes
+constexpr size_t kSmemBytes =
+    (size_t)kStages * kStageBytes + 2 * kStgBytes + 1024 /*align*/ + 256 /*barriers*/;
 
 struct TcMaps {
   CUtensorMap a;
   CUtensorMap b;
+  CUtensorMap d;  // output, 128-row boxes of 128 bytes (64 16-bit or 32 FP32 columns)
 };
+static_assert(sizeof(CUtensorMap) == 128, "tensor map slots are 128 bytes");
 
-// Epilogue of one 16-column chunk of one row.
-template <typename T>
-__device__ __forceinline__ void epilogue_chunk(const GemmProblem& P, int row, int n,
-                                               const float (&v)[16], float& head_acc) {
-  switch (P.epi) {
-    case (int)Epi::BiasCelu: {
-      float b[16];
-      ldg16(P.bias + n, b);
-      uint32_t o[8];
+// Row r, FP32 columns c..c+15 (c a multiple of 16) of a [128][32] FP32 box in
+// the 128-byte-swizzled layout: 16-byte chunk k of row r at k ^ (r % 8).
+__device__ __forceinline__ void put16_f32(unsigned char* box, int r, int c, const float (&v)[16]) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
-        o[i] = Pack<T>::two(celu01_fast(v[2 * i] + b[2 * i]), celu01_fast(v[2 * i + 1] + b[2 * i + 1]));
-      uint4* d = reinterpret_cast<uint4*>(static_cast<T*>(P.D) + (size_t)row * P.ldd + n);
-      d[0] = make_uint4(o[0], o[1], o[2], o[3]);
-      d[1] = make_uint4(o[4], o[5], o[6], o[7]);
-      break;
-    }
-    case (int)Epi::Head: {
-      uint32_t o[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        float dv[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int c = n + 2 * i + h;
-          const float z = v[2 * i + h] + P.bias[c];
-          const float ex = celu01_exp(z);  // celu'(z): 1 above zero
-          const float w = P.w4[c];
-          head_acc = fmaf(w, fmaxf(z, fmaf(0.1f, ex, -0.1f)), head_acc);
-          dv[h] = w * ex * P.inv_m;
-        }
-        o[i] = Pack<T>::two(dv[0], dv[1]);
-      }
-      uint4* d = reinterpret_cast<uint4*>(static_cast<T*>(P.D) + (size_t)row * P.ldd + n);
-      d[0] = make_uint4(o[0], o[1], o[2], o[3]);
-      d[1] = make_uint4(o[4], o[5], o[6], o[7]);
-      break;
-    }
-    case (int)Epi::Bias: {
-      float4* d = reinterpret_cast<float4*>(static_cast<float*>(P.D) + (size_t)row * P.ldd + n);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        d[i] = make_float4(v[4 * i] + P.bias[n + 4 * i], v[4 * i + 1] + P.bias[n + 4 * i + 1],
-                           v[4 * i + 2] + P.bias[n + 4 * i + 2], v[4 * i + 3] + P.bias[n + 4 * i + 3]);
-      break;
-    }
-    case (int)Epi::DCelu: {
-      uint4* d = reinterpret_cast<uint4*>(static_cast<T*>(P.D) + (size_t)row * P.ldd + n);
-      const uint4 h0 = d[0], h1 = d[1];
-      const uint32_t hin[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-      uint32_t o[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float ha = Pack<T>::lo(hin[i]), hb = Pack<T>::hi(hin[i]);
-        // celu' from celu (alpha 0.1): 1 + h / alpha below zero, where it is <= 1
-        const float ga = fminf(fmaf(10.f, ha, 1.f), 1.f);
-        const float gb = fminf(fmaf(10.f, hb, 1.f), 1.f);
-        o[i] = Pack<T>::two(v[2 * i] * ga, v[2 * i + 1] * gb);
-      }
-      d[0] = make_uint4(o[0], o[1], o[2], o[3]);
-      d[1] = make_uint4(o[4], o[5], o[6], o[7]);
-      break;
-    }
-    default: {
-      float4* d = reinterpret_cast<float4*>(static_cast<float*>(P.D) + (size_t)row * P.ldd + n);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) d[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-      break;
-    }
+  for (int i = 0; i < 4; ++i) {
+    const int k = (c >> 2) + i;
+    *reinterpret_cast<float4*>(box + r * 128 + ((k ^ (r & 7)) << 4)) =
+        make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
   }
 }
 
@@ -126,9 +71,11 @@ __global__ void __launch_bounds__(kThreads, 1)
               const GemmTile* __restrict__ tiles, int n_tiles, int b_box_rows,
               unsigned* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  // rounded up to 1024 bytes by pointer arithmetic, so that accesses through
+  // it stay shared-memory accesses
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  unsigned char* stg_base = smem + kStages * kStageBytes;  // [2] output staging boxes
+  uint64_t* full = reinterpret_cast<uint64_t*>(stg_base + 2 * kStgBytes);
   uint64_t* empty = full + kStages;
   uint64_t* tfull = empty + kStages;  // [2] accumulator ready
   uint64_t* tempty = tfull + 2;       // [2] accumulator drained
@@ -229,8 +176,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---- epilogue warps 2..9: TMEM lane quarter = warp % 4, column half ----
+    // ---- epilogue warps 2..9: TMEM lane quarter = warp % 4; half h takes the
+    // output boxes h, h + 2, ... of each tile through staging buffer h ----
     const int quarter = warp & 3, half = (warp - 2) >> 2;
+    const int r = quarter * 32 + lane;  // tile row = TMEM lane
+    unsigned char* stg = stg_base + half * kStgBytes;
+    const bool leader = quarter == 0 && lane == 0;  // issues this half's stores
+    bool in_flight = false;                         // leader: a store may still read stg
+    auto half_sync = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(2 + half) : "memory"); };
     uint32_t tcount = 0;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tcount) {
       const GemmTile tl = tiles[tile];
@@ -244,66 +197,51 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int epi = P.epi;
-      const int row = tl.m0 + quarter * 32 + lane;
-      const bool row_ok = row < P.M;
+      const bool f32 = P.epi == (int)Epi::Store;  // else bias + CELU into T
+      const int bw = f32 ? 32 : 64;               // box columns
+      const int nbox = (n_tile + bw - 1) / bw;
       const uint32_t tbase = tmem + acc * kBNMax + ((uint32_t)(quarter * 32) << 16);
-      // column range of this warp: the output layer needs whole rows (first half only)
-      int c0 = 0, c1 = n_tile;
-      if (epi != (int)Epi::Head) {
-        c0 = half * (n_tile >> 1);
-        c1 = c0 + (n_tile >> 1);
-      } else if (half) {
-        c1 = 0;
-      }
-      if (epi == (int)Epi::DCelu) {
-        // prefetch the stored activations of every chunk before the first use
-        uint4 hv[2 * (kBNMax / 32)];
+      for (int bx = half; bx < nbox; bx += 2) {
+        if (leader && in_flight) bulk_wait_read();  // the previous store has read stg
+        half_sync();
+        for (int cc = 0; cc < bw; cc += 16) {
+          const int c = bx * bw + cc;  // column in the tile
+          float v[16];
+          if (c < n_tile) {
+            tmem_ld16(tbase + (uint32_t)c, v);
+          } else {  // past the problem's columns: zeros
 #pragma unroll
-        for (int i = 0; i < kBNMax / 32; ++i) {
-          const int c = c0 + 16 * i;
-          if (row_ok && c < c1) {
-            const uint4* d = reinterpret_cast<const uint4*>(static_cast<const T*>(P.D) +
-                                                           (size_t)row * P.ldd + tl.n0 + c);
-            hv[2 * i] = d[0];
-            hv[2 * i + 1] = d[1];
+            for (int i = 0; i < 16; ++i) v[i] = 0.f;
+          }
+          if (f32) {
+            put16_f32(stg, r, cc, v);
+          } else {
+            float b[16];
+            if (c < n_tile) {
+              ldg16(P.bias + tl.n0 + c, b);
+#pragma unroll
+              for (int i = 0; i < 16; ++i) v[i] = celu01_fast(v[i] + b[i]);
+            }
+            uint32_t o[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) o[i] = Pack<T>::two(v[2 * i], v[2 * i + 1]);
+            *reinterpret_cast<uint4*>(stg + sw128_offset(r, cc)) = make_uint4(o[0], o[1], o[2], o[3]);
+            *reinterpret_cast<uint4*>(stg + sw128_offset(r, cc + 8)) = make_uint4(o[4], o[5], o[6], o[7]);
           }
         }
-#pragma unroll
-        for (int i = 0; i < kBNMax / 32; ++i) {
-          const int c = c0 + 16 * i;
-          if (c >= c1) break;
-          float v[16];
-          tmem_ld16(tbase + (uint32_t)c, v);
-          if (!row_ok) continue;
-          const uint32_t hin[8] = {hv[2 * i].x, hv[2 * i].y, hv[2 * i].z, hv[2 * i].w,
-                                   hv[2 * i + 1].x, hv[2 * i + 1].y, hv[2 * i + 1].z,
-                                   hv[2 * i + 1].w};
-          uint32_t o[8];
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const float ha = Pack<T>::lo(hin[k]), hb = Pack<T>::hi(hin[k]);
-            const float ga = fminf(fmaf(10.f, ha, 1.f), 1.f);  // celu' from celu, alpha 0.1
-            const float gb = fminf(fmaf(10.f, hb, 1.f), 1.f);
-            o[k] = Pack<T>::two(v[2 * k] * ga, v[2 * k + 1] * gb);
-          }
-          uint4* d = reinterpret_cast<uint4*>(static_cast<T*>(P.D) + (size_t)row * P.ldd + tl.n0 + c);
-          d[0] = make_uint4(o[0], o[1], o[2], o[3]);
-          d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        half_sync();
+        if (leader) {
+          tma_store_2d(&maps.d, stg, tl.n0 + bx * bw, P.a_row0 + tl.m0);
+          bulk_commit();
+          in_flight = true;
         }
-      } else {
-        float head_acc = 0.f;
-        for (int c = c0; c < c1; c += 16) {
-          float v[16];
-          tmem_ld16(tbase + (uint32_t)c, v);  // all lanes take part (sync.aligned)
-          if (row_ok) epilogue_chunk<T>(P, row, tl.n0 + c, v, head_acc);
-        }
-        if (epi == (int)Epi::Head && half == 0 && row_ok) P.y[(size_t)row * P.ldy] = head_acc + P.b4;
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
     }
+    if (leader && in_flight) bulk_wait_all();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -353,10 +291,13 @@ bool tc_make_map(void* out_map, const void* base, Prec p, uint64_t rows, uint64_
   CUtensorMap* m = static_cast<CUtensorMap*>(out_map);
   std::memset(m, 0, sizeof(*m));
   const cuuint64_t dims[2] = {cols, rows};
-  const cuuint64_t strides[1] = {row_stride_elems * 2};
+  const cuuint64_t strides[1] = {row_stride_elems * (p == Prec::F32 ? 4 : 2)};
   const cuuint32_t box[2] = {box_cols, box_rows};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = fn(m, p == Prec::BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+  const CUtensorMapDataType dt = p == Prec::F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : p == Prec::BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  const CUresult r = fn(m, dt,
                         2, const_cast<void*>(base), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE,
                         swizzle64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,

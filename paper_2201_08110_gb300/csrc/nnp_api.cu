@@ -76,7 +76,7 @@ struct nnp_ctx {
   bool use_cells = false;
   CellGrid cells{};
   CellBuffers cellbuf{};
-  alignas(64) unsigned char tc_maps[6][256];  // tensor-core path: {A, B} TMA descriptors per layer
+  alignas(64) unsigned char tc_maps[6][384];  // tensor-core path: {A, B, D} TMA descriptors per layer
   alignas(64) unsigned char tail_maps[6 * 128];  // fused tail: h1, w2, w3, w3t, w2t, h1 (32-col boxes)
   std::vector<TailProblem> tail_probs;
   std::vector<GemmTile> tail_tiles;
@@ -300,7 +300,7 @@ nnp_status set_l1_tiles(nnp_ctx* h, int bn) {
     if (!L.tiles.empty())
       CK(cudaMemcpy(L.d_tiles, L.tiles.data(), sizeof(GemmTile) * L.tiles.size(), cudaMemcpyHostToDevice));
     const int i = layer == 0 ? 0 : 1;
-    if (!tc_make_map(h->tc_maps[layer] + tc_maps_bytes() / 2, h->l1_b_base[i], h->prec, h->l1_b_rows[i],
+    if (!tc_make_map(h->tc_maps[layer] + 128, h->l1_b_base[i], h->prec, h->l1_b_rows[i],
                      h->l1_b_cols[i], h->l1_b_cols[i], (uint32_t)bn))
       return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the first layer");
     h->tc_box[layer] = bn;
@@ -746,7 +746,6 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
                           {wb + h->w_off[3] * es, rows_w3t, ld_w3t},
                           {wb + h->w_off[4] * es, rows_w2t, ld_w2t},
                           {wb + h->w_off[5] * es, (uint64_t)kSpecies * kFeaturesPad, ld_w1t}};
-    const size_t half = tc_maps_bytes() / 2;
     h->l1_b_base[0] = B[0].base;
     h->l1_b_rows[0] = B[0].rows;
     h->l1_b_cols[0] = B[0].cols;
@@ -755,10 +754,16 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
     h->l1_b_cols[1] = B[5].cols;
     for (int l = 0; l < 6; ++l) {
       if (!tc_make_map(h->tc_maps[l], A[l].base, h->prec, A[l].rows, A[l].cols, A[l].cols, 128) ||
-          !tc_make_map(h->tc_maps[l] + half, B[l].base, h->prec, B[l].rows, B[l].cols, B[l].cols,
+          !tc_make_map(h->tc_maps[l] + 128, B[l].base, h->prec, B[l].rows, B[l].cols, B[l].cols,
                        (uint32_t)h->tc_box[l]))
         return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for layer " + std::to_string(l));
     }
+    // outputs of the two first-layer products, stored by TMA: h1 (16-bit, 64-column
+    // boxes) and dE/dG (FP32, 32-column boxes)
+    if (!tc_make_map(h->tc_maps[0] + 256, h->d_h1, h->prec, R64, (uint64_t)h->ldh1, (uint64_t)h->ldh1, 128) ||
+        !tc_make_map(h->tc_maps[5] + 256, h->d_dG, Prec::F32, R64, (uint64_t)kFeaturesPad,
+                     (uint64_t)kFeaturesPad, 128, 32))
+      return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for a first-layer output");
     CK(tc_set_smem());
     // fused tail: one problem per (element, member), tiles of 128 rows
     for (int e = 0; e < kSpecies; ++e) {
