@@ -411,38 +411,50 @@ __device__ __forceinline__ void add_force(double* acc_w, int local, const int* o
   }
 }
 
+// Per-warp staging capacity (angular neighbours) of the reverse pass's main
+// launch; centres with more angular neighbours are deferred to a second
+// launch with staging for the full capacity, so the common case keeps its
+// shared memory, and with it the occupancy, small.
+constexpr int kAdjStage = 64;
+
 // Reverse pass of the featurizer: given dE/dG of every atom, the forces.
-// One work item (CTA) = a chunk of centres of one molecule; warps take
-// centres as they free up.  Per centre: radial terms lane per neighbour,
+// Main pass (pass 0): one work item (CTA) = a chunk of centres of one
+// molecule; warps take centres as they free up; a centre with more than
+// stage_cap angular neighbours is appended to the overflow list ovf
+// (ovf[0] = count, ovf[1..] = centres).  Overflow pass (pass 1): the CTAs
+// share out the listed centres, staging for stage_cap = the full capacity,
+// forces by FP64 atomics.  Per centre: radial terms lane per neighbour,
 // angular terms lane per pair; each pair's gradients go to per-neighbour
 // accumulators in shared memory
 // (the lanes of a chunk that share the first neighbour are reduced by a
 // segmented scan first), then to the warp's FP64 accumulator of the molecule.
-__global__ void __launch_bounds__(128, 6) k_aev_adjoint(Geometry g, NeighborLists nl, AevConst c,
+__global__ void __launch_bounds__(128, 8) k_aev_adjoint(Geometry g, NeighborLists nl, AevConst c,
                               const int* __restrict__ row_of_int, const float* __restrict__ dG,
                               const int4* __restrict__ work, const int* __restrict__ orig,
-                              double* __restrict__ F, int smem_atoms_max) {
+                              double* __restrict__ F, int smem_atoms_max, int stage_cap,
+                              int* __restrict__ ovf, int pass) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const unsigned FULL = 0xffffffffu;
   const int nwarps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int4 w = work[blockIdx.x];
+  const int4 w = pass == 0 ? work[blockIdx.x] : make_int4(0, 0, 0, 0);
   const int a0 = w.x, n_mol = w.y, q0 = w.z, q1 = w.w;
-  const bool smem_acc = n_mol <= smem_atoms_max;
+  const bool smem_acc = pass == 0 && n_mol <= smem_atoms_max;
+  const int n_ovf = pass == 0 ? 0 : ovf[0];
   double* accm = reinterpret_cast<double*>(smem_raw);  // [nwarps][smem_atoms_max][3]
   float* gR = reinterpret_cast<float*>(accm + (size_t)nwarps * smem_atoms_max * 3) +
-              (size_t)warp * adj_warp_floats(nl.cap_r, nl.cap_a);
+              (size_t)warp * adj_warp_floats(nl.cap_r, stage_cap);
   float* gA = gR + kRadial;  // [28][36]
   float4* avec = reinterpret_cast<float4*>(gA + kPairBlocks * kGAStride);
-  float* afc = reinterpret_cast<float*>(avec + nl.cap_a);
-  float* adfc = afc + nl.cap_a;
-  float* ainv = adfc + nl.cap_a;
-  int* asp = reinterpret_cast<int*>(ainv + nl.cap_a);
-  float* sg = reinterpret_cast<float*>(asp + nl.cap_a);  // [cap_a][3]
+  float* afc = reinterpret_cast<float*>(avec + stage_cap);
+  float* adfc = afc + stage_cap;
+  float* ainv = adfc + stage_cap;
+  int* asp = reinterpret_cast<int*>(ainv + stage_cap);
+  float* sg = reinterpret_cast<float*>(asp + stage_cap);  // [stage_cap][3]
   double* acc_w = smem_acc ? accm + (size_t)warp * smem_atoms_max * 3 : nullptr;
 
-  __shared__ int next_centre;  // centres are handed to warps as they free up
-  if (threadIdx.x == 0) next_centre = q0;
+  __shared__ int next_centre;  // centres (or overflow-list entries) handed to warps as they free up
+  if (threadIdx.x == 0) next_centre = pass == 0 ? q0 : 0;
   if (smem_acc)
     for (int t = threadIdx.x; t < nwarps * smem_atoms_max * 3; t += blockDim.x) accm[t] = 0.0;
   __syncthreads();
@@ -455,7 +467,18 @@ __global__ void __launch_bounds__(128, 6) k_aev_adjoint(Geometry g, NeighborList
     int q = 0;
     if (lane == 0) q = atomicAdd(&next_centre, 1);
     q = __shfl_sync(FULL, q, 0);
-    if (q >= q1) break;
+    if (pass == 0) {
+      if (q >= q1) break;
+    } else {
+      const int e = blockIdx.x + gridDim.x * q;  // overflow-list entry
+      if (e >= n_ovf) break;
+      q = ovf[1 + e];
+    }
+    const int na = min(nl.cnt_a[q], nl.cap_a);
+    if (na > stage_cap) {  // main pass only: defer to the overflow pass
+      if (lane == 0) ovf[1 + atomicAdd(ovf, 1)] = q;
+      continue;
+    }
     {
       // dE/dG row: 252 float4 (1008 floats), 8 per lane, loads issued together
       const float4* grow = reinterpret_cast<const float4*>(dG + (size_t)row_of_int[q] * kFeaturesPad);
@@ -482,7 +505,6 @@ __global__ void __launch_bounds__(128, 6) k_aev_adjoint(Geometry g, NeighborList
     float gix = 0.f, giy = 0.f, giz = 0.f;
 
     // ---- angular staging (first: its loads overlap the dE/dG row's) ----
-    const int na = min(nl.cnt_a[q], nl.cap_a);
     const int* la = nl.nbr_a + (size_t)q * nl.cap_a;
     for (int t = lane; t < na; t += 32) {
       const int j = la[t];
@@ -677,14 +699,36 @@ void launch_aev(const Geometry& g, const NeighborLists& nl, const AevConst& c,
   }
 }
 
+int aev_adj_stage_cap(int cap_a) { return cap_a < kAdjStage ? cap_a : kAdjStage; }
+
+size_t aev_adj_launch_smem(int cap_r, int cap_a, int warps, int mol_atoms_smem_max) {
+  const size_t main = aev_adj_smem_bytes(cap_r, aev_adj_stage_cap(cap_a), warps, mol_atoms_smem_max);
+  const size_t over = aev_adj_smem_bytes(cap_r, cap_a, warps, 0);
+  return main > over ? main : over;
+}
+
+int aev_adj_launches(int cap_a) { return cap_a > kAdjStage ? 2 : 1; }
+
 void launch_aev_adjoint(const Geometry& g, const NeighborLists& nl, const AevConst& c,
                         const int* row_of_int, const float* dG, const int4* work, int n_work,
-                        const int* orig, double* F, int warps, int mol_atoms_smem_max,
+                        const int* orig, double* F, int warps, int mol_atoms_smem_max, int* ovf,
                         cudaStream_t s) {
   if (n_work <= 0) return;
-  const size_t smem = aev_adj_smem_bytes(nl.cap_r, nl.cap_a, warps, mol_atoms_smem_max);
-  k_aev_adjoint<<<n_work, warps * 32, smem, s>>>(g, nl, c, row_of_int, dG, work, orig, F,
-                                                mol_atoms_smem_max);
+  const int stage = aev_adj_stage_cap(nl.cap_a);
+  cudaMemsetAsync(ovf, 0, sizeof(int), s);
+  k_aev_adjoint<<<n_work, warps * 32, aev_adj_smem_bytes(nl.cap_r, stage, warps, mol_atoms_smem_max),
+                  s>>>(g, nl, c, row_of_int, dG, work, orig, F, mol_atoms_smem_max, stage, ovf, 0);
+  if (stage < nl.cap_a) {
+    static int sms = 0;
+    if (!sms) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (sms <= 0) sms = 148;
+    }
+    k_aev_adjoint<<<sms, warps * 32, aev_adj_smem_bytes(nl.cap_r, nl.cap_a, warps, 0), s>>>(
+        g, nl, c, row_of_int, dG, work, orig, F, 0, nl.cap_a, ovf, 1);
+  }
 }
 
 // Raises (never lowers) the dynamic shared-memory limits of the featurizer

@@ -84,6 +84,7 @@ struct nnp_ctx {
   GemmTile* d_tail_tiles = nullptr;
   // reverse pass work list
   int4* d_work = nullptr;
+  int* d_ovf = nullptr;  // reverse pass: [0] count, [1..] deferred centres
   int n_work = 0;
   int fwd_warps = 4, adj_warps = 4, adj_chunk = 0, adj_shared_acc = 1, smem_atoms_max = 0;
   int l1_bn = 256;                  // N tile of the first layer's products (tensor cores)
@@ -248,7 +249,7 @@ namespace {
 // memory (molecules that fit), 0 = FP64 atomics straight into the forces.
 nnp_status build_work_list(nnp_ctx* h, int warps, int chunk, int shared_acc = 1) {
   const size_t budget = 160 * 1024;
-  const size_t fixed = aev_adj_smem_bytes(h->nl.cap_r, h->nl.cap_a, warps, 0);
+  const size_t fixed = aev_adj_smem_bytes(h->nl.cap_r, aev_adj_stage_cap(h->nl.cap_a), warps, 0);
   int smax = 0;
   if (shared_acc && fixed < budget)
     smax = (int)std::min<size_t>((budget - fixed) / ((size_t)warps * 24), 1 << 20);
@@ -279,7 +280,7 @@ nnp_status build_work_list(nnp_ctx* h, int warps, int chunk, int shared_acc = 1)
   h->smem_atoms_max = smax;
   h->adj_warps = warps;
   h->adj_chunk = chunk;
-  CK(aev_set_smem_limits(0, aev_adj_smem_bytes(h->nl.cap_r, h->nl.cap_a, warps, smax)));
+  CK(aev_set_smem_limits(0, aev_adj_launch_smem(h->nl.cap_r, h->nl.cap_a, warps, smax)));
   return NNP_OK;
 }
 
@@ -327,7 +328,7 @@ void nnp_destroy(nnp_handle h) {
                   h->d_mol_start, h->d_mol_end, h->d_row_elem, h->d_pos, h->nl.cnt_r,
                   h->nl.nbr_r, h->nl.cnt_a, h->nl.nbr_a, h->d_aev, h->d_h1,
                   h->d_h2, h->d_z3, h->d_d3, h->d_y, h->d_dG, h->d_atom_e, h->d_status, h->d_w, h->d_b,
-                  h->d_w4, h->d_b4, h->d_maps, h->d_work, h->d_pos_in, h->d_E, h->d_F};
+                  h->d_w4, h->d_b4, h->d_maps, h->d_work, h->d_ovf, h->d_pos_in, h->d_E, h->d_F};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& L : h->L) {
@@ -460,6 +461,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   }
   CK(cudaMemcpy(d_er0, h->elem_row0, sizeof(int) * (kSpecies + 1), cudaMemcpyHostToDevice));
   CK(dalloc(&h->d_orig, N));
+  CK(dalloc(&h->d_ovf, N + 1));
   CK(dalloc(&h->d_row_of_int, N));
   CK(dalloc(&h->d_species_int, N));
   CK(dalloc(&h->d_mol_start, N));
@@ -914,8 +916,8 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
   gemm(5);
   mark(9);
   launch_aev_adjoint(g, h->nl, h->aevc, h->d_row_of_int, h->d_dG, h->d_work, h->n_work, h->d_orig,
-                     F, h->adj_warps, h->smem_atoms_max, s);
-  ++kernels;
+                     F, h->adj_warps, h->smem_atoms_max, h->d_ovf, s);
+  kernels += aev_adj_launches(h->nl.cap_a);
   mark(10);
   return kernels;
 }

@@ -161,10 +161,17 @@ void launch_neighbors_cells(const Geometry& g, const NeighborLists& nl, const Ae
 void launch_aev(const Geometry& g, const NeighborLists& nl, const AevConst& c,
                 const int* row_of_int, void* aev_out, Prec out_prec, int warps_per_cta,
                 cudaStream_t s);
+// Reverse pass: a main launch over the work items, plus, when cap_a exceeds
+// the main launch's staging capacity, a second launch for the centres with
+// more angular neighbours (ovf: DEVICE int[n_atoms + 1] scratch).
 void launch_aev_adjoint(const Geometry& g, const NeighborLists& nl, const AevConst& c,
                         const int* row_of_int, const float* dG, const int4* work, int n_work,
-                        const int* orig_of_int, double* forces_out, int warps_per_cta,
-                        int mol_atoms_smem_max, cudaStream_t s);
+                        const int* orig, double* F, int warps, int mol_atoms_smem_max, int* ovf,
+                        cudaStream_t s);
+int aev_adj_stage_cap(int cap_a);  // main launch's per-warp staging capacity
+int aev_adj_launches(int cap_a);   // kernels per reverse pass
+// dynamic shared memory to allow for both launches of the reverse pass
+size_t aev_adj_launch_smem(int cap_r, int cap_a, int warps, int mol_atoms_smem_max);
 void launch_head(const float* z3, long ldz, Prec prec, const int* row_elem, const float* w4,
                  const float* b4, void* delta3, float* y, int n_rows, int n_models,
                  cudaStream_t s);

@@ -294,7 +294,9 @@ def test_pocket_and_dense_molecules(lib, prec):
     """The 1500-atom periodic region (24.7 A box, too large for the per-warp
     shared-memory force accumulators, so the global FP64 atomics path runs) and
     250-atom molecules in the 8 A cube (about 0.49 atoms / A^3, the densest
-    lists of the workloads), against the oracle."""
+    lists of the workloads: centres with more angular neighbours than the
+    reverse pass's main launch stages go through its overflow launch), against
+    the oracle."""
     w, M = W.weights(99, 2), 2
     pocket = W.pocket(W.workload_seed(5) + 2)
     _, E, F = run(lib, pocket, w, M, prec)
@@ -304,6 +306,8 @@ def test_pocket_and_dense_molecules(lib, prec):
     check_batch(prec, E, F, dense, oracle_batch(dense, w, M))
     ca, _ = model.neighbors(1)
     print(f"dense molecules: max angular neighbours {int(ca.max())} of capacity {model.capacity()[1]}")
+    # more than the reverse pass stages per warp (64): its overflow launch ran
+    assert int(ca.max()) > 64
 
 
 def test_autotuner_keeps_results_and_picks_valid_schedule(lib):
