@@ -428,7 +428,7 @@ constexpr int kAdjStage = 64;
 // accumulators in shared memory
 // (the lanes of a chunk that share the first neighbour are reduced by a
 // segmented scan first), then to the warp's FP64 accumulator of the molecule.
-__global__ void __launch_bounds__(128, 8) k_aev_adjoint(Geometry g, NeighborLists nl, AevConst c,
+__global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborLists nl, AevConst c,
                               const int* __restrict__ row_of_int, const float* __restrict__ dG,
                               const int4* __restrict__ work, const int* __restrict__ orig,
                               double* __restrict__ F, int smem_atoms_max, int stage_cap,
