@@ -356,6 +356,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       // anyone writes h2 there; the barrier also ends the readers of ypart
       if (et == 0) bulk_wait_read();
       if (epi_stop()) break;
+      {  // warm the L1 with this tile's b2, b3 and w4 (128-byte lines, one per thread)
+        const int l2 = (P.h2 + 31) / 32, l3 = (P.h3 + 31) / 32;
+        const float* line = et < l2 ? P.b2 + 32 * et
+                            : et < l2 + l3 ? P.b3 + 32 * (et - l2)
+                            : et < l2 + 2 * l3 ? P.w4 + 32 * (et - l2 - l3) : nullptr;
+        if (line) asm volatile("prefetch.global.L1 [%0];" ::"l"(line));
+      }
 
       // phase 1, L2 forward (accumulator 0): h2 = celu(acc + b2) -> A2, block by block
       {
@@ -364,10 +371,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           int c0, c1;
           my_cols(b, P.h2, c0, c1);
           for (int c = c0; ok && c < c1; c += 16) {
-            float v[16];
+            float bias[16], v[16];
+            ldg16(P.b2 + c, bias);  // in flight during the TMEM load
             tmem_ld16(t + (uint32_t)c, v);
-            float bias[16];
-            ldg16(P.b2 + c, bias);
             uint32_t o[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
@@ -388,11 +394,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           int c0, c1;
           my_cols(b, P.h3, c0, c1);
           for (int c = c0; ok && c < c1; c += 16) {
-            float v[16];
-            tmem_ld16(t + (uint32_t)c, v);
-            float b3[16], w4[16];
-            ldg16(P.b3 + c, b3);
+            float b3[16], w4[16], v[16];
+            ldg16(P.b3 + c, b3);  // in flight during the TMEM load
             ldg16(P.w4 + c, w4);
+            tmem_ld16(t + (uint32_t)c, v);
             uint32_t o[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
