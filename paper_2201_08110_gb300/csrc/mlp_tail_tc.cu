@@ -16,6 +16,7 @@
 //
 // Roles (persistent CTA per SM over the tile list):
 //   warp 0, one lane: TMA producer (h1 tile, then W2, W3, W3^T, W2^T blocks);
+//   warp 18, one lane: TMA loads of phase 4's staged h1 tile;
 //   warp 1, one lane: tcgen05.mma issuer; the four phases of a tile alternate
 //     between two 256-column accumulators, and K block b of a phase waits
 //     only until the epilogue has written block b of its A operand, so a
@@ -42,7 +43,7 @@ constexpr uint32_t kRingBytes = 256 * kBK * 2;  // a weight block of up to 256 r
 constexpr int kA1Blocks = 4;                 // h1 (<= 256 columns); d3 reuses it
 constexpr int kA2Blocks = 3;                 // h2, then d2 (<= 192 columns)
 constexpr int kEpiWarps = 16;  // four per TMEM lane quarter, 16 of every 64 columns each
-constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kThreads = 64 + 32 * kEpiWarps + 32;  // + the phase-4 staging loader
 constexpr int kTmemCols = 512;  // two accumulators of 256 columns
 // Phase 4 stages h1 in and d1 out through [kP4Boxes][128 rows][32 cols] boxes
 // (64-byte swizzle) over A2 and the 16 KB after it.
@@ -190,16 +191,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ---- TMA producer ----
       uint32_t it = 0, tcount = 0;
       bool ok = true;
-      int prev_h1 = 0, prev_col = 0, prev_row = 0;
-      // h1 of this CTA's k-th tile into P4, once its phase-4 MMAs are done with A2
-      auto load_p4 = [&](uint32_t k) -> bool {
-        if (!mbar_wait(a2_free, k & 1, abort_flag)) return false;
-        const int nbox = prev_h1 / 32;
-        mbar_expect_tx(p4_full, (uint32_t)nbox * kP4Box);
-        for (int j = 0; j < nbox; ++j)
-          tma_load_2d(P4 + (size_t)j * kP4Box, &maps.h1s, prev_col + 32 * j, prev_row, p4_full);
-        return true;
-      };
       for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x, ++tcount) {
         const GemmTile tl = tiles[tile];
         const TailProblem P = probs[tl.problem];
@@ -211,20 +202,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_expect_tx(a1_full, (uint32_t)nb1 * kBlk);
         for (int kb = 0; kb < nb1; ++kb)
           tma_load_2d(A1 + (size_t)kb * kBlk, &maps.h1, P.a_col0 + kb * kBK, P.row0 + tl.m0, a1_full);
-        if (reverse && tcount > 0 && !load_p4(tcount - 1)) {
-          ok = false;
-          break;
-        }
-        prev_h1 = P.h1;
-        prev_col = P.a_col0;
-        prev_row = P.row0 + tl.m0;
         ok = produce_weights(&maps.w2, P.w2_row0, nblocks(P.h1), kBoxW2, ring, full, empty, it, abort_flag) &&
              produce_weights(&maps.w3, P.w3_row0, nblocks(P.h2), kBoxW3, ring, full, empty, it, abort_flag);
         if (ok && reverse)
           ok = produce_weights(&maps.w3t, P.w3t_row0, nblocks(P.h3), kBoxW3T, ring, full, empty, it, abort_flag) &&
                produce_weights(&maps.w2t, P.w2t_row0, nblocks(P.h2), kBoxW2T, ring, full, empty, it, abort_flag);
       }
-      if (ok && reverse && tcount > 0) ok = load_p4(tcount - 1);
       if (!ok) {
         atomicOr(status, kStatTimeout);
         atomicExch(abort_flag, 1);
@@ -289,6 +272,30 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (ok) mma_commit(a1_free);     // d3 (over h1) consumed once these MMAs finish
         phase(1, A2, P.h2, P.h1, true);  // L2 reverse, block by block of d2
         if (ok) mma_commit(a2_free);     // d2 (A2) consumed once these MMAs finish
+      }
+      if (!ok) {
+        atomicOr(status, kStatTimeout);
+        atomicExch(abort_flag, 1);
+      }
+    }
+  } else if (warp == 2 + kEpiWarps) {
+    if (lane == 0 && reverse) {
+      // ---- phase-4 staging loader: h1 of each tile into P4 once the tile's
+      // phase-4 MMAs are done with A2 (apart from the ring producer, whose
+      // next weights must not wait for that) ----
+      uint32_t k = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++k) {
+        const GemmTile tl = tiles[tile];
+        const TailProblem P = probs[tl.problem];
+        if (!mbar_wait(a2_free, k & 1, abort_flag)) {
+          ok = false;
+          break;
+        }
+        const int nbox = P.h1 / 32;
+        mbar_expect_tx(p4_full, (uint32_t)nbox * kP4Box);
+        for (int j = 0; j < nbox; ++j)
+          tma_load_2d(P4 + (size_t)j * kP4Box, &maps.h1s, P.a_col0 + 32 * j, P.row0 + tl.m0, p4_full);
       }
       if (!ok) {
         atomicOr(status, kStatTimeout);
