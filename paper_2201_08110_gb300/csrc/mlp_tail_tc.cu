@@ -130,7 +130,7 @@ __device__ __forceinline__ void put16_p4(unsigned char* p4, int r, int c, const 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1)
     k_mlp_tail(const __grid_constant__ TailMaps maps, const TailProblem* __restrict__ probs,
-               const GemmTile* __restrict__ tiles, int n_tiles, int reverse,
+               const GemmTile* __restrict__ tiles, const int* __restrict__ cta_off, int reverse,
                unsigned* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // rounded up to 1024 bytes by pointer arithmetic, so that accesses through
@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t fmt = Pack<T>::fmt;
+  const int tile_begin = cta_off[blockIdx.x], tile_end = cta_off[blockIdx.x + 1];  // this CTA's tiles
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kRing; ++s) {
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ---- TMA producer ----
       uint32_t it = 0, tcount = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x, ++tcount) {
+      for (int tile = tile_begin; ok && tile < tile_end; ++tile, ++tcount) {
         const GemmTile tl = tiles[tile];
         const TailProblem P = probs[tl.problem];
         if (tcount > 0 && !mbar_wait(a1_free, (tcount - 1) & 1, abort_flag)) {
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         mma_commit(&acc_ready[x]);
         ++used[x];
       };
-      for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x, ++tcount) {
+      for (int tile = tile_begin; ok && tile < tile_end; ++tile, ++tcount) {
         const GemmTile tl = tiles[tile];
         const TailProblem P = probs[tl.problem];
         if (!mbar_wait(a1_full, tcount & 1, abort_flag)) {
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // next weights must not wait for that) ----
       uint32_t k = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++k) {
+      for (int tile = tile_begin; tile < tile_end; ++tile, ++k) {
         const GemmTile tl = tiles[tile];
         const TailProblem P = probs[tl.problem];
         if (!mbar_wait(a2_free, k & 1, abort_flag)) {
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       c0 = b * kBK + grp * 16;
       c1 = min(c0 + 16, n);
     };
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    for (int tile = tile_begin; tile < tile_end; ++tile) {
       const GemmTile tl = tiles[tile];
       const TailProblem P = probs[tl.problem];
       const int row = tl.m0 + r;
@@ -515,24 +516,17 @@ cudaError_t tail_set_smem() {
                               (int)kSmemBytes);
 }
 
-// maps: HOST pointer to the five TMA descriptors (h1, w2, w3, w3t, w2t).
-void launch_mlp_tail(const TailProblem* probs, const GemmTile* tiles, int n_tiles, Prec p,
-                     const void* maps, int reverse, unsigned* status, cudaStream_t s) {
-  if (n_tiles <= 0) return;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 148;
-  }
+// maps: HOST pointer to the TMA descriptors (h1, w2, w3, w3t, w2t, h1 in
+// 32-column boxes); CTA c runs the tiles cta_off[c] .. cta_off[c + 1].
+void launch_mlp_tail(const TailProblem* probs, const GemmTile* tiles, const int* cta_off, int n_ctas,
+                     Prec p, const void* maps, int reverse, unsigned* status, cudaStream_t s) {
+  if (n_ctas <= 0) return;
   TailMaps m;
   std::memcpy(&m, maps, sizeof(m));
-  const int grid = n_tiles < sms ? n_tiles : sms;
   if (p == Prec::BF16)
-    k_mlp_tail<__nv_bfloat16><<<grid, kThreads, kSmemBytes, s>>>(m, probs, tiles, n_tiles, reverse, status);
+    k_mlp_tail<__nv_bfloat16><<<n_ctas, kThreads, kSmemBytes, s>>>(m, probs, tiles, cta_off, reverse, status);
   else
-    k_mlp_tail<__half><<<grid, kThreads, kSmemBytes, s>>>(m, probs, tiles, n_tiles, reverse, status);
+    k_mlp_tail<__half><<<n_ctas, kThreads, kSmemBytes, s>>>(m, probs, tiles, cta_off, reverse, status);
 }
 
 }  // namespace nnp

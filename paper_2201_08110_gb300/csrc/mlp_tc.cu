@@ -68,7 +68,7 @@ __device__ __forceinline__ void put16_f32(unsigned char* box, int r, int c, cons
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ TcMaps maps, const GemmProblem* __restrict__ probs,
-              const GemmTile* __restrict__ tiles, int n_tiles, int b_box_rows,
+              const GemmTile* __restrict__ tiles, const int* __restrict__ cta_off, int b_box_rows,
               unsigned* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // rounded up to 1024 bytes by pointer arithmetic, so that accesses through
@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t stage_tx = kABytes + (uint32_t)b_box_rows * kBK * 2;
+  const int tile_begin = cta_off[blockIdx.x], tile_end = cta_off[blockIdx.x + 1];  // this CTA's tiles
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       // ---- TMA producer ----
       uint32_t it = 0;
-      for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+      for (int tile = tile_begin; tile < tile_end; ++tile) {
         const GemmTile tl = tiles[tile];
         const GemmProblem P = probs[tl.problem];  // by value: asm memory clobbers force reloads of references
         const int nkb = (P.K + kBK - 1) / kBK;
@@ -142,11 +143,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       // ---- MMA issuer ----
       uint32_t it = 0, tcount = 0;
-      for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tcount) {
+      for (int tile = tile_begin; tile < tile_end; ++tile, ++tcount) {
         const GemmTile tl = tiles[tile];
         const GemmProblem P = probs[tl.problem];  // by value: asm memory clobbers force reloads of references
         const int nkb = (P.K + kBK - 1) / kBK;
-        const int n_tile = min(b_box_rows, P.N - tl.n0);  // tile width = weight-box rows
+        const int n_tile = tl.width > 0 ? tl.width : min(b_box_rows, P.N - tl.n0);
         const uint32_t idesc = instr_desc(Pack<T>::fmt, (uint32_t)n_tile);
         const uint32_t acc = tcount & 1, use = tcount >> 1;
         bool ok = use == 0 || mbar_wait(&tempty[acc], (use - 1) & 1, abort_flag);
@@ -185,10 +186,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool in_flight = false;                         // leader: a store may still read stg
     auto half_sync = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(2 + half) : "memory"); };
     uint32_t tcount = 0;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tcount) {
+    for (int tile = tile_begin; tile < tile_end; ++tile, ++tcount) {
       const GemmTile tl = tiles[tile];
       const GemmProblem P = probs[tl.problem];  // by value: asm memory clobbers force reloads of references
-      const int n_tile = min(b_box_rows, P.N - tl.n0);  // tile width = weight-box rows
+      const int n_tile = tl.width > 0 ? tl.width : min(b_box_rows, P.N - tl.n0);
       const uint32_t acc = tcount & 1, use = tcount >> 1;
       const bool got = mbar_wait(&tfull[acc], use & 1, abort_flag);
       if (!__all_sync(0xffffffffu, got)) {  // the warp leaves together (tcgen05.ld is .sync.aligned)
@@ -313,26 +314,18 @@ cudaError_t tc_set_smem() {
                               (int)kSmemBytes);
 }
 
-// maps: HOST pointer to the layer's {A map, B map} pair (copied into the
-// launch's parameters); b_box_rows: rows of the B map's box.
-void launch_gemm_tc(const GemmProblem* probs, const GemmTile* tiles, int n_tiles, Prec p,
-                    int b_box_rows, const void* maps, unsigned* status, cudaStream_t s) {
-  if (n_tiles <= 0) return;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 148;
-  }
+// maps: HOST pointer to the layer's {A, B, D} maps (copied into the launch's
+// parameters); b_box_rows: rows of the B map's box; CTA c runs the tiles
+// cta_off[c] .. cta_off[c + 1] of the (device) tile list.
+void launch_gemm_tc(const GemmProblem* probs, const GemmTile* tiles, const int* cta_off, int n_ctas,
+                    Prec p, int b_box_rows, const void* maps, unsigned* status, cudaStream_t s) {
+  if (n_ctas <= 0) return;
   TcMaps m;
   std::memcpy(&m, maps, sizeof(m));
-  const int grid = n_tiles < sms ? n_tiles : sms;
   if (p == Prec::BF16)
-    k_gemm_tc<__nv_bfloat16><<<grid, kThreads, kSmemBytes, s>>>(m, probs, tiles, n_tiles, b_box_rows,
-                                                                status);
+    k_gemm_tc<__nv_bfloat16><<<n_ctas, kThreads, kSmemBytes, s>>>(m, probs, tiles, cta_off, b_box_rows, status);
   else
-    k_gemm_tc<__half><<<grid, kThreads, kSmemBytes, s>>>(m, probs, tiles, n_tiles, b_box_rows, status);
+    k_gemm_tc<__half><<<n_ctas, kThreads, kSmemBytes, s>>>(m, probs, tiles, cta_off, b_box_rows, status);
 }
 
 }  // namespace nnp

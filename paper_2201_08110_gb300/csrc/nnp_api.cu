@@ -13,8 +13,8 @@
 #include "nnp_internal.cuh"
 
 namespace nnp {
-void launch_gemm_tc(const GemmProblem* probs, const GemmTile* tiles, int n_tiles, Prec p,
-                    int b_box_rows, const void* maps, unsigned* status, cudaStream_t s);
+void launch_gemm_tc(const GemmProblem* probs, const GemmTile* tiles, const int* cta_off, int n_ctas,
+                    Prec p, int b_box_rows, const void* maps, unsigned* status, cudaStream_t s);
 bool tc_available();
 size_t tc_maps_bytes();
 // box_cols x box_rows boxes of a [rows][cols] 16-bit matrix; 128-byte swizzle
@@ -34,9 +34,41 @@ thread_local std::string g_create_error;
 struct Layer {
   std::vector<GemmProblem> probs;
   std::vector<GemmTile> tiles;
+  std::vector<int> cta_off;  // tensor-core path: CTA c runs tiles cta_off[c] .. cta_off[c + 1]
   GemmProblem* d_probs = nullptr;
   GemmTile* d_tiles = nullptr;
+  int* d_cta_off = nullptr;
 };
+
+// Longest-processing-time assignment of tiles to ctas persistent CTAs: tiles
+// in decreasing cost go to the least-loaded CTA; the list is then reordered
+// so that each CTA's tiles are contiguous (largest first), CTA c owning
+// off[c] .. off[c + 1].  Fewer CTAs than ctas when there are fewer tiles.
+void balance_tiles(std::vector<GemmTile>& tiles, const std::vector<double>& cost, int ctas,
+                   std::vector<int>& off) {
+  const int n = (int)tiles.size();
+  ctas = std::max(1, std::min(ctas, n));
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<double> load(ctas, 0.0);
+  std::vector<std::vector<int>> own(ctas);
+  for (int i : order) {
+    int best = 0;
+    for (int c = 1; c < ctas; ++c)
+      if (load[c] < load[best]) best = c;
+    load[best] += cost[i];
+    own[best].push_back(i);
+  }
+  std::vector<GemmTile> out;
+  out.reserve(n);
+  off.assign(1, 0);
+  for (int c = 0; c < ctas; ++c) {
+    for (int i : own[c]) out.push_back(tiles[i]);
+    off.push_back((int)out.size());
+  }
+  tiles.swap(out);
+}
 
 size_t elem_size(Prec p) { return p == Prec::F32 ? 4 : 2; }
 
@@ -80,6 +112,9 @@ struct nnp_ctx {
   alignas(64) unsigned char tail_maps[6 * 128];  // fused tail: h1, w2, w3, w3t, w2t, h1 (32-col boxes)
   std::vector<TailProblem> tail_probs;
   std::vector<GemmTile> tail_tiles;
+  std::vector<int> tail_off;  // CTA c runs tail tiles tail_off[c] .. tail_off[c + 1]
+  int* d_tail_off = nullptr;
+  int sms = 152;
   TailProblem* d_tail_probs = nullptr;
   GemmTile* d_tail_tiles = nullptr;
   // reverse pass work list
@@ -290,16 +325,51 @@ nnp_status set_l1_tiles(nnp_ctx* h, int bn) {
   for (int layer : {0, 5}) {
     Layer& L = h->L[layer];
     L.tiles.clear();
+    std::vector<double> cost;
     for (int pi = 0; pi < (int)L.probs.size(); ++pi) {
       const GemmProblem& P = L.probs[pi];
       for (int m0 = 0; m0 < P.M; m0 += 128)
-        for (int n0 = 0; n0 < P.N; n0 += bn) L.tiles.push_back(GemmTile{pi, m0, n0, 0});
+        for (int n0 = 0; n0 < P.N; n0 += bn) {
+          L.tiles.push_back(GemmTile{pi, m0, n0, 0});
+          cost.push_back((double)P.K * std::min(bn, P.N - n0));
+        }
     }
+    // the last, partly filled wave: split its cheapest tiles into 2 or 4
+    // column pieces (at least 64 columns) so they spread over more CTAs
+    const int S = h->sms, r = (int)L.tiles.size() % S;
+    const int k = (r > 0 && 4 * r <= S) ? 4 : (r > 0 && 2 * r <= S) ? 2 : 1;
+    if (k > 1 && bn / k >= 64) {
+      std::vector<int> order(L.tiles.size());
+      for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] < cost[b]; });
+      std::vector<GemmTile> extra;
+      std::vector<double> extra_cost;
+      for (int q = 0; q < r; ++q) {
+        const int i = order[q];
+        GemmTile& t = L.tiles[i];
+        const int w = std::min(bn, L.probs[t.problem].N - t.n0);
+        if (w < 64 * k || w % (16 * k)) continue;
+        const int pw = w / k;
+        for (int piece = 1; piece < k; ++piece) {
+          extra.push_back(GemmTile{t.problem, t.m0, t.n0 + piece * pw, pw});
+          extra_cost.push_back(cost[i] / k);
+        }
+        t.width = pw;
+        cost[i] /= k;
+      }
+      L.tiles.insert(L.tiles.end(), extra.begin(), extra.end());
+      cost.insert(cost.end(), extra_cost.begin(), extra_cost.end());
+    }
+    balance_tiles(L.tiles, cost, S, L.cta_off);
     if (L.d_tiles) cudaFree(L.d_tiles);
+    if (L.d_cta_off) cudaFree(L.d_cta_off);
     L.d_tiles = nullptr;
+    L.d_cta_off = nullptr;
     CK(dalloc(&L.d_tiles, L.tiles.size()));
+    CK(dalloc(&L.d_cta_off, L.cta_off.size()));
     if (!L.tiles.empty())
       CK(cudaMemcpy(L.d_tiles, L.tiles.data(), sizeof(GemmTile) * L.tiles.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.d_cta_off, L.cta_off.data(), sizeof(int) * L.cta_off.size(), cudaMemcpyHostToDevice));
     const int i = layer == 0 ? 0 : 1;
     if (!tc_make_map(h->tc_maps[layer] + 128, h->l1_b_base[i], h->prec, h->l1_b_rows[i],
                      h->l1_b_cols[i], h->l1_b_cols[i], (uint32_t)bn))
@@ -334,7 +404,9 @@ void nnp_destroy(nnp_handle h) {
   for (auto& L : h->L) {
     if (L.d_probs) cudaFree(L.d_probs);
     if (L.d_tiles) cudaFree(L.d_tiles);
+    if (L.d_cta_off) cudaFree(L.d_cta_off);
   }
+  if (h->d_tail_off) cudaFree(h->d_tail_off);
   for (void* p : {(void*)h->cellbuf.cell_of, (void*)h->cellbuf.count, (void*)h->cellbuf.start,
                   (void*)h->cellbuf.fill, (void*)h->cellbuf.atoms})
     if (p) cudaFree(p);
@@ -397,6 +469,8 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   } guard{h};
 
   cudaGetDevice(&h->dev);
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev);
+  if (h->sms <= 0) h->sms = 152;
   h->n_atoms = N;
   h->n_mols = n_mols;
   h->n_models = params->n_models;
@@ -807,6 +881,17 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
                      128, 32, true))
       return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the fused tail");
     CK(tail_set_smem());
+    {  // balance the tail's tiles by network size (two products per layer and direction)
+      std::vector<double> cost;
+      for (const GemmTile& t : h->tail_tiles) {
+        const TailProblem& T = h->tail_probs[t.problem];
+        cost.push_back((double)T.h1 * T.h2 + (double)T.h2 * T.h3);
+      }
+      balance_tiles(h->tail_tiles, cost, h->sms, h->tail_off);
+      CK(dalloc(&h->d_tail_off, h->tail_off.size()));
+      CK(cudaMemcpy(h->d_tail_off, h->tail_off.data(), sizeof(int) * h->tail_off.size(),
+                    cudaMemcpyHostToDevice));
+    }
     CK(dalloc(&h->d_tail_probs, h->tail_probs.size()));
     CK(dalloc(&h->d_tail_tiles, h->tail_tiles.size()));
     if (!h->tail_probs.empty()) {
@@ -825,6 +910,10 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
       CK(cudaMemcpy(L.d_tiles, L.tiles.data(), sizeof(GemmTile) * L.tiles.size(), cudaMemcpyHostToDevice));
   }
 
+  if (h->prec != Prec::F32) {  // first-layer tiles balanced over the SMs
+    const nnp_status st = set_l1_tiles(h, h->l1_bn);
+    if (st != NNP_OK) return st;
+  }
   h->mol_off_h.assign(mol_offsets, mol_offsets + n_mols + 1);
   h->adj_chunk = N >= 152 * 64 ? 8 * h->adj_warps : h->adj_warps;
   {
@@ -848,8 +937,8 @@ void run_gemm(nnp_ctx* h, int layer, cudaStream_t s) {
   if (h->prec == Prec::F32)
     launch_gemm_simt(L.d_probs, L.d_tiles, (int)L.tiles.size(), s);
   else
-    launch_gemm_tc(L.d_probs, L.d_tiles, (int)L.tiles.size(), h->prec, h->tc_box[layer],
-                   h->tc_maps[layer], h->d_status, s);
+    launch_gemm_tc(L.d_probs, L.d_tiles, L.d_cta_off, (int)L.cta_off.size() - 1, h->prec,
+                   h->tc_box[layer], h->tc_maps[layer], h->d_status, s);
 }
 
 // The whole step, enqueued on s.  With ev != nullptr an event is recorded
@@ -884,7 +973,7 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
   if (h->prec != Prec::F32) {
     // tensor cores: L2 fwd, L3 fwd + output layer, L3 rev, L2 rev in one kernel
     if (!h->tail_tiles.empty()) {
-      launch_mlp_tail(h->d_tail_probs, h->d_tail_tiles, (int)h->tail_tiles.size(), h->prec,
+      launch_mlp_tail(h->d_tail_probs, h->d_tail_tiles, h->d_tail_off, (int)h->tail_off.size() - 1, h->prec,
                       h->tail_maps, F ? 1 : 0, h->d_status, s);
       ++kernels;
     }
@@ -1011,15 +1100,15 @@ nnp_status nnp_autotune(nnp_handle h, const float* pos, void* stream, int32_t* c
   CK(dalloc(&dE, h->n_mols));
   CK(dalloc(&dF, 3 * (size_t)h->n_atoms));
   float ms[NNP_NUM_STAGES];
-  auto time_stages = [&](int a, int b) -> float {  // median of 3 of stages [a, b]
-    float t[3];
-    for (int r = 0; r < 3; ++r) {
+  auto time_stages = [&](int a, int b) -> float {  // median of 7 of stages [a, b]
+    float t[7];
+    for (int r = 0; r < 7; ++r) {
       if (nnp_compute_timed(h, pos, dE, dF, stream, ms, NNP_NUM_STAGES) != NNP_OK) return 1e30f;
       t[r] = 0.f;
       for (int k = a; k <= b; ++k) t[r] += ms[k];
     }
-    std::sort(t, t + 3);
-    return t[1];
+    std::sort(t, t + 7);
+    return t[3];
   };
   nnp_status st = NNP_OK;
   // featurizer: atoms (warps) per CTA

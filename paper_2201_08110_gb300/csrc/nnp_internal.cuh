@@ -146,7 +146,8 @@ struct TailProblem {
 
 // A tile of the flattened problem list.
 struct GemmTile {
-  int problem, m0, n0, pad;
+  int problem, m0, n0;
+  int width;  // columns of the tile; 0: the weight box's rows (clipped to N)
 };
 
 // ---- kernels' host launchers ------------------------------------------------
@@ -196,8 +197,8 @@ void launch_export_atomic_energies(const double* atom_energy_row, const int* row
 size_t tail_maps_bytes();
 int tail_weight_box(int which);  // box rows of the w2, w3, w3t, w2t maps
 cudaError_t tail_set_smem();
-void launch_mlp_tail(const TailProblem* probs, const GemmTile* tiles, int n_tiles, Prec p,
-                     const void* maps, int reverse, unsigned* status, cudaStream_t s);
+void launch_mlp_tail(const TailProblem* probs, const GemmTile* tiles, const int* cta_off, int n_ctas,
+                     Prec p, const void* maps, int reverse, unsigned* status, cudaStream_t s);
 
 // Featurizer constants (cutoffs, shift grids, species-pair table, box).
 void aev_constants(AevConst& c, const double box[3]);
