@@ -132,6 +132,8 @@ struct nnp_ctx {
   double *d_E = nullptr, *d_F = nullptr;
   // graph
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t side = nullptr;  // the energy reduction runs beside the reverse pass
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t gexec = nullptr;
   const float* g_pos = nullptr;
   double *g_E = nullptr, *g_F = nullptr;
@@ -394,6 +396,9 @@ void nnp_destroy(nnp_handle h) {
   cudaDeviceSynchronize();
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   void* ptrs[] = {h->d_Z, h->d_mol_off, h->d_orig, h->d_row_of_int, h->d_species_int,
                   h->d_mol_start, h->d_mol_end, h->d_row_elem, h->d_pos, h->nl.cnt_r,
                   h->nl.nbr_r, h->nl.cnt_a, h->nl.nbr_a, h->d_aev, h->d_h1,
@@ -484,6 +489,9 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   const int M = h->n_models;
   cudaStream_t s0 = nullptr;
   CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   s0 = h->cap_stream;
 
   // ---- element sort on the device (a1) ----
@@ -970,6 +978,7 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
   mark(2);
   gemm(0);
   mark(3);
+  bool fork = false;
   if (h->prec != Prec::F32) {
     // tensor cores: L2 fwd, L3 fwd + output layer, L3 rev, L2 rev in one kernel
     if (!h->tail_tiles.empty()) {
@@ -979,7 +988,17 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
     }
     mark(4);
     mark(5);
-    launch_energy(h->d_y, h->n_models, h->d_row_of_int, h->d_mol_off, h->n_mols, E, h->d_atom_e, s);
+    // with forces (and no per-stage events) the energy reduction runs on a
+    // side stream, concurrently with the reverse pass, joined at the end
+    cudaStream_t se = s;
+    if (F && !ev) {
+      fork = true;
+      cudaEventRecord(h->ev_fork, s);
+      cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+      se = h->side;
+    }
+    launch_energy(h->d_y, h->n_models, h->d_row_of_int, h->d_mol_off, h->n_mols, E, h->d_atom_e, se);
+    if (fork) cudaEventRecord(h->ev_join, h->side);
     ++kernels;
     mark(6);
     if (!F) return kernels;
@@ -1007,6 +1026,7 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
   launch_aev_adjoint(g, h->nl, h->aevc, h->d_row_of_int, h->d_dG, h->d_work, h->n_work, h->d_orig,
                      F, h->adj_warps, h->smem_atoms_max, h->d_ovf, s);
   kernels += aev_adj_launches(h->nl.cap_a);
+  if (fork) cudaStreamWaitEvent(s, h->ev_join, 0);
   mark(10);
   return kernels;
 }
