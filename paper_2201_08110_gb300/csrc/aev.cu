@@ -105,6 +105,65 @@ __global__ void k_neighbors(Geometry g, NeighborLists nl, AevConst c, unsigned* 
   }
 }
 
+// The same search with one CTA per work item (a chunk of up to kNbrChunk
+// centres of one molecule): the molecule's positions are staged in shared
+// memory once (when they fit) and each warp takes centres of the chunk.
+constexpr int kNbrChunk = 64;
+constexpr int kNbrWarps = 8;
+constexpr int kNbrStageMax = 2048;  // atoms of a molecule staged in shared memory
+
+__global__ void __launch_bounds__(32 * kNbrWarps) k_neighbors_mol(Geometry g, NeighborLists nl,
+                                                                  AevConst c, const int4* __restrict__ work,
+                                                                  unsigned* status) {
+  extern __shared__ float4 spos[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int4 w = work[blockIdx.x];
+  const int a0 = w.x, n = w.y, a1 = a0 + n;
+  const bool staged = n <= kNbrStageMax;
+  if (staged)
+    for (int t = threadIdx.x; t < n; t += blockDim.x) spos[t] = g.pos[a0 + t];
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+  for (int q = w.z + warp; q < w.w; q += kNbrWarps) {
+    const float4 xi = staged ? spos[q - a0] : g.pos[q];
+    int nr = 0, na = 0;
+    int* lr = nl.nbr_r + (size_t)q * nl.cap_r;
+    int* la = nl.nbr_a + (size_t)q * nl.cap_a;
+    for (int base = a0; base < a1; base += 32) {
+      const int j = base + lane;
+      bool inR = false, inA = false;
+      if (j < a1 && j != q) {
+        const float4 xj = staged ? spos[j - a0] : g.pos[j];
+        const float3 d = disp(xi, xj, c);
+        const float d2 = d.x * d.x + d.y * d.y + d.z * d.z;
+        inR = d2 < c.Rcr2;
+        inA = d2 < c.Rca2;
+        if (fabsf(d2 - c.Rcr2) <= 1e-4f * c.Rcr2) inR = exact_d2(xi, xj, c) < c.Rcr2d;
+        if (fabsf(d2 - c.Rca2) <= 1e-4f * c.Rca2) inA = exact_d2(xi, xj, c) < c.Rca2d;
+        inA = inA && inR;
+      }
+      const unsigned mR = __ballot_sync(0xffffffffu, inR);
+      const unsigned mA = __ballot_sync(0xffffffffu, inA);
+      if (inR) {
+        const int slot = nr + __popc(mR & lt);
+        if (slot < nl.cap_r) lr[slot] = j;
+        if (inA) {
+          const int sl = na + __popc(mA & lt);
+          if (sl < nl.cap_a) la[sl] = j;
+        }
+      }
+      nr += __popc(mR);
+      na += __popc(mA);
+    }
+    if (lane == 0) {
+      nl.cnt_r[q] = nr;
+      nl.cnt_a[q] = na;
+      if (nr > nl.cap_r) atomicOr(status, kStatCapRadial);
+      if (na > nl.cap_a) atomicOr(status, kStatCapAngular);
+    }
+  }
+}
+
 // Row j and column k of the P-th pair (j < k) of n items, pairs ordered
 // row-major over the strict upper triangle.
 __device__ __forceinline__ void decode_pair(int P, int n, int& j, int& k) {
@@ -663,6 +722,25 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
 }
 
 }  // namespace
+
+int nbr_chunk() { return kNbrChunk; }
+
+size_t nbr_smem_bytes(int max_mol) {
+  return (size_t)(max_mol < kNbrStageMax ? max_mol : kNbrStageMax) * sizeof(float4);
+}
+
+cudaError_t nbr_set_smem(size_t bytes) {
+  static size_t cur = 0;
+  if (bytes <= cur) return cudaSuccess;
+  cur = bytes;
+  return cudaFuncSetAttribute(k_neighbors_mol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+void launch_neighbors_mol(const Geometry& g, const NeighborLists& nl, const AevConst& c,
+                          const int4* work, int n_work, int max_mol, unsigned* status, cudaStream_t s) {
+  if (n_work <= 0) return;
+  k_neighbors_mol<<<n_work, 32 * kNbrWarps, nbr_smem_bytes(max_mol), s>>>(g, nl, c, work, status);
+}
 
 void launch_neighbors(const Geometry& g, const NeighborLists& nl, const AevConst& c,
                       unsigned* status, cudaStream_t s) {

@@ -120,6 +120,8 @@ struct nnp_ctx {
   // reverse pass work list
   int4* d_work = nullptr;
   int* d_ovf = nullptr;  // reverse pass: [0] count, [1..] deferred centres
+  int4* d_nbr_work = nullptr;  // neighbour search: chunks of centres of one molecule
+  int n_nbr_work = 0;
   int n_work = 0;
   int fwd_warps = 4, adj_warps = 4, adj_chunk = 0, adj_shared_acc = 1, smem_atoms_max = 0;
   int l1_bn = 256;                  // N tile of the first layer's products (tensor cores)
@@ -403,7 +405,7 @@ void nnp_destroy(nnp_handle h) {
                   h->d_mol_start, h->d_mol_end, h->d_row_elem, h->d_pos, h->nl.cnt_r,
                   h->nl.nbr_r, h->nl.cnt_a, h->nl.nbr_a, h->d_aev, h->d_h1,
                   h->d_h2, h->d_z3, h->d_d3, h->d_y, h->d_dG, h->d_atom_e, h->d_status, h->d_w, h->d_b,
-                  h->d_w4, h->d_b4, h->d_maps, h->d_work, h->d_ovf, h->d_pos_in, h->d_E, h->d_F};
+                  h->d_w4, h->d_b4, h->d_maps, h->d_work, h->d_ovf, h->d_nbr_work, h->d_pos_in, h->d_E, h->d_F};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& L : h->L) {
@@ -588,6 +590,28 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
       return fail(h, NNP_ERR_UNSUPPORTED,
                   "cell list needs one periodic region of at most 32768 atoms");
     }
+  }
+  if (!h->use_cells) {  // all-pairs search per molecule: work items of nbr_chunk() centres, largest first
+    std::vector<int4> work;
+    std::vector<long> cost;
+    for (int m = 0; m < n_mols; ++m) {
+      const int a0 = mol_offsets[m], n = mol_offsets[m + 1] - a0;
+      for (int c0 = 0; c0 < n; c0 += nbr_chunk()) {
+        const int c1 = std::min(n, c0 + nbr_chunk());
+        work.push_back(make_int4(a0, n, a0 + c0, a0 + c1));
+        cost.push_back((long)(c1 - c0) * n);
+      }
+    }
+    std::vector<int> order(work.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<int4> sorted(work.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = work[order[i]];
+    h->n_nbr_work = (int)sorted.size();
+    CK(dalloc(&h->d_nbr_work, sorted.size()));
+    if (!sorted.empty())
+      CK(cudaMemcpy(h->d_nbr_work, sorted.data(), sizeof(int4) * sorted.size(), cudaMemcpyHostToDevice));
+    CK(nbr_set_smem(nbr_smem_bytes(h->max_mol)));
   }
   CK(dalloc(&h->d_pos, N));
   CK(dalloc(&h->nl.cnt_r, N));
@@ -969,7 +993,7 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
     launch_neighbors_cells(g, h->nl, h->aevc, h->cells, h->cellbuf, h->n_atoms, h->d_status, s);
     kernels += 5;  // gather, bin count, scan, fill, neighbours
   } else {
-    launch_neighbors(g, h->nl, h->aevc, h->d_status, s);
+    launch_neighbors_mol(g, h->nl, h->aevc, h->d_nbr_work, h->n_nbr_work, h->max_mol, h->d_status, s);
     kernels += 2;
   }
   mark(1);

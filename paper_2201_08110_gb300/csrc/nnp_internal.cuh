@@ -154,6 +154,13 @@ struct GemmTile {
 
 void launch_gather_positions(const float* pos_caller, const int* orig_of_int, float4* pos_int,
                              int n, unsigned* status, cudaStream_t s);
+// Neighbour search by work items (a0, molecule atoms, first centre, end centre),
+// chunks of nbr_chunk() centres of one molecule, one CTA each.
+int nbr_chunk();
+size_t nbr_smem_bytes(int max_mol);
+cudaError_t nbr_set_smem(size_t bytes);
+void launch_neighbors_mol(const Geometry& g, const NeighborLists& nl, const AevConst& c,
+                          const int4* work, int n_work, int max_mol, unsigned* status, cudaStream_t s);
 void launch_neighbors(const Geometry& g, const NeighborLists& nl, const AevConst& c,
                       unsigned* status, cudaStream_t s);
 void launch_neighbors_cells(const Geometry& g, const NeighborLists& nl, const AevConst& c,
