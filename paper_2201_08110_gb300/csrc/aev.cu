@@ -475,7 +475,6 @@ __device__ __forceinline__ void add_force(double* acc_w, int local, const int* o
 // launch with staging for the full capacity, so the common case keeps its
 // shared memory, and with it the occupancy, small.
 constexpr int kAdjStage = 64;
-constexpr int kAdjOverflowCtas = 32;
 
 // Reverse pass of the featurizer: given dE/dG of every atom, the forces.
 // Main pass (pass 0): one work item (CTA) = a chunk of centres of one
@@ -797,9 +796,17 @@ void launch_aev_adjoint(const Geometry& g, const NeighborLists& nl, const AevCon
   cudaMemsetAsync(ovf, 0, sizeof(int), s);
   k_aev_adjoint<<<n_work, warps * 32, aev_adj_smem_bytes(nl.cap_r, stage, warps, mol_atoms_smem_max),
                   s>>>(g, nl, c, row_of_int, dG, work, orig, F, mol_atoms_smem_max, stage, ovf, 0);
-  if (stage < nl.cap_a)  // few CTAs: the deferred centres are rare, an empty pass stays cheap
-    k_aev_adjoint<<<kAdjOverflowCtas, warps * 32, aev_adj_smem_bytes(nl.cap_r, nl.cap_a, warps, 0), s>>>(
+  if (stage < nl.cap_a) {  // two CTAs per SM: dense systems defer most centres; an empty pass is cheap
+    static int sms = 0;
+    if (!sms) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (sms <= 0) sms = 152;
+    }
+    k_aev_adjoint<<<2 * sms, warps * 32, aev_adj_smem_bytes(nl.cap_r, nl.cap_a, warps, 0), s>>>(
         g, nl, c, row_of_int, dG, work, orig, F, 0, nl.cap_a, ovf, 1);
+  }
 }
 
 // Raises (never lowers) the dynamic shared-memory limits of the featurizer
