@@ -1144,16 +1144,19 @@ nnp_status nnp_autotune(nnp_handle h, const float* pos, void* stream, int32_t* c
   CK(dalloc(&dE, h->n_mols));
   CK(dalloc(&dF, 3 * (size_t)h->n_atoms));
   float ms[NNP_NUM_STAGES];
-  auto time_stages = [&](int a, int b) -> float {  // median of 7 of stages [a, b]
-    float t[7];
-    for (int r = 0; r < 7; ++r) {
+  auto time_stages = [&](int a, int b) -> float {  // median of 9 of stages [a, b]
+    float t[9];
+    for (int r = 0; r < 9; ++r) {
       if (nnp_compute_timed(h, pos, dE, dF, stream, ms, NNP_NUM_STAGES) != NNP_OK) return 1e30f;
       t[r] = 0.f;
       for (int k = a; k <= b; ++k) t[r] += ms[k];
     }
-    std::sort(t, t + 7);
-    return t[3];
+    std::sort(t, t + 9);
+    return t[4];
   };
+  // warm-up: the first candidates must not be timed while clocks and caches settle
+  for (int r = 0; r < 10; ++r)
+    if (nnp_compute_timed(h, pos, dE, dF, stream, ms, NNP_NUM_STAGES) != NNP_OK) break;
   nnp_status st = NNP_OK;
   // featurizer: atoms (warps) per CTA
   {
