@@ -447,10 +447,13 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
 constexpr int kGAStride = 36;  // padded row of an angular block (16-byte aligned, bank spread)
 
 // Per-warp shared memory of the reverse pass (floats):
-//   gR[112] | gA[28][36] | avec float4[cap_a] (unit vector, distance) | afc[cap_a] |
+//   gR[7][20] | gA[28][36] | avec float4[cap_a] (unit vector, distance) | afc[cap_a] |
 //   adfc[cap_a] | ainv[cap_a] (1 / distance) | asp[cap_a] | sg[cap_a][3]
+// (rows padded to 20 and 36 floats: 16-byte aligned, and the rows that a
+// warp's 16-byte loads hit at once fall in distinct banks)
+constexpr int kGRStride = 20;
 __host__ __device__ constexpr int adj_warp_floats(int /*cap_r*/, int cap_a) {
-  return kRadial + kPairBlocks * kGAStride + 11 * cap_a;
+  return kSpecies * kGRStride + kPairBlocks * kGAStride + 11 * cap_a;
 }
 
 // Adds a gradient to the force of atom a_glob (internal index): into the
@@ -503,7 +506,7 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
   double* accm = reinterpret_cast<double*>(smem_raw);  // [nwarps][smem_atoms_max][3]
   float* gR = reinterpret_cast<float*>(accm + (size_t)nwarps * smem_atoms_max * 3) +
               (size_t)warp * adj_warp_floats(nl.cap_r, stage_cap);
-  float* gA = gR + kRadial;  // [28][36]
+  float* gA = gR + kSpecies * kGRStride;  // [28][36]
   float4* avec = reinterpret_cast<float4*>(gA + kPairBlocks * kGAStride);
   float* afc = reinterpret_cast<float*>(avec + stage_cap);
   float* adfc = afc + stage_cap;
@@ -547,17 +550,15 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
         const int f4 = lane + 32 * i;
         if (f4 < kFeatures / 4) v[i] = __ldg(grow + f4);
       }
+      // 16-byte stores: radial float4 f4 < 28 is (species f4 / 4, shifts 4 (f4 % 4) ..),
+      // angular float4 f4 is (block (f4 - 28) / 8, features 4 ((f4 - 28) % 8) ..)
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int f = 4 * (lane + 32 * i);
-        if (f >= kFeatures) continue;
-        const float e[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const int ff = f + h;
-          if (ff < kRadial) gR[ff] = e[h];
-          else gA[((ff - kRadial) >> 5) * kGAStride + ((ff - kRadial) & 31)] = e[h];
-        }
+        const int f4 = lane + 32 * i;
+        if (f4 >= kFeatures / 4) continue;
+        float* d = f4 < kRadial / 4 ? gR + (f4 >> 2) * kGRStride + 4 * (f4 & 3)
+                                    : gA + ((f4 - kRadial / 4) >> 3) * kGAStride + 4 * ((f4 - kRadial / 4) & 7);
+        *reinterpret_cast<float4*>(d) = v[i];
       }
     }
     const float4 xi = g.pos[q];
@@ -594,13 +595,18 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
         sincospif(r * inv_rcr, &sn, &cs);
         const float fc = 0.5f * cs + 0.5f;
         const float dfc = dfc_r * sn;
-        const float* gsp = gR + g.species[j] * kShfR;
+        const float4* gsp = reinterpret_cast<const float4*>(gR + g.species[j] * kGRStride);
         float dEdr = 0.f;
 #pragma unroll
-        for (int k = 0; k < kShfR; ++k) {
-          const float x = r - c.ShfR[k];
-          const float e = ex2_ftz(etaR * x * x);
-          dEdr = fmaf(gsp[k] * e, fmaf(m2etaR * x, fc, dfc), dEdr);
+        for (int k4 = 0; k4 < kShfR / 4; ++k4) {
+          const float4 g4 = gsp[k4];
+          const float gk[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const float x = r - c.ShfR[4 * k4 + h];
+            const float e = ex2_ftz(etaR * x * x);
+            dEdr = fmaf(gk[h] * e, fmaf(m2etaR * x, fc, dfc), dEdr);
+          }
         }
         const float s = 0.25f * dEdr * ir;
         gix -= s * d.x;
