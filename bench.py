@@ -198,8 +198,8 @@ def src_hash(*names):
 # kernel, keyed by the kernel's source hash at capture time, in bytes per atom;
 # scaled to the bench workload by atoms.
 NCU_TRAFFIC = {
-    ("adjoint", "10cf27704530"): 4608.4,  # ncu --set full, 512-molecule batch, FP16
-    ("tail", "721acd50a1e8"): 6416.8,  # ncu --set full, 512-molecule batch, FP16
+    ("adjoint", "c878888524d4"): 4607.6,  # ncu --set full, 512-molecule batch, FP16
+    ("tail", "686ac585ff42"): 6406.1,  # ncu --set full, 512-molecule batch, FP16
 }
 
 
