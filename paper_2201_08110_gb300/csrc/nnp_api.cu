@@ -629,14 +629,14 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   CK(cudaMemset(h->d_aev, 0, R * kFeaturesPad * es));
   CK(cudaMalloc(&h->d_h1, R * h->ldh1 * es));
   CK(cudaMemset(h->d_h1, 0, R * h->ldh1 * es));
-  CK(cudaMalloc(&h->d_h2, R * h->ldh2 * es));
-  CK(cudaMemset(h->d_h2, 0, R * h->ldh2 * es));
-  if (h->prec == Prec::F32) {  // the tensor-core path fuses the output layer: no z3
+  if (h->prec == Prec::F32) {  // the tensor-core path keeps h2, z3, d3 and d2 on chip
+    CK(cudaMalloc(&h->d_h2, R * h->ldh2 * es));
+    CK(cudaMemset(h->d_h2, 0, R * h->ldh2 * es));
     CK(dalloc(&h->d_z3, R * h->ldz3));
     CK(cudaMemset(h->d_z3, 0, R * h->ldz3 * sizeof(float)));
+    CK(cudaMalloc(&h->d_d3, R * h->ldz3 * es));
+    CK(cudaMemset(h->d_d3, 0, R * h->ldz3 * es));
   }
-  CK(cudaMalloc(&h->d_d3, R * h->ldz3 * es));
-  CK(cudaMemset(h->d_d3, 0, R * h->ldz3 * es));
   CK(dalloc(&h->d_y, R * M));
   CK(dalloc(&h->d_dG, R * kFeaturesPad));
   CK(cudaMemset(h->d_dG, 0, R * kFeaturesPad * sizeof(float)));
@@ -779,7 +779,9 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
       h->L[5].probs.push_back(P);
       add_tiles(h->L[5], bm, tc ? 256 : 64);
     }
-    for (int m = 0; m < M; ++m) {
+    // layers 2 and 3 and their reverse as grouped products: the FP32 path only
+    // (on tensor cores the fused tail keeps h2, d3 and d2 on chip)
+    for (int m = 0; m < (tc ? 0 : M); ++m) {
       {  // layer 2 forward
         GemmProblem P{};
         P.A = H1 + (row0 * h->ldh1 + (size_t)m * n1) * es; P.lda = h->ldh1;
@@ -860,7 +862,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
     h->l1_b_base[1] = B[5].base;
     h->l1_b_rows[1] = B[5].rows;
     h->l1_b_cols[1] = B[5].cols;
-    for (int l = 0; l < 6; ++l) {
+    for (int l : {0, 5}) {  // the two first-layer products (layers 1-4 run in the fused tail)
       if (!tc_make_map(h->tc_maps[l], A[l].base, h->prec, A[l].rows, A[l].cols, A[l].cols, 128) ||
           !tc_make_map(h->tc_maps[l] + 128, B[l].base, h->prec, B[l].rows, B[l].cols, B[l].cols,
                        (uint32_t)h->tc_box[l]))
@@ -1131,7 +1133,8 @@ int32_t nnp_kernels_per_step(nnp_handle h, int32_t with_forces) {
   } else {
     k += h->tail_tiles.empty() ? 0 : 1;
   }
-  if (with_forces) k += 1 + (h->L[5].tiles.empty() ? 0 : 1);  // L1 reverse, featurizer reverse
+  if (with_forces)  // L1 reverse, featurizer reverse (main and overflow launches)
+    k += aev_adj_launches(h->nl.cap_a) + (h->L[5].tiles.empty() ? 0 : 1);
   return k;
 }
 
