@@ -447,8 +447,8 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
 constexpr int kGAStride = 36;  // padded row of an angular block (16-byte aligned, bank spread)
 
 // Per-warp shared memory of the reverse pass (floats):
-//   gR[7][20] | gA[28][36] | avec float4[cap_a] (unit vector, distance) | afc[cap_a] |
-//   adfc[cap_a] | ainv[cap_a] (1 / distance) | asp[cap_a] | sg[cap_a][3]
+//   gR[7][20] | gA[28][36] | nb float4[cap_a][2] | sg[cap_a][3]
+// nb[t] = {(unit vector, distance), (fc, dfc/dr, 1 / distance, species bits)}
 // (rows padded to 20 and 36 floats: 16-byte aligned, and the rows that a
 // warp's 16-byte loads hit at once fall in distinct banks)
 constexpr int kGRStride = 20;
@@ -507,12 +507,8 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
   float* gR = reinterpret_cast<float*>(accm + (size_t)nwarps * smem_atoms_max * 3) +
               (size_t)warp * adj_warp_floats(nl.cap_r, stage_cap);
   float* gA = gR + kSpecies * kGRStride;  // [28][36]
-  float4* avec = reinterpret_cast<float4*>(gA + kPairBlocks * kGAStride);
-  float* afc = reinterpret_cast<float*>(avec + stage_cap);
-  float* adfc = afc + stage_cap;
-  float* ainv = adfc + stage_cap;
-  int* asp = reinterpret_cast<int*>(ainv + stage_cap);
-  float* sg = reinterpret_cast<float*>(asp + stage_cap);  // [stage_cap][3]
+  float4* nb = reinterpret_cast<float4*>(gA + kPairBlocks * kGAStride);  // [stage_cap][2]
+  float* sg = reinterpret_cast<float*>(nb + 2 * stage_cap);                // [stage_cap][3]
   double* acc_w = smem_acc ? accm + (size_t)warp * smem_atoms_max * 3 : nullptr;
 
   __shared__ int next_centre;  // centres (or overflow-list entries) handed to warps as they free up
@@ -571,13 +567,10 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
       const float3 d = disp(xi, g.pos[j], c);
       const float ir = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
       const float r = (d.x * d.x + d.y * d.y + d.z * d.z) * ir;
-      avec[t] = make_float4(d.x * ir, d.y * ir, d.z * ir, r);
-      ainv[t] = ir;
+      nb[2 * t] = make_float4(d.x * ir, d.y * ir, d.z * ir, r);
       float sn, cs;
       sincospif(r * inv_rca, &sn, &cs);
-      afc[t] = 0.5f * cs + 0.5f;
-      adfc[t] = dfc_a * sn;
-      asp[t] = g.species[j];
+      nb[2 * t + 1] = make_float4(0.5f * cs + 0.5f, dfc_a * sn, ir, __int_as_float(g.species[j]));
       sg[3 * t] = sg[3 * t + 1] = sg[3 * t + 2] = 0.f;
     }
     __syncwarp();
@@ -626,13 +619,14 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
       float gjx = 0.f, gjy = 0.f, gjz = 0.f;
       if (valid) {
         decode_pair(P, na, j, k);
-        const int b = pair_block(asp[j], asp[k]);
-        const float4 uj = avec[j], uk = avec[k];  // unit vectors, distances
+        const float4 uj = nb[2 * j], uk = nb[2 * k];  // unit vectors, distances
+        const float4 pj = nb[2 * j + 1], pk = nb[2 * k + 1];  // fc, dfc/dr, 1 / r, species
+        const int b = pair_block(__float_as_int(pj.w), __float_as_int(pk.w));
         const float cost = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
         const float cp = 0.95f * cost;
         const float sp = sqrtf(fmaxf(1.f - cp * cp, 1e-12f));
         const float qs = __fdividef(cp, sp);
-        const float fcj = afc[j], fck = afc[k];
+        const float fcj = pj.x, fck = pk.x;
         const float u = 0.5f * (uj.w + uk.w);
         const float4* gp = reinterpret_cast<const float4*>(gA + b * kGAStride);
         float A[kShfZ], dA[kShfZ];
@@ -660,10 +654,10 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
         const float fcjk = fcj * fck;
         const float dEdcos = 0.95f * fcjk * dVdc;
         const float dEdu = fcjk * dVdu;
-        const float dEdrj = 0.5f * dEdu + V * adfc[j] * fck;
-        const float dEdrk = 0.5f * dEdu + V * fcj * adfc[k];
+        const float dEdrj = 0.5f * dEdu + V * pj.y * fck;
+        const float dEdrk = 0.5f * dEdu + V * fcj * pk.y;
         // d cos / d r_j = (u_k - cos u_j) / |r_j|,  d |r_j| / d r_j = u_j
-        const float aj = dEdcos * ainv[j], ak = dEdcos * ainv[k];
+        const float aj = dEdcos * pj.z, ak = dEdcos * pk.z;
         gjx = fmaf(aj, fmaf(-cost, uj.x, uk.x), dEdrj * uj.x);
         gjy = fmaf(aj, fmaf(-cost, uj.y, uk.y), dEdrj * uj.y);
         gjz = fmaf(aj, fmaf(-cost, uj.z, uk.z), dEdrj * uj.z);
