@@ -295,6 +295,9 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
   const unsigned FULL = 0xffffffffu;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = blockIdx.x * (blockDim.x >> 5) + warp;
+  // the first-layer product may launch (and run its prologue) once every CTA
+  // of this grid has started; it waits for this grid's results
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (q >= g.n_atoms) return;  // warp-uniform; no block-level barriers below
   float* buf = smem + (size_t)warp * aev_fwd_warp_floats(nl.cap_r, nl.cap_a);  // [12][36]
   float* R2 = buf;                                       // [2][112], radial phase only

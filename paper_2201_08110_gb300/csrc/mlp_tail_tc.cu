@@ -186,6 +186,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  // prologue done: the next kernel may launch; h1 comes from the kernel before
+  pdl_launch_dependents();
+  pdl_wait();
 
   if (warp == 0) {
     if (lane == 0) {
@@ -524,9 +527,9 @@ void launch_mlp_tail(const TailProblem* probs, const GemmTile* tiles, const int*
   TailMaps m;
   std::memcpy(&m, maps, sizeof(m));
   if (p == Prec::BF16)
-    k_mlp_tail<__nv_bfloat16><<<n_ctas, kThreads, kSmemBytes, s>>>(m, probs, tiles, cta_off, reverse, status);
+    launch_pdl(k_mlp_tail<__nv_bfloat16>, n_ctas, kThreads, kSmemBytes, s, m, probs, tiles, cta_off, reverse, status);
   else
-    k_mlp_tail<__half><<<n_ctas, kThreads, kSmemBytes, s>>>(m, probs, tiles, cta_off, reverse, status);
+    launch_pdl(k_mlp_tail<__half>, n_ctas, kThreads, kSmemBytes, s, m, probs, tiles, cta_off, reverse, status);
 }
 
 }  // namespace nnp

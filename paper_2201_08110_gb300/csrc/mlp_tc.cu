@@ -109,6 +109,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  // prologue done: the next kernel may launch; the inputs (and the outputs'
+  // previous readers) belong to the kernels before this one
+  pdl_launch_dependents();
+  pdl_wait();
 
   if (warp == 0) {
     if (lane == 0) {
@@ -323,9 +327,9 @@ void launch_gemm_tc(const GemmProblem* probs, const GemmTile* tiles, const int* 
   TcMaps m;
   std::memcpy(&m, maps, sizeof(m));
   if (p == Prec::BF16)
-    k_gemm_tc<__nv_bfloat16><<<n_ctas, kThreads, kSmemBytes, s>>>(m, probs, tiles, cta_off, b_box_rows, status);
+    launch_pdl(k_gemm_tc<__nv_bfloat16>, n_ctas, kThreads, kSmemBytes, s, m, probs, tiles, cta_off, b_box_rows, status);
   else
-    k_gemm_tc<__half><<<n_ctas, kThreads, kSmemBytes, s>>>(m, probs, tiles, cta_off, b_box_rows, status);
+    launch_pdl(k_gemm_tc<__half>, n_ctas, kThreads, kSmemBytes, s, m, probs, tiles, cta_off, b_box_rows, status);
 }
 
 }  // namespace nnp

@@ -11,6 +11,8 @@
 //     element's atoms form one contiguous block for the matrix products.
 #pragma once
 
+#include <utility>
+
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -149,6 +151,25 @@ struct GemmTile {
   int problem, m0, n0;
   int width;  // columns of the tile; 0: the weight box's rows (clipped to N)
 };
+
+// Launch with programmatic stream serialization: the kernel may start while
+// the previous kernel in the stream finishes; it waits (griddepcontrol.wait)
+// before touching that kernel's results.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // ---- kernels' host launchers ------------------------------------------------
 

@@ -206,6 +206,15 @@ __device__ __forceinline__ float celu01_fast(float z) {
   return fmaxf(z, fmaf(0.1f, celu01_exp(z), -0.1f));
 }
 
+// Programmatic dependent launch: let the next kernel in the stream start its
+// prologue, and wait until the kernels this one depends on have completed
+// (with their memory visible).  Both are no-ops in a launch without the
+// programmatic-serialization attribute.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // TMA tile store from shared memory (bulk-group completion) and the waits on
 // this thread's committed stores.
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
