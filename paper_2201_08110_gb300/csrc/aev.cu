@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_neighbors_mol(Geometry g, Ne
                                                                   unsigned* status) {
   extern __shared__ float4 spos[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // the featurizer may launch
   const int4 w = work[blockIdx.x];
   const int a0 = w.x, n = w.y, a1 = a0 + n;
   const bool staged = n <= kNbrStageMax;
@@ -298,6 +299,7 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
   // the first-layer product may launch (and run its prologue) once every CTA
   // of this grid has started; it waits for this grid's results
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");  // neighbour lists of the kernel before
   if (q >= g.n_atoms) return;  // warp-uniform; no block-level barriers below
   float* buf = smem + (size_t)warp * aev_fwd_warp_floats(nl.cap_r, nl.cap_a);  // [12][36]
   float* R2 = buf;                                       // [2][112], radial phase only
@@ -505,7 +507,6 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
   const int4 w = pass == 0 ? work[blockIdx.x] : make_int4(0, 0, 0, 0);
   const int a0 = w.x, n_mol = w.y, q0 = w.z, q1 = w.w;
   const bool smem_acc = pass == 0 && n_mol <= smem_atoms_max;
-  const int n_ovf = pass == 0 ? 0 : ovf[0];
   double* accm = reinterpret_cast<double*>(smem_raw);  // [nwarps][smem_atoms_max][3]
   float* gR = reinterpret_cast<float*>(accm + (size_t)nwarps * smem_atoms_max * 3) +
               (size_t)warp * adj_warp_floats(nl.cap_r, stage_cap);
@@ -519,6 +520,9 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
   if (smem_acc)
     for (int t = threadIdx.x; t < nwarps * smem_atoms_max * 3; t += blockDim.x) accm[t] = 0.0;
   __syncthreads();
+  // dE/dG (and the overflow list) come from the kernels before this one
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int n_ovf = pass == 0 ? 0 : ovf[0];
 
   const float etaR = -c.EtaR * kLog2e, etaA = -c.EtaA * kLog2e;
   const float inv_rcr = 1.f / c.Rcr, inv_rca = 1.f / c.Rca;
@@ -768,14 +772,14 @@ void launch_aev(const Geometry& g, const NeighborLists& nl, const AevConst& c,
   const size_t smem = aev_fwd_smem_bytes(nl.cap_r, nl.cap_a, warps);
   switch (prec) {
     case Prec::F32:
-      k_aev<float><<<blocks, warps * 32, smem, s>>>(g, nl, c, row_of_int, (float*)out);
+      launch_pdl(k_aev<float>, blocks, warps * 32, smem, s, g, nl, c, row_of_int, (float*)out);
       break;
     case Prec::BF16:
-      k_aev<__nv_bfloat16><<<blocks, warps * 32, smem, s>>>(g, nl, c, row_of_int,
-                                                           (__nv_bfloat16*)out);
+      launch_pdl(k_aev<__nv_bfloat16>, blocks, warps * 32, smem, s, g, nl, c, row_of_int,
+                 (__nv_bfloat16*)out);
       break;
     case Prec::F16:
-      k_aev<__half><<<blocks, warps * 32, smem, s>>>(g, nl, c, row_of_int, (__half*)out);
+      launch_pdl(k_aev<__half>, blocks, warps * 32, smem, s, g, nl, c, row_of_int, (__half*)out);
       break;
   }
 }
@@ -796,9 +800,9 @@ void launch_aev_adjoint(const Geometry& g, const NeighborLists& nl, const AevCon
                         cudaStream_t s) {
   if (n_work <= 0) return;
   const int stage = aev_adj_stage_cap(nl.cap_a);
-  cudaMemsetAsync(ovf, 0, sizeof(int), s);
-  k_aev_adjoint<<<n_work, warps * 32, aev_adj_smem_bytes(nl.cap_r, stage, warps, mol_atoms_smem_max),
-                  s>>>(g, nl, c, row_of_int, dG, work, orig, F, mol_atoms_smem_max, stage, ovf, 0);
+  // ovf[0] was zeroed at the start of the step
+  launch_pdl(k_aev_adjoint, n_work, warps * 32, aev_adj_smem_bytes(nl.cap_r, stage, warps, mol_atoms_smem_max),
+             s, g, nl, c, row_of_int, dG, work, orig, F, mol_atoms_smem_max, stage, ovf, 0);
   if (stage < nl.cap_a) {  // two CTAs per SM: dense systems defer most centres; an empty pass is cheap
     static int sms = 0;
     if (!sms) {
