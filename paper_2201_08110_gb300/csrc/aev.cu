@@ -186,11 +186,12 @@ template <> __device__ __forceinline__ __nv_bfloat16 cvt_out<__nv_bfloat16>(floa
 template <> __device__ __forceinline__ __half cvt_out<__half>(float v) { return __float2half_rn(v); }
 
 // Per-warp shared memory of the forward kernel (floats):
-//   buf[12][36] (the radial accumulators R2[2][112] alias it) | meta: block prefix
-//   bpre[32], group start gs[8], group count gn[8] (ints) |
+//   buf[12][36] (the radial accumulators R2[2][112] alias it) | meta (ints): block
+//   prefix bpre[32], block decode records bm int4[28] and be int2[28], group
+//   start gs[8], group count gn[8] |
 //   staging union: radial {rd, rfc, rsp}[cap_r]  or  angular {avec float4, afc, asp}[cap_a]
 constexpr int kBufStride = 36;  // phase-1 factor rows: 16-byte aligned, bank-spread
-constexpr int kMeta = 48;
+constexpr int kMeta = 32 + 4 * kPairBlocks + 2 * kPairBlocks + 16;
 __host__ __device__ constexpr int aev_fwd_warp_floats(int cap_r, int cap_a) {
   return 12 * kBufStride + kMeta + (3 * cap_r > 6 * cap_a ? 3 * cap_r : 6 * cap_a);
 }
@@ -225,10 +226,18 @@ __device__ __forceinline__ int pair_block(int s, int t) {
 // Element groups of an element-sorted angular neighbour list and the prefix
 // of the block-major pair enumeration, each block padded to a multiple of 4
 // pairs (the padding pairs contribute zero).  cnt_s: on lanes 0..6 the size
-// of element group s.  Writes gs[7] (group starts), gn[7] (sizes) and
-// bpre[29] (first pair of each block, bpre[28] = padded number of pairs);
-// call with the whole warp, then __syncwarp before reading.
-__device__ __forceinline__ void angular_blocks(int cnt_s, int lane, int* gs, int* gn, int* bpre) {
+// of element group s.  Writes gs[7] (group starts), gn[7] (sizes), bpre[29]
+// (first pair of each block, bpre[28] = padded number of pairs) and for each
+// block its decode record: bm[b] = (row width W, first list position of the
+// j group, of the k group, pairs), be[b] = (n for a same-element block, else
+// 0; bits of 1/W).  A block of two elements is a rectangle: pair l is (row
+// l / W, column l % W).  A same-element block of n atoms is its upper
+// triangle folded into a rectangle of width W = n - 1 (n even) or n (n odd):
+// row a holds the n-1-a pairs (a, a+1..) followed by the pairs of row
+// n-1-a (n even) or n-2-a (n odd), so that every row has W pairs.  Call with
+// the whole warp, then __syncwarp before reading.
+__device__ __forceinline__ void angular_blocks(int cnt_s, int lane, int* gs, int* gn, int* bpre,
+                                               int4* bm, int2* be) {
   const unsigned FULL = 0xffffffffu;
   int start = cnt_s;
 #pragma unroll
@@ -243,7 +252,14 @@ __device__ __forceinline__ void angular_blocks(int cnt_s, int lane, int* gs, int
   }
   const int bs = lane < kPairBlocks ? kBlkS[lane] : 0, bt = lane < kPairBlocks ? kBlkT[lane] : 0;
   const int ns = __shfl_sync(FULL, cnt_s, bs), nt = __shfl_sync(FULL, cnt_s, bt);
+  const int gss = __shfl_sync(FULL, start, bs), gst = __shfl_sync(FULL, start, bt);
   const int size = lane < kPairBlocks ? (bs == bt ? ns * (ns - 1) / 2 : ns * nt) : 0;
+  if (lane < kPairBlocks) {
+    const int w = bs == bt ? ((ns & 1) ? ns : ns - 1) : nt;
+    const int wd = w > 0 ? w : 1;
+    bm[lane] = make_int4(wd, gss, gst, size);
+    be[lane] = make_int2(bs == bt ? ns : 0, __float_as_int(1.f / (float)wd));
+  }
   int incl = (size + 3) & ~3;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -256,28 +272,38 @@ __device__ __forceinline__ void angular_blocks(int cnt_s, int lane, int* gs, int
 
 // Pair P of the (padded) block-major enumeration: its block and the list
 // positions j < k of its two neighbours, or j = -1 for a padding pair.
-__device__ __forceinline__ int decode_block_pair(int P, const int* bpre, const int* gs,
-                                                 const int* gn, int& j, int& k) {
+__device__ __forceinline__ int decode_block_pair(int P, const int* bpre, const int4* bm, const int2* be,
+                                                 int& j, int& k) {
   int b = 0;
 #pragma unroll
   for (int step = 16; step; step >>= 1)
     if (b + step <= kPairBlocks - 1 && bpre[b + step] <= P) b += step;
   const int l = P - bpre[b];
-  const int s = kBlkS[b], t = kBlkT[b];
-  const int size = s == t ? gn[s] * (gn[s] - 1) / 2 : gn[s] * gn[t];
-  if (l >= size) {
+  const int4 m = bm[b];  // W, j-group start, k-group start, pairs
+  const int2 e = be[b];  // n (same-element block) or 0, 1/W
+  if (l >= m.w) {
     j = k = -1;
-  } else if (s != t) {
-    const int n_t = gn[t];
-    int qd = (int)__fdividef((float)l + 0.5f, (float)n_t);
-    if (qd * n_t > l) --qd;
-    else if ((qd + 1) * n_t <= l) ++qd;
-    j = gs[s] + qd;
-    k = gs[t] + (l - qd * n_t);
-  } else {
-    decode_pair(l, gn[s], j, k);
-    j += gs[s];
-    k += gs[s];
+    return b;
+  }
+  int q = (int)((float)l * __int_as_float(e.y));  // l / W, then exact
+  int c = l - q * m.x;
+  if (c < 0) {
+    --q;
+    c += m.x;
+  } else if (c >= m.x) {
+    ++q;
+    c -= m.x;
+  }
+  const int n = e.x;
+  if (n == 0) {  // two elements: rectangle
+    j = m.y + q;
+    k = m.z + c;
+  } else {  // one element: folded triangle, row q
+    const int span = n - 1 - q;
+    const int jj = c < span ? q : n - 1 - q - (n & 1);
+    const int kk = c < span ? q + 1 + c : jj + 1 + (c - span);
+    j = m.y + jj;
+    k = m.y + kk;
   }
   return b;
 }
@@ -304,7 +330,9 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
   float* buf = smem + (size_t)warp * aev_fwd_warp_floats(nl.cap_r, nl.cap_a);  // [12][36]
   float* R2 = buf;                                       // [2][112], radial phase only
   int* bpre = reinterpret_cast<int*>(buf + 12 * kBufStride);  // [29] block prefix
-  int* gs = bpre + 32;                                   // [7] group start
+  int4* bm = reinterpret_cast<int4*>(bpre + 32);         // [28] block decode records
+  int2* be = reinterpret_cast<int2*>(bm + kPairBlocks);  // [28]
+  int* gs = reinterpret_cast<int*>(be + kPairBlocks);    // [7] group start
   int* gn = gs + 8;                                      // [7] group size
   float* U = buf + 12 * kBufStride + kMeta;              // staging union (16-byte aligned)
   float* rd = U;
@@ -371,7 +399,7 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
       }
     }
   }
-  angular_blocks(cnt_s, lane, gs, gn, bpre);
+  angular_blocks(cnt_s, lane, gs, gn, bpre, bm, be);
   __syncwarp();
   const int T = bpre[kPairBlocks];
 
@@ -387,7 +415,7 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
     if (valid) {
       // phase 1: this lane's pair -> 8 distance factors, 4 angle factors
       int j, k;
-      const int b = decode_block_pair(P, bpre, gs, gn, j, k);
+      const int b = decode_block_pair(P, bpre, bm, be, j, k);
       if (j >= 0) {
         const float4 rj = avec[j], rk = avec[k];
         const float cost = __fdividef(rj.x * rk.x + rj.y * rk.y + rj.z * rk.z, rj.w * rk.w);
