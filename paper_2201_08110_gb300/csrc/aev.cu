@@ -165,17 +165,23 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_neighbors_mol(Geometry g, Ne
   }
 }
 
-// Row j and column k of the P-th pair (j < k) of n items, pairs ordered
-// row-major over the strict upper triangle.
-__device__ __forceinline__ void decode_pair(int P, int n, int& j, int& k) {
-  const float b = (float)(2 * n - 1);
-  int jj = (int)((b - sqrtf(fmaxf(b * b - 8.f * (float)P, 0.f))) * 0.5f);
-  jj = max(0, min(jj, n - 2));
-  // start of row r: r (2n - r - 1) / 2
-  while (jj > 0 && (jj * (2 * n - jj - 1)) / 2 > P) --jj;
-  while (jj + 1 <= n - 2 && ((jj + 1) * (2 * n - jj - 2)) / 2 <= P) ++jj;
-  j = jj;
-  k = P - (jj * (2 * n - jj - 1)) / 2 + jj + 1;
+// Pair P (0 <= P < n(n-1)/2) of n items, j < k, in the folded-triangle
+// order: rows of width W = n - 1 (n even) or n (n odd); row a holds the pairs
+// (a, a+1 .. n-1) followed by those of row n-1-a (n even) or n-2-a (n odd),
+// so each row is two runs of constant j.  invW = 1/W as a float.
+__device__ __forceinline__ void fold_pair(int P, int n, int W, float invW, int& j, int& k) {
+  int q = (int)((float)P * invW);  // P / W, then exact
+  int c = P - q * W;
+  if (c < 0) {
+    --q;
+    c += W;
+  } else if (c >= W) {
+    ++q;
+    c -= W;
+  }
+  const int span = n - 1 - q;
+  j = c < span ? q : n - 1 - q - (n & 1);
+  k = c < span ? q + 1 + c : j + 1 + (c - span);
 }
 
 template <typename T> __device__ __forceinline__ T cvt_out(float v);
@@ -298,7 +304,7 @@ __device__ __forceinline__ int decode_block_pair(int P, const int* bpre, const i
   if (n == 0) {  // two elements: rectangle
     j = m.y + q;
     k = m.z + c;
-  } else {  // one element: folded triangle, row q
+  } else {  // one element: folded triangle (as fold_pair), row q
     const int span = n - 1 - q;
     const int jj = c < span ? q : n - 1 - q - (n & 1);
     const int kk = c < span ? q + 1 + c : jj + 1 + (c - span);
@@ -644,16 +650,18 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
       }
     }
 
-    // ---- angular: lane per pair, pairs row-major over the list (j rising,
-    //      so lanes sharing j are contiguous and k differs between lanes) ----
+    // ---- angular: lane per pair, pairs in folded-triangle order over the list
+    //      (runs of equal j on contiguous lanes, k differing between lanes) ----
     const int T = na * (na - 1) / 2;
+    const int fw = (na & 1) ? na : max(na - 1, 1);
+    const float inv_fw = 1.f / (float)fw;
     for (int base = 0; base < T; base += 32) {
       const int P = base + lane;
       const bool valid = P < T;
       int j = -1, k = -1;
       float gjx = 0.f, gjy = 0.f, gjz = 0.f;
       if (valid) {
-        decode_pair(P, na, j, k);
+        fold_pair(P, na, fw, inv_fw, j, k);
         const float4 uj = nb[2 * j], uk = nb[2 * k];  // unit vectors, distances
         const float4 pj = nb[2 * j + 1], pk = nb[2 * k + 1];  // fc, dfc/dr, 1 / r, species
         const int b = pair_block(__float_as_int(pj.w), __float_as_int(pk.w));
