@@ -629,6 +629,7 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
         sincospif(r * inv_rcr, &sn, &cs);
         const float fc = 0.5f * cs + 0.5f;
         const float dfc = dfc_r * sn;
+        const float afc = m2etaR * fc;  // d(e fc)/dr / e = -2 eta x fc + dfc = afc x + dfc
         const float4* gsp = reinterpret_cast<const float4*>(gR + g.species[j] * kGRStride);
         float dEdr = 0.f;
 #pragma unroll
@@ -639,7 +640,7 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
           for (int h = 0; h < 4; ++h) {
             const float x = r - c.ShfR[4 * k4 + h];
             const float e = ex2_ftz(etaR * x * x);
-            dEdr = fmaf(gk[h] * e, fmaf(m2etaR * x, fc, dfc), dEdr);
+            dEdr = fmaf(gk[h] * e, fmaf(afc, x, dfc), dEdr);
           }
         }
         const float s = 0.25f * dEdr * ir;
@@ -692,11 +693,11 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
           const float SdA = fmaf(g4.x, dA[0], fmaf(g4.y, dA[1], fmaf(g4.z, dA[2], g4.w * dA[3])));
           V = fmaf(R, SA, V);
           dVdc = fmaf(R, SdA, dVdc);
-          dVdu = fmaf(m2etaA * x * R, SA, dVdu);
+          dVdu = fmaf(x * R, SA, dVdu);  // times -2 eta below
         }
         const float fcjk = fcj * fck;
         const float dEdcos = 0.95f * fcjk * dVdc;
-        const float dEdu = fcjk * dVdu;
+        const float dEdu = m2etaA * fcjk * dVdu;
         const float dEdrj = 0.5f * dEdu + V * pj.y * fck;
         const float dEdrk = 0.5f * dEdu + V * fcj * pk.y;
         // d cos / d r_j = (u_k - cos u_j) / |r_j|,  d |r_j| / d r_j = u_j
