@@ -198,8 +198,8 @@ def src_hash(*names):
 # kernel, keyed by the kernel's source hash at capture time, in bytes per atom;
 # scaled to the bench workload by atoms.
 NCU_TRAFFIC = {
-    ("adjoint", "c878888524d4"): 4607.6,  # ncu --set full, 512-molecule batch, FP16
-    ("tail", "686ac585ff42"): 6406.1,  # ncu --set full, 512-molecule batch, FP16
+    ("adjoint", "b1cd173b9794"): 4601.9,  # ncu --set full, 512-molecule batch, FP16
+    ("tail", "91331307bf31"): 6404.3,  # ncu --set full, 512-molecule batch, FP16
 }
 
 
