@@ -278,12 +278,14 @@ __device__ __forceinline__ void angular_blocks(int cnt_s, int lane, int* gs, int
 
 // Pair P of the (padded) block-major enumeration: its block and the list
 // positions j < k of its two neighbours, or j = -1 for a padding pair.
-__device__ __forceinline__ int decode_block_pair(int P, const int* bpre, const int4* bm, const int2* be,
-                                                 int& j, int& k) {
-  int b = 0;
-#pragma unroll
-  for (int step = 16; step; step >>= 1)
-    if (b + step <= kPairBlocks - 1 && bpre[b + step] <= P) b += step;
+// b0: the block holding the warp's first pair of this iteration, base: that
+// pair (the iteration covers base .. base + 31).
+__device__ __forceinline__ int decode_block_pair(int P, int b0, int base, const int* bpre, const int4* bm,
+                                                 const int2* be, int& j, int& k) {
+  // the last block starting at or before P among those starting in the
+  // iteration's window (a uniform walk over the window's few block starts)
+  int b = b0;
+  for (int bb = b0 + 1; bb < kPairBlocks && bpre[bb] < base + 32; ++bb) b = bpre[bb] <= P ? bb : b;
   const int l = P - bpre[b];
   const int4 m = bm[b];  // W, j-group start, k-group start, pairs
   const int2 e = be[b];  // n (same-element block) or 0, 1/W
@@ -414,14 +416,16 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
   const float etaA = -c.EtaA * kLog2e;
   float acc = 0.f;
   int pcur = -1;  // block being accumulated; blocks before it are written
+  int b0 = 0;  // block holding the iteration's first pair
   for (int base = 0; base < T; base += 32) {
+    while (bpre[b0 + 1] <= base) ++b0;  // uniform; bpre[28] = T > base
     const int P = base + lane;
     const bool valid = P < T;
     int pl = -1;
     if (valid) {
       // phase 1: this lane's pair -> 8 distance factors, 4 angle factors
       int j, k;
-      const int b = decode_block_pair(P, bpre, bm, be, j, k);
+      const int b = decode_block_pair(P, b0, base, bpre, bm, be, j, k);
       if (j >= 0) {
         const float4 rj = avec[j], rk = avec[k];
         const float cost = __fdividef(rj.x * rk.x + rj.y * rk.y + rj.z * rk.z, rj.w * rk.w);
@@ -444,34 +448,35 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
         for (int f = 0; f < kShfA + kShfZ; ++f) buf[f * kBufStride + lane] = 0.f;
       }
       pl = b;
+    } else {  // past the last pair: zero factors, so phase 2 can walk all 8 groups
+#pragma unroll
+      for (int f = 0; f < kShfA + kShfZ; ++f) buf[f * kBufStride + lane] = 0.f;
     }
     // phase 2: lane = feature (a, z).  Blocks are padded to multiples of 4
-    // pairs, so each group of 4 pairs lies in one block: walk the 8 groups,
-    // writing the accumulated block where the next one starts.
+    // pairs, so each group of 4 pairs lies in one block: walk the 8 groups
+    // (groups past the last pair hold zeros and add nothing), writing the
+    // accumulated block where the next one starts.
     const int prev = __shfl_up_sync(FULL, pl, 1);
     const unsigned starts = __ballot_sync(FULL, valid && (lane == 0 || prev != pl));
-    const int ng = min(32, T - base) >> 2;
     __syncwarp();
     const float4* ra4 = reinterpret_cast<const float4*>(buf + fa * kBufStride);
     const float4* za4 = reinterpret_cast<const float4*>(buf + (kShfA + fz) * kBufStride);
 #pragma unroll
     for (int gi = 0; gi < 8; ++gi) {
-      if (gi < ng) {
-        if ((starts >> (4 * gi)) & 1u) {
-          const int p = __shfl_sync(FULL, pl, 4 * gi);
-          if (p != pcur) {  // block pcur is complete: write it, and zeros for empty blocks
-            if (pcur >= 0) dst[kRadial + pcur * kAngPerBlock + lane] = cvt_out<TOut>(acc);
-            for (int e = pcur + 1; e < p; ++e) dst[kRadial + e * kAngPerBlock + lane] = cvt_out<TOut>(0.f);
-            acc = 0.f;
-            pcur = p;
-          }
+      if ((starts >> (4 * gi)) & 1u) {
+        const int p = __shfl_sync(FULL, pl, 4 * gi);
+        if (p != pcur) {  // block pcur is complete: write it, and zeros for empty blocks
+          if (pcur >= 0) dst[kRadial + pcur * kAngPerBlock + lane] = cvt_out<TOut>(acc);
+          for (int e = pcur + 1; e < p; ++e) dst[kRadial + e * kAngPerBlock + lane] = cvt_out<TOut>(0.f);
+          acc = 0.f;
+          pcur = p;
         }
-        const float4 r4 = ra4[gi], z4 = za4[gi];
-        acc = fmaf(r4.x, z4.x, acc);
-        acc = fmaf(r4.y, z4.y, acc);
-        acc = fmaf(r4.z, z4.z, acc);
-        acc = fmaf(r4.w, z4.w, acc);
       }
+      const float4 r4 = ra4[gi], z4 = za4[gi];
+      acc = fmaf(r4.x, z4.x, acc);
+      acc = fmaf(r4.y, z4.y, acc);
+      acc = fmaf(r4.z, z4.z, acc);
+      acc = fmaf(r4.w, z4.w, acc);
     }
     __syncwarp();
   }
