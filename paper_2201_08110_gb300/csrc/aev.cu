@@ -1,26 +1,33 @@
 // aev.cu -- neighbour lists, the ANI featurizer and its reverse pass.
 //
-// Neighbour search: one warp per centre atom scans its molecule (or periodic
-// region) 32 candidates at a time; a ballot and a prefix popcount compact the
-// accepted candidates in ascending internal index, so every list is sorted
-// and therefore grouped by element.  The cutoff test is FP32 with an FP64
-// recheck of the exact squared distance inside a 1e-4 relative guard band,
-// which makes the pair sets identical to an FP64 evaluation.
+// Neighbour search: one CTA per chunk of 64 centres of a molecule, the
+// molecule's positions staged in shared memory; one warp per centre scans
+// the molecule 32 candidates at a time; a ballot and a prefix popcount
+// compact the accepted candidates in ascending internal index, so every list
+// is sorted and therefore grouped by element.  The cutoff test is FP32 with
+// an FP64 recheck of the exact squared distance inside a 1e-4 relative guard
+// band, which makes the pair sets identical to an FP64 evaluation.  (The
+// one-warp-per-centre kernel without staging serves the allocation-free
+// entry point.)
 //
 // Featurizer (the modified Behler-Parrinello functions the paper names in
 // Sec. 1; Sec. 2 "Optimization" describes the custom CUDA featurizer): one
 // warp per centre.  Radial terms: lanes = 16 shifts x 2 neighbours, summed
 // into a per-warp shared-memory row (each lane owns one column: no atomics).
-// Angular terms, two phases per 32 neighbour pairs: (1) lane per pair
-// computes the 4 angle factors, 8 distance factors and its species-pair block;
-// (2) lane per feature (8 x 4) walks the 32 pairs and accumulates
-// R_a * A_z into the block in registers, flushing on a block change.
+// Angular terms: neighbour pairs enumerated block by block (species pair),
+// each block padded to a multiple of 4 pairs and decoded in closed form
+// (rectangle, or folded triangle for one element); two phases per 32 pairs:
+// (1) lane per pair computes the 4 angle factors and 8 distance factors;
+// (2) lane per feature (8 x 4) walks the 8 groups of 4 pairs and accumulates
+// R_a * A_z into its block in registers, writing the block when the next
+// one starts.
 //
 // Reverse pass: one warp per centre, lane per neighbour (radial) and lane per
-// pair (angular); per-neighbour gradients gather in shared memory, then go to
-// a per-warp FP64 accumulator of the molecule (or FP64 global atomics for
-// large regions); each CTA adds its molecule totals to the forces with FP64
-// atomics.
+// pair (angular, folded-triangle order); per-neighbour gradients gather in
+// shared memory (the j side of a run of pairs by a segmented warp scan), then
+// go to a per-warp FP64 accumulator of the molecule or to FP64 global
+// atomics.  Centres with more angular neighbours than the main launch stages
+// are deferred to a second launch.
 #include "nnp_internal.cuh"
 
 namespace nnp {
