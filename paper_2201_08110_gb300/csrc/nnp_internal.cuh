@@ -173,8 +173,10 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, siz
 
 // ---- kernels' host launchers ------------------------------------------------
 
+// F_zero / ovf_zero (or null): forces and the reverse pass's overflow count
+// to zero in the same launch.
 void launch_gather_positions(const float* pos_caller, const int* orig_of_int, float4* pos_int,
-                             int n, unsigned* status, cudaStream_t s);
+                             int n, unsigned* status, double* F_zero, int* ovf_zero, cudaStream_t s);
 // Neighbour search by work items (a0, molecule atoms, first centre, end centre),
 // chunks of nbr_chunk() centres of one molecule, one CTA each.
 int nbr_chunk();

@@ -80,11 +80,21 @@ __global__ void k_species_place(const int* __restrict__ species, const int* __re
   }
 }
 
+// Caller-order positions into internal order (float4), with a status bit for
+// non-finite input; when forces follow, also zeroes the forces (caller order,
+// FP64) and the reverse pass's overflow count.
 __global__ void k_gather_positions(const float* __restrict__ pos, const int* __restrict__ orig,
-                                   float4* __restrict__ out, int n, unsigned* __restrict__ status) {
+                                   float4* __restrict__ out, int n, unsigned* __restrict__ status,
+                                   double* __restrict__ F, int* __restrict__ ovf) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q == 0 && ovf) *ovf = 0;
   if (q >= n) return;
   const int a = orig[q];
+  if (F) {
+    F[3 * (size_t)a] = 0.0;
+    F[3 * (size_t)a + 1] = 0.0;
+    F[3 * (size_t)a + 2] = 0.0;
+  }
   const float x = pos[3 * (size_t)a], y = pos[3 * (size_t)a + 1], z = pos[3 * (size_t)a + 2];
   if (!(isfinite(x) && isfinite(y) && isfinite(z))) atomicOr(status, kStatNonFinite);
   out[q] = make_float4(x, y, z, 0.f);
@@ -218,9 +228,10 @@ void launch_species_place(const int* species, const int* mol_off, int n_mols,
                                              species_int, mol_start, mol_end, row_elem);
 }
 
-void launch_gather_positions(const float* pos, const int* orig, float4* out, int n,
-                             unsigned* status, cudaStream_t s) {
-  if (n > 0) k_gather_positions<<<(n + 255) / 256, 256, 0, s>>>(pos, orig, out, n, status);
+void launch_gather_positions(const float* pos, const int* orig, float4* out, int n, unsigned* status,
+                             double* F_zero, int* ovf_zero, cudaStream_t s) {
+  if (n > 0)
+    k_gather_positions<<<(n + 255) / 256, 256, 0, s>>>(pos, orig, out, n, status, F_zero, ovf_zero);
 }
 
 void launch_head(const float* z3, long ldz, Prec prec, const int* row_elem, const float* w4,
