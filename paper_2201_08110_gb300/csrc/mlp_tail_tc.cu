@@ -8,14 +8,17 @@
 //   d3 = (1/M) w4 * celu'(z3)                (start of the reverse pass)
 //   d2 = (d3 W3) * celu'(h2)                 (L3 reverse)
 //   d1 = (d2 W2) * celu'(h1)                 (L2 reverse, written over h1)
-// Only h1 comes from HBM (TMA, once) and only y and d1 go back: h2, d3 and
-// d2 live in shared memory, written by the epilogue warps directly in the
-// 128B-swizzled K-major layout that the next tcgen05.mma reads as its A
-// operand; every accumulator lives in tensor memory.  The weights stream
-// through a 3-stage TMA ring in the order the MMAs consume them.
+// Only h1 comes from HBM (TMA; phase 4 reads it again) and only y and d1 go
+// back: h2, d3 and d2 live in shared memory, written by the epilogue warps
+// directly in the 128B-swizzled K-major layout that the next tcgen05.mma
+// reads as its A operand; every accumulator lives in tensor memory.  The
+// weights stream through a 3-stage TMA ring in the order the MMAs consume
+// them.
 //
 // Roles (persistent CTA per SM over the tile list):
-//   warp 0, one lane: TMA producer (h1 tile, then W2, W3, W3^T, W2^T blocks);
+//   warp 0, one lane: TMA producer (h1 and W2 block by block, each h1 block
+//     as soon as the previous tile's MMAs are done with that block of A1;
+//     then the W3, W3^T, W2^T blocks);
 //   warp 18, one lane: TMA loads of phase 4's staged h1 tile;
 //   warp 1, one lane: tcgen05.mma issuer; the four phases of a tile alternate
 //     between two 256-column accumulators, and K block b of a phase waits
@@ -40,8 +43,8 @@ constexpr int kBK = 64;
 constexpr int kRing = 3;
 constexpr uint32_t kBlk = 128 * kBK * 2;     // one [128][64] 16-bit block: 16 KB
 constexpr uint32_t kRingBytes = 256 * kBK * 2;  // a weight block of up to 256 rows
-constexpr int kA1Blocks = 4;                 // h1 (<= 256 columns); d3 reuses it
-constexpr int kA2Blocks = 3;                 // h2, then d2 (<= 192 columns)
+constexpr int kA1Blocks = 4;                 // h1 (<= 256 columns), then h2 and d2 over it
+constexpr int kA2Blocks = 3;                 // d3 (<= 160 columns)
 constexpr int kEpiWarps = 16;  // four per TMEM lane quarter, 16 of every 64 columns each
 constexpr int kThreads = 64 + 32 * kEpiWarps + 32;  // + the phase-4 staging loader
 constexpr int kTmemCols = 512;  // two accumulators of 256 columns
@@ -136,19 +139,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   // rounded up to 1024 bytes by pointer arithmetic, so that accesses through
   // it stay shared-memory accesses
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  unsigned char* A1 = smem;                              // h1, later d3
-  unsigned char* A2 = A1 + kA1Blocks * kBlk;             // h2, later d2
+  unsigned char* A1 = smem;                              // h1, then h2, then d2 in place
+  unsigned char* A2 = A1 + kA1Blocks * kBlk;             // d3
   unsigned char* P4 = A2;  // phase 4: h1 in, d1 out, over A2 and the next 16 KB
   unsigned char* ring = A2 + (kA2Blocks + 1) * kBlk;
   uint64_t* full = reinterpret_cast<uint64_t*>(ring + kRing * kRingBytes);
   uint64_t* empty = full + kRing;
-  uint64_t* a1_full = empty + kRing;
-  uint64_t* a1_free = a1_full + 1;
-  uint64_t* acc_ready = a1_free + 1;  // [2] MMA -> epilogue, per accumulator
+  uint64_t* a1_full = empty + kRing;  // [4] producer -> MMA: block b of h1 loaded
+  uint64_t* a1_free = a1_full + 4;    // [4] MMA -> producer: block b of A1 consumed
+  uint64_t* acc_ready = a1_free + 4;  // [2] MMA -> epilogue, per accumulator
   uint64_t* acc_free = acc_ready + 2;  // [2] epilogue -> MMA: accumulator drained
   uint64_t* blk_done = acc_free + 2;   // [4] epilogue -> MMA: 64-column block of the next A written
   uint64_t* p4_full = blk_done + 4;    // producer -> epilogue: the tile's h1 is in P4
-  uint64_t* a2_free = p4_full + 1;     // MMA -> producer: phase-4 MMAs are done with A2
+  uint64_t* a2_free = p4_full + 1;     // MMA -> P4 loader: phase-3 MMAs are done with d3 (A2)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(a2_free + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   // [3][128]: the output-layer dot of each row over the column groups 1-3
@@ -163,8 +166,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(a1_full, 1);
-    mbar_init(a1_free, 1);
+    for (int b = 0; b < kA1Blocks; ++b) {
+      mbar_init(&a1_full[b], 1);
+      mbar_init(&a1_free[b], 1);
+    }
     for (int x = 0; x < 2; ++x) {
       mbar_init(&acc_ready[x], 1);
       mbar_init(&acc_free[x], kEpiWarps);
@@ -194,20 +199,39 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       // ---- TMA producer ----
       uint32_t it = 0, tcount = 0;
+      int first = 0;  // first A1 block the previous tile freed (past its h2 blocks)
       bool ok = true;
       for (int tile = tile_begin; ok && tile < tile_end; ++tile, ++tcount) {
         const GemmTile tl = tiles[tile];
         const TailProblem P = probs[tl.problem];
-        if (tcount > 0 && !mbar_wait(a1_free, (tcount - 1) & 1, abort_flag)) {
-          ok = false;
-          break;
-        }
         const int nb1 = nblocks(P.h1);
-        mbar_expect_tx(a1_full, (uint32_t)nb1 * kBlk);
-        for (int kb = 0; kb < nb1; ++kb)
-          tma_load_2d(A1 + (size_t)kb * kBlk, &maps.h1, P.a_col0 + kb * kBK, P.row0 + tl.m0, a1_full);
-        ok = produce_weights(&maps.w2, P.w2_row0, nblocks(P.h1), kBoxW2, ring, full, empty, it, abort_flag) &&
-             produce_weights(&maps.w3, P.w3_row0, nblocks(P.h2), kBoxW3, ring, full, empty, it, abort_flag);
+        // h1 and the matching W2 block, block by block, each as soon as the
+        // previous tile is done with that block of A1 (the blocks it freed
+        // first, first); blocks past h1 get a plain arrival
+        for (int i = 0; ok && i < kA1Blocks; ++i) {
+          const int kb = (first + i) % kA1Blocks;
+          if (tcount > 0 && !mbar_wait(&a1_free[kb], (tcount - 1) & 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          if (kb >= nb1) {
+            mbar_arrive(&a1_full[kb]);
+            continue;
+          }
+          mbar_expect_tx(&a1_full[kb], kBlk);
+          tma_load_2d(A1 + (size_t)kb * kBlk, &maps.h1, P.a_col0 + kb * kBK, P.row0 + tl.m0, &a1_full[kb]);
+          const int s = it % kRing;
+          const uint32_t use = it / kRing;
+          if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], kBoxW2 * kBK * 2);
+          tma_load_2d(ring + (size_t)s * kRingBytes, &maps.w2, kb * kBK, P.w2_row0, &full[s]);
+          ++it;
+        }
+        first = nblocks(P.h2);
+        ok = ok && produce_weights(&maps.w3, P.w3_row0, nblocks(P.h2), kBoxW3, ring, full, empty, it, abort_flag);
         if (ok && reverse)
           ok = produce_weights(&maps.w3t, P.w3t_row0, nblocks(P.h3), kBoxW3T, ring, full, empty, it, abort_flag) &&
                produce_weights(&maps.w2t, P.w2t_row0, nblocks(P.h2), kBoxW2T, ring, full, empty, it, abort_flag);
@@ -225,7 +249,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t used[2] = {0, 0};       // phases issued per accumulator
       uint32_t blk_waits[4] = {0, 0, 0, 0};
       bool ok = true;
-      auto phase = [&](int x, const unsigned char* a_base, int k, int n, bool wait_blocks) {
+      // phases 2-4: K block b waits for block b of the A operand from the
+      // epilogue; blk_free: commit each K block's completion there (the
+      // last reader of that block of A1)
+      auto phase = [&](int x, const unsigned char* a_base, int k, int n, uint64_t* blk_free) {
         if (!ok) return;
         if (used[x] > 0 && !mbar_wait(&acc_free[x], (used[x] - 1) & 1, abort_flag)) {
           ok = false;
@@ -236,13 +263,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t d = tmem + (uint32_t)(x * kTmemCols / 2);
         const int n_kb = nblocks(k);
         for (int kb = 0; kb < n_kb; ++kb, ++it) {
-          if (wait_blocks) {
-            if (!mbar_wait(&blk_done[kb], blk_waits[kb] & 1, abort_flag)) {
-              ok = false;
-              return;
-            }
-            ++blk_waits[kb];
+          if (!mbar_wait(&blk_done[kb], blk_waits[kb] & 1, abort_flag)) {
+            ok = false;
+            return;
           }
+          ++blk_waits[kb];
           const int s = it % kRing;
           if (!mbar_wait(&full[s], (it / kRing) & 1, abort_flag)) {
             ok = false;
@@ -255,27 +280,65 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int j = 0; j < ksteps; ++j)
             mma_f16(d, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc, (kb > 0 || j > 0) ? 1u : 0u);
           mma_commit(&empty[s]);
+          if (blk_free) mma_commit(&blk_free[kb]);
         }
         mma_commit(&acc_ready[x]);
         ++used[x];
       };
+      // L2 forward: A = h1, taken block by block in the order the producer
+      // loads it (the blocks the previous tile freed first, first)
+      auto phase1 = [&](const TailProblem& P, int first) {
+        if (!ok) return;
+        if (used[0] > 0 && !mbar_wait(&acc_free[0], (used[0] - 1) & 1, abort_flag)) {
+          ok = false;
+          return;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t idesc = instr_desc(fmt, (uint32_t)P.h2);
+        const uint32_t d = tmem;
+        const int nb1 = nblocks(P.h1);
+        bool acc = false;
+        for (int i = 0; i < kA1Blocks; ++i) {
+          const int kb = (first + i) % kA1Blocks;
+          if (!mbar_wait(&a1_full[kb], tcount & 1, abort_flag)) {
+            ok = false;
+            return;
+          }
+          if (kb >= nb1) continue;
+          const int s = it % kRing;
+          if (!mbar_wait(&full[s], (it / kRing) & 1, abort_flag)) {
+            ok = false;
+            return;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t da = smem_desc_sw128(A1 + (size_t)kb * kBlk);
+          const uint64_t db = smem_desc_sw128(ring + (size_t)s * kRingBytes);
+          const int ksteps = min(kBK, P.h1 - kb * kBK) / 16;
+          for (int j = 0; j < ksteps; ++j) {
+            mma_f16(d, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc, acc ? 1u : 0u);
+            acc = true;
+          }
+          mma_commit(&empty[s]);
+          ++it;
+        }
+        mma_commit(&acc_ready[0]);
+        ++used[0];
+        // A1 blocks past h2 are not read again in this tile
+        for (int kb = nblocks(P.h2); kb < kA1Blocks; ++kb) mma_commit(&a1_free[kb]);
+      };
+      int first = 0;
       for (int tile = tile_begin; ok && tile < tile_end; ++tile, ++tcount) {
         const GemmTile tl = tiles[tile];
         const TailProblem P = probs[tl.problem];
-        if (!mbar_wait(a1_full, tcount & 1, abort_flag)) {
-          ok = false;
-          break;
-        }
-        phase(0, A1, P.h1, P.h2, false);  // L2 forward
-        phase(1, A2, P.h2, P.h3, true);   // L3 forward, block by block of h2
-        if (!reverse) {
-          if (ok) mma_commit(a1_free);
-          continue;
-        }
-        phase(0, A1, P.h3, P.h2, true);  // L3 reverse, block by block of d3
-        if (ok) mma_commit(a1_free);     // d3 (over h1) consumed once these MMAs finish
-        phase(1, A2, P.h2, P.h1, true);  // L2 reverse, block by block of d2
-        if (ok) mma_commit(a2_free);     // d2 (A2) consumed once these MMAs finish
+        phase1(P, first);                 // L2 forward
+        first = nblocks(P.h2);
+        // L3 forward, block by block of h2 (over h1); without the reverse
+        // pass it is the last reader of those blocks of A1
+        phase(1, A1, P.h2, P.h3, reverse ? nullptr : a1_free);
+        if (!reverse) continue;
+        phase(0, A2, P.h3, P.h2, nullptr);  // L3 reverse, block by block of d3
+        if (ok) mma_commit(a2_free);        // d3 consumed: A2 may take phase 4's h1
+        phase(1, A1, P.h2, P.h1, a1_free);  // L2 reverse, block by block of d2 (over h2)
       }
       if (!ok) {
         atomicOr(status, kStatTimeout);
@@ -285,8 +348,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 2 + kEpiWarps) {
     if (lane == 0 && reverse) {
       // ---- phase-4 staging loader: h1 of each tile into P4 once the tile's
-      // phase-4 MMAs are done with A2 (apart from the ring producer, whose
-      // next weights must not wait for that) ----
+      // phase-3 MMAs are done with d3 in A2 (apart from the ring producer,
+      // whose next weights must not wait for that) ----
       uint32_t k = 0;
       bool ok = true;
       for (int tile = tile_begin; tile < tile_end; ++tile, ++k) {
@@ -363,9 +426,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const TailProblem P = probs[tl.problem];
       const int row = tl.m0 + r;
       const bool row_ok = row < P.Me;
-      // the previous tile's d1 store has read P4 (which overlaps A2) before
-      // anyone writes h2 there; the barrier also ends the readers of ypart
-      if (et == 0) bulk_wait_read();
+      // the barrier ends the previous tile's readers of ypart
       if (epi_stop()) break;
       {  // warm the L1 with this tile's b2, b3 and w4 (128-byte lines, one per thread)
         const int l2 = (P.h2 + 31) / 32, l3 = (P.h3 + 31) / 32;
@@ -375,7 +436,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (line) asm volatile("prefetch.global.L1 [%0];" ::"l"(line));
       }
 
-      // phase 1, L2 forward (accumulator 0): h2 = celu(acc + b2) -> A2, block by block
+      // phase 1, L2 forward (accumulator 0): h2 = celu(acc + b2) -> A1 (its
+      // MMAs, the last readers of h1 there, are complete), block by block
       {
         const uint32_t t = wait_acc(0);
         for (int b = 0; b < nblocks(P.h2); ++b) {
@@ -390,16 +452,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int i = 0; i < 8; ++i)
               o[i] = Pack<T>::two(celu01_fast(v[2 * i] + bias[2 * i]),
                                   celu01_fast(v[2 * i + 1] + bias[2 * i + 1]));
-            put16(A2, r, c, o);
+            put16(A1, r, c, o);
           }
           arrive(&blk_done[b]);
         }
         release(&acc_free[0]);
       }
 
-      // phase 2, L3 forward + output layer (accumulator 1): y, d3 -> A1
+      // phase 2, L3 forward + output layer (accumulator 1): y, d3 -> A2
       {
         const uint32_t t = wait_acc(1);
+        if (reverse) {  // the previous tile's d1 store has read P4 (over A2)
+          if (et == 0) bulk_wait_read();
+          epi_sync();
+        }
         float yacc = 0.f;
         for (int b = 0; b < nblocks(P.h3); ++b) {
           int c0, c1;
@@ -423,7 +489,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               o[i] = Pack<T>::two(dv[0], dv[1]);
             }
-            if (reverse) put16(A1, r, c, o);
+            if (reverse) put16(A2, r, c, o);
           }
           if (reverse) arrive(&blk_done[b]);
         }
@@ -435,7 +501,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!reverse) continue;
 
-      // phase 3, L3 reverse (accumulator 0): d2 = acc * celu'(h2), in place in A2
+      // phase 3, L3 reverse (accumulator 0): d2 = acc * celu'(h2), in place in A1
       {
         const uint32_t t = wait_acc(0);
         for (int b = 0; b < nblocks(P.h2); ++b) {
@@ -445,12 +511,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             float v[16];
             tmem_ld16(t + (uint32_t)c, v);
             uint32_t hin[8], o[8];
-            get16(A2, r, c, hin);
+            get16(A1, r, c, hin);
 #pragma unroll
             for (int i = 0; i < 8; ++i)
               o[i] = Pack<T>::two(v[2 * i] * dcelu_from_act(Pack<T>::lo(hin[i])),
                                   v[2 * i + 1] * dcelu_from_act(Pack<T>::hi(hin[i])));
-            put16(A2, r, c, o);
+            put16(A1, r, c, o);
           }
           arrive(&blk_done[b]);
         }
