@@ -198,8 +198,9 @@ def src_hash(*names):
 # kernel, keyed by the kernel's source hash at capture time, in bytes per atom;
 # scaled to the bench workload by atoms.
 NCU_TRAFFIC = {
-    ("adjoint", "b1cd173b9794"): 4601.9,  # ncu --set full, 512-molecule batch, FP16
-    ("tail", "91331307bf31"): 6404.3,  # ncu --set full, 512-molecule batch, FP16
+    ("adjoint", "9457105f8002"): 4600.3,  # ncu --set full, 512-molecule batch, FP16
+    ("features", "9457105f8002"): 811.0,  # ncu --set full, 512-molecule batch, FP16
+    ("tail", "b875ce9262f5"): 6404.4,  # ncu --set full, 512-molecule batch, FP16
 }
 
 
