@@ -371,19 +371,18 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
       const float3 d = disp(xi, g.pos[j], c);
       const float r = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
       rd[t] = r;
-      rfc[t] = 0.5f * cospif(r / c.Rcr) + 0.5f;
+      rfc[t] = 0.125f * cospif(r / c.Rcr) + 0.125f;  // fc / 4 (the radial prefactor)
       rsp[t] = g.species[j];
     }
   }
   __syncwarp();
   {
     const int half = lane >> 4, k = lane & 15;
-    const float shf = c.ShfR[k];
-    const float eta = -c.EtaR * kLog2e;
+    const float shs = c.ShfRs[k];
     float* acc = R2 + half * kRadial;
     for (int t = half; t < nr; t += 2) {
-      const float x = rd[t] - shf;
-      acc[rsp[t] * kShfR + k] += 0.25f * ex2_ftz(eta * x * x) * rfc[t];
+      const float y = fmaf(rd[t], c.sqEtaR, -shs);  // exp(-EtaR (r - ShfR)^2) = 2^(-y^2)
+      acc[rsp[t] * kShfR + k] += ex2_ftz(-y * y) * rfc[t];
     }
   }
   __syncwarp();
@@ -420,7 +419,6 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
 
   // ---- angular, 32 neighbour pairs at a time ----
   const int fa = lane >> 2, fz = lane & 3;
-  const float etaA = -c.EtaA * kLog2e;
   float acc = 0.f;
   int pcur = -1;  // block being accumulated; blocks before it are written
   int b0 = 0;  // block holding the iteration's first pair
@@ -442,13 +440,14 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
         const float u = 0.5f * (rj.w + rk.w);
 #pragma unroll
         for (int a = 0; a < kShfA; ++a) {
-          const float x = u - c.ShfA[a];
-          buf[a * kBufStride + lane] = ex2_ftz(etaA * x * x);
+          const float y = fmaf(u, c.sqEtaA, -c.ShfAs[a]);  // 2^(-y^2) = exp(-EtaA (u - ShfA)^2)
+          buf[a * kBufStride + lane] = ex2_ftz(-y * y);
         }
 #pragma unroll
         for (int z = 0; z < kShfZ; ++z) {
-          const float bb = fmaxf(0.5f * (1.f + cp * c.cosZ[z] + sp * c.sinZ[z]), 0.f);
-          buf[(kShfA + z) * kBufStride + lane] = ex2_ftz(c.Zeta * lg2_ftz(bb)) * fcjk;
+          // t = 1 + cos(theta' - ThetaS): ((1 + cos) / 2)^Zeta = 2^(Zeta (lg2 t - 1))
+          const float t = fmaxf(fmaf(sp, c.sinZ[z], fmaf(cp, c.cosZ[z], 1.f)), 0.f);
+          buf[(kShfA + z) * kBufStride + lane] = ex2_ftz(fmaf(c.Zeta, lg2_ftz(t), -c.Zeta)) * fcjk;
         }
       } else {  // padding pair: zero factors
 #pragma unroll
@@ -570,10 +569,8 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const int n_ovf = pass == 0 ? 0 : ovf[0];
 
-  const float etaR = -c.EtaR * kLog2e, etaA = -c.EtaA * kLog2e;
   const float inv_rcr = 1.f / c.Rcr, inv_rca = 1.f / c.Rca;
   const float dfc_r = -0.5f * kPi * inv_rcr, dfc_a = -0.5f * kPi * inv_rca;  // d fc / dr = dfc_x sin(pi r / Rc)
-  const float m2etaR = -2.f * c.EtaR, m2etaA = -2.f * c.EtaA;
   for (;;) {
     int q = 0;
     if (lane == 0) q = atomicAdd(&next_centre, 1);
@@ -641,7 +638,8 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
         sincospif(r * inv_rcr, &sn, &cs);
         const float fc = 0.5f * cs + 0.5f;
         const float dfc = dfc_r * sn;
-        const float afc = m2etaR * fc;  // d(e fc)/dr / e = -2 eta x fc + dfc = afc x + dfc
+        // d(e fc)/dr / e = -2 EtaR (r - ShfR) fc + dfc = afc y + dfc, y = sqEtaR (r - ShfR)
+        const float afc = c.gradR * fc;
         const float4* gsp = reinterpret_cast<const float4*>(gR + g.species[j] * kGRStride);
         float dEdr = 0.f;
 #pragma unroll
@@ -650,9 +648,9 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
           const float gk[4] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
           for (int h = 0; h < 4; ++h) {
-            const float x = r - c.ShfR[4 * k4 + h];
-            const float e = ex2_ftz(etaR * x * x);
-            dEdr = fmaf(gk[h] * e, fmaf(afc, x, dfc), dEdr);
+            const float y = fmaf(r, c.sqEtaR, -c.ShfRs[4 * k4 + h]);
+            const float e = ex2_ftz(-y * y);  // exp(-EtaR (r - ShfR)^2)
+            dEdr = fmaf(gk[h] * e, fmaf(afc, y, dfc), dEdr);
           }
         }
         const float s = 0.25f * dEdr * ir;
@@ -685,31 +683,41 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
         const float fcj = pj.x, fck = pk.x;
         const float u = 0.5f * (uj.w + uk.w);
         const float4* gp = reinterpret_cast<const float4*>(gA + b * kGAStride);
-        float A[kShfZ], dA[kShfZ];
-#pragma unroll
-        for (int z = 0; z < kShfZ; ++z) {
-          const float bb = fmaxf(0.5f * (1.f + cp * c.cosZ[z] + sp * c.sinZ[z]), 0.f);
-          // A = 2 b^Zeta = 2 b b^(Zeta-1);  dA/dcp = 2 Zeta b^(Zeta-1) db/dcp,
-          // db/dcp = (cosZ - cp/sp sinZ) / 2
-          const float pz = ex2_ftz((c.Zeta - 1.f) * lg2_ftz(bb));
-          A[z] = 2.f * bb * pz;
-          dA[z] = c.Zeta * pz * fmaf(-qs, c.sinZ[z], c.cosZ[z]);
-        }
-        float V = 0.f, dVdc = 0.f, dVdu = 0.f;
+        // V = sum_a R_a sum_z g[a][z] A_z with R_a = exp(-EtaA (u - ShfA[a])^2)
+        // = 2^(-y_a^2), y_a = sqEtaA (u - ShfA[a]): the distance sums first,
+        // GR[z] = sum_a R_a g[a][z] and GY[z] = sum_a y_a R_a g[a][z]
+        float GR[kShfZ] = {0.f, 0.f, 0.f, 0.f}, GY[kShfZ] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int a = 0; a < kShfA; ++a) {
-          const float x = u - c.ShfA[a];
-          const float R = ex2_ftz(etaA * x * x);
+          const float y = fmaf(u, c.sqEtaA, -c.ShfAs[a]);
+          const float R = ex2_ftz(-y * y);
+          const float yR = y * R;
           const float4 g4 = gp[a];  // g[a][0..3]
-          const float SA = fmaf(g4.x, A[0], fmaf(g4.y, A[1], fmaf(g4.z, A[2], g4.w * A[3])));
-          const float SdA = fmaf(g4.x, dA[0], fmaf(g4.y, dA[1], fmaf(g4.z, dA[2], g4.w * dA[3])));
-          V = fmaf(R, SA, V);
-          dVdc = fmaf(R, SdA, dVdc);
-          dVdu = fmaf(x * R, SA, dVdu);  // times -2 eta below
+          GR[0] = fmaf(R, g4.x, GR[0]);
+          GR[1] = fmaf(R, g4.y, GR[1]);
+          GR[2] = fmaf(R, g4.z, GR[2]);
+          GR[3] = fmaf(R, g4.w, GR[3]);
+          GY[0] = fmaf(yR, g4.x, GY[0]);
+          GY[1] = fmaf(yR, g4.y, GY[1]);
+          GY[2] = fmaf(yR, g4.z, GY[2]);
+          GY[3] = fmaf(yR, g4.w, GY[3]);
+        }
+        // angle factors, t = 2b = 1 + cp cosZ + sp sinZ: A = 2 b^Zeta = t pz
+        // with pz = b^(Zeta-1) = 2^((Zeta-1)(lg2 t - 1)); dA/dcp = Zeta pz
+        // (cosZ - cp/sp sinZ), Zeta applied once below
+        float V = 0.f, dVdc = 0.f, dVdu = 0.f;
+#pragma unroll
+        for (int z = 0; z < kShfZ; ++z) {
+          const float t = fmaxf(fmaf(sp, c.sinZ[z], fmaf(cp, c.cosZ[z], 1.f)), 0.f);
+          const float pz = ex2_ftz(fmaf(c.Zeta - 1.f, lg2_ftz(t), 1.f - c.Zeta));
+          const float A = t * pz;
+          V = fmaf(GR[z], A, V);
+          dVdu = fmaf(GY[z], A, dVdu);  // dV/du = gradA x this
+          dVdc = fmaf(GR[z] * pz, fmaf(-qs, c.sinZ[z], c.cosZ[z]), dVdc);  // x Zeta
         }
         const float fcjk = fcj * fck;
-        const float dEdcos = 0.95f * fcjk * dVdc;
-        const float dEdu = m2etaA * fcjk * dVdu;
+        const float dEdcos = (0.95f * c.Zeta) * fcjk * dVdc;
+        const float dEdu = c.gradA * fcjk * dVdu;
         const float dEdrj = 0.5f * dEdu + V * pj.y * fck;
         const float dEdrk = 0.5f * dEdu + V * fcj * pk.y;
         // d cos / d r_j = (u_k - cos u_j) / |r_j|,  d |r_j| / d r_j = u_j

@@ -194,6 +194,14 @@ void init_aev_const(AevConst& c, const double box[3]) {
     c.cosZ[k] = (float)std::cos(z);
     c.sinZ[k] = (float)std::sin(z);
   }
+  const double log2e = 1.4426950408889634;
+  const double sqR = std::sqrt((double)c.EtaR * log2e), sqA = std::sqrt((double)c.EtaA * log2e);
+  c.sqEtaR = (float)sqR;
+  c.sqEtaA = (float)sqA;
+  for (int k = 0; k < kShfR; ++k) c.ShfRs[k] = (float)(sqR * (double)c.ShfR[k]);
+  for (int k = 0; k < kShfA; ++k) c.ShfAs[k] = (float)(sqA * (double)c.ShfA[k]);
+  c.gradR = (float)(-2.0 * (double)c.EtaR / sqR);
+  c.gradA = (float)(-2.0 * (double)c.EtaA / sqA);
   int p = 0;
   for (int s = 0; s < kSpecies; ++s)
     for (int t = s; t < kSpecies; ++t) {

@@ -58,6 +58,9 @@ struct AevConst {
   double Rcr2d, Rca2d;         // FP64 squares of the FP32 cutoffs (exact predicate)
   float EtaR, EtaA, Zeta;
   float ShfR[kShfR], ShfA[kShfA], cosZ[kShfZ], sinZ[kShfZ];
+  // exp(-Eta (r - Shf)^2) = 2^(-y^2) with y = sqEta r - ShfS = sqEta (r - Shf),
+  // sqEta = sqrt(Eta log2(e)); gradX = -2 Eta / sqEta turns y into d/dr
+  float sqEtaR, sqEtaA, ShfRs[kShfR], ShfAs[kShfA], gradR, gradA;
   int pair_index[kSpecies][kSpecies];
   float box[3];
   double boxd[3];
