@@ -681,15 +681,15 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
         const float sp = sqrtf(fmaxf(1.f - cp * cp, 1e-12f));
         const float qs = __fdividef(cp, sp);
         const float fcj = pj.x, fck = pk.x;
-        const float u = 0.5f * (uj.w + uk.w);
+        const float rjk = uj.w + uk.w;  // twice the angular distance u
         const float4* gp = reinterpret_cast<const float4*>(gA + b * kGAStride);
         // V = sum_a R_a sum_z g[a][z] A_z with R_a = exp(-EtaA (u - ShfA[a])^2)
-        // = 2^(-y_a^2), y_a = sqEtaA (u - ShfA[a]): the distance sums first,
+        // = 2^(-y_a^2), y_a = sqEtaA (u - ShfA[a]), u = rjk / 2: the distance sums first,
         // GR[z] = sum_a R_a g[a][z] and GY[z] = sum_a y_a R_a g[a][z]
         float GR[kShfZ] = {0.f, 0.f, 0.f, 0.f}, GY[kShfZ] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int a = 0; a < kShfA; ++a) {
-          const float y = fmaf(u, c.sqEtaA, -c.ShfAs[a]);
+          const float y = fmaf(rjk, c.hsqEtaA, -c.ShfAs[a]);
           const float R = ex2_ftz(-y * y);
           const float yR = y * R;
           const float4 g4 = gp[a];  // g[a][0..3]
@@ -716,18 +716,20 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
           dVdc = fmaf(GR[z] * pz, fmaf(-qs, c.sinZ[z], c.cosZ[z]), dVdc);  // x Zeta
         }
         const float fcjk = fcj * fck;
-        const float dEdcos = (0.95f * c.Zeta) * fcjk * dVdc;
-        const float dEdu = c.gradA * fcjk * dVdu;
-        const float dEdrj = 0.5f * dEdu + V * pj.y * fck;
-        const float dEdrk = 0.5f * dEdu + V * fcj * pk.y;
-        // d cos / d r_j = (u_k - cos u_j) / |r_j|,  d |r_j| / d r_j = u_j
+        const float dEdcos = c.dcosA * fcjk * dVdc;
+        const float hdEdu = c.hgradA * fcjk * dVdu;  // dE/du / 2 = dE/dr_j via u
+        const float dEdrj = fmaf(V * fck, pj.y, hdEdu);
+        const float dEdrk = fmaf(V * fcj, pk.y, hdEdu);
+        // d cos / d r_j = (u_k - cos u_j) / |r_j|,  d |r_j| / d r_j = u_j, so
+        // g_j = aj u_k + (dE/dr_j - aj cos) u_j with aj = dE/dcos / |r_j|
         const float aj = dEdcos * pj.z, ak = dEdcos * pk.z;
-        gjx = fmaf(aj, fmaf(-cost, uj.x, uk.x), dEdrj * uj.x);
-        gjy = fmaf(aj, fmaf(-cost, uj.y, uk.y), dEdrj * uj.y);
-        gjz = fmaf(aj, fmaf(-cost, uj.z, uk.z), dEdrj * uj.z);
-        const float gkx = fmaf(ak, fmaf(-cost, uk.x, uj.x), dEdrk * uk.x);
-        const float gky = fmaf(ak, fmaf(-cost, uk.y, uj.y), dEdrk * uk.y);
-        const float gkz = fmaf(ak, fmaf(-cost, uk.z, uj.z), dEdrk * uk.z);
+        const float bj = fmaf(-aj, cost, dEdrj), bk = fmaf(-ak, cost, dEdrk);
+        gjx = fmaf(aj, uk.x, bj * uj.x);
+        gjy = fmaf(aj, uk.y, bj * uj.y);
+        gjz = fmaf(aj, uk.z, bj * uj.z);
+        const float gkx = fmaf(ak, uj.x, bk * uk.x);
+        const float gky = fmaf(ak, uj.y, bk * uk.y);
+        const float gkz = fmaf(ak, uj.z, bk * uk.z);
         gix -= gjx + gkx;
         giy -= gjy + gky;
         giz -= gjz + gkz;

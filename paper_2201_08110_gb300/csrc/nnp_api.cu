@@ -202,6 +202,9 @@ void init_aev_const(AevConst& c, const double box[3]) {
   for (int k = 0; k < kShfA; ++k) c.ShfAs[k] = (float)(sqA * (double)c.ShfA[k]);
   c.gradR = (float)(-2.0 * (double)c.EtaR / sqR);
   c.gradA = (float)(-2.0 * (double)c.EtaA / sqA);
+  c.hsqEtaA = (float)(0.5 * sqA);
+  c.hgradA = (float)(-(double)c.EtaA / sqA);
+  c.dcosA = (float)(0.95 * (double)c.Zeta);
   int p = 0;
   for (int s = 0; s < kSpecies; ++s)
     for (int t = s; t < kSpecies; ++t) {

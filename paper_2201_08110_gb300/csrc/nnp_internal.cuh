@@ -61,6 +61,9 @@ struct AevConst {
   // exp(-Eta (r - Shf)^2) = 2^(-y^2) with y = sqEta r - ShfS = sqEta (r - Shf),
   // sqEta = sqrt(Eta log2(e)); gradX = -2 Eta / sqEta turns y into d/dr
   float sqEtaR, sqEtaA, ShfRs[kShfR], ShfAs[kShfA], gradR, gradA;
+  // the same halved (the angular distance is (r_j + r_k) / 2), and
+  // 0.95 Zeta (d cos' / d cos times the exponent)
+  float hsqEtaA, hgradA, dcosA;
   int pair_index[kSpecies][kSpecies];
   float box[3];
   double boxd[3];
