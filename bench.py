@@ -198,8 +198,8 @@ def src_hash(*names):
 # kernel, keyed by the kernel's source hash at capture time, in bytes per atom;
 # scaled to the bench workload by atoms.
 NCU_TRAFFIC = {
-    ("adjoint", "9457105f8002"): 4600.3,  # ncu --set full, 512-molecule batch, FP16
-    ("features", "9457105f8002"): 811.0,  # ncu --set full, 512-molecule batch, FP16
+    ("adjoint", "1dd06ca99192"): 4604.8,  # ncu --set full, 512-molecule batch, FP16
+    ("features", "1dd06ca99192"): 807.2,  # ncu --set full, 512-molecule batch, FP16
     ("tail", "b875ce9262f5"): 6404.4,  # ncu --set full, 512-molecule batch, FP16
 }
 
