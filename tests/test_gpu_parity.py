@@ -188,10 +188,20 @@ def test_autograd_function_returns_minus_forces(lib):
         np.testing.assert_allclose(E.detach().cpu().numpy(), E0, rtol=1e-12)
 
 
-def test_energy_only_call_matches(lib):
-    b, w, M = small_batch(), W.weights(6, 2), 2
-    model, E0, _ = run(lib, b, w, M)
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+def test_energy_only_call_matches(lib, prec):
+    """Energies without forces run the forward kernels alone (for 16-bit
+    networks, the fused tail without its reverse phases); on the full batch
+    each persistent tensor-core CTA takes many tiles of mixed elements.  The
+    energies equal those of the energy-and-forces call."""
+    if prec == "fp32":
+        b, w, M = small_batch(), W.weights(6, 2), 2
+    else:
+        b, w, M = W.config3()
+    model, E0, _ = run(lib, b, w, M, prec)
     E, F = model.compute(torch.tensor(b.pos, device="cuda"), forces=False)
+    torch.cuda.synchronize()
+    model.status()
     assert F is None
     np.testing.assert_allclose(E.cpu().numpy(), E0, rtol=1e-12)
 
@@ -263,11 +273,13 @@ def test_capacity_overflow_is_reported_not_written(lib):
 
 # --- full-size batch in the benchmark's configuration -------------------------------
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 def test_full_batch_sampled_against_oracle(lib, prec):
     b, w, M = W.config3()
     model = lib.NNP(b.Z, w, M, mol_off=b.mol_off, precision=prec, use_graph=True)
     pos = torch.tensor(b.pos, device="cuda")
+    if prec == "fp16":  # exactly what the benchmark times: FP16 networks, tuned schedule
+        model.autotune(pos)
     for _ in range(2):
         E, F = model.compute(pos)
     torch.cuda.synchronize()
