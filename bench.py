@@ -237,7 +237,7 @@ def run_reference(args):
     oracle.build()
     b, w, M = W.config3(args.molecules)
     cores = os.cpu_count() or 1
-    per_step_mols = max(cores, 16)
+    per_step_mols = min(max(cores, 16), b.n_mols)
     sub = slice(0, per_step_mols)
     a1 = int(b.mol_off[per_step_mols])
     Z, pos, off = b.Z[:a1], b.pos[:a1], b.mol_off[:per_step_mols + 1]
@@ -255,8 +255,12 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "workload 3 batch (512 molecules, 20-120 atoms), 8 networks",
-                       "sample": sample},
+            # the same workload as the kernel arm's line (its config keys), timed on a
+            # bounded sample of its molecules
+            "config": {"workload": f"{args.molecules} molecules, 20-120 atoms, 8-network ensemble "
+                                   f"(workload 3 batch; {args.precision} networks as workload 4)",
+                       "n_molecules": b.n_mols, "n_atoms_per_rank": b.n_atoms, "n_models": M,
+                       "precision": "fp64 (the oracle)", "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
