@@ -11,7 +11,8 @@ module compiles it with gcc on first use and marshals numpy arrays.  What is
 computed is the NNP term V_NNP(Z, r) of the paper's Sec. 2 (Eqs. 2-3) and
 F = -grad V_NNP, with the ANI featurizer and ensemble of atomic networks the
 paper names in Sec. 1 and Sec. 2 ("Optimization").  The functional form is
-written out in the header of ``ani_oracle.c``.
+written out in the header of ``ani_oracle.c``; the NNP-MM coupling term of
+Eq. 4 (``coupling``) is written out beside its function there.
 """
 from __future__ import annotations
 
@@ -70,6 +71,9 @@ def _load():
         lib.ani_oracle_aev_adjoint.argtypes = [ctypes.c_int, P, P, P, P, P]
         lib.ani_oracle_hyper.restype = None
         lib.ani_oracle_hyper.argtypes = [P]
+        lib.ani_oracle_coupling.restype = ctypes.c_int
+        lib.ani_oracle_coupling.argtypes = [ctypes.c_int, P, P, P, P, ctypes.c_int, P, P, P, P,
+                                            ctypes.c_double, P, P, P]
         _lib = lib
         return lib
 
@@ -193,3 +197,26 @@ def aev_adjoint(Z, pos, g, box=None):
                                   _ptr(out)) != 0:
         raise ValueError("oracle: unsupported atomic number")
     return out
+
+
+def coupling(nnp_pos, nnp_q, nnp_sigma, nnp_eps, mm_pos, mm_q, mm_sigma, mm_eps, ke):
+    """The NNP-MM coupling term of Eq. 4 (Coulomb + Lennard-Jones over every
+    NNP-MM pair, Lorentz-Berthelot combination, no cutoff): FP64 energy and
+    forces (-dV/dx) on the NNP atoms [n_nnp, 3] and the MM atoms [n_mm, 3]."""
+    lib = _load()
+    f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    xn, xm = f64(nnp_pos).reshape(-1, 3), f64(mm_pos).reshape(-1, 3)
+    qn, sn, en = f64(nnp_q), f64(nnp_sigma), f64(nnp_eps)
+    qm, sm, em = f64(mm_q), f64(mm_sigma), f64(mm_eps)
+    n_nnp, n_mm = xn.shape[0], xm.shape[0]
+    for a, n in ((qn, n_nnp), (sn, n_nnp), (en, n_nnp), (qm, n_mm), (sm, n_mm), (em, n_mm)):
+        if a.shape != (n,):
+            raise ValueError("oracle: parameter arrays must match the atom counts")
+    e = np.zeros(1, dtype=np.float64)
+    fn = np.zeros((n_nnp, 3), dtype=np.float64)
+    fm = np.zeros((n_mm, 3), dtype=np.float64)
+    if lib.ani_oracle_coupling(n_nnp, _ptr(xn), _ptr(qn), _ptr(sn), _ptr(en), n_mm, _ptr(xm),
+                               _ptr(qm), _ptr(sm), _ptr(em), float(ke), _ptr(e), _ptr(fn),
+                               _ptr(fm)) != 0:
+        raise ValueError("oracle: an NNP atom and an MM atom coincide")
+    return float(e[0]), fn, fm

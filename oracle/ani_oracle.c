@@ -37,6 +37,9 @@
  * d - L * floor(d / L + 0.5).
  *
  * Everything is FP64; weights arrive as FP32 and are promoted.
+ *
+ * The file also holds the NNP-MM coupling term of Eq. 4 (at its end), the
+ * pair sum that couples the NNP region to the MM region.
  */
 #include <math.h>
 #include <stdint.h>
@@ -494,4 +497,58 @@ void ani_oracle_hyper(double* out /* 5 + 16 + 8 + 4 */) {
   for (k = 0; k < O_NSHFR; ++k) out[5 + k] = h.ShfR[k];
   for (k = 0; k < O_NSHFA; ++k) out[21 + k] = h.ShfA[k];
   for (k = 0; k < O_NSHFZ; ++k) out[29 + k] = h.ShfZ[k];
+}
+
+/* ---------------------------------------------------------------------------
+ * NNP-MM coupling term (Eq. 4, the mechanical-embedding scheme of Sec. 2):
+ *
+ *   V_NNP-MM = sum_{i in NNP} sum_{j in MM} ( V_C(i,j) + V_LJ(i,j) )
+ *   V_C  = ke q_i q_j / r_ij                       (ke = 1 / (4 pi eps0) in the
+ *                                                   caller's units)
+ *   V_LJ = 4 eps_ij ((sigma_ij / r_ij)^12 - (sigma_ij / r_ij)^6)
+ *   sigma_ij = (sigma_i + sigma_j) / 2,  eps_ij = sqrt(eps_i eps_j)
+ *                                                  (Lorentz-Berthelot, the
+ *                                                   rule of the GAFF2 / TIP3P
+ *                                                   force fields of Sec. 3)
+ *
+ * every pair, no cutoff and no periodic images, as the equation is written.
+ * Adds the energy to *energy and the forces -dV/dx to f_nnp [n_nnp][3] and
+ * f_mm [n_mm][3].  Returns -1 (and adds nothing) if two atoms coincide.
+ */
+int ani_oracle_coupling(int n_nnp, const double* xn, const double* qn, const double* sn,
+                        const double* en, int n_mm, const double* xm, const double* qm,
+                        const double* sm, const double* em, double ke, double* energy,
+                        double* f_nnp, double* f_mm) {
+  int i, j, k;
+  double e_sum = 0.0;
+  for (i = 0; i < n_nnp; ++i)
+    for (j = 0; j < n_mm; ++j) {
+      double d[3];
+      for (k = 0; k < 3; ++k) d[k] = xm[3 * j + k] - xn[3 * i + k];
+      if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] == 0.0) return -1;
+    }
+  for (i = 0; i < n_nnp; ++i) {
+    for (j = 0; j < n_mm; ++j) {
+      double d[3], r2, r, sig, eps, vc, sr, s6, s12, vlj, dvdr;
+      for (k = 0; k < 3; ++k) d[k] = xm[3 * j + k] - xn[3 * i + k];  /* from i to j */
+      r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      r = sqrt(r2);
+      sig = 0.5 * (sn[i] + sm[j]);
+      eps = sqrt(en[i] * em[j]);
+      vc = ke * qn[i] * qm[j] / r;
+      sr = sig / r;
+      s6 = sr * sr * sr * sr * sr * sr;
+      s12 = s6 * s6;
+      vlj = 4.0 * eps * (s12 - s6);
+      e_sum += vc + vlj;
+      /* dV/dr; d r / d x_j = d / r, d r / d x_i = -d / r */
+      dvdr = -vc / r + 4.0 * eps * (-12.0 * s12 + 6.0 * s6) / r;
+      for (k = 0; k < 3; ++k) {
+        f_mm[3 * j + k] -= dvdr * d[k] / r;
+        f_nnp[3 * i + k] += dvdr * d[k] / r;
+      }
+    }
+  }
+  *energy += e_sum;
+  return 0;
 }

@@ -25,6 +25,14 @@ Workloads (seed of workload k is 1000 + k, its weights use seed + 1):
 4. the batch of 3, with the networks' matrix products in BF16 / FP16;
 5. 4096 molecules, counts log-uniform in [30, 250], plus one 1500-atom
    periodic pocket (24.7 A cube, density 0.1 / A^3).
+
+For the NNP-MM coupling term (Eq. 4) the molecule of workload 2 is placed in
+an MM region of the size of the paper's solvated systems (Table 1: 38-60 k
+atoms): TIP3P-like water (O -0.834 e, two H +0.417 e at 0.9572 A and
+104.52 degrees; Lennard-Jones sigma / eps 3.15061 A / 0.1521 kcal/mol on O,
+none on H) at 0.1 atoms / A^3 around it, and the NNP atoms get charges
+N(0, 0.3^2) shifted to a zero total with sigma ~ U(2.5, 3.5) A and
+eps ~ U(0.02, 0.2) kcal/mol (GAFF2-like ranges).
 """
 from __future__ import annotations
 
@@ -196,3 +204,75 @@ def config5_sizes(n_mols: int = 4096) -> np.ndarray:
 def config5(n_mols: int = 4096) -> tuple[Batch, Batch, np.ndarray, int]:
     s = workload_seed(5)
     return batch(s, config5_sizes(n_mols)), pocket(s + 2), weights(s + 1, 8), 8
+
+
+# --- the MM region around an NNP region (coupling term, Eq. 4) ----------------
+
+COULOMB_KCAL = 332.0637133  # 1 / (4 pi eps0) in kcal/mol * A / e^2
+
+
+@dataclass
+class Environment:
+    """Coupling-term inputs: per-atom Lennard-Jones parameters and charges of the
+    NNP atoms (in the order of their positions) and the MM atoms."""
+    nnp_q: np.ndarray       # float32 [n_nnp], e
+    nnp_sigma: np.ndarray   # float32 [n_nnp], A
+    nnp_eps: np.ndarray     # float32 [n_nnp], kcal/mol
+    mm_pos: np.ndarray      # float32 [n_mm, 3], A
+    mm_q: np.ndarray        # float32 [n_mm]
+    mm_sigma: np.ndarray    # float32 [n_mm]
+    mm_eps: np.ndarray      # float32 [n_mm]
+
+    @property
+    def n_mm(self) -> int:
+        return int(self.mm_pos.shape[0])
+
+
+def mm_environment(seed: int, nnp_pos: np.ndarray, n_mm: int = 60000, density: float = 0.1,
+                   dmin: float = 2.0) -> Environment:
+    """Water-like MM atoms around the NNP atoms nnp_pos [n, 3]: oxygens uniform
+    in a cube of n_mm / density A^3 centred on the NNP region, none closer than
+    dmin + 1 A to an NNP atom, each followed by its two hydrogens (a randomly
+    oriented H-O-H of 104.52 degrees, 0.9572 A bonds); the last water is cut
+    short when n_mm is not a multiple of 3."""
+    g = rng(seed)
+    nnp_pos = np.asarray(nnp_pos, dtype=np.float64).reshape(-1, 3)
+    n_nnp = nnp_pos.shape[0]
+    q = g.normal(0.0, 0.3, size=n_nnp)
+    q -= q.mean()
+    sig = g.uniform(2.5, 3.5, size=n_nnp)
+    eps = g.uniform(0.02, 0.2, size=n_nnp)
+    n_w = (n_mm + 2) // 3
+    edge = (n_mm / density) ** (1.0 / 3.0)
+    centre = nnp_pos.mean(axis=0) if n_nnp else np.zeros(3)
+    oxy = np.zeros((0, 3))
+    while oxy.shape[0] < n_w:
+        cand = centre + g.uniform(-0.5 * edge, 0.5 * edge, size=(2 * n_w, 3))
+        if n_nnp:
+            d2 = ((cand[:, None, :] - nnp_pos[None, :, :]) ** 2).sum(-1).min(axis=1)
+            cand = cand[d2 >= (dmin + 1.0) ** 2]
+        oxy = np.concatenate([oxy, cand])[:n_w]
+    # two hydrogens per oxygen: bond vectors in a random frame
+    half = 0.5 * np.deg2rad(104.52)
+    local = 0.9572 * np.array([[np.sin(half), 0.0, np.cos(half)],
+                               [-np.sin(half), 0.0, np.cos(half)]])
+    a = g.normal(size=(n_w, 3))
+    a /= np.linalg.norm(a, axis=1, keepdims=True)
+    b = g.normal(size=(n_w, 3))
+    b -= (b * a).sum(1, keepdims=True) * a
+    b /= np.linalg.norm(b, axis=1, keepdims=True)
+    c = np.cross(a, b)
+    frames = np.stack([b, c, a], axis=1)  # rows: x, y, z axes of each water
+    hyd = oxy[:, None, :] + np.einsum("hk,wkd->whd", local, frames)
+    pos = np.concatenate([oxy[:, None, :], hyd], axis=1).reshape(-1, 3)[:n_mm]
+    mq = np.tile([-0.834, 0.417, 0.417], n_w)[:n_mm]
+    ms = np.tile([3.15061, 0.0, 0.0], n_w)[:n_mm]
+    me = np.tile([0.1521, 0.0, 0.0], n_w)[:n_mm]
+    f32 = lambda x: np.ascontiguousarray(x, dtype=np.float32)
+    return Environment(f32(q), f32(sig), f32(eps), f32(pos), f32(mq), f32(ms), f32(me))
+
+
+def coupling_config(n_mm: int = 60000) -> tuple[Batch, Environment]:
+    """The 60-atom molecule of workload 2 in an MM region of n_mm atoms."""
+    b, _, _ = config2()
+    return b, mm_environment(workload_seed(2) + 50, b.pos, n_mm)
