@@ -73,7 +73,7 @@ def _load():
         lib.ani_oracle_hyper.argtypes = [P]
         lib.ani_oracle_coupling.restype = ctypes.c_int
         lib.ani_oracle_coupling.argtypes = [ctypes.c_int, P, P, P, P, ctypes.c_int, P, P, P, P,
-                                            ctypes.c_double, P, P, P]
+                                            ctypes.c_double, P, P, P, P, P, P]
         _lib = lib
         return lib
 
@@ -199,10 +199,14 @@ def aev_adjoint(Z, pos, g, box=None):
     return out
 
 
-def coupling(nnp_pos, nnp_q, nnp_sigma, nnp_eps, mm_pos, mm_q, mm_sigma, mm_eps, ke):
+def coupling(nnp_pos, nnp_q, nnp_sigma, nnp_eps, mm_pos, mm_q, mm_sigma, mm_eps, ke,
+             norms=False):
     """The NNP-MM coupling term of Eq. 4 (Coulomb + Lennard-Jones over every
     NNP-MM pair, Lorentz-Berthelot combination, no cutoff): FP64 energy and
-    forces (-dV/dx) on the NNP atoms [n_nnp, 3] and the MM atoms [n_mm, 3]."""
+    forces (-dV/dx) on the NNP atoms [n_nnp, 3] and the MM atoms [n_mm, 3].
+    norms=True also returns the sum of the squared pair energies and, per atom,
+    the sum of the magnitudes of its pair forces (NNP, MM): the scales of the
+    rounding error of a sum of independently rounded terms."""
     lib = _load()
     f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
     xn, xm = f64(nnp_pos).reshape(-1, 3), f64(mm_pos).reshape(-1, 3)
@@ -215,8 +219,13 @@ def coupling(nnp_pos, nnp_q, nnp_sigma, nnp_eps, mm_pos, mm_q, mm_sigma, mm_eps,
     e = np.zeros(1, dtype=np.float64)
     fn = np.zeros((n_nnp, 3), dtype=np.float64)
     fm = np.zeros((n_mm, 3), dtype=np.float64)
+    e2 = np.zeros(1, dtype=np.float64)
+    gn = np.zeros(n_nnp, dtype=np.float64)
+    gm = np.zeros(n_mm, dtype=np.float64)
     if lib.ani_oracle_coupling(n_nnp, _ptr(xn), _ptr(qn), _ptr(sn), _ptr(en), n_mm, _ptr(xm),
                                _ptr(qm), _ptr(sm), _ptr(em), float(ke), _ptr(e), _ptr(fn),
-                               _ptr(fm)) != 0:
+                               _ptr(fm), _ptr(e2), _ptr(gn), _ptr(gm)) != 0:
         raise ValueError("oracle: an NNP atom and an MM atom coincide")
+    if norms:
+        return float(e[0]), fn, fm, float(e2[0]), gn, gm
     return float(e[0]), fn, fm

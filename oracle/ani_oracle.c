@@ -513,14 +513,17 @@ void ani_oracle_hyper(double* out /* 5 + 16 + 8 + 4 */) {
  *
  * every pair, no cutoff and no periodic images, as the equation is written.
  * Adds the energy to *energy and the forces -dV/dx to f_nnp [n_nnp][3] and
- * f_mm [n_mm][3].  Returns -1 (and adds nothing) if two atoms coincide.
+ * f_mm [n_mm][3].  For error bounds it can also add the sum of the squared
+ * pair energies (e_sq) and, per atom, the sum of the magnitudes of its pair
+ * forces (g_nnp, g_mm); null pointers skip them.  Returns -1 (and adds
+ * nothing) if two atoms coincide.
  */
 int ani_oracle_coupling(int n_nnp, const double* xn, const double* qn, const double* sn,
                         const double* en, int n_mm, const double* xm, const double* qm,
                         const double* sm, const double* em, double ke, double* energy,
-                        double* f_nnp, double* f_mm) {
+                        double* f_nnp, double* f_mm, double* e_sq, double* g_nnp, double* g_mm) {
   int i, j, k;
-  double e_sum = 0.0;
+  double e_sum = 0.0, e2_sum = 0.0;
   for (i = 0; i < n_nnp; ++i)
     for (j = 0; j < n_mm; ++j) {
       double d[3];
@@ -541,14 +544,18 @@ int ani_oracle_coupling(int n_nnp, const double* xn, const double* qn, const dou
       s12 = s6 * s6;
       vlj = 4.0 * eps * (s12 - s6);
       e_sum += vc + vlj;
+      e2_sum += (vc + vlj) * (vc + vlj);
       /* dV/dr; d r / d x_j = d / r, d r / d x_i = -d / r */
       dvdr = -vc / r + 4.0 * eps * (-12.0 * s12 + 6.0 * s6) / r;
       for (k = 0; k < 3; ++k) {
         f_mm[3 * j + k] -= dvdr * d[k] / r;
         f_nnp[3 * i + k] += dvdr * d[k] / r;
       }
+      if (g_nnp) g_nnp[i] += fabs(dvdr);
+      if (g_mm) g_mm[j] += fabs(dvdr);
     }
   }
   *energy += e_sum;
+  if (e_sq) *e_sq += e2_sum;
   return 0;
 }

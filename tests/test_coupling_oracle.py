@@ -121,3 +121,16 @@ def test_coincident_atoms_rejected():
     with pytest.raises(ValueError):
         oracle.coupling([[0.0, 0.0, 0.0]], [1.0], [3.0], [0.1], [[0.0, 0.0, 0.0]], [1.0], [3.0],
                         [0.1], KE)
+
+
+def test_error_scales_of_one_pair():
+    """For one pair the squared-energy sum is the energy squared and each atom's
+    gross force is the magnitude of the pair force."""
+    u = np.array([0.0, 0.6, 0.8])
+    xn = np.array([[0.0, 0.0, 0.0]])
+    xm = 2.5 * u[None, :]
+    e, fn, fm, e2, gn, gm = oracle.coupling(xn, [0.4], [3.0], [0.1], xm, [-0.8], [3.4], [0.4], KE,
+                                            norms=True)
+    assert e2 == pytest.approx(e * e, rel=1e-14)
+    assert gn[0] == pytest.approx(np.linalg.norm(fn[0]), rel=1e-14)
+    assert gm[0] == pytest.approx(np.linalg.norm(fm[0]), rel=1e-14)
