@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--molecules", type=int, default=512)
     ap.add_argument("--unbatched-sample", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-coupling", action="store_true",
+                    help="skip the NNP-MM coupling term's measurement")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default schedule instead of nnp_autotune's choice")
     ap.add_argument("--schedule", default=None,
@@ -224,6 +226,59 @@ def cpu_oracle_rate(b, w, M, target_s: float = 12.0):
         m = hi
     dt = time.perf_counter() - t0
     return atoms / dt, f"first {n_done} molecules ({atoms} atoms) of the batch, {dt:.1f} s", cores
+
+
+# FP32 arithmetic of one NNP-MM pair of the coupling term (FMA = 2 FLOP):
+# displacement 3, r^2 5, 1/sqrt 1, r^-2 1, combination 2, (sigma/r)^6 4,
+# Coulomb 2, energy 4, -dV/dr / r 6, the two force updates 12.
+FLOP_COUPLING_PAIR = 40
+
+
+def measure_coupling(steps: int, flush, stream, fp32_peak: float, with_oracle: bool):
+    """The NNP-MM coupling term (Eq. 4) of the 60-atom workload-2 molecule in
+    60,000 water-like MM atoms: CUDA-event time per call with the L2 flushed
+    between calls, pair throughput, roofline, and the FP64 oracle's time for
+    the same call on the host cores."""
+    import torch
+    from paper_2201_08110_gb300 import nnp
+    b, env = W.coupling_config()
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+    ins = [dev(b.pos), dev(env.nnp_q), dev(env.nnp_sigma), dev(env.nnp_eps), dev(env.mm_pos),
+           dev(env.mm_q), dev(env.mm_sigma), dev(env.mm_eps)]
+    e = torch.zeros(1, dtype=torch.float64, device="cuda")
+    fn = torch.zeros(b.n_atoms, 3, dtype=torch.float64, device="cuda")
+    fm = torch.zeros(env.n_mm, 3, dtype=torch.float64, device="cuda")
+    call = lambda: nnp.mm_coupling(*ins, W.COULOMB_KCAL, energy=e, nnp_forces=fn, mm_forces=fm,
+                                   stream=stream)
+    for _ in range(3):
+        call()
+    torch.cuda.synchronize()
+    t_ms = []
+    for _ in range(steps):
+        flush.zero_()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        call()
+        s1.record(stream)
+        s1.synchronize()
+        t_ms.append(s0.elapsed_time(s1))
+    ms = statistics.median(t_ms)
+    pairs = b.n_atoms * env.n_mm
+    achieved = FLOP_COUPLING_PAIR * pairs / (ms * 1e-3) / 1e12
+    out = {"workload": f"{b.n_atoms}-atom molecule (workload 2) in {env.n_mm} water-like MM atoms",
+           "n_nnp": b.n_atoms, "n_mm": env.n_mm, "ms_per_call": ms,
+           "pairs_per_s": pairs / (ms * 1e-3), "calls": steps,
+           "l2": "flushed between calls, outside the timed events",
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                        "frac": achieved / fp32_peak, "work": FLOP_COUPLING_PAIR * pairs,
+                        "peak_note": "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 x max SM clock"}}
+    if with_oracle:
+        import oracle
+        t0 = time.perf_counter()
+        oracle.coupling(b.pos, env.nnp_q, env.nnp_sigma, env.nnp_eps, env.mm_pos, env.mm_q,
+                        env.mm_sigma, env.mm_eps, W.COULOMB_KCAL)
+        out["cpu_oracle_ms"] = 1e3 * (time.perf_counter() - t0)
+    return out
 
 
 # ------------------------------------------------------------------ arms ----
@@ -488,6 +543,9 @@ def run_ours(args):
         line["speedup_vs_fp32_unbatched"] = value / world / unb["value"]
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if not args.no_coupling:
+        line["coupling"] = measure_coupling(max(args.steps, 10), flush, stream, fp32_peak,
+                                            rank == 0 and world == 1 and not args.no_cpu_baseline)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

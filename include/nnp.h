@@ -248,6 +248,37 @@ nnp_status nnp_set_schedule(nnp_handle h, const int32_t* schedule);
 nnp_status nnp_features_static(const int32_t* Z_dev, const float* positions_dev, int32_t n_atoms,
                                float* features_out_dev, void* stream);
 
+/* ---- NNP-MM coupling term ---------------------------------------------------------
+ * The coupling term of the hybrid potential (Eq. 4, the mechanical-embedding
+ * scheme of Sec. 2): Coulomb plus Lennard-Jones between every NNP atom i and
+ * every MM atom j,
+ *   V = sum_i sum_j  coulomb_k q_i q_j / r_ij
+ *                  + 4 eps_ij ((sigma_ij / r_ij)^12 - (sigma_ij / r_ij)^6),
+ *   sigma_ij = (sigma_i + sigma_j) / 2,  eps_ij = sqrt(eps_i eps_j)  (Lorentz-Berthelot),
+ * with no cutoff and no periodic images, as the equation is written (the MM
+ * engine treats the MM region's own long-range electrostatics).  coulomb_k is
+ * 1 / (4 pi eps0) in the caller's units (332.0637133 kcal/mol A / e^2 for
+ * positions in A, charges in e and eps in kcal/mol).  It needs no handle and
+ * allocates nothing; it is asynchronous on `stream`.
+ *   nnp_positions_dev, mm_positions_dev: DEVICE FP32 [n][3];
+ *   *_charges_dev, *_sigma_dev, *_epsilon_dev: DEVICE FP32 [n] (eps >= 0);
+ *   energy_dev: DEVICE FP64 scalar, the term's energy is ADDED to it;
+ *   nnp_forces_dev [n_nnp][3], mm_forces_dev [n_mm][3]: DEVICE FP64, the forces
+ *     -dV/dx are ADDED (so the NNP forces of nnp_compute can be passed as is).
+ * Pair arithmetic is FP32, sums FP64 across warps; results differ between calls
+ * only by the order of FP64 additions across CTAs.  Returns NNP_ERR_ARG for
+ * negative counts or null buffers, NNP_ERR_TOO_LARGE for more than
+ * NNP_COUPLING_MAX_NNP NNP atoms (they are staged in shared memory), NNP_OK
+ * without work when a count is 0, NNP_ERR_CUDA if the launch failed.  An NNP
+ * atom and an MM atom at the same position make the outputs non-finite. */
+#define NNP_COUPLING_MAX_NNP 512
+nnp_status nnp_mm_coupling(const float* nnp_positions_dev, const float* nnp_charges_dev,
+                           const float* nnp_sigma_dev, const float* nnp_epsilon_dev, int32_t n_nnp,
+                           const float* mm_positions_dev, const float* mm_charges_dev,
+                           const float* mm_sigma_dev, const float* mm_epsilon_dev, int32_t n_mm,
+                           double coulomb_k, double* energy_dev, double* nnp_forces_dev,
+                           double* mm_forces_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

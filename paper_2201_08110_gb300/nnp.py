@@ -28,8 +28,9 @@ EXPORTS = ("nnp_weights_per_model", "nnp_num_features", "nnp_create", "nnp_creat
            "nnp_compute", "nnp_compute_host", "nnp_get_status", "nnp_last_error", "nnp_destroy",
            "nnp_get_capacity", "nnp_get_neighbors", "nnp_get_features",
            "nnp_get_atomic_energies", "nnp_compute_timed", "nnp_kernels_per_step",
-           "nnp_features_static", "nnp_autotune", "nnp_set_schedule")
+           "nnp_features_static", "nnp_autotune", "nnp_set_schedule", "nnp_mm_coupling")
 STATIC_MAX_ATOMS = 256
+COUPLING_MAX_NNP = 512
 STAGES = ("neighbors", "features", "l1_fwd", "l2_fwd", "l3_fwd", "energy", "l3_rev", "l2_rev",
           "l1_rev", "adjoint")
 
@@ -97,6 +98,8 @@ def load_library(path: str = LIB_PATH):
     lib.nnp_set_schedule.argtypes = [P, P]
     lib.nnp_set_schedule.restype = I32
     lib.nnp_features_static.restype = ctypes.c_int
+    lib.nnp_mm_coupling.argtypes = [P, P, P, P, I32, P, P, P, P, I32, ctypes.c_double, P, P, P, P]
+    lib.nnp_mm_coupling.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -272,6 +275,32 @@ def features_static(Z, positions, out=None, stream=None):
     if rc != 0:
         raise NNPError(rc, "nnp_features_static")
     return out
+
+
+def mm_coupling(nnp_pos, nnp_q, nnp_sigma, nnp_eps, mm_pos, mm_q, mm_sigma, mm_eps, coulomb_k,
+                energy=None, nnp_forces=None, mm_forces=None, stream=None):
+    """The NNP-MM coupling term (Coulomb + Lennard-Jones over every NNP-MM
+    pair; see nnp_mm_coupling in include/nnp.h).  CUDA float32 inputs
+    (positions [n, 3], charges / sigma / eps [n]); the energy (CUDA float64 [1])
+    and the forces (CUDA float64 [n, 3]) are ADDED to the given buffers, or to
+    zeroed ones that are returned: (energy, nnp_forces, mm_forces)."""
+    import torch
+    lib = load_library()
+    dev = mm_pos.device
+    n_nnp, n_mm = int(nnp_pos.shape[0]), int(mm_pos.shape[0])
+    if energy is None:
+        energy = torch.zeros(1, dtype=torch.float64, device=dev)
+    if nnp_forces is None:
+        nnp_forces = torch.zeros(n_nnp, 3, dtype=torch.float64, device=dev)
+    if mm_forces is None:
+        mm_forces = torch.zeros(n_mm, 3, dtype=torch.float64, device=dev)
+    rc = lib.nnp_mm_coupling(_ptr(nnp_pos), _ptr(nnp_q), _ptr(nnp_sigma), _ptr(nnp_eps), n_nnp,
+                             _ptr(mm_pos), _ptr(mm_q), _ptr(mm_sigma), _ptr(mm_eps), n_mm,
+                             float(coulomb_k), _ptr(energy), _ptr(nnp_forces), _ptr(mm_forces),
+                             _stream_ptr(stream))
+    if rc != 0:
+        raise NNPError(rc, "nnp_mm_coupling")
+    return energy, nnp_forces, mm_forces
 
 
 def _autograd_function():

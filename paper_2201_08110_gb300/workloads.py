@@ -231,10 +231,11 @@ class Environment:
 def mm_environment(seed: int, nnp_pos: np.ndarray, n_mm: int = 60000, density: float = 0.1,
                    dmin: float = 2.0) -> Environment:
     """Water-like MM atoms around the NNP atoms nnp_pos [n, 3]: oxygens uniform
-    in a cube of n_mm / density A^3 centred on the NNP region, none closer than
-    dmin + 1 A to an NNP atom, each followed by its two hydrogens (a randomly
-    oriented H-O-H of 104.52 degrees, 0.9572 A bonds); the last water is cut
-    short when n_mm is not a multiple of 3."""
+    in a cube of n_mm / density A^3 centred on the NNP region (enlarged, for
+    small n_mm, to the NNP region plus twice the exclusion distance and 4 A),
+    none closer than dmin + 1 A to an NNP atom, each followed by its two
+    hydrogens (a randomly oriented H-O-H of 104.52 degrees, 0.9572 A bonds);
+    the last water is cut short when n_mm is not a multiple of 3."""
     g = rng(seed)
     nnp_pos = np.asarray(nnp_pos, dtype=np.float64).reshape(-1, 3)
     n_nnp = nnp_pos.shape[0]
@@ -243,15 +244,20 @@ def mm_environment(seed: int, nnp_pos: np.ndarray, n_mm: int = 60000, density: f
     sig = g.uniform(2.5, 3.5, size=n_nnp)
     eps = g.uniform(0.02, 0.2, size=n_nnp)
     n_w = (n_mm + 2) // 3
-    edge = (n_mm / density) ** (1.0 / 3.0)
+    span = float(np.ptp(nnp_pos, axis=0).max()) if n_nnp else 0.0
+    edge = max((n_mm / density) ** (1.0 / 3.0), span + 2.0 * (dmin + 1.0) + 4.0)
     centre = nnp_pos.mean(axis=0) if n_nnp else np.zeros(3)
     oxy = np.zeros((0, 3))
-    while oxy.shape[0] < n_w:
-        cand = centre + g.uniform(-0.5 * edge, 0.5 * edge, size=(2 * n_w, 3))
+    for _ in range(1000):  # the corners of the cube always stay outside the exclusion
+        if oxy.shape[0] >= n_w:
+            break
+        cand = centre + g.uniform(-0.5 * edge, 0.5 * edge, size=(2 * n_w + 16, 3))
         if n_nnp:
             d2 = ((cand[:, None, :] - nnp_pos[None, :, :]) ** 2).sum(-1).min(axis=1)
             cand = cand[d2 >= (dmin + 1.0) ** 2]
         oxy = np.concatenate([oxy, cand])[:n_w]
+    if oxy.shape[0] < n_w:
+        raise RuntimeError("mm_environment: could not place the oxygens")
     # two hydrogens per oxygen: bond vectors in a random frame
     half = 0.5 * np.deg2rad(104.52)
     local = 0.9572 * np.array([[np.sin(half), 0.0, np.cos(half)],

@@ -64,3 +64,20 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
     p.box[0] = p.box[1] = p.box[2] = 9.0
     assert lib.nnp_create(Z.ctypes.data, 2, ctypes.byref(p), ctypes.byref(h)) == 1  # box < 2 Rc
     assert not h.value
+
+
+def test_coupling_rejects_bad_arguments_before_touching_the_device(lib):
+    """nnp_mm_coupling checks its counts and buffers on the host: a negative
+    count or a null buffer is NNP_ERR_ARG, more NNP atoms than fit in shared
+    memory NNP_ERR_TOO_LARGE, and an empty side returns NNP_OK without work
+    (none of these launches anything, so they run without a GPU)."""
+    from paper_2201_08110_gb300 import nnp
+    args = lambda n_nnp, n_mm, bufs: (*bufs[:4], n_nnp, *bufs[4:8], n_mm, 332.0, *bufs[8:11], None)
+    nulls = [None] * 11
+    fake = [ctypes.c_void_p(16 * (k + 1)) for k in range(11)]  # never dereferenced on these paths
+    assert lib.nnp_mm_coupling(*args(-1, 10, fake)) == 1
+    assert lib.nnp_mm_coupling(*args(5, -1, fake)) == 1
+    assert lib.nnp_mm_coupling(*args(5, 10, nulls)) == 1
+    assert lib.nnp_mm_coupling(*args(nnp.COUPLING_MAX_NNP + 1, 10, fake)) == 10
+    assert lib.nnp_mm_coupling(*args(0, 10, nulls)) == 0
+    assert lib.nnp_mm_coupling(*args(5, 0, nulls)) == 0
