@@ -544,8 +544,11 @@ def run_ours(args):
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if not args.no_coupling:
-        line["coupling"] = measure_coupling(max(args.steps, 10), flush, stream, fp32_peak,
-                                            rank == 0 and world == 1 and not args.no_cpu_baseline)
+        try:
+            line["coupling"] = measure_coupling(max(args.steps, 10), flush, stream, fp32_peak,
+                                                rank == 0 and world == 1 and not args.no_cpu_baseline)
+        except Exception as exc:  # reported in the line; the step's measurement above stands
+            line["coupling"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
