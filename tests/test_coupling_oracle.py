@@ -134,3 +134,34 @@ def test_error_scales_of_one_pair():
     assert e2 == pytest.approx(e * e, rel=1e-14)
     assert gn[0] == pytest.approx(np.linalg.norm(fn[0]), rel=1e-14)
     assert gm[0] == pytest.approx(np.linalg.norm(fm[0]), rel=1e-14)
+
+
+@pytest.mark.parametrize("n_mm", [1, 2, 3, 257, 4099])
+def test_mm_environment_follows_its_recipe(n_mm):
+    """The MM region is what the input recipe states: n_mm atoms in waters of
+    O then two H (0.9572 A bonds, 104.52 degrees), TIP3P charges and
+    Lennard-Jones on O only, oxygens at least 3 A from every NNP atom, NNP
+    charges summing to zero; the same seed gives the same region."""
+    xn = W.geometry(W.rng(4), 20, edge=8.0, dmin=0.95)
+    env = W.mm_environment(21, xn, n_mm)
+    assert env.n_mm == n_mm and env.mm_q.shape == (n_mm,)
+    assert abs(float(env.nnp_q.astype(np.float64).sum())) < 1e-5
+    assert np.all((env.nnp_sigma >= 2.5) & (env.nnp_sigma <= 3.5))
+    assert np.all((env.nnp_eps >= 0.02) & (env.nnp_eps <= 0.2))
+    role = np.arange(n_mm) % 3  # 0: O, 1-2: H
+    np.testing.assert_allclose(env.mm_q, np.where(role == 0, -0.834, 0.417), rtol=1e-6)
+    np.testing.assert_allclose(env.mm_sigma, np.where(role == 0, 3.15061, 0.0), rtol=1e-6)
+    np.testing.assert_allclose(env.mm_eps, np.where(role == 0, 0.1521, 0.0), rtol=1e-6)
+    x = env.mm_pos.astype(np.float64)
+    oxy = x[role == 0]
+    d_on = np.sqrt(((oxy[:, None, :] - xn[None, :, :]) ** 2).sum(-1)).min()
+    assert d_on >= 3.0 - 1e-5
+    for w in range(n_mm // 3):
+        o, h1, h2 = x[3 * w], x[3 * w + 1], x[3 * w + 2]
+        b1, b2 = h1 - o, h2 - o
+        assert np.linalg.norm(b1) == pytest.approx(0.9572, abs=1e-5)
+        assert np.linalg.norm(b2) == pytest.approx(0.9572, abs=1e-5)
+        ang = np.degrees(np.arccos(b1 @ b2 / (np.linalg.norm(b1) * np.linalg.norm(b2))))
+        assert ang == pytest.approx(104.52, abs=1e-3)
+    again = W.mm_environment(21, xn, n_mm)
+    assert np.array_equal(again.mm_pos, env.mm_pos) and np.array_equal(again.nnp_q, env.nnp_q)
