@@ -12,7 +12,9 @@ computed is the NNP term V_NNP(Z, r) of the paper's Sec. 2 (Eqs. 2-3) and
 F = -grad V_NNP, with the ANI featurizer and ensemble of atomic networks the
 paper names in Sec. 1 and Sec. 2 ("Optimization").  The functional form is
 written out in the header of ``ani_oracle.c``; the NNP-MM coupling term of
-Eq. 4 (``coupling``) is written out beside its function there.
+Eq. 4 (``coupling``) is written out beside its function there.  The MD
+integrators of the step loop around both terms (``md_velocity_verlet``,
+``md_langevin_baoab``) are plain numpy.
 """
 from __future__ import annotations
 
@@ -229,3 +231,49 @@ def coupling(nnp_pos, nnp_q, nnp_sigma, nnp_eps, mm_pos, mm_q, mm_sigma, mm_eps,
     if norms:
         return float(e[0]), fn, fm, float(e2[0]), gn, gm
     return float(e[0]), fn, fm
+
+
+def md_velocity_verlet(x0, v0, masses, force, dt, n_steps):
+    """Velocity Verlet (the NVE integrator of an MD step loop) in FP64: for
+    each step, v += dt/2 F/m; x += dt v; F = force(x); v += dt/2 F/m.
+    force(x) -> [n, 3] is -dV/dx.  Returns the positions and velocities after
+    every step, [n_steps + 1, n, 3] each (index 0 = the input)."""
+    x = np.array(x0, dtype=np.float64).reshape(-1, 3)
+    v = np.array(v0, dtype=np.float64).reshape(-1, 3)
+    m = np.asarray(masses, dtype=np.float64).reshape(-1, 1)
+    xs, vs = [x.copy()], [v.copy()]
+    f = np.asarray(force(x), dtype=np.float64)
+    for _ in range(n_steps):
+        v = v + 0.5 * dt * f / m
+        x = x + dt * v
+        f = np.asarray(force(x), dtype=np.float64)
+        v = v + 0.5 * dt * f / m
+        xs.append(x.copy())
+        vs.append(v.copy())
+    return np.stack(xs), np.stack(vs)
+
+
+def md_langevin_baoab(x0, v0, masses, force, dt, gamma, kT, noise):
+    """Langevin dynamics by the BAOAB splitting in FP64, one step per row of
+    noise [n_steps, n, 3] (standard normal draws, passed in so that any
+    implementation can use the same ones): B: v += dt/2 F/m; A: x += dt/2 v;
+    O: v = c1 v + c2 sqrt(kT/m) xi with c1 = exp(-gamma dt), c2 = sqrt(1 - c1^2);
+    A: x += dt/2 v; F = force(x); B: v += dt/2 F/m.  Returns positions and
+    velocities after every step, [n_steps + 1, n, 3] each."""
+    x = np.array(x0, dtype=np.float64).reshape(-1, 3)
+    v = np.array(v0, dtype=np.float64).reshape(-1, 3)
+    m = np.asarray(masses, dtype=np.float64).reshape(-1, 1)
+    c1 = np.exp(-gamma * dt)
+    c2 = np.sqrt(1.0 - c1 * c1)
+    xs, vs = [x.copy()], [v.copy()]
+    f = np.asarray(force(x), dtype=np.float64)
+    for xi in np.asarray(noise, dtype=np.float64):
+        v = v + 0.5 * dt * f / m
+        x = x + 0.5 * dt * v
+        v = c1 * v + c2 * np.sqrt(kT / m) * xi
+        x = x + 0.5 * dt * v
+        f = np.asarray(force(x), dtype=np.float64)
+        v = v + 0.5 * dt * f / m
+        xs.append(x.copy())
+        vs.append(v.copy())
+    return np.stack(xs), np.stack(vs)
