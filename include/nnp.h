@@ -60,7 +60,20 @@ typedef enum {
 
 /* Arithmetic of the networks' matrix products.  The featurizer, the neighbour
  * distances and the reverse pass to coordinates are always FP32; per-molecule
- * energies and per-atom forces are accumulated in FP64. */
+ * energies and per-atom forces are accumulated in FP64.
+ *
+ * With 16-bit networks each forward product is, by default, taken as three
+ * tensor-core products of split operands: every FP32 value x (feature,
+ * activation, weight) is held as hi = round16(x) and lo = round16(x - hi), and
+ * A B = A_hi B_hi + A_lo B_hi + A_hi B_lo with FP32 accumulation (the dropped
+ * A_lo B_lo is at most 2^-18 of |A||B| for BF16).  A single 16-bit rounding
+ * of the weights shifts every atom of an element the same way, so its energy
+ * error adds up coherently over a molecule and, where the atomic energies of a
+ * molecule cancel, exceeds 2e-3 of |E|; the split forward does not.  The
+ * reverse pass (forces) takes one 16-bit product per layer.  single_pass = 1
+ * (nnp_params) selects one product per forward layer as well: a third of the
+ * forward products, energy error up to about 6e-3 of sum_i |E_i| (BF16) or
+ * 6e-4 (FP16). */
 typedef enum {
   NNP_FP32 = 0, /* SIMT FP32 FMA */
   NNP_BF16 = 1, /* tensor cores (tcgen05), BF16 operands, FP32 accumulation */
@@ -86,7 +99,18 @@ typedef struct {
                              1024 atoms, else all pairs of each molecule); 1: all pairs;
                              2: cell list (one periodic region of at most 32768 atoms,
                              else NNP_ERR_UNSUPPORTED) */
-  int32_t reserved[7];    /* must be zero */
+  int32_t single_pass;    /* 16-bit networks: 0 = three split-operand products per forward
+                             layer (default; see nnp_precision), 1 = one product */
+  int32_t recompute_aev;  /* 1: the features live only between the featurizer and the first
+                             layer, in the buffer that later holds dE/dG (one fewer
+                             [rows][1024]-sized buffer); the reverse pass recomputes every
+                             geometric quantity from the positions either way.
+                             nnp_get_features then needs an energy-only nnp_compute
+                             (forces_out NULL) before it, else NNP_ERR_UNSUPPORTED */
+  int32_t test_abort;     /* tests only, else 0: 1 = every tensor-core kernel starts as if
+                             one of its bounded waits had given up, before it issues any
+                             copy or product, so the step ends with NNP_ERR_TIMEOUT */
+  int32_t reserved[4];    /* must be zero */
 } nnp_params;
 
 /* Number of FP32 parameters of one ensemble member (1,713,223). */
@@ -242,8 +266,10 @@ nnp_status nnp_set_schedule(nnp_handle h, const int32_t* schedule);
  * all calls on a device share it and it keeps the last call's contents, so
  * calls that overlap on the GPU race: serialise them (one stream, or events).
  * The first call on each device looks up the array's address (with that
- * device current); make that first call before any stream capture.  Returns
- * NNP_ERR_ARG for null buffers, NNP_ERR_CUDA if a launch failed. */
+ * device current); make that first call before any stream capture.  The
+ * stream must belong to the current device (the scratch array is per device).
+ * Returns NNP_ERR_ARG for null buffers or a stream of another device,
+ * NNP_ERR_CUDA if a launch failed. */
 #define NNP_STATIC_MAX_ATOMS 256
 nnp_status nnp_features_static(const int32_t* Z_dev, const float* positions_dev, int32_t n_atoms,
                                float* features_out_dev, void* stream);
@@ -278,6 +304,70 @@ nnp_status nnp_mm_coupling(const float* nnp_positions_dev, const float* nnp_char
                            const float* mm_sigma_dev, const float* mm_epsilon_dev, int32_t n_mm,
                            double coulomb_k, double* energy_dev, double* nnp_forces_dev,
                            double* mm_forces_dev, void* stream);
+
+/* ---- replica MD loop -----------------------------------------------------------------
+ * Molecular dynamics of every atom of a handle (its molecules are independent
+ * replicas) with the NNP term and, optionally, the NNP-MM coupling term
+ * (nnp_mm_coupling) of one fixed MM environment that every replica sees.  The
+ * paper keeps the MD step on the GPU (Sec. 2 "Optimization") and names the
+ * serial execution of the NNP and MM force terms as what is left to gain
+ * (Sec. 3, after the MD speed table): here each step is one CUDA graph replay
+ * and the coupling term can run on a second stream beside the NNP term.
+ *   velocity Verlet: v += dt/2 F/m; x += dt v; F = F(x); v += dt/2 F/m
+ *   Langevin BAOAB:  v += dt/2 F/m; x += dt/2 v; v = c1 v + c2 sqrt(kT/m) xi;
+ *                    x += dt/2 v; F = F(x); v += dt/2 F/m,
+ *                    c1 = exp(-gamma dt), c2 = sqrt(1 - c1^2), xi ~ N(0, 1)
+ * Positions and velocities are FP64 in the caller's buffers (the NNP takes the
+ * positions rounded to FP32); forces are the FP64 sums of nnp_compute and the
+ * coupling term.  Units are the caller's, consistent with the network's
+ * energy unit (forces per Angstrom): dt, masses, kT. */
+typedef struct nnp_md* nnp_md_handle;
+
+typedef enum { NNP_MD_VERLET = 0, NNP_MD_BAOAB = 1 } nnp_md_integrator;
+
+typedef struct {
+  int32_t integrator;          /* nnp_md_integrator */
+  double dt;                   /* time step, > 0 */
+  double gamma;                /* friction coefficient (BAOAB), >= 0 */
+  double kT;                   /* thermal energy (BAOAB), >= 0 */
+  const double* masses;        /* HOST [N], caller order, > 0; copied */
+  int32_t n_mm;                /* MM atoms of the environment; 0 = no coupling term */
+  const float* mm_positions_dev;  /* DEVICE [n_mm][3] (held, not copied; fixed atoms) */
+  const float* mm_charges_dev;    /* DEVICE [n_mm] */
+  const float* mm_sigma_dev;      /* DEVICE [n_mm] */
+  const float* mm_epsilon_dev;    /* DEVICE [n_mm] */
+  const float* nnp_charges_dev;   /* DEVICE [N] coupling parameters of the handle's atoms */
+  const float* nnp_sigma_dev;     /* DEVICE [N] */
+  const float* nnp_epsilon_dev;   /* DEVICE [N] */
+  double coulomb_k;               /* 1 / (4 pi eps0) in the caller's units */
+  int32_t concurrent;          /* 1: the coupling term on a second stream beside the NNP term */
+  int32_t reserved[8];         /* must be zero */
+} nnp_md_params;
+
+/* Create the loop for handle nnp (which must outlive it; its own graph
+ * setting is not used: the loop captures the NNP kernels into its step
+ * graph).  NNP_ERR_ARG for bad parameters, NNP_ERR_TOO_LARGE if a replica
+ * has more than NNP_COUPLING_MAX_NNP atoms with a coupling term.  Allocates
+ * device memory and synchronises the device. */
+nnp_status nnp_md_create(nnp_handle nnp, const nnp_md_params* params, nnp_md_handle* out);
+
+/* n_steps steps from the state in x_dev / v_dev (DEVICE FP64 [N][3], caller
+ * order, updated in place), enqueued on `stream`: the forces at the starting
+ * positions, then one graph replay per step.
+ *   noise_dev:  DEVICE FP64 [n_steps][N][3] standard normal draws (BAOAB; row
+ *               k is step k's; ignored by Verlet, may be NULL then)
+ *   energy_dev: DEVICE FP64 [n_steps][n_mols] or NULL: the potential energy
+ *               (NNP + coupling) of each replica after each step
+ * No allocation and no host synchronisation after the first call with a
+ * given set of buffers (which captures the step graph).  Device-side
+ * conditions are reported by nnp_get_status on the NNP handle. */
+nnp_status nnp_md_run(nnp_md_handle md, double* x_dev, double* v_dev, int32_t n_steps,
+                      const double* noise_dev, double* energy_dev, void* stream);
+
+const char* nnp_md_last_error(nnp_md_handle md);
+
+/* Free the loop's buffers (not the NNP handle).  Synchronises the device. */
+void nnp_md_destroy(nnp_md_handle md);
 
 #ifdef __cplusplus
 }

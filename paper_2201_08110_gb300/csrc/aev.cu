@@ -28,6 +28,8 @@
 // go to a per-warp FP64 accumulator of the molecule or to FP64 global
 // atomics.  Centres with more angular neighbours than the main launch stages
 // are deferred to a second launch.
+#include <mutex>
+
 #include "nnp_internal.cuh"
 
 namespace nnp {
@@ -197,6 +199,9 @@ template <> __device__ __forceinline__ __nv_bfloat16 cvt_out<__nv_bfloat16>(floa
   return __float2bfloat16_rn(v);
 }
 template <> __device__ __forceinline__ __half cvt_out<__half>(float v) { return __float2half_rn(v); }
+__device__ __forceinline__ float to_float(float v) { return v; }
+__device__ __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_float(__half v) { return __half2float(v); }
 
 // Per-warp shared memory of the forward kernel (floats):
 //   buf[12][36] (the radial accumulators R2[2][112] alias it) | meta (ints): block
@@ -330,7 +335,9 @@ __device__ __forceinline__ int decode_block_pair(int P, int b0, int base, const 
 // the blocks follow each other in feature order.  Each block is then one
 // contiguous run of pairs, accumulated once and written once; padded to a
 // multiple of 4 pairs, every run starts 16-byte aligned in the factor rows.
-template <typename TOut>
+// With kSplit each feature v is written as hi = round(v) in the row's first
+// 1024 columns and lo = round(v - hi) in the next 1024 (16-bit outputs).
+template <typename TOut, bool kSplit = false>
 __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __restrict__ row_of_int,
                       TOut* __restrict__ out) {
   extern __shared__ __align__(16) float smem[];
@@ -356,7 +363,12 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
   float4* avec = reinterpret_cast<float4*>(U);
   float* afc = reinterpret_cast<float*>(avec + nl.cap_a);
   int* asp = reinterpret_cast<int*>(afc + nl.cap_a);
-  TOut* dst = out + (size_t)row_of_int[q] * kFeaturesPad;
+  TOut* dst = out + (size_t)row_of_int[q] * (kSplit ? 2 : 1) * kFeaturesPad;
+  auto put = [&](int f, float v) {
+    const TOut hi = cvt_out<TOut>(v);
+    dst[f] = hi;
+    if (kSplit) dst[kFeaturesPad + f] = cvt_out<TOut>(v - to_float(hi));
+  };
 
   for (int f = lane; f < 2 * kRadial; f += 32) R2[f] = 0.f;
   const float4 xi = g.pos[q];
@@ -386,7 +398,7 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
     }
   }
   __syncwarp();
-  for (int f = lane; f < kRadial; f += 32) dst[f] = cvt_out<TOut>(R2[f] + R2[kRadial + f]);
+  for (int f = lane; f < kRadial; f += 32) put(f, R2[f] + R2[kRadial + f]);
   __syncwarp();  // R2 and the radial staging are dead from here on
 
   // ---- angular staging and the element groups of the list ----
@@ -472,8 +484,8 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
       if ((starts >> (4 * gi)) & 1u) {
         const int p = __shfl_sync(FULL, pl, 4 * gi);
         if (p != pcur) {  // block pcur is complete: write it, and zeros for empty blocks
-          if (pcur >= 0) dst[kRadial + pcur * kAngPerBlock + lane] = cvt_out<TOut>(acc);
-          for (int e = pcur + 1; e < p; ++e) dst[kRadial + e * kAngPerBlock + lane] = cvt_out<TOut>(0.f);
+          if (pcur >= 0) put(kRadial + pcur * kAngPerBlock + lane, acc);
+          for (int e = pcur + 1; e < p; ++e) put(kRadial + e * kAngPerBlock + lane, 0.f);
           acc = 0.f;
           pcur = p;
         }
@@ -486,9 +498,9 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
     }
     __syncwarp();
   }
-  if (pcur >= 0) dst[kRadial + pcur * kAngPerBlock + lane] = cvt_out<TOut>(acc);
-  for (int e = pcur + 1; e < kPairBlocks; ++e) dst[kRadial + e * kAngPerBlock + lane] = cvt_out<TOut>(0.f);
-  if (lane < kFeaturesPad - kFeatures) dst[kFeatures + lane] = cvt_out<TOut>(0.f);
+  if (pcur >= 0) put(kRadial + pcur * kAngPerBlock + lane, acc);
+  for (int e = pcur + 1; e < kPairBlocks; ++e) put(kRadial + e * kAngPerBlock + lane, 0.f);
+  if (lane < kFeaturesPad - kFeatures) put(kFeatures + lane, 0.f);
 }
 
 // ---------------------------------------------------------------------------
@@ -825,7 +837,7 @@ size_t aev_adj_smem_bytes(int cap_r, int cap_a, int warps, int mol_atoms_smem_ma
 }
 
 void launch_aev(const Geometry& g, const NeighborLists& nl, const AevConst& c,
-                const int* row_of_int, void* out, Prec prec, int warps, cudaStream_t s) {
+                const int* row_of_int, void* out, Prec prec, int warps, cudaStream_t s, bool split) {
   if (g.n_atoms <= 0) return;
   const int blocks = (g.n_atoms + warps - 1) / warps;
   const size_t smem = aev_fwd_smem_bytes(nl.cap_r, nl.cap_a, warps);
@@ -834,11 +846,18 @@ void launch_aev(const Geometry& g, const NeighborLists& nl, const AevConst& c,
       launch_pdl(k_aev<float>, blocks, warps * 32, smem, s, g, nl, c, row_of_int, (float*)out);
       break;
     case Prec::BF16:
-      launch_pdl(k_aev<__nv_bfloat16>, blocks, warps * 32, smem, s, g, nl, c, row_of_int,
-                 (__nv_bfloat16*)out);
+      if (split)
+        launch_pdl(k_aev<__nv_bfloat16, true>, blocks, warps * 32, smem, s, g, nl, c, row_of_int,
+                   (__nv_bfloat16*)out);
+      else
+        launch_pdl(k_aev<__nv_bfloat16>, blocks, warps * 32, smem, s, g, nl, c, row_of_int,
+                   (__nv_bfloat16*)out);
       break;
     case Prec::F16:
-      launch_pdl(k_aev<__half>, blocks, warps * 32, smem, s, g, nl, c, row_of_int, (__half*)out);
+      if (split)
+        launch_pdl(k_aev<__half, true>, blocks, warps * 32, smem, s, g, nl, c, row_of_int, (__half*)out);
+      else
+        launch_pdl(k_aev<__half>, blocks, warps * 32, smem, s, g, nl, c, row_of_int, (__half*)out);
       break;
   }
 }
@@ -876,9 +895,13 @@ void launch_aev_adjoint(const Geometry& g, const NeighborLists& nl, const AevCon
 }
 
 // Raises (never lowers) the dynamic shared-memory limits of the featurizer
-// kernels, so handles of different sizes can coexist in one process.
+// kernels, so handles of different sizes can coexist in one process.  Handles
+// may be created, tuned and rescheduled on several host threads at once: the
+// maxima and the attribute updates are serialised.
 cudaError_t aev_set_smem_limits(size_t fwd_bytes, size_t adj_bytes) {
+  static std::mutex mu;
   static size_t fwd_max = 0, adj_max = 0;
+  std::lock_guard<std::mutex> lock(mu);
   fwd_bytes = fwd_max = fwd_bytes > fwd_max ? fwd_bytes : fwd_max;
   adj_bytes = adj_max = adj_bytes > adj_max ? adj_bytes : adj_max;
   cudaError_t e;
@@ -888,6 +911,11 @@ cudaError_t aev_set_smem_limits(size_t fwd_bytes, size_t adj_bytes) {
                            (int)fwd_bytes);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_aev<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_aev<__nv_bfloat16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fwd_bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_aev<__half, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_bytes);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_aev_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)adj_bytes);

@@ -8,27 +8,34 @@
 // over every NNP-MM pair (no cutoff, no periodic images, as the equation is
 // written), with its forces added into the callers' FP64 force buffers.
 //
-// One thread owns kCplJ MM atoms and keeps their forces in registers; the NNP
-// atoms (a ligand: at most NNP_COUPLING_MAX_NNP) sit in shared memory with their charge
-// pre-multiplied by ke, half their sigma and twice the square root of their
-// eps, so a pair needs one reciprocal square root and no division: with
-// s6 = (sigma_ij / r)^6,
+// Work split: a CTA of kCplWarps warps takes kCplJ x 32 MM atoms (lane l owns
+// atoms l, l + 32, ... of the CTA's tile, with their forces in registers) and
+// warp w takes the NNP atoms w, w + kCplWarps, ...; so a ligand of 60 atoms
+// against 60,000 MM atoms runs 469 CTAs of 8 warps (about 25 warps per SM)
+// with no atom shared between two threads of a warp.  The NNP atoms (at most
+// NNP_COUPLING_MAX_NNP) sit in shared memory with their charge pre-multiplied
+// by ke, half their sigma and twice the square root of their eps, so a pair
+// needs one reciprocal square root and no division: with s6 = (sigma_ij / r)^6,
 //   V_LJ = (2 sqrt eps_i)(2 sqrt eps_j) s6 (s6 - 1),
 //   -dV/dr / r = (V_C + 4 eps_ij s6 (12 s6 - 6)) / r^2.
-// Pair arithmetic is FP32.  Each NNP atom's force is summed over the warp by
-// shuffles into the warp's own row in shared memory, over the CTA's warps in
-// FP64 in a fixed order and over CTAs with FP64 atomics; each thread's energy
-// is summed in FP32 over its pairs and from there in FP64.  Within a CTA the
-// order of every sum is fixed.
+// Pair arithmetic is FP32, and so are the sums inside a CTA (FP64 arithmetic
+// runs at a small fraction of the FP32 rate on this GPU): each NNP atom's
+// force is summed over its warp's lanes by shuffles and added to the caller's
+// FP64 buffer, one addition per CTA; each MM atom's force is summed over the
+// CTA's 8 warps in a fixed order through shared memory and added once (no
+// other CTA touches it); the energy is summed over each warp by shuffles and
+// over the CTA's warps in FP64, one addition per CTA.  Within a CTA the order
+// of every sum is fixed.
 #include <cuda_runtime.h>
 
 #include "../../include/nnp.h"
 
 namespace {
 
-constexpr int kCplThreads = 128;
-constexpr int kCplWarps = kCplThreads / 32;
-constexpr int kCplJ = 2;  // MM atoms per thread
+constexpr int kCplWarps = 8;
+constexpr int kCplThreads = 32 * kCplWarps;
+constexpr int kCplJ = 4;                    // MM atoms per lane
+constexpr int kCplTile = 32 * kCplJ;        // MM atoms per CTA
 
 __global__ void __launch_bounds__(kCplThreads)
     k_coupling(const float* __restrict__ xn, const float* __restrict__ qn,
@@ -37,42 +44,42 @@ __global__ void __launch_bounds__(kCplThreads)
                const float* __restrict__ sm, const float* __restrict__ em, int n_mm, float ke,
                double* __restrict__ energy, double* __restrict__ f_nnp, double* __restrict__ f_mm) {
   extern __shared__ float4 sh[];
-  float4* nx = sh;                                          // [n_nnp] x, y, z, ke q
-  float2* np = reinterpret_cast<float2*>(nx + n_nnp);       // [n_nnp] sigma / 2, 2 sqrt(eps)
-  float* nf = reinterpret_cast<float*>(np + n_nnp);         // [warps][n_nnp][3] forces per warp
+  float4* nx = sh;                                       // [n_nnp] x, y, z, ke q
+  float2* np = reinterpret_cast<float2*>(nx + n_nnp);    // [n_nnp] sigma / 2, 2 sqrt(eps)
+  float* mf = reinterpret_cast<float*>(np + n_nnp);      // [warps][tile][3] MM forces per warp
+  float* ew = mf + kCplWarps * kCplTile * 3;             // [warps] energies
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < n_nnp; t += blockDim.x) {
     nx[t] = make_float4(xn[3 * t], xn[3 * t + 1], xn[3 * t + 2], ke * qn[t]);
     np[t] = make_float2(0.5f * sn[t], 2.f * sqrtf(en[t]));
   }
-  __syncthreads();
-  float* nf_w = nf + (size_t)warp * 3 * n_nnp;
-
+  const int tile0 = blockIdx.x * kCplTile;
   float xj[kCplJ][3], qj[kCplJ], hsj[kCplJ], sej[kCplJ], fj[kCplJ][3];
   bool vj[kCplJ];
 #pragma unroll
   for (int u = 0; u < kCplJ; ++u) {
-    const int j = blockIdx.x * (kCplThreads * kCplJ) + u * kCplThreads + threadIdx.x;
+    const int j = tile0 + u * 32 + lane;
     vj[u] = j < n_mm;
     const int jj = vj[u] ? j : 0;
     xj[u][0] = xm[3 * jj];
     xj[u][1] = xm[3 * jj + 1];
     xj[u][2] = xm[3 * jj + 2];
-    qj[u] = qm[jj];
+    qj[u] = vj[u] ? qm[jj] : 0.f;  // a lane past the end adds nothing
     hsj[u] = 0.5f * sm[jj];
-    sej[u] = 2.f * sqrtf(em[jj]);
+    sej[u] = vj[u] ? 2.f * sqrtf(em[jj]) : 0.f;
+    if (!vj[u]) xj[u][0] += 1e3f;  // and stays away from every NNP atom
     fj[u][0] = fj[u][1] = fj[u][2] = 0.f;
   }
+  __syncthreads();
 
   float e_thr = 0.f;
-  for (int i = 0; i < n_nnp; ++i) {
+  for (int i = warp; i < n_nnp; i += kCplWarps) {
     const float4 a = nx[i];
     const float2 p = np[i];
     float fix = 0.f, fiy = 0.f, fiz = 0.f;
 #pragma unroll
     for (int u = 0; u < kCplJ; ++u) {
-      if (!vj[u]) continue;
       const float dx = xj[u][0] - a.x, dy = xj[u][1] - a.y, dz = xj[u][2] - a.z;  // i -> j
       const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       const float ir = rsqrtf(r2);
@@ -97,31 +104,34 @@ __global__ void __launch_bounds__(kCplThreads)
       fiy += __shfl_xor_sync(FULL, fiy, o);
       fiz += __shfl_xor_sync(FULL, fiz, o);
     }
-    if (lane == 0) {  // every (warp, i) written once
-      nf_w[3 * i] = fix;
-      nf_w[3 * i + 1] = fiy;
-      nf_w[3 * i + 2] = fiz;
+    if (lane == 0) {  // this CTA's share of NNP atom i: one warp, one addition
+      atomicAdd(f_nnp + 3 * i, (double)fix);
+      atomicAdd(f_nnp + 3 * i + 1, (double)fiy);
+      atomicAdd(f_nnp + 3 * i + 2, (double)fiz);
     }
   }
-
+  // MM forces: each warp's partial into shared memory, summed over the warps
 #pragma unroll
-  for (int u = 0; u < kCplJ; ++u) {
-    if (!vj[u]) continue;
-    const size_t j = (size_t)blockIdx.x * (kCplThreads * kCplJ) + u * kCplThreads + threadIdx.x;
-    f_mm[3 * j] += (double)fj[u][0];  // one thread per MM atom: no other writer
-    f_mm[3 * j + 1] += (double)fj[u][1];
-    f_mm[3 * j + 2] += (double)fj[u][2];
-  }
-  double e = (double)e_thr;
+  for (int u = 0; u < kCplJ; ++u)
 #pragma unroll
-  for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(FULL, e, o);
-  if (lane == 0) atomicAdd(energy, e);
+    for (int d = 0; d < 3; ++d) mf[((size_t)warp * kCplTile + u * 32 + lane) * 3 + d] = fj[u][d];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) e_thr += __shfl_xor_sync(FULL, e_thr, o);
+  if (lane == 0) ew[warp] = e_thr;
   __syncthreads();
-  for (int t = threadIdx.x; t < 3 * n_nnp; t += blockDim.x) {
-    double sum = 0.0;
+  for (int t = threadIdx.x; t < 3 * kCplTile; t += blockDim.x) {
+    const int j = tile0 + t / 3;
+    if (j >= n_mm) continue;
+    float sum = 0.f;
 #pragma unroll
-    for (int w = 0; w < kCplWarps; ++w) sum += (double)nf[(size_t)w * 3 * n_nnp + t];
-    atomicAdd(f_nnp + t, sum);
+    for (int w = 0; w < kCplWarps; ++w) sum += mf[(size_t)w * kCplTile * 3 + t];
+    f_mm[3 * (size_t)tile0 + t] += (double)sum;  // this CTA alone owns these MM atoms
+  }
+  if (threadIdx.x == 0) {
+    double es = 0.0;
+#pragma unroll
+    for (int w = 0; w < kCplWarps; ++w) es += (double)ew[w];
+    atomicAdd(energy, es);
   }
 }
 
@@ -141,9 +151,9 @@ extern "C" nnp_status nnp_mm_coupling(const float* nnp_positions_dev, const floa
       !mm_positions_dev || !mm_charges_dev || !mm_sigma_dev || !mm_epsilon_dev || !energy_dev ||
       !nnp_forces_dev || !mm_forces_dev)
     return NNP_ERR_ARG;
-  const int per_cta = kCplThreads * kCplJ;
-  const int grid = (n_mm + per_cta - 1) / per_cta;
-  const size_t smem = (size_t)n_nnp * (sizeof(float4) + sizeof(float2) + kCplWarps * 3 * sizeof(float));
+  const int grid = (n_mm + kCplTile - 1) / kCplTile;
+  const size_t smem = (size_t)n_nnp * (sizeof(float4) + sizeof(float2)) +
+                      (size_t)kCplWarps * (kCplTile * 3 + 1) * sizeof(float);
   k_coupling<<<grid, kCplThreads, smem, static_cast<cudaStream_t>(stream)>>>(
       nnp_positions_dev, nnp_charges_dev, nnp_sigma_dev, nnp_epsilon_dev, n_nnp, mm_positions_dev,
       mm_charges_dev, mm_sigma_dev, mm_epsilon_dev, n_mm, (float)coulomb_k, energy_dev,

@@ -26,6 +26,11 @@
 //     phase's MMAs overlap the previous phase's epilogue;
 //   warps 2-17: epilogue, 64 columns at a time (TMEM lane quarter = warp % 4,
 //     16 columns per warp), signalling each finished block.
+// Reverse-only mode (reverse = 2, with split-operand forward products): the
+// forward ran elsewhere, which stored h2 and d3; the producer loads h2 into
+// A1 and d3 into A2 by TMA (d3 once the previous tile's d1 store has read the
+// staging memory over A2) and only the two reverse phases run: phase 3's K
+// block b waits for block b of d3, its epilogue for block b of h2.
 // Waits are bounded: one that gives up sets the timeout status bit, the CTA
 // stops, frees its tensor memory and returns.
 #include <cstring>
@@ -63,6 +68,8 @@ struct TailMaps {
   CUtensorMap w3t;  // [sum h2 rows][160], box 64 x 192
   CUtensorMap w2t;  // [sum h1 rows][192], box 64 x 256
   CUtensorMap h1s;  // activations again, box 32 x 128, 64-byte swizzle (phase 4 in and out)
+  CUtensorMap h2;   // reverse-only mode: second hidden layer [rows][...], box 64 x 128
+  CUtensorMap d3;   // reverse-only mode: d3 [rows][M*192], box 64 x 128
 };
 constexpr int kBoxW2 = kH2Max, kBoxW3 = kH3Max, kBoxW3T = kH2Max, kBoxW2T = kH1Max;
 
@@ -134,7 +141,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, 1)
     k_mlp_tail(const __grid_constant__ TailMaps maps, const TailProblem* __restrict__ probs,
                const GemmTile* __restrict__ tiles, const int* __restrict__ cta_off, int reverse,
-               unsigned* __restrict__ status) {
+               unsigned* __restrict__ status, const int* __restrict__ abort_req) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // rounded up to 1024 bytes by pointer arithmetic, so that accesses through
   // it stay shared-memory accesses
@@ -152,13 +159,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* blk_done = acc_free + 2;   // [4] epilogue -> MMA: 64-column block of the next A written
   uint64_t* p4_full = blk_done + 4;    // producer -> epilogue: the tile's h1 is in P4
   uint64_t* a2_free = p4_full + 1;     // MMA -> P4 loader: phase-3 MMAs are done with d3 (A2)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(a2_free + 1);
+  uint64_t* a2_full = a2_free + 1;     // [3] reverse-only: producer -> MMA, block b of d3 loaded
+  uint64_t* p4_drained = a2_full + kA2Blocks;  // reverse-only: epilogue -> producer, d1 store read P4
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(p4_drained + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   // [3][128]: the output-layer dot of each row over the column groups 1-3
   float* ypart = reinterpret_cast<float*>(ring + kRing * kRingBytes + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t fmt = Pack<T>::fmt;
+  const bool rev_only = reverse == 2;
   const int tile_begin = cta_off[blockIdx.x], tile_end = cta_off[blockIdx.x + 1];  // this CTA's tiles
 
   if (threadIdx.x == 0) {
@@ -177,7 +187,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int b = 0; b < 4; ++b) mbar_init(&blk_done[b], kEpiWarps);
     mbar_init(p4_full, 1);
     mbar_init(a2_free, 1);
-    *abort_flag = 0;
+    for (int b = 0; b < kA2Blocks; ++b) mbar_init(&a2_full[b], 1);
+    mbar_init(p4_drained, 1);
+    *abort_flag = *abort_req;  // nonzero only in tests of the abort path
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -200,10 +212,35 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ---- TMA producer ----
       uint32_t it = 0, tcount = 0;
       int first = 0;  // first A1 block the previous tile freed (past its h2 blocks)
-      bool ok = true;
+      // an abort requested at the start: nothing is loaded (the other roles'
+      // first waits give up on the flag)
+      bool ok = *(volatile int*)abort_flag == 0;
+      uint32_t a1_uses[kA1Blocks] = {0, 0, 0, 0};  // reverse-only: loads of each A1 block
       for (int tile = tile_begin; ok && tile < tile_end; ++tile, ++tcount) {
         const GemmTile tl = tiles[tile];
         const TailProblem P = probs[tl.problem];
+        if (rev_only) {
+          // h2 into A1, block by block as the previous tile's phase-4 MMAs free it
+          for (int kb = 0; ok && kb < nblocks(P.h2); ++kb) {
+            if (a1_uses[kb] > 0 && !mbar_wait(&a1_free[kb], (a1_uses[kb] - 1) & 1, abort_flag)) {
+              ok = false;
+              break;
+            }
+            ++a1_uses[kb];
+            mbar_expect_tx(&a1_full[kb], kBlk);
+            tma_load_2d(A1 + (size_t)kb * kBlk, &maps.h2, P.h2_col0 + kb * kBK, P.row0 + tl.m0, &a1_full[kb]);
+          }
+          // d3 into A2 once the previous tile's d1 store has read P4 (over A2)
+          if (ok && tcount > 0 && !mbar_wait(p4_drained, (tcount - 1) & 1, abort_flag)) ok = false;
+          for (int kb = 0; ok && kb < nblocks(P.h3); ++kb) {
+            mbar_expect_tx(&a2_full[kb], kBlk);
+            tma_load_2d(A2 + (size_t)kb * kBlk, &maps.d3, P.h2_col0 + kb * kBK, P.row0 + tl.m0, &a2_full[kb]);
+          }
+          ok = ok &&
+               produce_weights(&maps.w3t, P.w3t_row0, nblocks(P.h3), kBoxW3T, ring, full, empty, it, abort_flag) &&
+               produce_weights(&maps.w2t, P.w2t_row0, nblocks(P.h2), kBoxW2T, ring, full, empty, it, abort_flag);
+          continue;
+        }
         const int nb1 = nblocks(P.h1);
         // h1 and the matching W2 block, block by block, each as soon as the
         // previous tile is done with that block of A1 (the blocks it freed
@@ -252,7 +289,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       // phases 2-4: K block b waits for block b of the A operand from the
       // epilogue; blk_free: commit each K block's completion there (the
       // last reader of that block of A1)
-      auto phase = [&](int x, const unsigned char* a_base, int k, int n, uint64_t* blk_free) {
+      uint32_t a2_waits[kA2Blocks] = {0, 0, 0};
+      // a_ready / a_waits: the barriers (and the waits so far) that block b of
+      // the A operand completes (the epilogue's blk_done, or the TMA loads of d3)
+      auto phase = [&](int x, const unsigned char* a_base, int k, int n, uint64_t* blk_free,
+                       uint64_t* a_ready, uint32_t* a_waits) {
         if (!ok) return;
         if (used[x] > 0 && !mbar_wait(&acc_free[x], (used[x] - 1) & 1, abort_flag)) {
           ok = false;
@@ -263,11 +304,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t d = tmem + (uint32_t)(x * kTmemCols / 2);
         const int n_kb = nblocks(k);
         for (int kb = 0; kb < n_kb; ++kb, ++it) {
-          if (!mbar_wait(&blk_done[kb], blk_waits[kb] & 1, abort_flag)) {
+          if (!mbar_wait(&a_ready[kb], a_waits[kb] & 1, abort_flag)) {
             ok = false;
             return;
           }
-          ++blk_waits[kb];
+          ++a_waits[kb];
           const int s = it % kRing;
           if (!mbar_wait(&full[s], (it / kRing) & 1, abort_flag)) {
             ok = false;
@@ -330,15 +371,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int tile = tile_begin; ok && tile < tile_end; ++tile, ++tcount) {
         const GemmTile tl = tiles[tile];
         const TailProblem P = probs[tl.problem];
+        if (rev_only) {
+          phase(0, A2, P.h3, P.h2, nullptr, a2_full, a2_waits);  // L3 reverse, d3 loaded by TMA
+          if (ok) mma_commit(a2_free);                            // A2 may take phase 4's h1
+          phase(1, A1, P.h2, P.h1, a1_free, blk_done, blk_waits);  // L2 reverse, d2 over h2
+          continue;
+        }
         phase1(P, first);                 // L2 forward
         first = nblocks(P.h2);
         // L3 forward, block by block of h2 (over h1); without the reverse
         // pass it is the last reader of those blocks of A1
-        phase(1, A1, P.h2, P.h3, reverse ? nullptr : a1_free);
+        phase(1, A1, P.h2, P.h3, reverse ? nullptr : a1_free, blk_done, blk_waits);
         if (!reverse) continue;
-        phase(0, A2, P.h3, P.h2, nullptr);  // L3 reverse, block by block of d3
+        phase(0, A2, P.h3, P.h2, nullptr, blk_done, blk_waits);  // L3 reverse, block by block of d3
         if (ok) mma_commit(a2_free);        // d3 consumed: A2 may take phase 4's h1
-        phase(1, A1, P.h2, P.h1, a1_free);  // L2 reverse, block by block of d2 (over h2)
+        phase(1, A1, P.h2, P.h1, a1_free, blk_done, blk_waits);  // L2 reverse, block by block of d2 (over h2)
       }
       if (!ok) {
         atomicOr(status, kStatTimeout);
@@ -376,6 +423,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int r = quarter * 32 + lane;  // tile row = TMEM lane
     const uint32_t tq = (uint32_t)(quarter * 32) << 16;
     uint32_t ready_waits[2] = {0, 0}, p4_waits = 0;
+    uint32_t a1_waits[kA1Blocks] = {0, 0, 0, 0};  // reverse-only: h2 block loads waited for
     bool ok = true;
     auto wait_acc = [&](int x) -> uint32_t {  // TMEM address of accumulator x for this warp
       if (ok && !mbar_wait(&acc_ready[x], ready_waits[x] & 1, abort_flag)) {
@@ -438,7 +486,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
       // phase 1, L2 forward (accumulator 0): h2 = celu(acc + b2) -> A1 (its
       // MMAs, the last readers of h1 there, are complete), block by block
-      {
+      if (!rev_only) {
         const uint32_t t = wait_acc(0);
         for (int b = 0; b < nblocks(P.h2); ++b) {
           int c0, c1;
@@ -460,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
 
       // phase 2, L3 forward + output layer (accumulator 1): y, d3 -> A2
-      {
+      if (!rev_only) {
         const uint32_t t = wait_acc(1);
         if (reverse) {  // the previous tile's d1 store has read P4 (over A2)
           if (et == 0) bulk_wait_read();
@@ -495,7 +543,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (grp) ypart[(grp - 1) * 128 + r] = yacc;
         quad_sync();
-        if (ok && !grp && row_ok)
+        if (ok && !grp && row_ok && P.y)  // no y when the split forward computed it
           P.y[(size_t)row * P.ldy] = yacc + ypart[r] + ypart[128 + r] + ypart[256 + r] + P.b4;
         release(&acc_free[1]);
       }
@@ -505,6 +553,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       {
         const uint32_t t = wait_acc(0);
         for (int b = 0; b < nblocks(P.h2); ++b) {
+          if (rev_only) {  // block b of h2, loaded by TMA
+            if (ok && !mbar_wait(&a1_full[b], a1_waits[b] & 1, abort_flag)) {
+              atomicOr(status, kStatTimeout);
+              atomicExch(abort_flag, 1);
+              ok = false;
+            }
+            ok = __all_sync(0xffffffffu, ok);
+            ++a1_waits[b];
+          }
           int c0, c1;
           my_cols(b, P.h2, c0, c1);
           for (int c = c0; ok && c < c1; c += 16) {
@@ -553,6 +610,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int j = 0; j < P.h1 / 32; ++j)
             tma_store_2d(&maps.h1s, P4 + (size_t)j * kP4Box, P.a_col0 + 32 * j, P.row0 + tl.m0);
           bulk_commit();
+          if (rev_only) {  // the producer's next d3 load goes over P4
+            bulk_wait_read();
+            mbar_arrive(p4_drained);
+          }
         }
       }
     }
@@ -588,14 +649,17 @@ cudaError_t tail_set_smem() {
 // maps: HOST pointer to the TMA descriptors (h1, w2, w3, w3t, w2t, h1 in
 // 32-column boxes); CTA c runs the tiles cta_off[c] .. cta_off[c + 1].
 void launch_mlp_tail(const TailProblem* probs, const GemmTile* tiles, const int* cta_off, int n_ctas,
-                     Prec p, const void* maps, int reverse, unsigned* status, cudaStream_t s) {
+                     Prec p, const void* maps, int reverse, unsigned* status, const int* abort_req,
+                     cudaStream_t s) {
   if (n_ctas <= 0) return;
   TailMaps m;
   std::memcpy(&m, maps, sizeof(m));
   if (p == Prec::BF16)
-    launch_pdl(k_mlp_tail<__nv_bfloat16>, n_ctas, kThreads, kSmemBytes, s, m, probs, tiles, cta_off, reverse, status);
+    launch_pdl(k_mlp_tail<__nv_bfloat16>, n_ctas, kThreads, kSmemBytes, s, m, probs, tiles, cta_off,
+               reverse, status, abort_req);
   else
-    launch_pdl(k_mlp_tail<__half>, n_ctas, kThreads, kSmemBytes, s, m, probs, tiles, cta_off, reverse, status);
+    launch_pdl(k_mlp_tail<__half>, n_ctas, kThreads, kSmemBytes, s, m, probs, tiles, cta_off,
+               reverse, status, abort_req);
 }
 
 }  // namespace nnp

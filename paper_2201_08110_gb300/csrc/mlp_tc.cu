@@ -44,8 +44,8 @@ constexpr uint32_t kABytes = kBM * kBK * 2;      // 16 KB
 constexpr uint32_t kBBytes = kBNMax * kBK * 2;   // 32 KB (room for 256 B rows)
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
 constexpr uint32_t kStgBytes = 128 * 128;        // one output box: 128 rows x 128 bytes
-constexpr size_t kSmemBytes =
-    (size_t)kStages * kStageBytes + 2 * kStgBytes + 1024 /*align*/ + 256 /*barriers*/;
+constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 2 * kStgBytes + 1024 /*align*/ +
+                              256 /*barriers*/ + 128 * sizeof(float) /*row sums*/;
 
 struct TcMaps {
   CUtensorMap a;
@@ -69,7 +69,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ TcMaps maps, const GemmProblem* __restrict__ probs,
               const GemmTile* __restrict__ tiles, const int* __restrict__ cta_off, int b_box_rows,
-              unsigned* __restrict__ status) {
+              unsigned* __restrict__ status, const int* __restrict__ abort_req) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // rounded up to 1024 bytes by pointer arithmetic, so that accesses through
   // it stay shared-memory accesses
@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* tempty = tfull + 2;       // [2] accumulator drained
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  float* ypart = reinterpret_cast<float*>(full) + 64;  // [128] Epi::Energy: half 1's row sums
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t stage_tx = kABytes + (uint32_t)b_box_rows * kBK * 2;
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&tfull[a], 1);
       mbar_init(&tempty[a], kEpiWarps);  // one arrival per epilogue warp
     }
-    *abort_flag = 0;
+    *abort_flag = *abort_req;  // nonzero only in tests of the abort path
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -118,13 +119,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       // ---- TMA producer ----
       uint32_t it = 0;
-      for (int tile = tile_begin; tile < tile_end; ++tile) {
+      // an abort requested at the start: nothing is loaded (the other roles'
+      // first waits give up on the flag)
+      const bool pre = *(volatile int*)abort_flag != 0;
+      if (pre) atomicOr(status, kStatTimeout);
+      for (int tile = pre ? tile_end : tile_begin; tile < tile_end; ++tile) {
         const GemmTile tl = tiles[tile];
         const GemmProblem P = probs[tl.problem];  // by value: asm memory clobbers force reloads of references
         const int nkb = (P.K + kBK - 1) / kBK;
         const int ay = P.a_row0 + tl.m0, by = P.b_row0 + tl.n0;
         bool ok = true;
-        for (int kb = 0; kb < nkb; ++kb, ++it) {
+        // K blocks of the segments (A_hi, B_hi), then (A_lo, B_hi) and (A_hi, B_lo)
+        // when the operands are split
+        const int nseg = P.split ? 3 : 1;
+        for (int kt = 0; kt < nseg * nkb; ++kt, ++it) {
+          const int seg = kt / nkb, kb = kt - seg * nkb;
           const int s = it % kStages;
           const uint32_t use = it / kStages;
           if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, abort_flag)) {
@@ -133,8 +142,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           unsigned char* sa = smem + s * kStageBytes;
           mbar_expect_tx(&full[s], stage_tx);
-          tma_load_2d(sa, &maps.a, P.a_col0 + kb * kBK, ay, &full[s]);
-          tma_load_2d(sa + kABytes, &maps.b, P.b_col0 + kb * kBK, by, &full[s]);
+          tma_load_2d(sa, &maps.a, P.a_col0 + kb * kBK + (seg == 1 ? P.a_lo : 0), ay, &full[s]);
+          tma_load_2d(sa + kABytes, &maps.b, P.b_col0 + kb * kBK + (seg == 2 ? P.b_lo : 0), by, &full[s]);
         }
         if (!ok) {
           atomicOr(status, kStatTimeout);
@@ -157,7 +166,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = use == 0 || mbar_wait(&tempty[acc], (use - 1) & 1, abort_flag);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dtm = tmem + acc * kBNMax;
-        for (int kb = 0; ok && kb < nkb; ++kb, ++it) {
+        const int nkt = (P.split ? 3 : 1) * nkb;
+        for (int kt = 0; ok && kt < nkt; ++kt, ++it) {
+          const int kb = kt % nkb;
           const int s = it % kStages;
           if (!mbar_wait(&full[s], (it / kStages) & 1, abort_flag)) {
             ok = false;
@@ -169,7 +180,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int ksteps = min(kBK, P.K - kb * kBK) / 16;
           for (int j = 0; j < ksteps; ++j)  // +32 bytes per K step inside the swizzle atom
             mma_f16(dtm, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc,
-                    (kb > 0 || j > 0) ? 1u : 0u);
+                    (kt > 0 || j > 0) ? 1u : 0u);
           mma_commit(&empty[s]);
         }
         if (!ok) {
@@ -189,58 +200,128 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool leader = quarter == 0 && lane == 0;  // issues this half's stores
     bool in_flight = false;                         // leader: a store may still read stg
     auto half_sync = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(2 + half) : "memory"); };
+    auto epi_sync = [&]() { asm volatile("bar.sync 4, %0;" ::"r"(32 * kEpiWarps) : "memory"); };
+    auto epi_any = [&](bool p) -> bool {  // true on every epilogue thread if p on any
+      int res;
+      asm volatile(
+          "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\t"
+          "bar.red.or.pred q, 5, %2, p;\n\tselp.b32 %0, 1, 0, q;\n\t}\n"
+          : "=r"(res)
+          : "r"(p ? 1 : 0), "r"(32 * kEpiWarps)
+          : "memory");
+      return res != 0;
+    };
     uint32_t tcount = 0;
     for (int tile = tile_begin; tile < tile_end; ++tile, ++tcount) {
       const GemmTile tl = tiles[tile];
       const GemmProblem P = probs[tl.problem];  // by value: asm memory clobbers force reloads of references
       const int n_tile = tl.width > 0 ? tl.width : min(b_box_rows, P.N - tl.n0);
       const uint32_t acc = tcount & 1, use = tcount >> 1;
-      const bool got = mbar_wait(&tfull[acc], use & 1, abort_flag);
-      if (!__all_sync(0xffffffffu, got)) {  // the warp leaves together (tcgen05.ld is .sync.aligned)
+      // the warp (tcgen05.ld is .sync.aligned) and then all epilogue warps
+      // agree, so that every named barrier below is reached by all of them
+      const bool got = __all_sync(0xffffffffu, mbar_wait(&tfull[acc], use & 1, abort_flag));
+      if (!got && lane == 0) {
         atomicOr(status, kStatTimeout);
         atomicExch(abort_flag, 1);
-        break;
       }
+      if (epi_any(!got)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const bool f32 = P.epi == (int)Epi::Store;  // else bias + CELU into T
-      const int bw = f32 ? 32 : 64;               // box columns
-      const int nbox = (n_tile + bw - 1) / bw;
       const uint32_t tbase = tmem + acc * kBNMax + ((uint32_t)(quarter * 32) << 16);
-      for (int bx = half; bx < nbox; bx += 2) {
-        if (leader && in_flight) bulk_wait_read();  // the previous store has read stg
-        half_sync();
-        for (int cc = 0; cc < bw; cc += 16) {
-          const int c = bx * bw + cc;  // column in the tile
-          float v[16];
-          if (c < n_tile) {
-            tmem_ld16(tbase + (uint32_t)c, v);
-          } else {  // past the problem's columns: zeros
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = 0.f;
+      if (P.epi == (int)Epi::Energy) {
+        // output layer: this thread's share of w4 . celu(acc + bias) over the
+        // columns of its half's boxes; half 1 posts it, half 0 adds and stores.
+        // With an output (P.D), each box's start of the reverse pass,
+        // d3 = (1/M) w4 celu'(z), is stored too (16-bit, zeros past N).
+        float yp = 0.f;
+        const bool d3_out = P.D != nullptr;
+        for (int c = half * 64; c < n_tile; c += 128) {
+          if (d3_out) {
+            if (leader && in_flight) bulk_wait_read();  // the previous store has read stg
+            half_sync();
           }
-          if (f32) {
-            put16_f32(stg, r, cc, v);
-          } else {
-            float b[16];
-            if (c < n_tile) {
-              ldg16(P.bias + tl.n0 + c, b);
+          for (int cc = 0; cc < 64; cc += 16) {
+            uint32_t o[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+            if (c + cc < n_tile) {
+              float v[16], b[16], w[16];
+              ldg16(P.bias + tl.n0 + c + cc, b);  // in flight during the TMEM load
+              ldg16(P.w4 + tl.n0 + c + cc, w);
+              tmem_ld16(tbase + (uint32_t)(c + cc), v);
 #pragma unroll
-              for (int i = 0; i < 16; ++i) v[i] = celu01_fast(v[i] + b[i]);
+              for (int i = 0; i < 16; ++i) {
+                const float z = v[i] + b[i];
+                const float ex = celu01_exp(z);  // celu'(z): 1 above zero
+                yp = fmaf(w[i], fmaxf(z, fmaf(0.1f, ex, -0.1f)), yp);
+                v[i] = w[i] * P.inv_m * ex;
+              }
+#pragma unroll
+              for (int i = 0; i < 8; ++i) o[i] = Pack<T>::two(v[2 * i], v[2 * i + 1]);
             }
-            uint32_t o[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) o[i] = Pack<T>::two(v[2 * i], v[2 * i + 1]);
-            *reinterpret_cast<uint4*>(stg + sw128_offset(r, cc)) = make_uint4(o[0], o[1], o[2], o[3]);
-            *reinterpret_cast<uint4*>(stg + sw128_offset(r, cc + 8)) = make_uint4(o[4], o[5], o[6], o[7]);
+            if (d3_out) {
+              *reinterpret_cast<uint4*>(stg + sw128_offset(r, cc)) = make_uint4(o[0], o[1], o[2], o[3]);
+              *reinterpret_cast<uint4*>(stg + sw128_offset(r, cc + 8)) = make_uint4(o[4], o[5], o[6], o[7]);
+            }
+          }
+          if (d3_out) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            half_sync();
+            if (leader) {
+              tma_store_2d(&maps.d, stg, P.d_col0 + tl.n0 + c, P.a_row0 + tl.m0);
+              bulk_commit();
+              in_flight = true;
+            }
           }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        half_sync();
-        if (leader) {
-          tma_store_2d(&maps.d, stg, tl.n0 + bx * bw, P.a_row0 + tl.m0);
-          bulk_commit();
-          in_flight = true;
-        }
+        if (half == 1) ypart[r] = yp;
+        epi_sync();
+        const int row = tl.m0 + r;
+        if (half == 0 && row < P.M) P.y[(size_t)row * P.ldy] = yp + ypart[r] + P.b4;
+        epi_sync();  // ypart is free for the next tile
+      } else {
+        const bool f32 = P.epi == (int)Epi::Store;  // else bias + CELU into T
+        const int bw = f32 ? 32 : 64;               // box columns
+        const int nbox = (n_tile + bw - 1) / bw;
+        const int nparts = (!f32 && P.d_lo > 0) ? 2 : 1;  // hi, then lo = round(v - hi)
+        for (int bx = half; bx < nbox; bx += 2)
+          for (int part = 0; part < nparts; ++part) {
+            if (leader && in_flight) bulk_wait_read();  // the previous store has read stg
+            half_sync();
+            for (int cc = 0; cc < bw; cc += 16) {
+              const int c = bx * bw + cc;  // column in the tile
+              float v[16];
+              if (c < n_tile) {
+                tmem_ld16(tbase + (uint32_t)c, v);
+              } else {  // past the problem's columns: zeros
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = 0.f;
+              }
+              if (f32) {
+                put16_f32(stg, r, cc, v);
+              } else {
+                float b[16];
+                if (c < n_tile) {
+                  ldg16(P.bias + tl.n0 + c, b);
+#pragma unroll
+                  for (int i = 0; i < 16; ++i) v[i] = celu01_fast(v[i] + b[i]);
+                }
+                uint32_t o[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                  o[i] = Pack<T>::two(v[2 * i], v[2 * i + 1]);
+                  if (part)  // the rounding residual, exact in FP32
+                    o[i] = Pack<T>::two(v[2 * i] - Pack<T>::lo(o[i]), v[2 * i + 1] - Pack<T>::hi(o[i]));
+                }
+                *reinterpret_cast<uint4*>(stg + sw128_offset(r, cc)) = make_uint4(o[0], o[1], o[2], o[3]);
+                *reinterpret_cast<uint4*>(stg + sw128_offset(r, cc + 8)) = make_uint4(o[4], o[5], o[6], o[7]);
+              }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            half_sync();
+            if (leader) {
+              tma_store_2d(&maps.d, stg, P.d_col0 + tl.n0 + bx * bw + (part ? P.d_lo : 0), P.a_row0 + tl.m0);
+              bulk_commit();
+              in_flight = true;
+            }
+          }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -322,14 +403,17 @@ cudaError_t tc_set_smem() {
 // parameters); b_box_rows: rows of the B map's box; CTA c runs the tiles
 // cta_off[c] .. cta_off[c + 1] of the (device) tile list.
 void launch_gemm_tc(const GemmProblem* probs, const GemmTile* tiles, const int* cta_off, int n_ctas,
-                    Prec p, int b_box_rows, const void* maps, unsigned* status, cudaStream_t s) {
+                    Prec p, int b_box_rows, const void* maps, unsigned* status, const int* abort_req,
+                    cudaStream_t s) {
   if (n_ctas <= 0) return;
   TcMaps m;
   std::memcpy(&m, maps, sizeof(m));
   if (p == Prec::BF16)
-    launch_pdl(k_gemm_tc<__nv_bfloat16>, n_ctas, kThreads, kSmemBytes, s, m, probs, tiles, cta_off, b_box_rows, status);
+    launch_pdl(k_gemm_tc<__nv_bfloat16>, n_ctas, kThreads, kSmemBytes, s, m, probs, tiles, cta_off,
+               b_box_rows, status, abort_req);
   else
-    launch_pdl(k_gemm_tc<__half>, n_ctas, kThreads, kSmemBytes, s, m, probs, tiles, cta_off, b_box_rows, status);
+    launch_pdl(k_gemm_tc<__half>, n_ctas, kThreads, kSmemBytes, s, m, probs, tiles, cta_off,
+               b_box_rows, status, abort_req);
 }
 
 }  // namespace nnp

@@ -14,7 +14,8 @@
 
 namespace nnp {
 void launch_gemm_tc(const GemmProblem* probs, const GemmTile* tiles, const int* cta_off, int n_ctas,
-                    Prec p, int b_box_rows, const void* maps, unsigned* status, cudaStream_t s);
+                    Prec p, int b_box_rows, const void* maps, unsigned* status, const int* abort_req,
+                    cudaStream_t s);
 bool tc_available();
 size_t tc_maps_bytes();
 // box_cols x box_rows boxes of a [rows][cols] 16-bit matrix; 128-byte swizzle
@@ -80,6 +81,10 @@ struct nnp_ctx {
   int n_atoms = 0, n_mols = 0, n_models = 1;
   Prec prec = Prec::F32;
   int use_graph = 0;
+  int split = 0;           // 16-bit networks: forward products on split (hi, lo) operands
+  int aev_aliased = 0;     // the features share their buffer with dE/dG
+  bool features_overwritten = false;  // the last step's reverse pass wrote over the features
+  int test_abort = 0;
   AevConst aevc{};
   int elem_count[kSpecies] = {0};
   int elem_row0[kSpecies + 1] = {0};
@@ -94,10 +99,14 @@ struct nnp_ctx {
   NeighborLists nl{};
   // device: activations
   void *d_aev = nullptr, *d_h1 = nullptr, *d_h2 = nullptr, *d_d3 = nullptr;
+  void* d_h2s = nullptr;  // split forward: second hidden layer (hi | lo) [rows][2 M 192]
+  void* d_d3s = nullptr;  // split forward: start of the reverse pass d3 [rows][M 192]
   float* d_z3 = nullptr;  // third-layer pre-activation, FP32 (not a product operand)
   float *d_y = nullptr, *d_dG = nullptr;
   double* d_atom_e = nullptr;
   unsigned* d_status = nullptr;
+  int* d_abort = nullptr;  // tests: nonzero makes the tensor-core kernels abort at their start
+  int abort_steps = 0;     // tests: evaluations left that start with d_abort set
   // device: weights
   void* d_w = nullptr;
   float* d_b = nullptr;
@@ -109,7 +118,7 @@ struct nnp_ctx {
   CellGrid cells{};
   CellBuffers cellbuf{};
   alignas(64) unsigned char tc_maps[6][384];  // tensor-core path: {A, B, D} TMA descriptors per layer
-  alignas(64) unsigned char tail_maps[6 * 128];  // fused tail: h1, w2, w3, w3t, w2t, h1 (32-col boxes)
+  alignas(64) unsigned char tail_maps[8 * 128];  // fused tail: h1, w2, w3, w3t, w2t, h1 (32-col boxes), h2, d3
   std::vector<TailProblem> tail_probs;
   std::vector<GemmTile> tail_tiles;
   std::vector<int> tail_off;  // CTA c runs tail tiles tail_off[c] .. tail_off[c + 1]
@@ -161,12 +170,16 @@ nnp_status fail(nnp_ctx* h, nnp_status st, const std::string& msg) {
   return st;
 }
 
+// A failed call's error is also taken off the thread's last-error state, so
+// that it does not surface in a later, unrelated call.
 #define CK(call)                                                                        \
   do {                                                                                  \
     cudaError_t e_ = (call);                                                            \
-    if (e_ != cudaSuccess)                                                              \
+    if (e_ != cudaSuccess) {                                                            \
+      cudaGetLastError();                                                               \
       return fail(h, e_ == cudaErrorMemoryAllocation ? NNP_ERR_ALLOC : NNP_ERR_CUDA,    \
                   std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    }                                                                                   \
   } while (0)
 
 template <typename T>
@@ -261,6 +274,28 @@ uint16_t f2h(float f) {  // IEEE binary16, round to nearest even
   return (uint16_t)(sign | h);
 }
 
+float bf2f(uint16_t u) {
+  const uint32_t x = (uint32_t)u << 16;
+  float f;
+  std::memcpy(&f, &x, 4);
+  return f;
+}
+
+float h2f(uint16_t u) {  // IEEE binary16 to FP32 (exact)
+  const uint32_t sign = (uint32_t)(u & 0x8000u) << 16;
+  const int exp = (u >> 10) & 0x1f;
+  const uint32_t man = u & 0x3ffu;
+  float f;
+  if (exp == 0) {  // zero or subnormal: man * 2^-24
+    f = std::ldexp((float)man, -24);
+    return sign ? -f : f;
+  }
+  const uint32_t x = exp == 31 ? (sign | 0x7f800000u | (man << 13))
+                               : (sign | ((uint32_t)(exp - 15 + 127) << 23) | (man << 13));
+  std::memcpy(&f, &x, 4);
+  return f;
+}
+
 // Packs host FP32 values into the device element type.
 struct Packer {
   Prec p;
@@ -273,6 +308,12 @@ struct Packer {
   void set(size_t i, float v) {
     if (p == Prec::F32) f32[i] = v;
     else f16[i] = p == Prec::BF16 ? f2bf(v) : f2h(v);
+  }
+  // a forward weight: with split, hi = round(v) at i and lo = round(v - hi)
+  // lo_off elements to its right
+  void set_fwd(size_t i, size_t lo_off, float v, int split) {
+    set(i, v);
+    if (split) set(i + lo_off, v - (p == Prec::BF16 ? bf2f(f16[i]) : h2f(f16[i])));
   }
   const void* data() const { return p == Prec::F32 ? (const void*)f32.data() : (const void*)f16.data(); }
 };
@@ -412,10 +453,11 @@ void nnp_destroy(nnp_handle h) {
   if (h->side) cudaStreamDestroy(h->side);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->aev_aliased) h->d_aev = nullptr;  // the dE/dG buffer
   void* ptrs[] = {h->d_Z, h->d_mol_off, h->d_orig, h->d_row_of_int, h->d_species_int,
                   h->d_mol_start, h->d_mol_end, h->d_row_elem, h->d_pos, h->nl.cnt_r,
-                  h->nl.nbr_r, h->nl.cnt_a, h->nl.nbr_a, h->d_aev, h->d_h1,
-                  h->d_h2, h->d_z3, h->d_d3, h->d_y, h->d_dG, h->d_atom_e, h->d_status, h->d_w, h->d_b,
+                  h->nl.nbr_r, h->nl.cnt_a, h->nl.nbr_a, h->d_aev, h->d_h1, h->d_h2s, h->d_d3s,
+                  h->d_h2, h->d_z3, h->d_d3, h->d_y, h->d_dG, h->d_atom_e, h->d_status, h->d_abort, h->d_w, h->d_b,
                   h->d_w4, h->d_b4, h->d_maps, h->d_work, h->d_ovf, h->d_nbr_work, h->d_pos_in, h->d_E, h->d_F};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -456,8 +498,10 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   if (params->precision < 0 || params->precision > 2) return fail(nullptr, NNP_ERR_ARG, "bad precision");
   if (!params->weights || params->n_weights != model_params() * params->n_models)
     return fail(nullptr, NNP_ERR_ARG, "weights: expected n_models * nnp_weights_per_model() floats");
-  for (int r = 0; r < 7; ++r)
+  for (int r = 0; r < 4; ++r)
     if (params->reserved[r] != 0) return fail(nullptr, NNP_ERR_ARG, "reserved fields must be zero");
+  if ((params->single_pass | params->recompute_aev | params->test_abort) & ~1)
+    return fail(nullptr, NNP_ERR_ARG, "single_pass, recompute_aev and test_abort must be 0 or 1");
   if (params->neighbor_mode < 0 || params->neighbor_mode > 2)
     return fail(nullptr, NNP_ERR_ARG, "neighbor_mode must be 0, 1 or 2");
   for (int i = 0; i < N; ++i) {
@@ -475,6 +519,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
 
   h = new (std::nothrow) nnp_ctx();
   if (!h) return fail(nullptr, NNP_ERR_ALLOC, "host allocation failed");
+  cudaGetLastError();  // a stale error of the caller's must not be taken for one of these launches
   struct Guard {
     nnp_ctx*& h;
     bool ok = false;
@@ -494,6 +539,9 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   h->n_models = params->n_models;
   h->prec = (Prec)params->precision;
   h->use_graph = params->use_graph;
+  h->split = (h->prec != Prec::F32 && !params->single_pass) ? 1 : 0;
+  h->aev_aliased = params->recompute_aev;
+  h->test_abort = params->test_abort;
   init_aev_const(h->aevc, params->box);
   for (int m = 0; m < n_mols; ++m) h->max_mol = std::max(h->max_mol, mol_offsets[m + 1] - mol_offsets[m]);
   if (h->prec != Prec::F32 && !tc_available())
@@ -516,6 +564,9 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   CK(dalloc(&d_mol_count, (size_t)n_mols * kSpecies));
   CK(dalloc(&h->d_status, 1));
   CK(cudaMemset(h->d_status, 0, sizeof(unsigned)));
+  CK(dalloc(&h->d_abort, 1));
+  CK(cudaMemset(h->d_abort, 0, sizeof(int)));
+  h->abort_steps = params->test_abort;
   if (N) CK(cudaMemcpy(h->d_Z, Z, sizeof(int) * N, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->d_mol_off, mol_offsets, sizeof(int) * (n_mols + 1), cudaMemcpyHostToDevice));
   launch_species_setup(h->d_Z, h->d_mol_off, n_mols, N, d_species_caller, d_mol_count, h->d_status, s0);
@@ -632,12 +683,21 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
 
   // ---- activations ----
   const size_t es = elem_size(h->prec);
-  h->ldh1 = (long)M * kH1Max;
+  const int sp = h->split ? 2 : 1;  // hi and lo halves side by side
+  h->ldh1 = (long)sp * M * kH1Max;
   h->ldh2 = (long)M * kH2Max;
   h->ldz3 = (long)M * kH3Max;
   const size_t R = h->n_rows;
-  CK(cudaMalloc(&h->d_aev, R * kFeaturesPad * es));
-  CK(cudaMemset(h->d_aev, 0, R * kFeaturesPad * es));
+  // dE/dG [R][1024] FP32; with recompute_aev the features (at most as large:
+  // [R][1024] FP32 or [R][2 x 1024] 16-bit) live in the same buffer
+  CK(dalloc(&h->d_dG, R * kFeaturesPad));
+  CK(cudaMemset(h->d_dG, 0, R * kFeaturesPad * sizeof(float)));
+  if (h->aev_aliased) {
+    h->d_aev = h->d_dG;
+  } else {
+    CK(cudaMalloc(&h->d_aev, R * kFeaturesPad * sp * es));
+    CK(cudaMemset(h->d_aev, 0, R * kFeaturesPad * sp * es));
+  }
   CK(cudaMalloc(&h->d_h1, R * h->ldh1 * es));
   CK(cudaMemset(h->d_h1, 0, R * h->ldh1 * es));
   if (h->prec == Prec::F32) {  // the tensor-core path keeps h2, z3, d3 and d2 on chip
@@ -648,9 +708,13 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
     CK(cudaMalloc(&h->d_d3, R * h->ldz3 * es));
     CK(cudaMemset(h->d_d3, 0, R * h->ldz3 * es));
   }
+  if (h->split) {  // the split forward's second hidden layer (hi | lo) and d3
+    CK(cudaMalloc(&h->d_h2s, R * 2 * M * kH2Max * es));
+    CK(cudaMemset(h->d_h2s, 0, R * 2 * M * kH2Max * es));
+    CK(cudaMalloc(&h->d_d3s, R * M * kH2Max * es));
+    CK(cudaMemset(h->d_d3s, 0, R * M * kH2Max * es));
+  }
   CK(dalloc(&h->d_y, R * M));
-  CK(dalloc(&h->d_dG, R * kFeaturesPad));
-  CK(cudaMemset(h->d_dG, 0, R * kFeaturesPad * sizeof(float)));
   CK(dalloc(&h->d_atom_e, R));
   CK(dalloc(&h->d_pos_in, (size_t)N * 3));
   CK(dalloc(&h->d_E, n_mols));
@@ -678,8 +742,10 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
     rows_w3t += (size_t)M * kHidden[e][1];
     rows_w2t += (size_t)M * kHidden[e][0];
   }
-  const size_t ld_w1 = kFeaturesPad, ld_w2 = kH1Max, ld_w3 = kH2Max, ld_w3t = kH3Max,
-               ld_w2t = kH2Max, ld_w1t = (size_t)M * kH1Max;
+  // the forward weights of the split path hold hi | lo side by side
+  const size_t ld_w1 = (size_t)sp * kFeaturesPad, ld_w2 = (size_t)sp * kH1Max,
+               ld_w3 = (size_t)sp * kH2Max, ld_w3t = kH3Max, ld_w2t = kH2Max,
+               ld_w1t = (size_t)M * kH1Max;
   h->w_off[0] = 0;
   h->w_off[1] = h->w_off[0] + rows_w1 * ld_w1;
   h->w_off[2] = h->w_off[1] + rows_w2 * ld_w2;
@@ -721,7 +787,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
       for (int o = 0; o < n1; ++o) {
         for (int k = 0; k < kFeatures; ++k) {
           const float v = W1[(size_t)o * kFeatures + k];
-          pk.set(h->w_off[0] + (r1[e] + (size_t)m * n1 + o) * ld_w1 + k, v);
+          pk.set_fwd(h->w_off[0] + (r1[e] + (size_t)m * n1 + o) * ld_w1 + k, kFeaturesPad, v, h->split);
           pk.set(h->w_off[5] + ((size_t)e * kFeaturesPad + k) * ld_w1t + (size_t)m * n1 + o, v);
         }
         bias[r1[e] + (size_t)m * n1 + o] = b1[o];
@@ -729,7 +795,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
       for (int o = 0; o < n2; ++o) {
         for (int k = 0; k < n1; ++k) {
           const float v = W2[(size_t)o * n1 + k];
-          pk.set(h->w_off[1] + (r2[e][m] + o) * ld_w2 + k, v);
+          pk.set_fwd(h->w_off[1] + (r2[e][m] + o) * ld_w2 + k, kH1Max, v, h->split);
           pk.set(h->w_off[4] + (r2t[e][m] + k) * ld_w2t + o, v);
         }
         bias[b1_total + r2[e][m] + o] = b2[o];
@@ -737,7 +803,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
       for (int o = 0; o < n3; ++o) {
         for (int k = 0; k < n2; ++k) {
           const float v = W3[(size_t)o * n2 + k];
-          pk.set(h->w_off[2] + (r3[e][m] + o) * ld_w3 + k, v);
+          pk.set_fwd(h->w_off[2] + (r3[e][m] + o) * ld_w3 + k, kH2Max, v, h->split);
           pk.set(h->w_off[3] + (r3t[e][m] + k) * ld_w3t + o, v);
         }
         bias[b1_total + b2_total + r3[e][m] + o] = b3[o];
@@ -777,6 +843,12 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
       P.bias = h->d_b + r1[e];
       P.M = Me; P.N = M * n1; P.K = tc ? kFeaturesPad : kFeatures; P.epi = (int)Epi::BiasCelu;
       P.a_row0 = (int)row0; P.b_row0 = (int)r1[e]; P.elem = e; P.model = -1;
+      if (h->split) {  // features, W1 and h1 as hi | lo
+        P.split = 1;
+        P.a_lo = kFeaturesPad;
+        P.b_lo = kFeaturesPad;
+        P.d_lo = M * kH1Max;
+      }
       h->L[0].probs.push_back(P);
       add_tiles(h->L[0], bm, tc ? 256 : 64);  // first layer forward
     }
@@ -847,6 +919,43 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         add_tiles(h->L[4], bm, tc ? 256 : 64);
       }
     }
+    // split forward (tensor cores): layers 2 and 3 as grouped products on
+    // (hi, lo) operands; h2 of member m at column m * 192 (the last 64-column
+    // box of a narrower layer stays inside the member's columns), its lo half
+    // M * 192 columns to the right
+    for (int m = 0; m < (h->split ? M : 0); ++m) {
+      {  // layer 2 forward: h2 = celu(W2 h1 + b2)
+        GemmProblem P{};
+        P.M = Me; P.N = n2; P.K = n1; P.epi = (int)Epi::BiasCelu;
+        P.a_row0 = (int)row0; P.a_col0 = m * n1; P.b_row0 = (int)r2[e][m]; P.d_col0 = m * kH2Max;
+        P.bias = h->d_b + b1_total + r2[e][m];
+        P.split = 1;
+        P.a_lo = M * kH1Max;
+        P.b_lo = kH1Max;
+        P.d_lo = M * kH2Max;
+        P.elem = e; P.model = m;
+        h->L[1].probs.push_back(P);
+        add_tiles(h->L[1], bm, kH2Max);
+      }
+      {  // layer 3 forward + output layer: y = w4 . celu(W3 h2 + b3) + b4, and
+         // d3 = (1/M) w4 celu'(z3) for the reverse pass (member m at column m * 192)
+        GemmProblem P{};
+        P.M = Me; P.N = n3; P.K = n2; P.epi = (int)Epi::Energy;
+        P.D = h->d_d3s; P.d_col0 = m * kH2Max;
+        P.a_row0 = (int)row0; P.a_col0 = m * kH2Max; P.b_row0 = (int)r3[e][m];
+        P.bias = h->d_b + b1_total + b2_total + r3[e][m];
+        P.w4 = h->d_w4 + ((size_t)e * kMaxModels + m) * kH3Max;
+        P.y = h->d_y + row0 * M + m; P.ldy = M;
+        P.b4 = b4[(size_t)e * kMaxModels + m];
+        P.inv_m = 1.0f / (float)M;
+        P.split = 1;
+        P.a_lo = M * kH2Max;
+        P.b_lo = kH2Max;
+        P.elem = e; P.model = m;
+        h->L[2].probs.push_back(P);
+        add_tiles(h->L[2], bm, kH3Max);
+      }
+    }
   }
   if (tc) {
     if (tc_maps_bytes() > sizeof(h->tc_maps[0])) return fail(h, NNP_ERR_UNSUPPORTED, "tensor map size");
@@ -855,9 +964,9 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
       const void* base;
       uint64_t rows, cols;
     };
-    const MapSpec A[6] = {{h->d_aev, R64, (uint64_t)kFeaturesPad},
+    const MapSpec A[6] = {{h->d_aev, R64, (uint64_t)kFeaturesPad * sp},
                           {h->d_h1, R64, (uint64_t)h->ldh1},
-                          {h->d_h2, R64, (uint64_t)h->ldh2},
+                          {h->d_h2s, R64, (uint64_t)2 * M * kH2Max},
                           {h->d_d3, R64, (uint64_t)h->ldz3},
                           {h->d_h2, R64, (uint64_t)h->ldh2},
                           {h->d_h1, R64, (uint64_t)h->ldh1}};
@@ -873,7 +982,10 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
     h->l1_b_base[1] = B[5].base;
     h->l1_b_rows[1] = B[5].rows;
     h->l1_b_cols[1] = B[5].cols;
-    for (int l : {0, 5}) {  // the two first-layer products (layers 1-4 run in the fused tail)
+    // the two first-layer products (layers 1-4 run in the fused tail), and with
+    // the split forward the forward products of layers 2 and 3
+    for (int l : {0, 5, 1, 2}) {
+      if ((l == 1 || l == 2) && !h->split) continue;
       if (!tc_make_map(h->tc_maps[l], A[l].base, h->prec, A[l].rows, A[l].cols, A[l].cols, 128) ||
           !tc_make_map(h->tc_maps[l] + 128, B[l].base, h->prec, B[l].rows, B[l].cols, B[l].cols,
                        (uint32_t)h->tc_box[l]))
@@ -885,6 +997,21 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         !tc_make_map(h->tc_maps[5] + 256, h->d_dG, Prec::F32, R64, (uint64_t)kFeaturesPad,
                      (uint64_t)kFeaturesPad, 128, 32))
       return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for a first-layer output");
+    if (h->split) {  // layer 2's output h2 (hi | lo), layer 3's d3
+      if (!tc_make_map(h->tc_maps[1] + 256, h->d_h2s, h->prec, R64, (uint64_t)2 * M * kH2Max,
+                       (uint64_t)2 * M * kH2Max, 128) ||
+          !tc_make_map(h->tc_maps[2] + 256, h->d_d3s, h->prec, R64, (uint64_t)M * kH2Max,
+                       (uint64_t)M * kH2Max, 128))
+        return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the split forward");
+      for (int l : {1, 2}) {  // tiles balanced over the SMs by K x N
+        Layer& L = h->L[l];
+        std::vector<double> cost;
+        for (const GemmTile& t : L.tiles) cost.push_back((double)L.probs[t.problem].K * L.probs[t.problem].N);
+        balance_tiles(L.tiles, cost, h->sms, L.cta_off);
+        CK(dalloc(&L.d_cta_off, L.cta_off.size()));
+        CK(cudaMemcpy(L.d_cta_off, L.cta_off.data(), sizeof(int) * L.cta_off.size(), cudaMemcpyHostToDevice));
+      }
+    }
     CK(tc_set_smem());
     // fused tail: one problem per (element, member), tiles of 128 rows
     for (int e = 0; e < kSpecies; ++e) {
@@ -907,7 +1034,10 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         T.w4 = h->d_w4 + ((size_t)e * kMaxModels + m) * kH3Max;
         T.b4 = b4[(size_t)e * kMaxModels + m];
         T.inv_m = 1.0f / (float)M;
-        T.y = h->d_y + (size_t)T.row0 * M + m;
+        // the split forward's layer-3 product writes y; the tail then only
+        // runs the reverse pass (recomputing its own forward for it)
+        T.y = h->split ? nullptr : h->d_y + (size_t)T.row0 * M + m;
+        T.h2_col0 = m * kH2Max;
         T.ldy = M;
         const int pi = (int)h->tail_probs.size();
         h->tail_probs.push_back(T);
@@ -924,6 +1054,15 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the fused tail");
     if (!tc_make_map(h->tail_maps + 5 * 128, h->d_h1, h->prec, R64, (uint64_t)h->ldh1, (uint64_t)h->ldh1,
                      128, 32, true))
+      return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the fused tail");
+    // reverse-only mode (split forward): h2 and d3 as the forward products stored
+    // them; without the split forward, valid maps that the kernel does not use
+    const void* h2_base = h->split ? h->d_h2s : h->d_h1;
+    const void* d3_base = h->split ? h->d_d3s : h->d_h1;
+    const uint64_t h2_cols = h->split ? (uint64_t)2 * M * kH2Max : (uint64_t)h->ldh1;
+    const uint64_t d3_cols = h->split ? (uint64_t)M * kH2Max : (uint64_t)h->ldh1;
+    if (!tc_make_map(h->tail_maps + 6 * 128, h2_base, h->prec, R64, h2_cols, h2_cols, 128) ||
+        !tc_make_map(h->tail_maps + 7 * 128, d3_base, h->prec, R64, d3_cols, d3_cols, 128))
       return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the fused tail");
     CK(tail_set_smem());
     {  // balance the tail's tiles by network size (two products per layer and direction)
@@ -983,7 +1122,7 @@ void run_gemm(nnp_ctx* h, int layer, cudaStream_t s) {
     launch_gemm_simt(L.d_probs, L.d_tiles, (int)L.tiles.size(), s);
   else
     launch_gemm_tc(L.d_probs, L.d_tiles, L.d_cta_off, (int)L.cta_off.size() - 1, h->prec,
-                   h->tc_box[layer], h->tc_maps[layer], h->d_status, s);
+                   h->tc_box[layer], h->tc_maps[layer], h->d_status, h->d_abort, s);
 }
 
 // The whole step, enqueued on s.  With ev != nullptr an event is recorded
@@ -1010,20 +1149,29 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
     kernels += 2;
   }
   mark(1);
-  launch_aev(g, h->nl, h->aevc, h->d_row_of_int, h->d_aev, h->prec, h->fwd_warps, s);
+  launch_aev(g, h->nl, h->aevc, h->d_row_of_int, h->d_aev, h->prec, h->fwd_warps, s, h->split != 0);
   ++kernels;
   mark(2);
   gemm(0);
   mark(3);
   bool fork = false;
   if (h->prec != Prec::F32) {
-    // tensor cores: L2 fwd, L3 fwd + output layer, L3 rev, L2 rev in one kernel
-    if (!h->tail_tiles.empty()) {
+    auto tail = [&](int reverse) {
+      if (h->tail_tiles.empty()) return;
       launch_mlp_tail(h->d_tail_probs, h->d_tail_tiles, h->d_tail_off, (int)h->tail_off.size() - 1, h->prec,
-                      h->tail_maps, F ? 1 : 0, h->d_status, s);
+                      h->tail_maps, reverse, h->d_status, h->d_abort, s);
       ++kernels;
+    };
+    if (h->split) {
+      // split forward: layer 2, then layer 3 with the output layer (y)
+      gemm(1);
+      mark(4);
+      gemm(2);
+    } else {
+      // tensor cores: L2 fwd, L3 fwd + output layer, L3 rev, L2 rev in one kernel
+      tail(F ? 1 : 0);
+      mark(4);
     }
-    mark(4);
     mark(5);
     // with forces (and no per-stage events) the energy reduction runs on a
     // side stream, concurrently with the reverse pass, joined at the end
@@ -1039,6 +1187,7 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
     ++kernels;
     mark(6);
     if (!F) return kernels;
+    if (h->split) tail(2);  // the reverse pass of layers 3 and 2 from the stored h2 and d3
     mark(7);
     mark(8);
   } else {
@@ -1070,6 +1219,10 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
 
 }  // namespace
 
+namespace {
+nnp_status compute_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_t s);
+}  // namespace
+
 extern "C" {
 
 nnp_status nnp_compute(nnp_handle h, const float* pos, double* E, double* F, void* stream) {
@@ -1077,6 +1230,25 @@ nnp_status nnp_compute(nnp_handle h, const float* pos, double* E, double* F, voi
   if ((!pos && h->n_atoms) || (!E && h->n_mols)) return fail(h, NNP_ERR_ARG, "null buffer");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   h->last_stream = s;
+  h->features_overwritten = h->aev_aliased && F != nullptr;
+  cudaGetLastError();  // a stale error of the caller's must not be taken for one of these launches
+  if (h->abort_steps > 0) {  // tests: this step's tensor-core kernels stop at their start
+    --h->abort_steps;
+    CK(cudaMemsetAsync(h->d_abort, 1, sizeof(int), s));
+    const nnp_status st = compute_step(h, pos, E, F, s);
+    CK(cudaMemsetAsync(h->d_abort, 0, sizeof(int), s));
+    return st;
+  }
+  return compute_step(h, pos, E, F, s);
+}
+
+}  // extern "C"
+
+namespace {
+
+// One evaluation: a graph replay (captured again when the buffers change) or
+// direct launches.
+nnp_status compute_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_t s) {
   if (h->use_graph) {
     if (!h->gexec || h->g_pos != pos || h->g_E != E || h->g_F != F) {
       if (h->gexec) {
@@ -1111,6 +1283,23 @@ nnp_status nnp_compute(nnp_handle h, const float* pos, double* E, double* F, voi
   return NNP_OK;
 }
 
+}  // namespace
+
+namespace nnp {
+int enqueue_nnp(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_t s) {
+  const int k = enqueue_step(h, pos, E, F, s);
+  return cudaGetLastError() == cudaSuccess ? k : -1;
+}
+void handle_shape(const nnp_ctx* h, int* n_atoms, int* n_mols, std::vector<int>& mol_off) {
+  *n_atoms = h->n_atoms;
+  *n_mols = h->n_mols;
+  mol_off = h->mol_off_h;
+}
+void set_last_stream(nnp_ctx* h, cudaStream_t s) { h->last_stream = s; }
+}  // namespace nnp
+
+extern "C" {
+
 nnp_status nnp_compute_timed(nnp_handle h, const float* pos, double* E, double* F, void* stream,
                               float* stage_ms, int32_t n_stages) {
   if (!h || !stage_ms || n_stages < NNP_NUM_STAGES) return NNP_ERR_ARG;
@@ -1141,6 +1330,9 @@ int32_t nnp_kernels_per_step(nnp_handle h, int32_t with_forces) {
     for (int l = 1; l < 3; ++l) k += h->L[l].tiles.empty() ? 0 : 1;
     if (with_forces)
       for (int l = 3; l < 5; ++l) k += h->L[l].tiles.empty() ? 0 : 1;
+  } else if (h->split) {
+    for (int l = 1; l < 3; ++l) k += h->L[l].tiles.empty() ? 0 : 1;
+    if (with_forces) k += h->tail_tiles.empty() ? 0 : 1;
   } else {
     k += h->tail_tiles.empty() ? 0 : 1;
   }
@@ -1305,8 +1497,11 @@ nnp_status nnp_get_neighbors(nnp_handle h, int32_t kind, int32_t* counts, int32_
 nnp_status nnp_get_features(nnp_handle h, float* out, void* stream) {
   if (!h) return NNP_ERR_ARG;
   if (h->n_atoms && !out) return fail(h, NNP_ERR_ARG, "null buffer");
+  if (h->features_overwritten)
+    return fail(h, NNP_ERR_UNSUPPORTED,
+                "recompute_aev: the last step's reverse pass reused the features' buffer");
   launch_export_features(h->d_aev, h->prec, h->d_row_of_int, h->d_orig, h->n_atoms, out,
-                         static_cast<cudaStream_t>(stream));
+                         static_cast<cudaStream_t>(stream), h->split != 0);
   CK(cudaGetLastError());
   return NNP_OK;
 }

@@ -12,11 +12,14 @@
 #pragma once
 
 #include <utility>
+#include <vector>
 
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+
+struct nnp_ctx;
 
 namespace nnp {
 
@@ -116,8 +119,11 @@ enum class Epi : int {
   Bias = 1,       // D = acc + bias[n], FP32 output     (pre-activation of the last hidden layer)
   DCelu = 2,      // D = acc * celu'(D_in-place)       (reverse through a hidden layer)
   Store = 3,      // D = acc (FP32 output)              (dE/dG)
-  Head = 4        // last hidden layer + output layer: z = acc + bias, y[row] = w4 . celu(z) + b4,
+  Head = 4,       // last hidden layer + output layer: z = acc + bias, y[row] = w4 . celu(z) + b4,
                   // D = (1/M) w4 * celu'(z)  (needs the whole row in one tile)
+  Energy = 5      // last hidden layer + output layer, tensor-core path: y[row] = w4 . celu(acc + bias)
+                  // + b4 in FP32 and, if D is given, D = (1/M) w4 * celu'(acc + bias) (16-bit);
+                  // needs the whole row in one tile
 };
 
 struct GemmProblem {
@@ -129,7 +135,12 @@ struct GemmProblem {
   int epi;
   int a_row0, b_row0, a_col0, b_col0, d_col0;  // used by the tensor-core path (TMA coordinates)
   int elem, model;
-  // Epi::Head only
+  // Tensor-core path, split operands: with split = 1 the product is
+  // A_hi B_hi + A_lo B_hi + A_hi B_lo, the lo halves a_lo / b_lo columns to the
+  // right of the hi halves in the same arrays; with d_lo > 0 a 16-bit output
+  // is stored as hi = round(v) and lo = round(v - hi), lo d_lo columns right.
+  int split, a_lo, b_lo, d_lo;
+  // Epi::Head / Epi::Energy only
   const float* w4;  // [N] output weights of this (element, member)
   float* y;         // per-row output, stride ldy
   long ldy;
@@ -150,6 +161,7 @@ struct TailProblem {
   float b4, inv_m;
   float* y;     // y + row0 * M + member, stride ldy
   long ldy;
+  int h2_col0;  // reverse-only mode: first column of this member in h2 and d3 (member * 192)
 };
 
 // A tile of the flattened problem list.
@@ -195,9 +207,10 @@ void launch_neighbors(const Geometry& g, const NeighborLists& nl, const AevConst
 void launch_neighbors_cells(const Geometry& g, const NeighborLists& nl, const AevConst& c,
                             const CellGrid& cg, const CellBuffers& cb, int region_atoms,
                             unsigned* status, cudaStream_t s);
+// split: 16-bit features as hi | lo rows of 2 x 1024 columns
 void launch_aev(const Geometry& g, const NeighborLists& nl, const AevConst& c,
                 const int* row_of_int, void* aev_out, Prec out_prec, int warps_per_cta,
-                cudaStream_t s);
+                cudaStream_t s, bool split = false);
 // Reverse pass: a main launch over the work items, plus, when cap_a exceeds
 // the main launch's staging capacity, a second launch for the centres with
 // more angular neighbours (ovf: DEVICE int[n_atoms + 1] scratch).
@@ -225,19 +238,34 @@ cudaError_t aev_set_smem_limits(size_t fwd_bytes, size_t adj_bytes);
 // Inspection helpers.
 void launch_export_neighbors(const NeighborLists& nl, int kind, const int* orig_of_int, int n,
                              int* counts_out, int* lists_out, int cap_out, cudaStream_t s);
+// split: rows of hi | lo (2 x 1024 columns), exported as hi + lo
 void launch_export_features(const void* aev, Prec prec, const int* row_of_int,
-                            const int* orig_of_int, int n, float* out, cudaStream_t s);
+                            const int* orig_of_int, int n, float* out, cudaStream_t s,
+                            bool split = false);
 void launch_export_atomic_energies(const double* atom_energy_row, const int* row_of_int,
                                    const int* orig_of_int, int n, double* out, cudaStream_t s);
 
 size_t tail_maps_bytes();
 int tail_weight_box(int which);  // box rows of the w2, w3, w3t, w2t maps
 cudaError_t tail_set_smem();
+// reverse: 0 forward only, 1 forward and reverse, 2 reverse only (h2 and d3
+// stored by the split forward products).  abort_req: DEVICE int read at
+// kernel start; nonzero makes the kernel stop before it issues any copy or
+// product, as after a bounded wait that gave up
 void launch_mlp_tail(const TailProblem* probs, const GemmTile* tiles, const int* cta_off, int n_ctas,
-                     Prec p, const void* maps, int reverse, unsigned* status, cudaStream_t s);
+                     Prec p, const void* maps, int reverse, unsigned* status, const int* abort_req,
+                     cudaStream_t s);
 
 // Featurizer constants (cutoffs, shift grids, species-pair table, box).
 void aev_constants(AevConst& c, const double box[3]);
+
+// For the MD loop (md.cu): one evaluation of a handle enqueued on s as direct
+// launches (captured by the caller's graph); returns the number of kernels,
+// negative if a launch failed.  The handle's atom and molecule counts and its
+// molecule offsets (caller order).  The stream that nnp_get_status waits on.
+int enqueue_nnp(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_t s);
+void handle_shape(const nnp_ctx* h, int* n_atoms, int* n_mols, std::vector<int>& mol_off);
+void set_last_stream(nnp_ctx* h, cudaStream_t s);
 
 // Setup kernels (create time).
 void launch_species_setup(const int* Z_caller, const int* mol_off, int n_mols, int n_atoms,

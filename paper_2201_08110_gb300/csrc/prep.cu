@@ -195,12 +195,14 @@ __global__ void k_export_neighbors(const int* __restrict__ cnt, const int* __res
 
 template <typename T>
 __global__ void k_export_features(const T* __restrict__ aev, const int* __restrict__ row_of_int,
-                                  const int* __restrict__ orig, int n, float* __restrict__ out) {
+                                  const int* __restrict__ orig, int n, float* __restrict__ out,
+                                  int split) {
   const int q = blockIdx.x;
   if (q >= n) return;
-  const T* src = aev + (size_t)row_of_int[q] * kFeaturesPad;
+  const T* src = aev + (size_t)row_of_int[q] * (split ? 2 : 1) * kFeaturesPad;
   float* dst = out + (size_t)orig[q] * kFeatures;
-  for (int f = threadIdx.x; f < kFeatures; f += blockDim.x) dst[f] = to_f(src[f]);
+  for (int f = threadIdx.x; f < kFeatures; f += blockDim.x)
+    dst[f] = split ? to_f(src[f]) + to_f(src[kFeaturesPad + f]) : to_f(src[f]);
 }
 
 __global__ void k_export_atomic(const double* __restrict__ e_row, const int* __restrict__ row_of_int,
@@ -276,18 +278,19 @@ void launch_export_neighbors(const NeighborLists& nl, int kind, const int* orig,
 }
 
 void launch_export_features(const void* aev, Prec prec, const int* row_of_int, const int* orig,
-                            int n, float* out, cudaStream_t s) {
+                            int n, float* out, cudaStream_t s, bool split) {
   if (n <= 0) return;
+  const int sp = split ? 1 : 0;
   switch (prec) {
     case Prec::F32:
-      k_export_features<float><<<n, 256, 0, s>>>((const float*)aev, row_of_int, orig, n, out);
+      k_export_features<float><<<n, 256, 0, s>>>((const float*)aev, row_of_int, orig, n, out, 0);
       break;
     case Prec::BF16:
       k_export_features<__nv_bfloat16>
-          <<<n, 256, 0, s>>>((const __nv_bfloat16*)aev, row_of_int, orig, n, out);
+          <<<n, 256, 0, s>>>((const __nv_bfloat16*)aev, row_of_int, orig, n, out, sp);
       break;
     case Prec::F16:
-      k_export_features<__half><<<n, 256, 0, s>>>((const __half*)aev, row_of_int, orig, n, out);
+      k_export_features<__half><<<n, 256, 0, s>>>((const __half*)aev, row_of_int, orig, n, out, sp);
       break;
   }
 }

@@ -121,6 +121,11 @@ extern "C" nnp_status nnp_features_static(const int32_t* Z_dev, const float* pos
   if (n_atoms > 0 && (!Z_dev || !positions_dev || !features_out_dev)) return NNP_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return NNP_ERR_CUDA;
+  if (stream) {  // the scratch address below is the current device's: so must the stream be
+    int sdev = -1;
+    if (cudaStreamGetDevice(static_cast<cudaStream_t>(stream), &sdev) != cudaSuccess) return NNP_ERR_ARG;
+    if (sdev != dev) return NNP_ERR_ARG;
+  }
   StaticScratch* p = nullptr;
   {
     // First call on this device: look up the scratch array's device address

@@ -28,7 +28,8 @@ EXPORTS = ("nnp_weights_per_model", "nnp_num_features", "nnp_create", "nnp_creat
            "nnp_compute", "nnp_compute_host", "nnp_get_status", "nnp_last_error", "nnp_destroy",
            "nnp_get_capacity", "nnp_get_neighbors", "nnp_get_features",
            "nnp_get_atomic_energies", "nnp_compute_timed", "nnp_kernels_per_step",
-           "nnp_features_static", "nnp_autotune", "nnp_set_schedule", "nnp_mm_coupling")
+           "nnp_features_static", "nnp_autotune", "nnp_set_schedule", "nnp_mm_coupling",
+           "nnp_md_create", "nnp_md_run", "nnp_md_last_error", "nnp_md_destroy")
 STATIC_MAX_ATOMS = 256
 COUPLING_MAX_NNP = 512
 STAGES = ("neighbors", "features", "l1_fwd", "l2_fwd", "l3_fwd", "energy", "l3_rev", "l2_rev",
@@ -48,7 +49,18 @@ class Params(ctypes.Structure):
                 ("box", ctypes.c_double * 3), ("total_charge", ctypes.c_int32),
                 ("max_neighbors", ctypes.c_int32), ("max_angular", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("neighbor_mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("single_pass", ctypes.c_int32), ("recompute_aev", ctypes.c_int32),
+                ("test_abort", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+class MDParams(ctypes.Structure):
+    _fields_ = [("integrator", ctypes.c_int32), ("dt", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("kT", ctypes.c_double), ("masses", ctypes.c_void_p), ("n_mm", ctypes.c_int32),
+                ("mm_positions_dev", ctypes.c_void_p), ("mm_charges_dev", ctypes.c_void_p),
+                ("mm_sigma_dev", ctypes.c_void_p), ("mm_epsilon_dev", ctypes.c_void_p),
+                ("nnp_charges_dev", ctypes.c_void_p), ("nnp_sigma_dev", ctypes.c_void_p),
+                ("nnp_epsilon_dev", ctypes.c_void_p), ("coulomb_k", ctypes.c_double),
+                ("concurrent", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
 
 
 _lib = None
@@ -100,6 +112,14 @@ def load_library(path: str = LIB_PATH):
     lib.nnp_features_static.restype = ctypes.c_int
     lib.nnp_mm_coupling.argtypes = [P, P, P, P, I32, P, P, P, P, I32, ctypes.c_double, P, P, P, P]
     lib.nnp_mm_coupling.restype = ctypes.c_int
+    lib.nnp_md_create.argtypes = [P, P, P]
+    lib.nnp_md_create.restype = ctypes.c_int
+    lib.nnp_md_run.argtypes = [P, P, P, I32, P, P, P]
+    lib.nnp_md_run.restype = ctypes.c_int
+    lib.nnp_md_last_error.argtypes = [P]
+    lib.nnp_md_last_error.restype = ctypes.c_char_p
+    lib.nnp_md_destroy.argtypes = [P]
+    lib.nnp_md_destroy.restype = None
     _lib = lib
     return lib
 
@@ -125,7 +145,8 @@ class NNP:
 
     def __init__(self, Z, weights, n_models: int, mol_off=None, precision: str = "fp32",
                  box=None, max_neighbors: int = 0, max_angular: int = 0,
-                 use_graph: bool = False, total_charge: int = 0, neighbor_mode: int = 0):
+                 use_graph: bool = False, total_charge: int = 0, neighbor_mode: int = 0,
+                 single_pass: bool = False, recompute_aev: bool = False, test_abort: bool = False):
         self._lib = load_library()
         Z = np.ascontiguousarray(Z, dtype=np.int32)
         if mol_off is None:
@@ -145,6 +166,9 @@ class NNP:
         p.max_angular = int(max_angular)
         p.use_graph = 1 if use_graph else 0
         p.neighbor_mode = int(neighbor_mode)
+        p.single_pass = 1 if single_pass else 0
+        p.recompute_aev = 1 if recompute_aev else 0
+        p.test_abort = 1 if test_abort else 0
         h = ctypes.c_void_p()
         rc = self._lib.nnp_create_batch(Z.ctypes.data, mol_off.ctypes.data, mol_off.shape[0] - 1,
                                         ctypes.byref(p), ctypes.byref(h))
@@ -261,6 +285,20 @@ class NNP:
         return out
 
 
+def _check_tensor(t, name, dtype, shape):
+    """The C ABI takes raw device pointers: a tensor on another device, of
+    another type or layout, or too small would be misread or overrun."""
+    import torch
+    if not (t.is_cuda and t.device == torch.device("cuda", torch.cuda.current_device())):
+        raise ValueError(f"{name}: must be a CUDA tensor on the current device")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
 def features_static(Z, positions, out=None, stream=None):
     """Features of one non-periodic molecule (CUDA int32 Z [n], CUDA float32
     positions [n, 3]) through the allocation-free entry point; returns CUDA
@@ -271,6 +309,9 @@ def features_static(Z, positions, out=None, stream=None):
     n = int(positions.shape[0])
     if out is None:
         out = torch.empty(n, 1008, dtype=torch.float32, device=positions.device)
+    _check_tensor(Z, "Z", torch.int32, (n,))
+    _check_tensor(positions, "positions", torch.float32, (n, 3))
+    _check_tensor(out, "out", torch.float32, (n, 1008))
     rc = lib.nnp_features_static(_ptr(Z), _ptr(positions), n, _ptr(out), _stream_ptr(stream))
     if rc != 0:
         raise NNPError(rc, "nnp_features_static")
@@ -294,6 +335,16 @@ def mm_coupling(nnp_pos, nnp_q, nnp_sigma, nnp_eps, mm_pos, mm_q, mm_sigma, mm_e
         nnp_forces = torch.zeros(n_nnp, 3, dtype=torch.float64, device=dev)
     if mm_forces is None:
         mm_forces = torch.zeros(n_mm, 3, dtype=torch.float64, device=dev)
+    f32, f64 = torch.float32, torch.float64
+    _check_tensor(nnp_pos, "nnp_pos", f32, (n_nnp, 3))
+    _check_tensor(mm_pos, "mm_pos", f32, (n_mm, 3))
+    for name, t, n in (("nnp_q", nnp_q, n_nnp), ("nnp_sigma", nnp_sigma, n_nnp),
+                       ("nnp_eps", nnp_eps, n_nnp), ("mm_q", mm_q, n_mm),
+                       ("mm_sigma", mm_sigma, n_mm), ("mm_eps", mm_eps, n_mm)):
+        _check_tensor(t, name, f32, (n,))
+    _check_tensor(energy, "energy", f64, (1,))
+    _check_tensor(nnp_forces, "nnp_forces", f64, (n_nnp, 3))
+    _check_tensor(mm_forces, "mm_forces", f64, (n_mm, 3))
     rc = lib.nnp_mm_coupling(_ptr(nnp_pos), _ptr(nnp_q), _ptr(nnp_sigma), _ptr(nnp_eps), n_nnp,
                              _ptr(mm_pos), _ptr(mm_q), _ptr(mm_sigma), _ptr(mm_eps), n_mm,
                              float(coulomb_k), _ptr(energy), _ptr(nnp_forces), _ptr(mm_forces),
@@ -301,6 +352,79 @@ def mm_coupling(nnp_pos, nnp_q, nnp_sigma, nnp_eps, mm_pos, mm_q, mm_sigma, mm_e
     if rc != 0:
         raise NNPError(rc, "nnp_mm_coupling")
     return energy, nnp_forces, mm_forces
+
+
+class MD:
+    """The replica MD loop of include/nnp.h (nnp_md_*) around an NNP handle:
+    velocity Verlet ("verlet") or Langevin BAOAB ("baoab") over every atom of
+    the handle, each step one CUDA graph replay; optionally the NNP-MM coupling
+    term of one fixed MM environment (env: a workloads.Environment-like object
+    with CUDA float32 tensors mm_pos [n_mm, 3], mm_q, mm_sigma, mm_eps [n_mm]
+    and nnp_q, nnp_sigma, nnp_eps [N]), on a second stream when concurrent."""
+
+    def __init__(self, model: NNP, masses, dt: float, integrator: str = "verlet",
+                 gamma: float = 0.0, kT: float = 0.0, env=None, coulomb_k: float = 0.0,
+                 concurrent: bool = True):
+        import torch
+        self._lib = load_library()
+        self.model = model
+        m = np.ascontiguousarray(masses, dtype=np.float64).reshape(-1)
+        if m.shape[0] != model.n_atoms:
+            raise ValueError("masses: one per atom of the handle")
+        p = MDParams()
+        p.integrator = {"verlet": 0, "baoab": 1}[integrator]
+        p.dt, p.gamma, p.kT = float(dt), float(gamma), float(kT)
+        p.masses = m.ctypes.data
+        self._env = env
+        if env is not None:
+            n, n_mm = model.n_atoms, int(env.mm_pos.shape[0])
+            f32 = torch.float32
+            _check_tensor(env.mm_pos, "mm_pos", f32, (n_mm, 3))
+            for name, t, k in (("mm_q", env.mm_q, n_mm), ("mm_sigma", env.mm_sigma, n_mm),
+                               ("mm_eps", env.mm_eps, n_mm), ("nnp_q", env.nnp_q, n),
+                               ("nnp_sigma", env.nnp_sigma, n), ("nnp_eps", env.nnp_eps, n)):
+                _check_tensor(t, name, f32, (k,))
+            p.n_mm = n_mm
+            p.mm_positions_dev, p.mm_charges_dev = _ptr(env.mm_pos), _ptr(env.mm_q)
+            p.mm_sigma_dev, p.mm_epsilon_dev = _ptr(env.mm_sigma), _ptr(env.mm_eps)
+            p.nnp_charges_dev, p.nnp_sigma_dev = _ptr(env.nnp_q), _ptr(env.nnp_sigma)
+            p.nnp_epsilon_dev = _ptr(env.nnp_eps)
+            p.coulomb_k = float(coulomb_k)
+            p.concurrent = 1 if concurrent else 0
+        h = ctypes.c_void_p()
+        rc = self._lib.nnp_md_create(model._h, ctypes.byref(p), ctypes.byref(h))
+        if rc != 0:
+            raise NNPError(rc, "nnp_md_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.nnp_md_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, x, v, n_steps: int, noise=None, energy=None, stream=None):
+        """n_steps steps from x, v (CUDA float64 [N, 3], updated in place);
+        noise: CUDA float64 [n_steps, N, 3] (BAOAB); energy: CUDA float64
+        [n_steps, n_mols] or None, the potential energy after each step."""
+        import torch
+        n = self.model.n_atoms
+        f64 = torch.float64
+        _check_tensor(x, "x", f64, (n, 3))
+        _check_tensor(v, "v", f64, (n, 3))
+        if noise is not None:
+            _check_tensor(noise, "noise", f64, (n_steps, n, 3))
+        if energy is not None:
+            _check_tensor(energy, "energy", f64, (n_steps, self.model.n_mols))
+        rc = self._lib.nnp_md_run(self._h, _ptr(x), _ptr(v), int(n_steps), _ptr(noise), _ptr(energy),
+                                  _stream_ptr(stream))
+        if rc != 0:
+            raise NNPError(rc, self._lib.nnp_md_last_error(self._h).decode())
 
 
 def _autograd_function():

@@ -1,26 +1,43 @@
 """Helpers shared by the GPU parity tests: building the library, running the
 oracle on the same seeded inputs, and the error measures with their bounds.
 
-Tolerances (per molecule, against the FP64 oracle):
-* FP32 networks: |dE| / S <= 1e-5 and max |dF| <= 1e-4 * RMS(F_ref);
-* FP16 networks: |dE| / S <= 2e-3 and RMS(dF) / RMS(F_ref) <= 1e-2;
-* BF16 networks, one pass: |dE| / S <= 6e-3 and RMS(dF) / RMS(F_ref) <= 1e-2.
-S = sum_i |E_i,ref| is the molecule's gross atomic energy.  It equals |E_ref|
-when the atomic energies share a sign (ANI's per-element offsets make them
-do), and it stays well conditioned when the atomic energies of random-weight
-networks cancel (|E_ref| reaches 1e-3 S on these workloads).  |dE| / |E_ref|
-is reported alongside.  The single-pass BF16 bound is derived from the
-arithmetic: rounding the weights to 8 significant bits perturbs every atom of
-an element the same way, so the energy error grows with S rather than with
-its square root; on the 512-molecule batch this reaches 3.6e-3 S, above the
-2e-3 of the FP16 bound.
+Energy rule, per molecule, against the FP64 oracle (relative energy error with
+the near-zero reading for molecules whose atomic energies cancel):
+    |dE| / |E_ref|   for molecules with |E_ref| >= kappa S,
+    |dE| / S         for the flagged ones (|E_ref| < kappa S),
+S = sum_i |E_i,ref| (the molecule's gross atomic energy).  Flagged molecules
+are counted and reported.
+* BF16 / FP16 networks (three split-operand products per forward layer):
+  |dE|/|E| <= 2e-3 with kappa = 1e-3, RMS(dF) / RMS(F_ref) <= 1e-2.
+* FP32 networks: |dE|/|E| <= 1e-5, max |dF| <= 1e-4 RMS(F_ref), with
+  kappa = 0.1.  With kappa = 1e-3 the rule cannot be met by FP32 arithmetic
+  at all on these random-weight networks: correctly rounded FP32 products
+  leave |dE| up to 3.5e-7 S on the 512-molecule batch, which exceeds
+  1e-5 |E| wherever |E| < 0.035 S (19 of its molecules; the worst,
+  |E| = 1.2e-3 S, reaches 1e-4 |E|).  tests/test_precision_reading.py pins this
+  with an emulation of exact FP32 and BF16 arithmetic on the oracle's
+  features.  kappa = 0.1 is the smallest round value above that conditioning.
+* Single-product 16-bit networks (single_pass = 1, not the default): the
+  weight rounding moves every atom of an element the same way, so the energy
+  error grows with S rather than with |E|: |dE| / S <= 2e-2 (BF16) and 3e-3
+  (FP16) are what the arithmetic gives (measured up to 1.2e-2 and 1.1e-3);
+  the relative rule is not met and is not claimed for them.
 """
 import numpy as np
 
 import oracle
 
-TOL = {"fp32": {"e": 1e-5, "f_max": 1e-4}, "bf16": {"e": 6e-3, "f_rms": 1e-2},
-       "fp16": {"e": 2e-3, "f_rms": 1e-2}}
+TOL = {"fp32": {"e": 1e-5, "kappa": 0.1, "f_max": 1e-4},
+       "bf16": {"e": 2e-3, "kappa": 1e-3, "f_rms": 1e-2},
+       "fp16": {"e": 2e-3, "kappa": 1e-3, "f_rms": 1e-2},
+       # single product per forward layer: gated on |dE| / S (kappa = inf)
+       "bf16-single": {"e": 2e-2, "kappa": np.inf, "f_rms": 1e-2},
+       "fp16-single": {"e": 3e-3, "kappa": np.inf, "f_rms": 1e-2}}
+
+
+def split_mode(prec):
+    """(precision name for the binding, single_pass flag) of a test mode."""
+    return (prec[:-7], True) if prec.endswith("-single") else (prec, False)
 
 
 def oracle_batch(b, w, M, mols=None, aev=False):
@@ -35,14 +52,32 @@ def oracle_batch(b, w, M, mols=None, aev=False):
     return out
 
 
-def energy_error(E, ref):
-    """|dE| / S with S the gross atomic energy sum_i |E_i,ref|."""
+def oracle_whole_batch(b, w, M):
+    """The same per-molecule dicts from one oracle call over the whole batch
+    (the oracle spreads molecules over the host cores)."""
+    r = oracle.compute(b.Z, b.pos, b.mol_off, w, M, box=b.box, atom_energies=True)
+    out = {}
+    for m in range(b.n_mols):
+        a0, a1 = int(b.mol_off[m]), int(b.mol_off[m + 1])
+        out[m] = {"energy": r["energy"][m:m + 1], "forces": r["forces"][a0:a1],
+                  "atom_energies": r["atom_energies"][a0:a1]}
+    return out
+
+
+def energy_error(E, ref, kappa):
+    """(error, flagged): |dE| / |E_ref|, or |dE| / S for a molecule flagged
+    near zero (|E_ref| < kappa S)."""
+    s = float(np.sum(np.abs(ref["atom_energies"])))
+    e_ref = float(ref["energy"][0])
+    flagged = abs(e_ref) < kappa * s
+    denom = s if flagged else abs(e_ref)
+    return abs(E - e_ref) / max(denom, 1e-300), flagged
+
+
+def energy_error_gross(E, ref):
+    """|dE| / S, reported alongside."""
     s = np.sum(np.abs(ref["atom_energies"]))
     return abs(E - ref["energy"][0]) / max(s, 1e-300)
-
-
-def energy_error_plain(E, ref):
-    return abs(E - ref["energy"][0]) / max(abs(ref["energy"][0]), 1e-300)
 
 
 def force_errors(F, Fref):
@@ -55,18 +90,23 @@ def force_errors(F, Fref):
 
 def check_batch(prec, E, F, b, refs):
     """Asserts the tolerances of `prec` on every molecule in refs; returns the
-    worst errors (reported by the caller)."""
+    worst errors and the number of flagged molecules (reported by the caller)."""
     tol = TOL[prec]
-    worst = {"e": 0.0, "e_plain": 0.0, "f_max": 0.0, "f_rms": 0.0}
+    worst = {"e": 0.0, "e_gross": 0.0, "f_max": 0.0, "f_rms": 0.0, "flagged": 0, "molecules": 0}
     for m, ref in refs.items():
         a0, a1 = int(b.mol_off[m]), int(b.mol_off[m + 1])
-        ee = energy_error(E[m], ref)
-        worst["e_plain"] = max(worst["e_plain"], energy_error_plain(E[m], ref))
+        if a1 == a0:
+            continue
+        ee, flagged = energy_error(E[m], ref, tol["kappa"])
+        worst["flagged"] += int(flagged)
+        worst["molecules"] += 1
+        worst["e_gross"] = max(worst["e_gross"], energy_error_gross(E[m], ref))
         fm, fr = force_errors(F[a0:a1], ref["forces"]) if F is not None else (0.0, 0.0)
         worst["e"] = max(worst["e"], ee)
         worst["f_max"] = max(worst["f_max"], fm)
         worst["f_rms"] = max(worst["f_rms"], fr)
-        assert ee <= tol["e"], f"{prec} molecule {m}: energy error {ee:.3e} > {tol['e']}"
+        what = "|dE|/S" if flagged else "|dE|/|E|"
+        assert ee <= tol["e"], f"{prec} molecule {m}: energy error {what} = {ee:.3e} > {tol['e']}"
         if "f_max" in tol:
             assert fm <= tol["f_max"], f"{prec} molecule {m}: max force error {fm:.3e}"
         if "f_rms" in tol:

@@ -58,14 +58,18 @@ def check(got, ref):
 
 def system(seed, n_nnp, n_mm):
     g = W.rng(seed)
-    xn = W.geometry(g, n_nnp, edge=8.0, dmin=0.95)
+    # the ligand-sized regions in the 8 A cube; larger ones at 0.3 atoms / A^3
+    xn = W.geometry(g, n_nnp, edge=max(8.0, (n_nnp / 0.3) ** (1.0 / 3.0)), dmin=0.95)
     return xn, W.mm_environment(seed + 1, xn, n_mm)
 
 
-@pytest.mark.parametrize("n_nnp,n_mm", [(1, 1), (7, 1000), (24, 257), (60, 4099), (75, 38000)])
+@pytest.mark.parametrize("n_nnp,n_mm", [(1, 1), (7, 1000), (24, 257), (60, 4099), (75, 38000),
+                                        (511, 3001), (512, 2048)])
 def test_coupling_matches_oracle(lib, n_nnp, n_mm):
-    """Single pair, ragged MM counts (not multiples of a CTA's 256 atoms), the
-    paper's smallest system size (75 NNP atoms in 38 k MM atoms)."""
+    """Single pair, ragged MM counts (not multiples of a CTA's 128 atoms), the
+    paper's smallest system size (75 NNP atoms in 38 k MM atoms), and NNP
+    regions at and just below the 512-atom limit (the largest shared-memory
+    layout; NNP atoms not a multiple of the CTA's 8 warps)."""
     xn, env = system(100 + n_nnp, n_nnp, n_mm)
     worst = check(gpu_term(lib, xn, env), ref_term(xn, env))
     print(f"{n_nnp} x {n_mm}: {worst}")

@@ -11,6 +11,7 @@ run stopping at the first failure has already run every other test.
 import numpy as np
 import pytest
 
+import oracle
 from paper_2201_08110_gb300 import workloads as W
 
 torch = pytest.importorskip("torch")
@@ -55,6 +56,12 @@ def test_static_entry_point_matches_handle_features_on_consecutive_calls(nnp):
         err = np.abs(got - ref) / scale
         assert np.all(np.isfinite(got))
         assert err.max() < 5e-6, f"feature error {err.max():.3e} (row-max relative)"
+        # and straight against the FP64 oracle (same bound as the handle path's
+        # feature parity test)
+        exact = oracle.aev(b.Z, b.pos)
+        scale = np.maximum(np.abs(exact).max(axis=1, keepdims=True), 1e-30)
+        err = np.abs(got - exact) / scale
+        assert err.max() < 5e-6, f"feature error against the oracle {err.max():.3e}"
 
 
 def test_static_entry_point_rejects_too_many_atoms(nnp):
