@@ -5,15 +5,21 @@ One step = one energy + force evaluation of a whole batch (neighbour lists,
 features, the 8-network ensemble forward and reverse, the featurizer's reverse
 pass to coordinates), i.e. every stage of the path.  Default workload: 512
 molecules with 20-120 atoms (H .45, C .35, N .08, O .08, F/S/Cl .04), random
-Xavier-normal ANI-2x-architecture weights, network products in FP16 (the
-16-bit format that meets the stated error bounds; BF16 is timed alongside),
+Xavier-normal ANI-2x-architecture weights, network products in BF16 on the
+tensor cores (three split-operand products per forward layer, the form that
+meets the stated per-molecule energy bound; FP16 is timed alongside),
 replayed as one CUDA graph per step.  An atom-eval is one atom's share of E
 and F for the full ensemble.
 
-Also reported: the plain FP32 unbatched GPU path on a sample of the same
-molecules (one molecule per call, direct launches), the end-to-end number
-through the host-buffer entry point, per-stage times with the roofline of the
-dominant stage, and the FP64 CPU oracle on the host cores.
+Also reported in the same line: the same batch with FP32 networks (batched,
+graph) and with single-product 16-bit networks; the plain FP32 unbatched GPU
+path on a sample of the same molecules (one molecule per call, direct
+launches); the per-molecule errors of every precision against the FP64 oracle
+over the whole batch; the end-to-end number through the host-buffer entry
+point; per-stage times with their rooflines; the 4096-molecule workload with
+its 1500-atom periodic pocket and its device memory; the 60-atom molecule over
+1000 perturbed steps; the NNP-MM coupling term; and the FP64 CPU oracle on all
+host cores and on one.
 
 Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 """
@@ -23,6 +29,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -47,16 +54,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp16", choices=["fp32", "bf16", "fp16"],
-                    help="arithmetic of the networks' matrix products (FP16 meets the stated "
-                         "2e-3 energy / 1e-2 force bounds; single-pass BF16 does not on every "
-                         "molecule: its weight rounding errors add coherently)")
-    ap.add_argument("--alt-precision", default="bf16", choices=["none", "fp32", "bf16", "fp16"],
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16"],
+                    help="arithmetic of the networks' matrix products (16-bit: three split-operand "
+                         "products per forward layer unless --single-pass)")
+    ap.add_argument("--single-pass", action="store_true",
+                    help="16-bit networks with one product per forward layer (faster; misses the "
+                         "per-molecule relative energy bound where atomic energies cancel)")
+    ap.add_argument("--alt-precision", default="fp16", choices=["none", "fp32", "bf16", "fp16"],
                     help="a second precision timed the same way and reported alongside")
     ap.add_argument("--workload", type=int, default=3, choices=[2, 3, 5],
-                    help="3: the 512-molecule batch (default, headline); 2: one 60-atom "
-                         "molecule on the plain FP32 path over perturbed coordinates; 5: 4096 "
-                         "molecules of 30-250 atoms plus a 1500-atom periodic pocket")
+                    help="3: the 512-molecule batch (default, headline, with every other "
+                         "measurement in the same line); 2: one 60-atom molecule over perturbed "
+                         "coordinates; 5: 4096 molecules of 30-250 atoms plus a 1500-atom "
+                         "periodic pocket")
     ap.add_argument("--w2-fast", action="store_true",
                     help="workload 2 on the --precision tensor-core path with graph replay "
                          "instead of the plain FP32 path")
@@ -65,6 +75,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-coupling", action="store_true",
                     help="skip the NNP-MM coupling term's measurement")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline only: skip the FP32 / single-pass batches, the error report, "
+                         "workloads 2 and 5 and the MD loop")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default schedule instead of nnp_autotune's choice")
     ap.add_argument("--schedule", default=None,
@@ -90,6 +103,24 @@ def rank_batch(n_mols: int, rank: int):
     sizes = np.random.Generator(np.random.PCG64(W.workload_seed(3) + 100 + rank)).integers(
         20, 121, size=n_mols)
     return W.batch(W.workload_seed(3) + 7919 * rank, sizes), w, M
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
 
 
 class Clocks:
@@ -153,40 +184,101 @@ def peaks():
     return 6800.0, 1900.0, 1700.0, "fallback", 2070.0
 
 
-# Algorithmic work per stage: operations per unit of work, times the units.
+
+
+# Algorithmic work per stage: operations (or bytes) per unit of work, times the units.
 HID = W.HIDDEN
 # FP32 operations of the featurizer per directed radial pair / unordered
 # angular pair of neighbours (exp2 and log2 counted as one operation each).
 FLOP_RADIAL_FWD, FLOP_ANGULAR_FWD = 100.0, 142.0
 FLOP_RADIAL_REV, FLOP_ANGULAR_REV = 137.0, 300.0
 FLOP_DISTANCE = 8.0  # one neighbour-search distance test
+N_FEATURES = 1008
 
 
-def stage_work(Z, M: int, n_pairs: float, n_triples: float, n_tests: float):
-    """{stage: (bound, algorithmic work)}: FLOPs of the matrix products from the
-    element counts (first-layer K = the 1008 real features), FP32 operations
-    of the featurizer from the pair / triple counts."""
+def stage_work(Z, M: int, n_pairs: float, n_triples: float, n_tests: float, prec: str,
+               split: bool):
+    """{stage: (bound, algorithmic work, work executed, hbm bytes)}.
+
+    Tensor stages: FLOPs of the method's matrix products from the element
+    counts (first-layer K = the 1008 real features); "executed" counts the
+    products the kernels issue (three per forward product with split operands;
+    the split path's reverse kernel also recomputes its single-product forward).
+    Featurizer stages: FP32 operations from the pair / triple counts, and the
+    bytes the method must move per atom: the feature row as stored (FP32, or
+    16-bit hi and lo halves) and its position (featurizer), dE/dG in FP32, the
+    position and the FP64 force (reverse pass)."""
     zs = list(W.ELEMENTS_Z)
     cnt = [int(np.sum(Z == z)) for z in zs]
+    n = float(sum(cnt))
     l1 = l2 = l3 = out = 0.0
-    for e, n in enumerate(cnt):
+    for e, k in enumerate(cnt):
         h1, h2, h3 = HID[e]
-        l1 += 2.0 * n * M * h1 * 1008
-        l2 += 2.0 * n * M * h1 * h2
-        l3 += 2.0 * n * M * h2 * h3
-        out += 2.0 * n * M * h3
-    return {
-        "neighbors": ("alu", n_tests * FLOP_DISTANCE),
-        "features": ("alu", n_pairs * FLOP_RADIAL_FWD + n_triples * FLOP_ANGULAR_FWD),
-        "l1_fwd": ("tensor", l1),
-        # on the tensor-core path the l2_fwd stage is the fused tail: both
-        # hidden layers forward, the output layer and both hidden layers reverse
-        "tail": ("tensor", 2 * l2 + 2 * l3 + out),
-        "l2_fwd": ("tensor", l2), "l3_fwd": ("tensor", l3 + out), "l3_rev": ("tensor", l3),
-        "l2_rev": ("tensor", l2),
-        "l1_rev": ("tensor", l1),
-        "adjoint": ("alu", n_pairs * FLOP_RADIAL_REV + n_triples * FLOP_ANGULAR_REV),
+        l1 += 2.0 * k * M * h1 * N_FEATURES
+        l2 += 2.0 * k * M * h1 * h2
+        l3 += 2.0 * k * M * h2 * h3
+        out += 2.0 * k * M * h3
+    f = 3.0 if split else 1.0
+    feat_bytes = {"fp32": 4.0, "bf16": 2.0, "fp16": 2.0}[prec] * (2.0 if split else 1.0)
+    work = {
+        "neighbors": ("alu", n_tests * FLOP_DISTANCE, None, None),
+        "features": ("alu", n_pairs * FLOP_RADIAL_FWD + n_triples * FLOP_ANGULAR_FWD, None,
+                     n * (N_FEATURES * feat_bytes + 16.0)),
+        "l1_fwd": ("tensor", l1, f * l1, None),
+        "l1_rev": ("tensor", l1, l1, None),
+        "adjoint": ("alu", n_pairs * FLOP_RADIAL_REV + n_triples * FLOP_ANGULAR_REV, None,
+                    n * (N_FEATURES * 4.0 + 16.0 + 24.0)),
     }
+    if prec == "fp32":
+        work.update({"l2_fwd": ("tensor", l2, l2, None), "l3_fwd": ("tensor", l3 + out, l3 + out, None),
+                     "l3_rev": ("tensor", l3, l3, None), "l2_rev": ("tensor", l2, l2, None)})
+    elif split:
+        work.update({"l2_fwd": ("tensor", l2, 3 * l2, None), "l3_fwd": ("tensor", l3 + out, 3 * l3 + out, None),
+                     # the reverse tail: both hidden layers reverse, after its own forward
+                     "tail_rev": ("tensor", l2 + l3, 2 * l2 + 2 * l3 + out, None)})
+    else:
+        # the fused tail: both hidden layers forward, the output layer and both reverse
+        work["tail"] = ("tensor", 2 * l2 + 2 * l3 + out, 2 * l2 + 2 * l3 + out, None)
+    return work
+
+
+def shown_stages(stages: dict, prec: str, split: bool) -> dict:
+    """Stage times under the names of the kernels that ran (nnp_compute_timed's
+    slots: the fused tail in l2_fwd; with split operands the reverse tail in l3_rev)."""
+    if prec == "fp32":
+        return dict(stages)
+    out = {k: v for k, v in stages.items() if k not in ("l2_fwd", "l3_fwd", "l3_rev", "l2_rev")}
+    if split:
+        out["l2_fwd"], out["l3_fwd"], out["tail_rev"] = stages["l2_fwd"], stages["l3_fwd"], stages["l3_rev"]
+    else:
+        out["tail"] = stages["l2_fwd"]
+    return out
+
+
+def rooflines_of(shown: dict, work: dict, tensor_path: bool, hbm: float, bf16: float,
+                 peak_kind: str, fp32_peak: float) -> dict:
+    out = {}
+    for k, ms in shown.items():
+        if k not in work or ms <= 0:
+            continue
+        bound, amount, executed, nbytes = work[k]
+        if bound == "tensor" and tensor_path:
+            peak, unit, note = bf16, "TFLOP/s", f"{peak_kind} dense bf16 (fp16 equal rate)"
+        else:
+            bound = "alu"
+            peak, unit, note = fp32_peak, "TFLOP/s", "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 x max SM clock"
+        achieved = amount / (ms * 1e-3) / 1e12
+        r = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+             "frac": achieved / peak, "work": amount, "ms": ms, "peak_note": note}
+        if executed is not None and executed != amount:
+            r["executed_work"] = executed
+            r["executed_frac"] = executed / (ms * 1e-3) / 1e12 / peak
+        if nbytes is not None:
+            gbs = nbytes / (ms * 1e-3) / 1e9
+            r["hbm"] = {"bytes": nbytes, "achieved_gbs": gbs, "peak_gbs": hbm,
+                        "frac": gbs / hbm, "peak_note": f"{peak_kind} copy bandwidth"}
+        out[k] = r
+    return out
 
 
 def src_hash(*names):
@@ -198,7 +290,8 @@ def src_hash(*names):
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
 # kernel, keyed by the kernel's source hash at capture time, in bytes per atom;
-# scaled to the bench workload by atoms.
+# scaled to the bench workload by atoms.  A kernel changed since its capture
+# finds no entry and reports null.
 NCU_TRAFFIC = {
     ("adjoint", "1dd06ca99192"): 4604.8,  # ncu --set full, 512-molecule batch, FP16
     ("features", "1dd06ca99192"): 807.2,  # ncu --set full, 512-molecule batch, FP16
@@ -206,26 +299,69 @@ NCU_TRAFFIC = {
 }
 
 
-def cpu_oracle_rate(b, w, M, target_s: float = 12.0):
-    """The FP64 oracle as it stands, on all host cores, over a bounded sample
-    of the batch's molecules (atom-evals/s, sample description, cores)."""
+# ------------------------------------------------------------ the oracle ----
+
+def oracle_refs(b, w, M, nthreads: int = 0):
+    """Per-molecule oracle results (energy, forces, atomic energies) from one
+    call over the whole batch, and the call's wall time."""
     import oracle
-    cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    n_done = 0
-    atoms = 0
-    m = 0
-    chunk = max(1, cores)
-    while time.perf_counter() - t0 < target_s and m < b.n_mols:
-        hi = min(b.n_mols, m + chunk)
-        sub_off = b.mol_off[m:hi + 1] - b.mol_off[m]
-        a0, a1 = int(b.mol_off[m]), int(b.mol_off[hi])
-        oracle.compute(b.Z[a0:a1], b.pos[a0:a1], sub_off, w, M, nthreads=cores)
-        atoms += a1 - a0
-        n_done += hi - m
-        m = hi
+    r = oracle.compute(b.Z, b.pos, b.mol_off, w, M, box=b.box, atom_energies=True, nthreads=nthreads)
     dt = time.perf_counter() - t0
-    return atoms / dt, f"first {n_done} molecules ({atoms} atoms) of the batch, {dt:.1f} s", cores
+    refs = {}
+    for m in range(b.n_mols):
+        a0, a1 = int(b.mol_off[m]), int(b.mol_off[m + 1])
+        refs[m] = (float(r["energy"][m]), r["forces"][a0:a1], r["atom_energies"][a0:a1])
+    return refs, dt
+
+
+def oracle_single_thread(b, w, M, target_s: float = 3.0):
+    """The oracle on one host thread over the batch's first molecules, until
+    target_s has passed: (atom-evals/s, sample)."""
+    import oracle
+    t0 = time.perf_counter()
+    atoms = mols = 0
+    while time.perf_counter() - t0 < target_s and mols < b.n_mols:
+        sub = b.molecule(mols)
+        oracle.compute(sub.Z, sub.pos, sub.mol_off, w, M, nthreads=1)
+        atoms += sub.n_atoms
+        mols += 1
+    dt = time.perf_counter() - t0
+    return atoms / dt, f"first {mols} molecules ({atoms} atoms) of the batch, one thread, {dt:.1f} s"
+
+
+# Energy rule per molecule (the parity tests' rule): |dE| / |E_ref|, or
+# |dE| / S (S = sum_i |E_i,ref|) for molecules flagged near zero, |E_ref| < kappa S.
+ERROR_RULE = {"fp32": (1e-5, 0.1, "max"), "bf16": (2e-3, 1e-3, "rms"), "fp16": (2e-3, 1e-3, "rms")}
+
+
+def error_stats(E, F, b, refs, prec: str) -> dict:
+    tol, kappa_used, ftype = ERROR_RULE[prec]  # single-product modes: the same rule, reported
+    a5, gross, fmax, frms, flagged, fails = [], [], [], [], 0, 0
+    for m in range(b.n_mols):
+        a0, a1 = int(b.mol_off[m]), int(b.mol_off[m + 1])
+        if a1 == a0:
+            continue
+        e_ref, f_ref, ea = refs[m]
+        s = float(np.abs(ea).sum())
+        de = abs(float(E[m]) - e_ref)
+        flag = abs(e_ref) < kappa_used * s
+        flagged += int(flag)
+        err = de / (s if flag else abs(e_ref))
+        a5.append(err)
+        gross.append(de / s)
+        fails += int(err > tol)
+        rms = float(np.sqrt(np.mean(f_ref ** 2)))
+        d = F[a0:a1] - f_ref
+        fmax.append(float(np.abs(d).max()) / rms)
+        frms.append(float(np.sqrt(np.mean(d ** 2))) / rms)
+    return {"molecules": len(a5), "energy_rule": f"|dE|/|E| <= {tol:g} (|dE|/S for |E| < {kappa_used:g} S)",
+            "flagged": flagged, "failing": fails,
+            "worst_rel_energy": max(a5), "median_rel_energy": float(np.median(a5)),
+            "worst_dE_over_S": max(gross), "worst_max_force_over_rms": max(fmax),
+            "worst_rms_force_over_rms": max(frms),
+            "force_rule": ("max |dF| <= 1e-4 RMS(F)" if ftype == "max" else "RMS(dF) <= 1e-2 RMS(F)"),
+            "force_failing": int(sum(x > 1e-4 for x in fmax) if ftype == "max" else sum(x > 1e-2 for x in frms))}
 
 
 # FP32 arithmetic of one NNP-MM pair of the coupling term (FMA = 2 FLOP):
@@ -281,7 +417,7 @@ def measure_coupling(steps: int, flush, stream, fp32_peak: float, with_oracle: b
     return out
 
 
-# ------------------------------------------------------------------ arms ----
+# ------------------------------------------------------- the reference arm ----
 
 def run_reference(args):
     """The oracle (FP64 C, OpenMP over molecules) timed on the host cores."""
@@ -347,6 +483,10 @@ def sum_over_ranks(x: float, dist) -> float:
     return float(t.item())
 
 
+
+
+# ------------------------------------------------------- measurement parts ----
+
 def timed_steps(model, pos, E, F, steps: int, flush, stream):
     """Sum of per-step CUDA-event times (ms); the L2 flush between steps is
     outside the events."""
@@ -361,6 +501,175 @@ def timed_steps(model, pos, E, F, steps: int, flush, stream):
     torch.cuda.synchronize()
     return sum(a.elapsed_time(b) for a, b in zip(starts, ends))
 
+
+def make_model(nnp, b, w, M, prec, single, pos, E, F, args, schedules, key):
+    """A graph-replay handle for the batch, tuned (or pinned) and warmed up."""
+    import torch
+    m = nnp.NNP(b.Z, w, M, mol_off=b.mol_off, precision=prec, single_pass=single, box=b.box,
+                use_graph=True)
+    if args.schedule:
+        vals = [int(v) for v in args.schedule.split(",")]
+        schedules[key] = dict(zip(nnp.NNP.SCHEDULE_KEYS, vals))
+        m.set_schedule(schedules[key])
+    elif not args.no_autotune:
+        schedules[key] = m.autotune(pos)
+    for _ in range(max(3, args.warmup)):
+        m.compute(pos, E, F)
+    torch.cuda.synchronize()
+    m.status()
+    return m
+
+
+def workload5_measurement(nnp, prec, steps: int, warmup: int, flush, stream):
+    """4096 molecules (30-250 atoms, log-uniform) plus the 1500-atom periodic
+    pocket, BF16 networks, features kept only for the forward pass
+    (recompute_aev): ms per step, atom-evals/s and the device memory of the two
+    handles (free memory before and after creating them)."""
+    import torch
+    batch, pocket, w, M = W.config5()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    hb = nnp.NNP(batch.Z, w, M, mol_off=batch.mol_off, precision=prec, use_graph=True,
+                 recompute_aev=True)
+    hp = nnp.NNP(pocket.Z, w, M, precision=prec, box=pocket.box, use_graph=True, recompute_aev=True)
+    pb = torch.tensor(batch.pos, device="cuda")
+    pp = torch.tensor(pocket.pos, device="cuda")
+    Eb = torch.empty(batch.n_mols, dtype=torch.float64, device="cuda")
+    Fb = torch.empty(batch.n_atoms, 3, dtype=torch.float64, device="cuda")
+    Ep = torch.empty(1, dtype=torch.float64, device="cuda")
+    Fp = torch.empty(pocket.n_atoms, 3, dtype=torch.float64, device="cuda")
+    for _ in range(max(3, warmup)):
+        hb.compute(pb, Eb, Fb)
+        hp.compute(pp, Ep, Fp)
+    torch.cuda.synchronize()
+    hb.status()
+    hp.status()
+    footprint = free0 - torch.cuda.mem_get_info()[0]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record(stream)
+        hb.compute(pb, Eb, Fb)
+        hp.compute(pp, Ep, Fp)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    hb.status()
+    hp.status()
+    ms = sum(a.elapsed_time(b2) for a, b2 in zip(starts, ends)) / steps
+    n = batch.n_atoms + pocket.n_atoms
+    stages_b = hb.compute_timed(pb, Eb, Fb)
+    stages_p = hp.compute_timed(pp, Ep, Fp)
+    out = {"workload": "4096 molecules, 30-250 atoms (log-uniform), plus a 1500-atom periodic pocket "
+                       "(24.7 A cube, cell list); 8 networks; features kept only for the forward "
+                       "pass (recompute_aev)",
+           "precision": prec, "n_atoms": n, "steps": steps, "ms_per_step": ms,
+           "value": n / (ms * 1e-3), "unit": UNIT,
+           "device_bytes": int(footprint),
+           "device_bytes_note": "device memory taken by the two handles and their outputs "
+                                "(free memory before and after), which is the peak: a step "
+                                "allocates nothing",
+           "stages_ms_batch": stages_b, "stages_ms_pocket": stages_p,
+           "gpu_launches_per_step": hb.kernels_per_step(True) + hp.kernels_per_step(True)}
+    hb.close()
+    hp.close()
+    return out
+
+
+def workload2_measurement(nnp, prec, steps: int, warmup: int):
+    """One 60-atom molecule, 8 networks, new coordinates every step (independent
+    N(0, 0.01^2) A perturbations, drawn beforehand and resident on the device):
+    the plain FP32 path with direct launches, and the 16-bit tensor-core path
+    replayed as one CUDA graph per step (the single-ligand MD case the paper
+    times)."""
+    import torch
+    b, w, M = W.config2()
+    g = W.rng(W.workload_seed(2) + 50)
+    P = torch.tensor(np.stack([W.perturb(g, b.pos) for _ in range(steps + warmup)]), device="cuda")
+    out = {"workload": "one 60-atom molecule (H27 C21 N5 O4 F S Cl), 8 networks, new coordinates "
+                       "each step (N(0, 0.01^2) A perturbations)", "steps": steps}
+    for key, p, graph in (("plain_fp32", "fp32", False), ("tensor_graph", prec, True)):
+        model = nnp.NNP(b.Z, w, M, precision=p, use_graph=graph)
+        pos = torch.empty(b.n_atoms, 3, dtype=torch.float32, device="cuda")
+        E = torch.empty(1, dtype=torch.float64, device="cuda")
+        F = torch.empty(b.n_atoms, 3, dtype=torch.float64, device="cuda")
+        for k in range(warmup):
+            pos.copy_(P[k])
+            model.compute(pos, E, F)
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        for k in range(steps):
+            pos.copy_(P[warmup + k])
+            model.compute(pos, E, F)
+        s1.record()
+        torch.cuda.synchronize()
+        model.status()
+        ms = s0.elapsed_time(s1) / steps
+        out[key] = {"precision": p, "graph": graph, "ms_per_step": ms,
+                    "value": b.n_atoms / (ms * 1e-3), "unit": UNIT,
+                    "gpu_launches_per_step": model.kernels_per_step(True)}
+        model.close()
+    return out
+
+
+def md_measurement(nnp, prec, steps: int, warmup: int):
+    """The replica MD loop (Langevin BAOAB, normal draws resident on the
+    device) of the 60-atom workload-2 molecule in its 60,000-atom water-like
+    environment (the coupling term with the MM atoms held), 1 and 8 replicas,
+    with the coupling term after the NNP term on one stream and on a second
+    stream beside it: ms and steps per second (each run also evaluates the
+    forces once at its starting positions), and the time the concurrent
+    stream saves."""
+    import torch
+    b, env = W.coupling_config()
+    _, w, M = W.config2()
+    mass = {1: 1.008, 6: 12.011, 7: 14.007, 8: 15.999, 9: 18.998, 16: 32.06, 17: 35.45}
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+    out = {"workload": "the 60-atom molecule of workload 2 in 60,000 fixed water-like MM atoms "
+                       "(coupling term of Eq. 4), Langevin BAOAB, one CUDA graph replay per step",
+           "precision": prec, "steps": steps}
+    for R in (1, 8):
+        Z = np.tile(b.Z, R)
+        pos = np.tile(b.pos, (R, 1))
+        off = np.arange(R + 1, dtype=np.int32) * b.n_atoms
+        model = nnp.NNP(Z, w, M, mol_off=off, precision=prec)
+
+        class Env:
+            pass
+        e = Env()
+        e.nnp_q, e.nnp_sigma, e.nnp_eps = dev(np.tile(env.nnp_q, R)), dev(np.tile(env.nnp_sigma, R)), \
+            dev(np.tile(env.nnp_eps, R))
+        e.mm_pos, e.mm_q, e.mm_sigma, e.mm_eps = dev(env.mm_pos), dev(env.mm_q), dev(env.mm_sigma), \
+            dev(env.mm_eps)
+        masses = np.array([mass[int(z)] for z in Z])
+        noise = torch.randn(steps, R * b.n_atoms, 3, dtype=torch.float64, device="cuda")
+        r = {"replicas": R, "atoms": R * b.n_atoms}
+        for conc in (False, True):
+            md = nnp.MD(model, masses, 0.5, integrator="baoab", gamma=0.01, kT=0.6, env=e,
+                        coulomb_k=W.COULOMB_KCAL, concurrent=conc)
+            x0 = torch.tensor(pos.astype(np.float64), device="cuda")
+            x, v = x0.clone(), torch.zeros_like(x0)
+            md.run(x, v, steps, noise=noise)  # captures the step graph for these buffers
+            torch.cuda.synchronize()
+            x.copy_(x0)
+            v.zero_()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            md.run(x, v, steps, noise=noise)
+            s1.record()
+            torch.cuda.synchronize()
+            model.status()
+            ms = s0.elapsed_time(s1) / steps
+            r["concurrent" if conc else "serial"] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms}
+            md.close()
+        r["overlap_saved_ms_per_step"] = r["serial"]["ms_per_step"] - r["concurrent"]["ms_per_step"]
+        out[f"replicas_{R}"] = r
+        model.close()
+    return out
+
+
+# ------------------------------------------------------------------ arms ----
 
 def run_ours(args):
     import torch
@@ -377,13 +686,22 @@ def run_ours(args):
         dist.barrier()
 
     b, w, M = rank_batch(args.molecules, rank)
-    # CPU baseline first (no CUDA work in flight; the oracle uses its own threads)
-    cpu = None
+    single = bool(args.single_pass) and args.precision != "fp32"
+    extras = rank == 0 and world == 1 and not args.no_extras
+    # the FP64 oracle over the whole batch first (no CUDA work in flight; it uses
+    # its own threads): the CPU baseline on all host cores and the reference
+    # values of the error report
+    cpu = refs = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        rate, sample, cores = cpu_oracle_rate(b, w, M)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        refs, dt = oracle_refs(b, w, M)
+        cores = os.cpu_count() or 1
+        cpu = {"value": b.n_atoms / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"all {b.n_mols} molecules ({b.n_atoms} atoms) of the batch, {dt:.1f} s",
+               "cpu_model": cpu_model()}
+        rate1, sample1 = oracle_single_thread(b, w, M)
+        cpu["single_thread"] = {"value": rate1, "unit": UNIT, "cores": 1, "sample": sample1}
 
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -391,24 +709,9 @@ def run_ours(args):
     E = torch.empty(b.n_mols, dtype=torch.float64, device="cuda")
     F = torch.empty(b.n_atoms, 3, dtype=torch.float64, device="cuda")
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
-
     schedules = {}
 
-    def make(prec):
-        m = nnp.NNP(b.Z, w, M, mol_off=b.mol_off, precision=prec, use_graph=True)
-        if args.schedule:
-            vals = [int(v) for v in args.schedule.split(",")]
-            schedules[prec] = dict(zip(nnp.NNP.SCHEDULE_KEYS, vals))
-            m.set_schedule(schedules[prec])
-        elif not args.no_autotune:
-            schedules[prec] = m.autotune(pos)
-        for _ in range(max(3, args.warmup)):
-            m.compute(pos, E, F)
-        torch.cuda.synchronize()
-        m.status()
-        return m
-
-    model = make(args.precision)
+    model = make_model(nnp, b, w, M, args.precision, single, pos, E, F, args, schedules, "headline")
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -424,12 +727,20 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     value = atoms_all * args.steps / (total_ms / 1e3)
 
+    def other(prec, one_product, key):
+        m2 = make_model(nnp, b, w, M, prec, one_product, pos, E, F, args, schedules, key)
+        t = max_over_ranks(timed_steps(m2, pos, E, F, args.steps, flush, stream), dist)
+        return m2, {"precision": prec, "single_pass": one_product,
+                    "value": atoms_all * args.steps / (t / 1e3), "unit": UNIT,
+                    "ms_per_step": t / args.steps}
+
     alt = None
     if args.alt_precision not in ("none", args.precision):
-        m2 = make(args.alt_precision)
-        alt_ms = max_over_ranks(timed_steps(m2, pos, E, F, args.steps, flush, stream), dist)
-        alt = {"precision": args.alt_precision, "value": atoms_all * args.steps / (alt_ms / 1e3),
-               "unit": UNIT, "ms_per_step": alt_ms / args.steps}
+        m2, alt = other(args.alt_precision, single and args.alt_precision != "fp32", "alt")
+        if extras and refs is not None:
+            m2.compute(pos, E, F)
+            torch.cuda.synchronize()
+            alt["errors"] = error_stats(E.cpu().numpy(), F.cpu().numpy(), b, refs, args.alt_precision)
         m2.close()
 
     if rank != 0:
@@ -437,7 +748,16 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
+    # ---- errors of the timed configuration against the oracle, every molecule ----
+    errors = None
+    if refs is not None:
+        model.compute(pos, E, F)
+        torch.cuda.synchronize()
+        model.status()
+        errors = error_stats(E.cpu().numpy(), F.cpu().numpy(), b, refs, args.precision)
+
     # ---- per-stage times, algorithmic work and rooflines ----
+    split = args.precision != "fp32" and not single
     stage_runs = [model.compute_timed(pos, E, F) for _ in range(5)]
     stages = {k: statistics.median(r[k] for r in stage_runs) for k in stage_runs[0]}
     cr, _ = model.neighbors(0)
@@ -446,30 +766,16 @@ def run_ours(args):
     ca = ca.cpu().numpy().astype(np.float64)
     sizes = np.diff(b.mol_off).astype(np.float64)
     work = stage_work(b.Z, M, float(cr.sum()), float((ca * (ca - 1) / 2).sum()),
-                      float((sizes * (sizes - 1)).sum()))
+                      float((sizes * (sizes - 1)).sum()), args.precision, split)
     hbm, bf16, bf16_sus, peak_kind, sm_max = peaks()
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 lanes x 2 x max SM clock, TFLOP/s
     tensor_path = args.precision != "fp32"
-    shown = dict(stages)
-    if tensor_path:  # the fused tail runs in the l2_fwd slot
-        shown = {k: v for k, v in stages.items() if k not in ("l2_fwd", "l3_fwd", "l3_rev", "l2_rev")}
-        shown["tail"] = stages["l2_fwd"]
-    rooflines = {}
-    for k, ms in shown.items():
-        if k not in work or ms <= 0:
-            continue
-        bound, amount = work[k]
-        if bound == "tensor" and tensor_path:
-            peak, unit, note = bf16, "TFLOP/s", f"{peak_kind} dense bf16 (fp16 equal rate)"
-        else:
-            bound = "alu"
-            peak, unit, note = fp32_peak, "TFLOP/s", "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 x max SM clock"
-        achieved = amount / (ms * 1e-3) / 1e12
-        rooflines[k] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                        "frac": achieved / peak, "work": amount, "ms": ms, "peak_note": note}
+    shown = shown_stages(stages, args.precision, split)
+    rooflines = rooflines_of(shown, work, tensor_path, hbm, bf16, peak_kind, fp32_peak)
     dom = max(rooflines, key=lambda k: rooflines[k]["ms"])
     kernel_src = {"features": "aev.cu", "adjoint": "aev.cu", "neighbors": "aev.cu",
-                  "tail": "mlp_tail_tc.cu"}.get(dom, "mlp_tc.cu" if tensor_path else "mlp_simt.cu")
+                  "tail": "mlp_tail_tc.cu", "tail_rev": "mlp_tail_tc.cu"}.get(
+                      dom, "mlp_tc.cu" if tensor_path else "mlp_simt.cu")
     tr = NCU_TRAFFIC.get((dom, src_hash(kernel_src)))
     roof = dict(rooflines[dom])
     roof.update({"stage": dom, "traffic": None if tr is None else tr * b.n_atoms})
@@ -493,6 +799,24 @@ def run_ours(args):
     e2e = {"value": b.n_atoms * args.steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(hpos.numel() * 4),
            "d2h_bytes_per_step": int(hE.numel() * 8 + hF.numel() * 8)}
+    launches = model.kernels_per_step(True)
+    model.close()
+
+    # ---- the same batch in the other arithmetics: FP32 networks (batched,
+    # graph) and single-product 16-bit networks, each with its errors ----
+    others = {}
+    if extras:
+        for key, prec, one in (("fp32_batched", "fp32", False), ("bf16_single_pass", "bf16", True),
+                               ("fp16_single_pass", "fp16", True)):
+            if prec == args.precision and one == single:
+                continue
+            m2, r = other(prec, one, key)
+            if refs is not None:
+                m2.compute(pos, E, F)
+                torch.cuda.synchronize()
+                r["errors"] = error_stats(E.cpu().numpy(), F.cpu().numpy(), b, refs, prec)
+            m2.close()
+            others[key] = r
 
     # ---- the plain FP32 unbatched path on a sample of the same molecules ----
     unb = None
@@ -523,26 +847,41 @@ def run_ours(args):
                "sample": f"{len(ids)} molecules of the batch, one per call, FP32 networks, "
                          "direct launches", "ms_per_molecule": tot_ms / len(ids)}
 
+    mode = ("single-product" if single else "three split-operand products per forward layer") \
+        if args.precision != "fp32" else "SIMT FP32"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": f"{args.molecules} molecules, 20-120 atoms, 8-network ensemble "
-                                   f"(workload 3 batch; {args.precision} networks as workload 4)",
+                                   f"(workload 3 batch with {args.precision} networks, {mode}: "
+                                   "workload 4)",
                        "n_molecules": b.n_mols, "n_atoms_per_rank": b.n_atoms, "n_models": M,
-                       "precision": args.precision, "graph": True,
-                       "schedule": schedules.get(args.precision, "default"),
+                       "precision": args.precision, "forward_products": mode, "graph": True,
+                       "schedule": schedules.get("headline", "default"),
                        "l2": "flushed (256 MB write) between timed steps, outside the timed events",
                        "parallelism": f"replicas x{world}, no collective on the data path"},
             "roofline": roof, "rooflines": rooflines, "stages_ms": shown, "stage_share": stage_share,
-            "e2e": e2e, "gpu_launches": model.kernels_per_step(True) * args.steps,
-            "clocks": clocks}
+            "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": clocks}
+    if errors is not None:
+        line["errors"] = errors
     if alt is not None:
         line["alt_precision"] = alt
+    line.update(others)
     if unb is not None:
         line["fp32_unbatched"] = unb
         line["speedup_vs_fp32_unbatched"] = value / world / unb["value"]
+        if "fp32_batched" in others:
+            line["speedup_fp32_batched_vs_unbatched"] = others["fp32_batched"]["value"] / unb["value"]
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if extras:
+        for key, fn in (("workload5", lambda: workload5_measurement(nnp, args.precision, 5, 3, flush, stream)),
+                        ("workload2", lambda: workload2_measurement(nnp, args.precision, 1000, 10)),
+                        ("md", lambda: md_measurement(nnp, args.precision, 200, 10))):
+            try:
+                line[key] = fn()
+            except Exception as exc:  # reported in the line; the measurements above stand
+                line[key] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
     if not args.no_coupling:
         try:
             line["coupling"] = measure_coupling(max(args.steps, 10), flush, stream, fp32_peak,
@@ -556,105 +895,46 @@ def run_ours(args):
 
 
 def run_workload2(args):
-    """One 60-atom molecule, 8 networks, new coordinates every step (independent
-    N(0, 0.01^2) A perturbations): the plain FP32 path with direct launches,
-    or with --w2-fast the tensor-core path replayed as one CUDA graph (the
-    single-ligand MD case the paper times)."""
+    """Workload 2 alone: one 60-atom molecule over perturbed coordinates."""
     import torch
     from paper_2201_08110_gb300 import build, nnp
     build.build()
-    b, w, M = W.config2()
-    steps = args.steps
-    g = W.rng(W.workload_seed(2) + 50)
-    P = torch.tensor(np.stack([W.perturb(g, b.pos) for _ in range(steps + args.warmup)]),
-                     device="cuda")
-    prec = args.precision if args.w2_fast else "fp32"
-    model = nnp.NNP(b.Z, w, M, precision=prec, use_graph=bool(args.w2_fast))
-    pos = torch.empty(b.n_atoms, 3, dtype=torch.float32, device="cuda")
-    E = torch.empty(1, dtype=torch.float64, device="cuda")
-    F = torch.empty(b.n_atoms, 3, dtype=torch.float64, device="cuda")
-    for k in range(args.warmup):
-        pos.copy_(P[k])
-        model.compute(pos, E, F)
-    torch.cuda.synchronize()
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record()
-    for k in range(steps):
-        pos.copy_(P[args.warmup + k])
-        model.compute(pos, E, F)
-    s1.record()
-    torch.cuda.synchronize()
-    model.status()
-    ms = s0.elapsed_time(s1)
-    line = {"metric": METRIC, "value": b.n_atoms * steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-            "steps": steps, "warmup": args.warmup, "ms_per_step": ms / steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
-            "data": "synthetic",
-            "config": {"workload": "one 60-atom molecule (H27 C21 N5 O4 F S Cl), 8 networks, "
-                                   + ("tensor-core networks, one CUDA graph replay per step"
-                                      if args.w2_fast else "plain FP32 path, direct launches")
-                                   + ", new coordinates each step"},
-            "gpu_launches": model.kernels_per_step(True) * steps}
+    torch.cuda.set_device(0)
+    r = workload2_measurement(nnp, args.precision, args.steps, args.warmup)
+    key = "tensor_graph" if args.w2_fast else "plain_fp32"
+    b, _, _ = W.config2()
+    line = {"metric": METRIC, "value": r[key]["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r[key]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": r[key]["precision"], "data": "synthetic",
+            "config": {"workload": r["workload"] + (", tensor-core networks, one CUDA graph replay "
+                                                    "per step" if args.w2_fast else
+                                                    ", plain FP32 path, direct launches")},
+            "gpu_launches": r[key]["gpu_launches_per_step"] * args.steps, "workload2": r}
     print(json.dumps(line), flush=True)
     return 0
 
 
 def run_workload5(args):
-    """4096 molecules (30-250 atoms, log-uniform) plus one 1500-atom periodic
-    pocket; one step evaluates both; reports the handles' device memory."""
+    """Workload 5 alone: 4096 molecules plus the 1500-atom periodic pocket."""
     import torch
     from paper_2201_08110_gb300 import build, nnp
     build.build()
-    batch, pocket, w, M = W.config5()
+    torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    free0 = torch.cuda.mem_get_info()[0]
-    hb = nnp.NNP(batch.Z, w, M, mol_off=batch.mol_off, precision=args.precision, use_graph=True)
-    hp = nnp.NNP(pocket.Z, w, M, precision=args.precision, box=pocket.box, use_graph=True)
-    torch.cuda.synchronize()
-    footprint = free0 - torch.cuda.mem_get_info()[0]
-    pb = torch.tensor(batch.pos, device="cuda")
-    pp = torch.tensor(pocket.pos, device="cuda")
-    Eb = torch.empty(batch.n_mols, dtype=torch.float64, device="cuda")
-    Fb = torch.empty(batch.n_atoms, 3, dtype=torch.float64, device="cuda")
-    Ep = torch.empty(1, dtype=torch.float64, device="cuda")
-    Fp = torch.empty(pocket.n_atoms, 3, dtype=torch.float64, device="cuda")
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
-    for _ in range(max(3, args.warmup)):
-        hb.compute(pb, Eb, Fb)
-        hp.compute(pp, Ep, Fp)
-    torch.cuda.synchronize()
-    hb.status()
-    hp.status()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clk = Clocks(0)
     clk.start()
-    for k in range(args.steps):
-        flush.zero_()
-        starts[k].record(stream)
-        hb.compute(pb, Eb, Fb)
-        hp.compute(pp, Ep, Fp)
-        ends[k].record(stream)
-    torch.cuda.synchronize()
+    r = workload5_measurement(nnp, args.precision, args.steps, args.warmup, flush, stream)
     clocks = clk.stop()
-    hb.status()
-    hp.status()
-    ms = sum(a.elapsed_time(b2) for a, b2 in zip(starts, ends))
-    n = batch.n_atoms + pocket.n_atoms
-    stages_b = hb.compute_timed(pb, Eb, Fb)
-    stages_p = hp.compute_timed(pp, Ep, Fp)
-    line = {"metric": METRIC, "value": n * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": "4096 molecules, 30-250 atoms (log-uniform), plus a 1500-atom "
-                                   "periodic pocket (24.7 A cube); 8 networks",
-                       "n_atoms": n, "precision": args.precision, "graph": True},
-            "device_bytes": int(footprint), "stages_ms_batch": stages_b,
-            "stages_ms_pocket": stages_p,
-            "gpu_launches": (hb.kernels_per_step(True) + hp.kernels_per_step(True)) * args.steps,
-            "clocks": clocks}
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": r["workload"], "n_atoms": r["n_atoms"], "precision": args.precision,
+                       "graph": True},
+            "device_bytes": r["device_bytes"], "gpu_launches": r["gpu_launches_per_step"] * args.steps,
+            "clocks": clocks, "workload5": r}
     print(json.dumps(line), flush=True)
     return 0
 
