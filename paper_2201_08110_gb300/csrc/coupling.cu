@@ -18,26 +18,33 @@
 // needs one reciprocal square root and no division: with s6 = (sigma_ij / r)^6,
 //   V_LJ = (2 sqrt eps_i)(2 sqrt eps_j) s6 (s6 - 1),
 //   -dV/dr / r = (V_C + 4 eps_ij s6 (12 s6 - 6)) / r^2.
-// Pair arithmetic is FP32, and so are the sums inside a CTA (FP64 arithmetic
-// runs at a small fraction of the FP32 rate on this GPU): each NNP atom's
-// force is summed over its warp's lanes by shuffles and added to the caller's
-// FP64 buffer, one addition per CTA; each MM atom's force is summed over the
-// CTA's 8 warps in a fixed order through shared memory and added once (no
-// other CTA touches it); the energy is summed over each warp by shuffles and
-// over the CTA's warps in FP64, one addition per CTA.  Within a CTA the order
-// of every sum is fixed.
+// Pair arithmetic is FP32, and so are the sums inside a cluster (FP64
+// arithmetic runs at a small fraction of the FP32 rate on this GPU): each NNP
+// atom's force is summed over its warp's lanes by shuffles, then by the first
+// CTA of a thread-block cluster over the 8 CTAs' shared memory (distributed
+// shared memory, in CTA order), and added to the caller's FP64 buffer once
+// per cluster: every cluster adds into the same few cache lines, so fewer
+// additions there is what bounds the kernel's time.  Each MM atom's force is
+// summed over the CTA's 8 warps in a fixed order through shared memory and
+// added once (no other CTA touches it); the energy goes like the NNP forces.
+// Results differ between calls only by the order of the FP64 additions of the
+// clusters.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "../../include/nnp.h"
 
 namespace {
 
+namespace cg = cooperative_groups;
+
 constexpr int kCplWarps = 8;
 constexpr int kCplThreads = 32 * kCplWarps;
 constexpr int kCplJ = 4;                    // MM atoms per lane
 constexpr int kCplTile = 32 * kCplJ;        // MM atoms per CTA
+constexpr int kCplCluster = 8;              // CTAs per cluster (the grid is padded to a multiple)
 
-__global__ void __launch_bounds__(kCplThreads)
+__global__ void __cluster_dims__(kCplCluster, 1, 1) __launch_bounds__(kCplThreads)
     k_coupling(const float* __restrict__ xn, const float* __restrict__ qn,
                const float* __restrict__ sn, const float* __restrict__ en, int n_nnp,
                const float* __restrict__ xm, const float* __restrict__ qm,
@@ -48,12 +55,15 @@ __global__ void __launch_bounds__(kCplThreads)
   float2* np = reinterpret_cast<float2*>(nx + n_nnp);    // [n_nnp] sigma / 2, 2 sqrt(eps)
   float* mf = reinterpret_cast<float*>(np + n_nnp);      // [warps][tile][3] MM forces per warp
   float* ew = mf + kCplWarps * kCplTile * 3;             // [warps] energies
+  float* part = ew + kCplWarps;                          // [3 n_nnp + 1] this CTA's NNP forces, energy
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  cg::cluster_group cluster = cg::this_cluster();
   for (int t = threadIdx.x; t < n_nnp; t += blockDim.x) {
     nx[t] = make_float4(xn[3 * t], xn[3 * t + 1], xn[3 * t + 2], ke * qn[t]);
     np[t] = make_float2(0.5f * sn[t], 2.f * sqrtf(en[t]));
   }
+
   const int tile0 = blockIdx.x * kCplTile;
   float xj[kCplJ][3], qj[kCplJ], hsj[kCplJ], sej[kCplJ], fj[kCplJ][3];
   bool vj[kCplJ];
@@ -104,10 +114,10 @@ __global__ void __launch_bounds__(kCplThreads)
       fiy += __shfl_xor_sync(FULL, fiy, o);
       fiz += __shfl_xor_sync(FULL, fiz, o);
     }
-    if (lane == 0) {  // this CTA's share of NNP atom i: one warp, one addition
-      atomicAdd(f_nnp + 3 * i, (double)fix);
-      atomicAdd(f_nnp + 3 * i + 1, (double)fiy);
-      atomicAdd(f_nnp + 3 * i + 2, (double)fiz);
+    if (lane == 0) {  // this CTA's share of NNP atom i: one warp owns it
+      part[3 * i] = fix;
+      part[3 * i + 1] = fiy;
+      part[3 * i + 2] = fiz;
     }
   }
   // MM forces: each warp's partial into shared memory, summed over the warps
@@ -128,11 +138,21 @@ __global__ void __launch_bounds__(kCplThreads)
     f_mm[3 * (size_t)tile0 + t] += (double)sum;  // this CTA alone owns these MM atoms
   }
   if (threadIdx.x == 0) {
-    double es = 0.0;
+    float es = 0.f;
 #pragma unroll
-    for (int w = 0; w < kCplWarps; ++w) es += (double)ew[w];
-    atomicAdd(energy, es);
+    for (int w = 0; w < kCplWarps; ++w) es += ew[w];
+    part[3 * n_nnp] = es;
   }
+  cluster.sync();  // every CTA's partial sums are written
+  if (cluster.block_rank() == 0) {
+    for (int t = threadIdx.x; t <= 3 * n_nnp; t += blockDim.x) {
+      float s = 0.f;
+#pragma unroll
+      for (int c = 0; c < kCplCluster; ++c) s += cluster.map_shared_rank(part, c)[t];
+      atomicAdd(t < 3 * n_nnp ? f_nnp + t : energy, (double)s);
+    }
+  }
+  cluster.sync();  // the other CTAs' shared memory stays until the first CTA has read it
 }
 
 }  // namespace
@@ -151,9 +171,10 @@ extern "C" nnp_status nnp_mm_coupling(const float* nnp_positions_dev, const floa
       !mm_positions_dev || !mm_charges_dev || !mm_sigma_dev || !mm_epsilon_dev || !energy_dev ||
       !nnp_forces_dev || !mm_forces_dev)
     return NNP_ERR_ARG;
-  const int grid = (n_mm + kCplTile - 1) / kCplTile;
+  const int tiles = (n_mm + kCplTile - 1) / kCplTile;
+  const int grid = (tiles + kCplCluster - 1) / kCplCluster * kCplCluster;  // CTAs past n_mm add zeros
   const size_t smem = (size_t)n_nnp * (sizeof(float4) + sizeof(float2)) +
-                      (size_t)kCplWarps * (kCplTile * 3 + 1) * sizeof(float);
+                      ((size_t)kCplWarps * (kCplTile * 3 + 1) + 3 * (size_t)n_nnp + 1) * sizeof(float);
   k_coupling<<<grid, kCplThreads, smem, static_cast<cudaStream_t>(stream)>>>(
       nnp_positions_dev, nnp_charges_dev, nnp_sigma_dev, nnp_epsilon_dev, n_nnp, mm_positions_dev,
       mm_charges_dev, mm_sigma_dev, mm_epsilon_dev, n_mm, (float)coulomb_k, energy_dev,
