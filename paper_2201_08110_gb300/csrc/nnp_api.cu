@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/nnp.h"
 #include "nnp_internal.cuh"
 
@@ -1125,14 +1127,36 @@ void run_gemm(nnp_ctx* h, int layer, cudaStream_t s) {
                    h->tc_box[layer], h->tc_maps[layer], h->d_status, h->d_abort, s);
 }
 
+// NVTX ranges named after the stages (nnp_stage order), around the host-side
+// enqueue of each stage: a profiler that projects them onto the GPU work
+// (or a timeline of the direct-launch path) shows which kernels belong to
+// which stage.  They cost nothing without a tool attached.
+const char* const kStageRange[NNP_NUM_STAGES] = {
+    "nnp/neighbors", "nnp/features", "nnp/l1_fwd", "nnp/l2_fwd", "nnp/l3_fwd",
+    "nnp/energy",    "nnp/l3_rev",   "nnp/l2_rev", "nnp/l1_rev", "nnp/adjoint"};
+
+struct StageRanges {
+  bool open = false;
+  void next(int i) {  // close the current stage's range, open stage i's
+    if (open) nvtxRangePop();
+    open = i < NNP_NUM_STAGES;
+    if (open) nvtxRangePushA(kStageRange[i]);
+  }
+  ~StageRanges() {
+    if (open) nvtxRangePop();
+  }
+};
+
 // The whole step, enqueued on s.  With ev != nullptr an event is recorded
 // after each stage (ev[0] before the first); stage order is nnp_stage.
 int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_t s,
                  cudaEvent_t* ev = nullptr) {
   const Geometry g = h->geometry();
   int kernels = 0;
+  StageRanges ranges;
   auto mark = [&](int i) {
     if (ev) cudaEventRecord(ev[i], s);
+    ranges.next(i);
   };
   auto gemm = [&](int layer) {
     if (!h->L[layer].tiles.empty()) ++kernels;
