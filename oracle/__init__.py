@@ -10,7 +10,9 @@ The arithmetic lives in ``ani_oracle.c`` (plain C, FP64, built with
 module compiles it with gcc on first use and marshals numpy arrays.  What is
 computed is the NNP term V_NNP(Z, r) of the paper's Sec. 2 (Eqs. 2-3) and
 F = -grad V_NNP, with the ANI featurizer and ensemble of atomic networks the
-paper names in Sec. 1 and Sec. 2 ("Optimization").  The functional form is
+paper names in Sec. 1 and Sec. 2 ("Optimization"): model "ani2x" (7 elements,
+1008 features, the default) or "ani1x" (H, C, N, O, 384 features; the other
+ANI model the paper runs, Sec. 3 "Extensibility with other NNPs").  The functional form is
 written out in the header of ``ani_oracle.c``; the NNP-MM coupling term of
 Eq. 4 (``coupling``) is written out beside its function there.  The MD
 integrators of the step loop around both terms (``md_velocity_verlet``,
@@ -32,6 +34,9 @@ _SO = os.path.join(_BUILD_DIR, "libani_oracle.so")
 
 NUM_FEATURES = 1008
 ELEMENTS_Z = (1, 6, 7, 8, 9, 16, 17)
+MODELS = {"ani2x": 0, "ani1x": 1}
+MODEL_ELEMENTS = {"ani2x": (1, 6, 7, 8, 9, 16, 17), "ani1x": (1, 6, 7, 8)}
+MODEL_FEATURES = {"ani2x": 1008, "ani1x": 384}
 
 _lock = threading.Lock()
 _lib = None
@@ -59,20 +64,25 @@ def _load():
         lib = ctypes.CDLL(build())
         P = ctypes.c_void_p
         lib.ani_oracle_weights_per_model.restype = ctypes.c_long
+        lib.ani_oracle_weights_per_model_m.restype = ctypes.c_long
+        lib.ani_oracle_weights_per_model_m.argtypes = [ctypes.c_int]
         lib.ani_oracle_compute.restype = ctypes.c_int
         lib.ani_oracle_compute.argtypes = [ctypes.c_int, P, P, P, P, ctypes.c_int, P,
                                            ctypes.c_long, P, P, P, P, P, ctypes.c_int]
+        lib.ani_oracle_compute_m.restype = ctypes.c_int
+        lib.ani_oracle_compute_m.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, P, ctypes.c_int, P,
+                                             ctypes.c_long, P, P, P, P, P, ctypes.c_int]
         lib.ani_oracle_pairs.restype = ctypes.c_long
         lib.ani_oracle_pairs.argtypes = [ctypes.c_int, P, P, ctypes.c_double, P, P, ctypes.c_long]
         lib.ani_oracle_triples.restype = ctypes.c_long
         lib.ani_oracle_triples.argtypes = [ctypes.c_int, P, P, ctypes.c_double, P, P, P,
                                            ctypes.c_long]
-        lib.ani_oracle_aev.restype = ctypes.c_int
-        lib.ani_oracle_aev.argtypes = [ctypes.c_int, P, P, P, P]
-        lib.ani_oracle_aev_adjoint.restype = ctypes.c_int
-        lib.ani_oracle_aev_adjoint.argtypes = [ctypes.c_int, P, P, P, P, P]
-        lib.ani_oracle_hyper.restype = None
-        lib.ani_oracle_hyper.argtypes = [P]
+        lib.ani_oracle_aev_m.restype = ctypes.c_int
+        lib.ani_oracle_aev_m.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, P]
+        lib.ani_oracle_aev_adjoint_m.restype = ctypes.c_int
+        lib.ani_oracle_aev_adjoint_m.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, P, P]
+        lib.ani_oracle_hyper_m.restype = ctypes.c_int
+        lib.ani_oracle_hyper_m.argtypes = [ctypes.c_int, P]
         lib.ani_oracle_coupling.restype = ctypes.c_int
         lib.ani_oracle_coupling.argtypes = [ctypes.c_int, P, P, P, P, ctypes.c_int, P, P, P, P,
                                             ctypes.c_double, P, P, P, P, P, P]
@@ -93,26 +103,39 @@ def _box(box):
     return b
 
 
-def weights_per_model() -> int:
-    return int(_load().ani_oracle_weights_per_model())
+def _model(model) -> int:
+    if model not in MODELS:
+        raise ValueError(f"oracle: unknown model {model!r}")
+    return MODELS[model]
 
 
-def hyper() -> dict:
+def weights_per_model(model: str = "ani2x") -> int:
+    return int(_load().ani_oracle_weights_per_model_m(_model(model)))
+
+
+_GRIDS = {"ani2x": (16, 8, 4), "ani1x": (16, 4, 8)}
+
+
+def hyper(model: str = "ani2x") -> dict:
     """The featurizer constants as the oracle uses them."""
-    out = np.zeros(33, dtype=np.float64)
-    _load().ani_oracle_hyper(_ptr(out))
+    out = np.zeros(5 + 48, dtype=np.float64)
+    _load().ani_oracle_hyper_m(_model(model), _ptr(out))
+    nr, na, nz = _GRIDS[model]
     return {"Rcr": out[0], "Rca": out[1], "EtaR": out[2], "EtaA": out[3], "Zeta": out[4],
-            "ShfR": out[5:21].copy(), "ShfA": out[21:29].copy(), "ShfZ": out[29:33].copy()}
+            "ShfR": out[5:5 + nr].copy(), "ShfA": out[5 + nr:5 + nr + na].copy(),
+            "ShfZ": out[5 + nr + na:5 + nr + na + nz].copy()}
 
 
 def compute(Z, pos, mol_off, weights, n_models, box=None, forces=True, aev=False,
-            atom_energies=False, dEdG=False, nthreads=0):
-    """Energies [n_mols] and (optionally) forces [N,3], features [N,1008],
-    per-atom energies [N] and dE/dG [N,1008] of a batch, all FP64.
+            atom_energies=False, dEdG=False, nthreads=0, model: str = "ani2x"):
+    """Energies [n_mols] and (optionally) forces [N,3], features [N,F],
+    per-atom energies [N] and dE/dG [N,F] of a batch, all FP64 (F = 1008 for
+    "ani2x", 384 for "ani1x").
 
     pos may be float32 or float64; float32 values are promoted exactly.
     """
     lib = _load()
+    nf = MODEL_FEATURES[model]
     Z = np.ascontiguousarray(Z, dtype=np.int32)
     pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
     mol_off = np.ascontiguousarray(mol_off, dtype=np.int32)
@@ -122,12 +145,12 @@ def compute(Z, pos, mol_off, weights, n_models, box=None, forces=True, aev=False
     n_mols = mol_off.shape[0] - 1
     E = np.zeros(n_mols, dtype=np.float64)
     F = np.zeros((n, 3), dtype=np.float64) if (forces or dEdG) else None
-    G = np.zeros((n, NUM_FEATURES), dtype=np.float64) if aev else None
+    G = np.zeros((n, nf), dtype=np.float64) if aev else None
     Ea = np.zeros(n, dtype=np.float64) if atom_energies else None
-    dG = np.zeros((n, NUM_FEATURES), dtype=np.float64) if dEdG else None
-    rc = lib.ani_oracle_compute(n_mols, _ptr(mol_off), _ptr(Z), _ptr(pos), _ptr(_box(box)),
-                                int(n_models), _ptr(w), int(w.size), _ptr(E), _ptr(F), _ptr(G),
-                                _ptr(Ea), _ptr(dG), int(nthreads))
+    dG = np.zeros((n, nf), dtype=np.float64) if dEdG else None
+    rc = lib.ani_oracle_compute_m(_model(model), n_mols, _ptr(mol_off), _ptr(Z), _ptr(pos),
+                                  _ptr(_box(box)), int(n_models), _ptr(w), int(w.size), _ptr(E),
+                                  _ptr(F), _ptr(G), _ptr(Ea), _ptr(dG), int(nthreads))
     if rc == -1:
         raise ValueError("oracle: unsupported atomic number")
     if rc != 0:
@@ -144,11 +167,11 @@ def compute(Z, pos, mol_off, weights, n_models, box=None, forces=True, aev=False
     return out
 
 
-def energy(Z, pos, weights, n_models, box=None):
+def energy(Z, pos, weights, n_models, box=None, model: str = "ani2x"):
     """Energy of a single molecule (all atoms), FP64."""
     n = len(Z)
     return float(compute(Z, pos, np.array([0, n]), weights, n_models, box=box,
-                         forces=False)["energy"][0])
+                         forces=False, model=model)["energy"][0])
 
 
 def pairs(pos, rc, box=None):
@@ -177,26 +200,27 @@ def triples(pos, rc, box=None):
     return np.stack([I[:cnt], J[:cnt], K[:cnt]], axis=1)
 
 
-def aev(Z, pos, box=None):
-    """Feature vectors [n, 1008] of one molecule, FP64."""
+def aev(Z, pos, box=None, model: str = "ani2x"):
+    """Feature vectors [n, F] of one molecule, FP64."""
     lib = _load()
     Z = np.ascontiguousarray(Z, dtype=np.int32)
     pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
-    out = np.zeros((Z.shape[0], NUM_FEATURES), dtype=np.float64)
-    if lib.ani_oracle_aev(Z.shape[0], _ptr(Z), _ptr(pos), _ptr(_box(box)), _ptr(out)) != 0:
+    out = np.zeros((Z.shape[0], MODEL_FEATURES[model]), dtype=np.float64)
+    if lib.ani_oracle_aev_m(_model(model), Z.shape[0], _ptr(Z), _ptr(pos), _ptr(_box(box)),
+                            _ptr(out)) != 0:
         raise ValueError("oracle: unsupported atomic number")
     return out
 
 
-def aev_adjoint(Z, pos, g, box=None):
+def aev_adjoint(Z, pos, g, box=None, model: str = "ani2x"):
     """d(sum_i g_i . G_i)/dx for one molecule, FP64 [n, 3]."""
     lib = _load()
     Z = np.ascontiguousarray(Z, dtype=np.int32)
     pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
-    g = np.ascontiguousarray(g, dtype=np.float64).reshape(Z.shape[0], NUM_FEATURES)
+    g = np.ascontiguousarray(g, dtype=np.float64).reshape(Z.shape[0], MODEL_FEATURES[model])
     out = np.zeros((Z.shape[0], 3), dtype=np.float64)
-    if lib.ani_oracle_aev_adjoint(Z.shape[0], _ptr(Z), _ptr(pos), _ptr(_box(box)), _ptr(g),
-                                  _ptr(out)) != 0:
+    if lib.ani_oracle_aev_adjoint_m(_model(model), Z.shape[0], _ptr(Z), _ptr(pos), _ptr(_box(box)),
+                                    _ptr(g), _ptr(out)) != 0:
         raise ValueError("oracle: unsupported atomic number")
     return out
 

@@ -38,6 +38,16 @@
  *
  * Everything is FP64; weights arrive as FP32 and are promoted.
  *
+ * Two models share the code through a model description (o_model): model 0
+ * is the ANI-2x-shaped one above (7 elements, 1008 features); model 1 is the
+ * ANI-1x-shaped one that the paper also runs (Sec. 3 "Extensibility with
+ * other NNPs"): elements H, C, N, O; Rcr = 5.2 A, EtaR = 16, 16 radial shifts
+ * 0.9 + 0.26875 k A; Rca = 3.5 A, EtaA = 8, Zeta = 32, 4 distance shifts
+ * 0.9 + 0.65 a A and 8 angle shifts pi/16 + z pi/8 rad; 4x16 radial + 10
+ * species-pair blocks of 4x8 = 384 features; networks H 384-160-128-96-1,
+ * C 384-144-112-96-1, N and O 384-128-112-96-1 (the paper prints none of
+ * these; they are the ANI-1x model's).
+ *
  * The file also holds the NNP-MM coupling term of Eq. 4 (at its end), the
  * pair sum that couples the NNP region to the MM region.
  */
@@ -49,77 +59,103 @@
 #include <omp.h>
 #endif
 
-#define O_NSPEC 7
-#define O_NSHFR 16
-#define O_NSHFA 8
-#define O_NSHFZ 4
-#define O_NRADIAL (O_NSPEC * O_NSHFR)                  /* 112 */
-#define O_NPAIRS 28
-#define O_NANGULAR (O_NPAIRS * O_NSHFA * O_NSHFZ)      /* 896 */
-#define O_NFEAT (O_NRADIAL + O_NANGULAR)               /* 1008 */
+#define O_MAXSPEC 7
+#define O_MAXSHF 16
 
 static const double O_PI = 3.14159265358979323846;
 
-/* Hyper-parameters of the ANI-2x-style featurizer (shift grids taken as
- * closed linspaces over the stated ranges). */
+/* A model: its elements, the featurizer's hyper-parameters and shift grids,
+ * and the hidden widths of each element's network.  Feature layout:
+ * [radial: species-major nspec x nshfr | angular: npairs species-pair blocks
+ * (row-major upper triangle s <= t), each ShfA-major then ShfZ]. */
 typedef struct {
+  int nspec, nshfr, nshfa, nshfz;
+  int nradial, npairs, nfeat;
+  int z[O_MAXSPEC];
+  int hidden[O_MAXSPEC][3];
   double Rcr, Rca, EtaR, EtaA, Zeta;
-  double ShfR[O_NSHFR], ShfA[O_NSHFA], ShfZ[O_NSHFZ];
-} o_hyper;
+  double ShfR[O_MAXSHF], ShfA[O_MAXSHF], ShfZ[O_MAXSHF];
+} o_model;
 
-static void o_hyper_init(o_hyper* h) {
-  int k;
-  h->Rcr = (double)5.1f;  /* FP32 constant promoted (pair predicate) */
-  h->Rca = (double)3.5f;
-  h->EtaR = 19.7;
-  h->EtaA = 12.5;
-  h->Zeta = 14.1;
-  for (k = 0; k < O_NSHFR; ++k) h->ShfR[k] = 0.8 + (4.9 - 0.8) * k / (O_NSHFR - 1);
-  for (k = 0; k < O_NSHFA; ++k) h->ShfA[k] = 0.8 + (3.1 - 0.8) * k / (O_NSHFA - 1);
-  for (k = 0; k < O_NSHFZ; ++k) h->ShfZ[k] = 0.39 + (2.75 - 0.39) * k / (O_NSHFZ - 1);
+/* Model 0 (ANI-2x-shaped, shift grids as closed linspaces over the stated
+ * ranges) or model 1 (ANI-1x-shaped); returns -1 for another id. */
+static int o_model_init(o_model* M, int id) {
+  int k, e;
+  memset(M, 0, sizeof(*M));
+  if (id == 0) {
+    static const int z[7] = {1, 6, 7, 8, 9, 16, 17};
+    static const int hid[7][3] = {{256, 192, 160}, {224, 192, 160}, {192, 160, 128}, {192, 160, 128},
+                                  {160, 128, 96},  {160, 128, 96},  {160, 128, 96}};
+    M->nspec = 7; M->nshfr = 16; M->nshfa = 8; M->nshfz = 4;
+    for (e = 0; e < 7; ++e) { M->z[e] = z[e]; M->hidden[e][0] = hid[e][0]; M->hidden[e][1] = hid[e][1]; M->hidden[e][2] = hid[e][2]; }
+    M->Rcr = (double)5.1f;  /* FP32 constant promoted (pair predicate) */
+    M->Rca = (double)3.5f;
+    M->EtaR = 19.7;
+    M->EtaA = 12.5;
+    M->Zeta = 14.1;
+    for (k = 0; k < 16; ++k) M->ShfR[k] = 0.8 + (4.9 - 0.8) * k / 15;
+    for (k = 0; k < 8; ++k) M->ShfA[k] = 0.8 + (3.1 - 0.8) * k / 7;
+    for (k = 0; k < 4; ++k) M->ShfZ[k] = 0.39 + (2.75 - 0.39) * k / 3;
+  } else if (id == 1) {
+    static const int z[4] = {1, 6, 7, 8};
+    static const int hid[4][3] = {{160, 128, 96}, {144, 112, 96}, {128, 112, 96}, {128, 112, 96}};
+    M->nspec = 4; M->nshfr = 16; M->nshfa = 4; M->nshfz = 8;
+    for (e = 0; e < 4; ++e) { M->z[e] = z[e]; M->hidden[e][0] = hid[e][0]; M->hidden[e][1] = hid[e][1]; M->hidden[e][2] = hid[e][2]; }
+    M->Rcr = (double)5.2f;
+    M->Rca = (double)3.5f;
+    M->EtaR = 16.0;
+    M->EtaA = 8.0;
+    M->Zeta = 32.0;
+    for (k = 0; k < 16; ++k) M->ShfR[k] = 0.9 + 0.26875 * k;
+    for (k = 0; k < 4; ++k) M->ShfA[k] = 0.9 + 0.65 * k;
+    for (k = 0; k < 8; ++k) M->ShfZ[k] = O_PI / 16.0 + k * O_PI / 8.0;
+  } else {
+    return -1;
+  }
+  M->nradial = M->nspec * M->nshfr;
+  M->npairs = M->nspec * (M->nspec + 1) / 2;
+  M->nfeat = M->nradial + M->npairs * M->nshfa * M->nshfz;
+  return 0;
 }
 
-/* Hidden widths per element (H, C, N, O, F, S, Cl). */
-static const int O_HIDDEN[O_NSPEC][3] = {
-    {256, 192, 160}, {224, 192, 160}, {192, 160, 128}, {192, 160, 128},
-    {160, 128, 96},  {160, 128, 96},  {160, 128, 96}};
-
-static int o_species(int z) {
-  switch (z) {
-    case 1: return 0;
-    case 6: return 1;
-    case 7: return 2;
-    case 8: return 3;
-    case 9: return 4;
-    case 16: return 5;
-    case 17: return 6;
-    default: return -1;
-  }
+static int o_species(const o_model* M, int z) {
+  int e;
+  for (e = 0; e < M->nspec; ++e)
+    if (M->z[e] == z) return e;
+  return -1;
 }
 
 /* Index of the unordered species pair {s, t} (s <= t) in the row-major upper
- * triangle of a 7x7 matrix. */
-static int o_pair_index(int s, int t) {
+ * triangle of an nspec x nspec matrix. */
+static int o_pair_index(const o_model* M, int s, int t) {
   int a = s < t ? s : t, b = s < t ? t : s, idx = 0, r;
-  for (r = 0; r < a; ++r) idx += O_NSPEC - r;
+  for (r = 0; r < a; ++r) idx += M->nspec - r;
   return idx + (b - a);
 }
 
 /* Number of floats of one element's network: W1 b1 W2 b2 W3 b3 w4 b4. */
-static long o_element_params(int e) {
-  const int n0 = O_NFEAT, n1 = O_HIDDEN[e][0], n2 = O_HIDDEN[e][1], n3 = O_HIDDEN[e][2];
+static long o_element_params(const o_model* M, int e) {
+  const int n0 = M->nfeat, n1 = M->hidden[e][0], n2 = M->hidden[e][1], n3 = M->hidden[e][2];
   return (long)n1 * n0 + n1 + (long)n2 * n1 + n2 + (long)n3 * n2 + n3 + n3 + 1;
 }
 
-static long o_model_params(void) {
+static long o_model_params(const o_model* M) {
   long s = 0;
   int e;
-  for (e = 0; e < O_NSPEC; ++e) s += o_element_params(e);
+  for (e = 0; e < M->nspec; ++e) s += o_element_params(M, e);
   return s;
 }
 
-long ani_oracle_weights_per_model(void) { return o_model_params(); }
-int ani_oracle_num_features(void) { return O_NFEAT; }
+long ani_oracle_weights_per_model_m(int model) {
+  o_model M;
+  return o_model_init(&M, model) ? -1 : o_model_params(&M);
+}
+long ani_oracle_weights_per_model(void) { return ani_oracle_weights_per_model_m(0); }
+int ani_oracle_num_features_m(int model) {
+  o_model M;
+  return o_model_init(&M, model) ? -1 : M.nfeat;
+}
+int ani_oracle_num_features(void) { return ani_oracle_num_features_m(0); }
 
 /* Displacement x_j - x_i, minimum image when box != NULL. */
 static void o_disp(const double* xi, const double* xj, const double* box, double out[3]) {
@@ -203,13 +239,13 @@ long ani_oracle_triples(int n, const double* pos, const double* box, double rc,
 /* ------------------------------------------------------------------------ */
 /* Featurizer of one molecule (atoms 0..n-1 of pos/spec).                    */
 
-static void o_aev_molecule(const o_hyper* h, int n, const int* spec, const double* pos,
-                           const double* box, double* aev /* [n][1008] */) {
+static void o_aev_molecule(const o_model* h, int n, const int* spec, const double* pos,
+                           const double* box, double* aev /* [n][nfeat] */) {
   const double rcr2 = h->Rcr * h->Rcr, rca2 = h->Rca * h->Rca;
   int i, j, k, a, z, s;
-  memset(aev, 0, sizeof(double) * (size_t)n * O_NFEAT);
+  memset(aev, 0, sizeof(double) * (size_t)n * h->nfeat);
   for (i = 0; i < n; ++i) {
-    double* G = aev + (size_t)i * O_NFEAT;
+    double* G = aev + (size_t)i * h->nfeat;
     /* radial */
     for (j = 0; j < n; ++j) {
       double d[3], r, fc;
@@ -218,9 +254,9 @@ static void o_aev_molecule(const o_hyper* h, int n, const int* spec, const doubl
       if (!(o_dist2(d) < rcr2)) continue;
       r = sqrt(o_dist2(d));
       fc = o_fc(r, h->Rcr);
-      for (s = 0; s < O_NSHFR; ++s) {
+      for (s = 0; s < h->nshfr; ++s) {
         double x = r - h->ShfR[s];
-        G[spec[j] * O_NSHFR + s] += 0.25 * exp(-h->EtaR * x * x) * fc;
+        G[spec[j] * h->nshfr + s] += 0.25 * exp(-h->EtaR * x * x) * fc;
       }
     }
     /* angular */
@@ -241,13 +277,13 @@ static void o_aev_molecule(const o_hyper* h, int n, const int* spec, const doubl
         theta = acos(0.95 * cos_t);
         fcjk = o_fc(rj, h->Rca) * o_fc(rk, h->Rca);
         u = 0.5 * (rj + rk);
-        blk = G + O_NRADIAL + o_pair_index(spec[j], spec[k]) * (O_NSHFA * O_NSHFZ);
-        for (a = 0; a < O_NSHFA; ++a) {
+        blk = G + h->nradial + o_pair_index(h, spec[j], spec[k]) * (h->nshfa * h->nshfz);
+        for (a = 0; a < h->nshfa; ++a) {
           double x = u - h->ShfA[a];
           double rad = exp(-h->EtaA * x * x);
-          for (z = 0; z < O_NSHFZ; ++z) {
+          for (z = 0; z < h->nshfz; ++z) {
             double ang = 2.0 * pow(0.5 * (1.0 + cos(theta - h->ShfZ[z])), h->Zeta);
-            blk[a * O_NSHFZ + z] += ang * rad * fcjk;
+            blk[a * h->nshfz + z] += ang * rad * fcjk;
           }
         }
       }
@@ -255,14 +291,14 @@ static void o_aev_molecule(const o_hyper* h, int n, const int* spec, const doubl
   }
 }
 
-/* Reverse mode of the featurizer: given g = dE/dG (per atom, 1008 each),
+/* Reverse mode of the featurizer: given g = dE/dG (per atom, nfeat each),
  * accumulate dE/dx into grad[n][3]. */
-static void o_aev_adjoint(const o_hyper* h, int n, const int* spec, const double* pos,
+static void o_aev_adjoint(const o_model* h, int n, const int* spec, const double* pos,
                           const double* box, const double* g, double* grad) {
   const double rcr2 = h->Rcr * h->Rcr, rca2 = h->Rca * h->Rca;
   int i, j, k, a, z, s, c;
   for (i = 0; i < n; ++i) {
-    const double* gi = g + (size_t)i * O_NFEAT;
+    const double* gi = g + (size_t)i * h->nfeat;
     /* radial: term = 1/4 exp(-EtaR (r - R)^2) fc(r) */
     for (j = 0; j < n; ++j) {
       double d[3], r, fc, dfc, dEdr = 0.0;
@@ -272,11 +308,11 @@ static void o_aev_adjoint(const o_hyper* h, int n, const int* spec, const double
       r = sqrt(o_dist2(d));
       fc = o_fc(r, h->Rcr);
       dfc = o_dfc(r, h->Rcr);
-      for (s = 0; s < O_NSHFR; ++s) {
+      for (s = 0; s < h->nshfr; ++s) {
         double x = r - h->ShfR[s];
         double e = exp(-h->EtaR * x * x);
         double dterm = 0.25 * (e * (-2.0 * h->EtaR * x) * fc + e * dfc);
-        dEdr += gi[spec[j] * O_NSHFR + s] * dterm;
+        dEdr += gi[spec[j] * h->nshfr + s] * dterm;
       }
       for (c = 0; c < 3; ++c) {
         grad[3 * j + c] += dEdr * d[c] / r;
@@ -307,13 +343,13 @@ static void o_aev_adjoint(const o_hyper* h, int n, const int* spec, const double
         dfcj = o_dfc(rj, h->Rca);
         dfck = o_dfc(rk, h->Rca);
         u = 0.5 * (rj + rk);
-        gb = gi + O_NRADIAL + o_pair_index(spec[j], spec[k]) * (O_NSHFA * O_NSHFZ);
-        for (a = 0; a < O_NSHFA; ++a) {
+        gb = gi + h->nradial + o_pair_index(h, spec[j], spec[k]) * (h->nshfa * h->nshfz);
+        for (a = 0; a < h->nshfa; ++a) {
           double x = u - h->ShfA[a];
           double rad = exp(-h->EtaA * x * x);
           double drad_du = rad * (-2.0 * h->EtaA * x);
-          for (z = 0; z < O_NSHFZ; ++z) {
-            double gv = gb[a * O_NSHFZ + z];
+          for (z = 0; z < h->nshfz; ++z) {
+            double gv = gb[a * h->nshfz + z];
             double base = 0.5 * (1.0 + cos(theta - h->ShfZ[z]));
             double ang = 2.0 * pow(base, h->Zeta);
             /* d ang / d theta = 2 Zeta base^(Zeta-1) * (-sin(theta - ShfZ) / 2) */
@@ -342,9 +378,9 @@ static void o_aev_adjoint(const o_hyper* h, int n, const int* spec, const double
 /* One element network of one model: forward y(G) and, when dG != NULL,
  * accumulate scale * dy/dG into dG.  w points at this element's packed
  * parameters (W1 b1 W2 b2 W3 b3 w4 b4, W row-major [out][in]). */
-static double o_network(int e, const float* w, const double* G, double scale, double* dG,
-                        double* work) {
-  const int n0 = O_NFEAT, n1 = O_HIDDEN[e][0], n2 = O_HIDDEN[e][1], n3 = O_HIDDEN[e][2];
+static double o_network(const o_model* M, int e, const float* w, const double* G, double scale,
+                        double* dG, double* work) {
+  const int n0 = M->nfeat, n1 = M->hidden[e][0], n2 = M->hidden[e][1], n3 = M->hidden[e][2];
   const float *W1 = w, *b1 = W1 + (long)n1 * n0, *W2 = b1 + n1, *b2 = W2 + (long)n2 * n1,
               *W3 = b2 + n2, *b3 = W3 + (long)n3 * n2, *w4 = b3 + n3, *b4 = w4 + n3;
   double *z1 = work, *z2 = z1 + n1, *z3 = z2 + n2, *h1 = z3 + n3, *h2 = h1 + n1, *h3 = h2 + n2;
@@ -403,21 +439,23 @@ static double o_network(int e, const float* w, const double* G, double scale, do
  * [model][element H..Cl][W1 b1 W2 b2 W3 b3 w4 b4].
  * Returns 0, -1 for an unknown atomic number, -2 for bad sizes.
  */
-int ani_oracle_compute(int n_mols, const int32_t* mol_off, const int32_t* Z, const double* pos,
-                       const double* box, int n_models, const float* weights, long n_weights,
-                       double* E, double* F, double* aev_out, double* atomE_out,
-                       double* dEdG_out, int nthreads) {
-  o_hyper h;
-  const long per_model = o_model_params();
-  long elem_off[O_NSPEC];
-  int m, e, bad = 0;
+int ani_oracle_compute_m(int model, int n_mols, const int32_t* mol_off, const int32_t* Z,
+                         const double* pos, const double* box, int n_models, const float* weights,
+                         long n_weights, double* E, double* F, double* aev_out, double* atomE_out,
+                         double* dEdG_out, int nthreads) {
+  o_model h;
+  long per_model;
+  long elem_off[O_MAXSPEC];
+  int m, e, bad = 0, nf;
   long acc = 0;
+  if (o_model_init(&h, model)) return -2;
+  per_model = o_model_params(&h);
+  nf = h.nfeat;
   if (n_mols < 0 || n_models < 1 || n_weights != per_model * n_models) return -2;
-  for (e = 0; e < O_NSPEC; ++e) { elem_off[e] = acc; acc += o_element_params(e); }
+  for (e = 0; e < h.nspec; ++e) { elem_off[e] = acc; acc += o_element_params(&h, e); }
   for (m = 0; m < mol_off[n_mols]; ++m)
-    if (o_species(Z[m]) < 0) bad = 1;
+    if (o_species(&h, Z[m]) < 0) bad = 1;
   if (bad) return -1;
-  o_hyper_init(&h);
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1)
@@ -425,28 +463,28 @@ int ani_oracle_compute(int n_mols, const int32_t* mol_off, const int32_t* Z, con
   for (m = 0; m < n_mols; ++m) {
     const int a0 = mol_off[m], n = mol_off[m + 1] - mol_off[m];
     int* spec = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
-    double* G = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * O_NFEAT);
-    double* dG = (double*)calloc((size_t)(n > 0 ? n : 1) * O_NFEAT, sizeof(double));
+    double* G = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * nf);
+    double* dG = (double*)calloc((size_t)(n > 0 ? n : 1) * nf, sizeof(double));
     double* grad = (double*)calloc((size_t)3 * (n > 0 ? n : 1), sizeof(double));
     double* work = (double*)malloc(sizeof(double) * 3 * (256 + 192 + 160));
     double Emol = 0.0;
     int i, mm, c;
-    for (i = 0; i < n; ++i) spec[i] = o_species(Z[a0 + i]);
+    for (i = 0; i < n; ++i) spec[i] = o_species(&h, Z[a0 + i]);
     o_aev_molecule(&h, n, spec, pos + 3 * (size_t)a0, box, G);
     for (i = 0; i < n; ++i) {
       double ei = 0.0;
       for (mm = 0; mm < n_models; ++mm) {
         const float* w = weights + mm * per_model + elem_off[spec[i]];
-        ei += o_network(spec[i], w, G + (size_t)i * O_NFEAT, 1.0 / n_models,
-                        F ? dG + (size_t)i * O_NFEAT : NULL, work);
+        ei += o_network(&h, spec[i], w, G + (size_t)i * nf, 1.0 / n_models,
+                        F ? dG + (size_t)i * nf : NULL, work);
       }
       ei /= n_models;
       if (atomE_out) atomE_out[a0 + i] = ei;
       Emol += ei;
     }
     E[m] = Emol;
-    if (aev_out) memcpy(aev_out + (size_t)a0 * O_NFEAT, G, sizeof(double) * (size_t)n * O_NFEAT);
-    if (dEdG_out && F) memcpy(dEdG_out + (size_t)a0 * O_NFEAT, dG, sizeof(double) * (size_t)n * O_NFEAT);
+    if (aev_out) memcpy(aev_out + (size_t)a0 * nf, G, sizeof(double) * (size_t)n * nf);
+    if (dEdG_out && F) memcpy(dEdG_out + (size_t)a0 * nf, dG, sizeof(double) * (size_t)n * nf);
     if (F) {
       o_aev_adjoint(&h, n, spec, pos + 3 * (size_t)a0, box, dG, grad);
       for (i = 0; i < n; ++i)
@@ -457,47 +495,68 @@ int ani_oracle_compute(int n_mols, const int32_t* mol_off, const int32_t* Z, con
   return 0;
 }
 
+int ani_oracle_compute(int n_mols, const int32_t* mol_off, const int32_t* Z, const double* pos,
+                       const double* box, int n_models, const float* weights, long n_weights,
+                       double* E, double* F, double* aev_out, double* atomE_out,
+                       double* dEdG_out, int nthreads) {
+  return ani_oracle_compute_m(0, n_mols, mol_off, Z, pos, box, n_models, weights, n_weights, E, F,
+                              aev_out, atomE_out, dEdG_out, nthreads);
+}
+
 /* Featurizer alone for one molecule (species given as atomic numbers). */
-int ani_oracle_aev(int n, const int32_t* Z, const double* pos, const double* box, double* aev) {
-  o_hyper h;
+int ani_oracle_aev_m(int model, int n, const int32_t* Z, const double* pos, const double* box,
+                     double* aev) {
+  o_model h;
   int i;
-  int* spec = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+  int* spec;
+  if (o_model_init(&h, model)) return -2;
+  spec = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
   for (i = 0; i < n; ++i) {
-    spec[i] = o_species(Z[i]);
+    spec[i] = o_species(&h, Z[i]);
     if (spec[i] < 0) { free(spec); return -1; }
   }
-  o_hyper_init(&h);
   o_aev_molecule(&h, n, spec, pos, box, aev);
   free(spec);
   return 0;
 }
+int ani_oracle_aev(int n, const int32_t* Z, const double* pos, const double* box, double* aev) {
+  return ani_oracle_aev_m(0, n, Z, pos, box, aev);
+}
 
 /* Featurizer adjoint alone: grad[n][3] += d(sum g . G)/dx for given g. */
-int ani_oracle_aev_adjoint(int n, const int32_t* Z, const double* pos, const double* box,
-                           const double* g, double* grad) {
-  o_hyper h;
+int ani_oracle_aev_adjoint_m(int model, int n, const int32_t* Z, const double* pos,
+                             const double* box, const double* g, double* grad) {
+  o_model h;
   int i;
-  int* spec = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+  int* spec;
+  if (o_model_init(&h, model)) return -2;
+  spec = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
   for (i = 0; i < n; ++i) {
-    spec[i] = o_species(Z[i]);
+    spec[i] = o_species(&h, Z[i]);
     if (spec[i] < 0) { free(spec); return -1; }
   }
-  o_hyper_init(&h);
   o_aev_adjoint(&h, n, spec, pos, box, g, grad);
   free(spec);
   return 0;
 }
-
-/* Hyper-parameters as the oracle uses them (for pins that check the grid). */
-void ani_oracle_hyper(double* out /* 5 + 16 + 8 + 4 */) {
-  o_hyper h;
-  int k;
-  o_hyper_init(&h);
-  out[0] = h.Rcr; out[1] = h.Rca; out[2] = h.EtaR; out[3] = h.EtaA; out[4] = h.Zeta;
-  for (k = 0; k < O_NSHFR; ++k) out[5 + k] = h.ShfR[k];
-  for (k = 0; k < O_NSHFA; ++k) out[21 + k] = h.ShfA[k];
-  for (k = 0; k < O_NSHFZ; ++k) out[29 + k] = h.ShfZ[k];
+int ani_oracle_aev_adjoint(int n, const int32_t* Z, const double* pos, const double* box,
+                           const double* g, double* grad) {
+  return ani_oracle_aev_adjoint_m(0, n, Z, pos, box, g, grad);
 }
+
+/* Hyper-parameters as the oracle uses them (for pins that check the grid):
+ * Rcr Rca EtaR EtaA Zeta, then nshfr ShfR, nshfa ShfA, nshfz ShfZ. */
+int ani_oracle_hyper_m(int model, double* out /* 5 + 3 x 16 */) {
+  o_model h;
+  int k;
+  if (o_model_init(&h, model)) return -2;
+  out[0] = h.Rcr; out[1] = h.Rca; out[2] = h.EtaR; out[3] = h.EtaA; out[4] = h.Zeta;
+  for (k = 0; k < h.nshfr; ++k) out[5 + k] = h.ShfR[k];
+  for (k = 0; k < h.nshfa; ++k) out[5 + h.nshfr + k] = h.ShfA[k];
+  for (k = 0; k < h.nshfz; ++k) out[5 + h.nshfr + h.nshfa + k] = h.ShfZ[k];
+  return 0;
+}
+void ani_oracle_hyper(double* out /* 5 + 16 + 8 + 4 */) { ani_oracle_hyper_m(0, out); }
 
 /* ---------------------------------------------------------------------------
  * NNP-MM coupling term (Eq. 4, the mechanical-embedding scheme of Sec. 2):

@@ -46,6 +46,13 @@ ELEMENT_P = (0.45, 0.35, 0.08, 0.08, 0.04 / 3, 0.04 / 3, 0.04 / 3)
 HIDDEN = ((256, 192, 160), (224, 192, 160), (192, 160, 128), (192, 160, 128),
           (160, 128, 96), (160, 128, 96), (160, 128, 96))
 N_INPUT = 1008
+# The ANI-1x architecture: elements H, C, N, O, input 384.
+ELEMENTS_Z_ANI1X = (1, 6, 7, 8)
+HIDDEN_ANI1X = ((160, 128, 96), (144, 112, 96), (128, 112, 96), (128, 112, 96))
+N_INPUT_ANI1X = 384
+# H, C, N, O molecules for the ANI-1x model: the mix above without F/S/Cl,
+# renormalised
+ELEMENT_P_ANI1X = tuple(p / 0.96 for p in (0.45, 0.35, 0.08, 0.08))
 
 
 @dataclass
@@ -99,9 +106,10 @@ def geometry(g: np.random.Generator, n: int, edge: float = 8.0, dmin: float = 0.
     return out.astype(np.float32)
 
 
-def species_iid(g: np.random.Generator, n: int) -> np.ndarray:
-    idx = g.choice(len(ELEMENTS_Z), size=n, p=np.array(ELEMENT_P))
-    return np.asarray(ELEMENTS_Z, dtype=np.int32)[idx]
+def species_iid(g: np.random.Generator, n: int, model: str = "ani2x") -> np.ndarray:
+    zs, ps = (ELEMENTS_Z, ELEMENT_P) if model == "ani2x" else (ELEMENTS_Z_ANI1X, ELEMENT_P_ANI1X)
+    idx = g.choice(len(zs), size=n, p=np.array(ps))
+    return np.asarray(zs, dtype=np.int32)[idx]
 
 
 def species_counts(g: np.random.Generator, counts) -> np.ndarray:
@@ -118,13 +126,13 @@ def single(seed: int, counts, edge: float = 8.0) -> Batch:
     return Batch(Z, pos, np.array([0, Z.shape[0]], dtype=np.int32))
 
 
-def batch(seed: int, sizes) -> Batch:
+def batch(seed: int, sizes, model: str = "ani2x") -> Batch:
     """Molecules with the given atom counts, species i.i.d. from the mix."""
     g = rng(seed)
     Zs, Ps, off = [], [], [0]
     for n in sizes:
         n = int(n)
-        Zs.append(species_iid(g, n))
+        Zs.append(species_iid(g, n, model))
         Ps.append(geometry(g, n))
         off.append(off[-1] + n)
     Z = np.concatenate(Zs) if Zs else np.zeros(0, np.int32)
@@ -140,14 +148,24 @@ def pocket(seed: int, n: int = 1500, edge: float = 24.7) -> Batch:
     return Batch(Z, pos, np.array([0, n], dtype=np.int32), np.full(3, edge))
 
 
-def weights(seed: int, n_models: int, bias_std: float = 0.0) -> np.ndarray:
+def architecture(model: str = "ani2x"):
+    """(elements, hidden widths per element, input width) of a model."""
+    if model == "ani2x":
+        return ELEMENTS_Z, HIDDEN, N_INPUT
+    if model == "ani1x":
+        return ELEMENTS_Z_ANI1X, HIDDEN_ANI1X, N_INPUT_ANI1X
+    raise ValueError(model)
+
+
+def weights(seed: int, n_models: int, bias_std: float = 0.0, model: str = "ani2x") -> np.ndarray:
     """Packed FP32 parameters [model][element][W1 b1 W2 b2 W3 b3 w4 b4],
     each W row-major [out][in]."""
+    zs, hidden, n_in = architecture(model)
     g = rng(seed)
     chunks = []
     for _m in range(n_models):
-        for e in range(len(ELEMENTS_Z)):
-            dims = (N_INPUT,) + HIDDEN[e] + (1,)
+        for e in range(len(zs)):
+            dims = (n_in,) + hidden[e] + (1,)
             for l in range(4):
                 fi, fo = dims[l], dims[l + 1]
                 std = np.sqrt(2.0 / (fi + fo))
@@ -159,10 +177,11 @@ def weights(seed: int, n_models: int, bias_std: float = 0.0) -> np.ndarray:
     return np.concatenate(chunks)
 
 
-def weights_per_model() -> int:
+def weights_per_model(model: str = "ani2x") -> int:
+    zs, hidden, n_in = architecture(model)
     s = 0
-    for e in range(len(ELEMENTS_Z)):
-        dims = (N_INPUT,) + HIDDEN[e] + (1,)
+    for e in range(len(zs)):
+        dims = (n_in,) + hidden[e] + (1,)
         s += sum(dims[l] * dims[l + 1] + dims[l + 1] for l in range(4))
     return s
 
