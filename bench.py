@@ -301,12 +301,13 @@ NCU_TRAFFIC = {
 
 # ------------------------------------------------------------ the oracle ----
 
-def oracle_refs(b, w, M, nthreads: int = 0):
+def oracle_refs(b, w, M, nthreads: int = 0, model: str = "ani2x"):
     """Per-molecule oracle results (energy, forces, atomic energies) from one
     call over the whole batch, and the call's wall time."""
     import oracle
     t0 = time.perf_counter()
-    r = oracle.compute(b.Z, b.pos, b.mol_off, w, M, box=b.box, atom_energies=True, nthreads=nthreads)
+    r = oracle.compute(b.Z, b.pos, b.mol_off, w, M, box=b.box, atom_energies=True, nthreads=nthreads,
+                       model=model)
     dt = time.perf_counter() - t0
     refs = {}
     for m in range(b.n_mols):
@@ -502,11 +503,11 @@ def timed_steps(model, pos, E, F, steps: int, flush, stream):
     return sum(a.elapsed_time(b) for a, b in zip(starts, ends))
 
 
-def make_model(nnp, b, w, M, prec, single, pos, E, F, args, schedules, key):
+def make_model(nnp, b, w, M, prec, single, pos, E, F, args, schedules, key, model="ani2x"):
     """A graph-replay handle for the batch, tuned (or pinned) and warmed up."""
     import torch
     m = nnp.NNP(b.Z, w, M, mol_off=b.mol_off, precision=prec, single_pass=single, box=b.box,
-                use_graph=True)
+                use_graph=True, model=model)
     if args.schedule:
         vals = [int(v) for v in args.schedule.split(",")]
         schedules[key] = dict(zip(nnp.NNP.SCHEDULE_KEYS, vals))
@@ -573,6 +574,40 @@ def workload5_measurement(nnp, prec, steps: int, warmup: int, flush, stream):
            "gpu_launches_per_step": hb.kernels_per_step(True) + hp.kernels_per_step(True)}
     hb.close()
     hp.close()
+    return out
+
+
+def ani1x_measurement(nnp, args, flush, stream, with_oracle: bool):
+    """The ANI-1x model (Sec. 3, "Extensibility with other NNPs") on a batch of
+    the 512-molecule batch's sizes with H, C, N, O molecules, 8 networks: the
+    timed step in the headline arithmetic and in FP32, each with its
+    per-molecule errors against the oracle's ANI-1x model."""
+    import torch
+    b, w, M = W.config3_ani1x()
+    refs = dt = None
+    if with_oracle:
+        refs, dt = oracle_refs(b, w, M, model="ani1x")
+    pos = torch.tensor(b.pos, device="cuda")
+    E = torch.empty(b.n_mols, dtype=torch.float64, device="cuda")
+    F = torch.empty(b.n_atoms, 3, dtype=torch.float64, device="cuda")
+    out = {"workload": f"{b.n_mols} H/C/N/O molecules, 20-120 atoms, 8-network ANI-1x ensemble "
+                       "(384 features; widths 144 and 112 padded to 160 and 128 with zero weights)",
+           "n_atoms": b.n_atoms, "unit": UNIT}
+    if dt is not None:
+        out["oracle_all_cores"] = {"value": b.n_atoms / dt, "unit": UNIT, "cores": os.cpu_count() or 1}
+    schedules = {}
+    for prec in dict.fromkeys((args.precision, "fp32")):
+        m = make_model(nnp, b, w, M, prec, False, pos, E, F, args, schedules, prec, model="ani1x")
+        t = timed_steps(m, pos, E, F, args.steps, flush, stream)
+        r = {"ms_per_step": t / args.steps, "value": b.n_atoms * args.steps / (t / 1e3),
+             "stages_ms": m.compute_timed(pos, E, F), "schedule": schedules.get(prec)}
+        if refs is not None:
+            m.compute(pos, E, F)
+            torch.cuda.synchronize()
+            m.status()
+            r["errors"] = error_stats(E.cpu().numpy(), F.cpu().numpy(), b, refs, prec)
+        m.close()
+        out[prec] = r
     return out
 
 
@@ -877,7 +912,9 @@ def run_ours(args):
     if extras:
         for key, fn in (("workload5", lambda: workload5_measurement(nnp, args.precision, 5, 3, flush, stream)),
                         ("workload2", lambda: workload2_measurement(nnp, args.precision, 1000, 10)),
-                        ("md", lambda: md_measurement(nnp, args.precision, 200, 10))):
+                        ("md", lambda: md_measurement(nnp, args.precision, 200, 10)),
+                        ("ani1x", lambda: ani1x_measurement(nnp, args, flush, stream,
+                                                            not args.no_cpu_baseline))):
             try:
                 line[key] = fn()
             except Exception as exc:  # reported in the line; the measurements above stand

@@ -47,7 +47,8 @@ typedef struct nnp_ctx* nnp_handle;
 typedef enum {
   NNP_OK = 0,
   NNP_ERR_ARG = 1,        /* bad argument (null pointer, size, layout) */
-  NNP_ERR_SPECIES = 2,    /* atomic number outside {1, 6, 7, 8, 9, 16, 17} */
+  NNP_ERR_SPECIES = 2,    /* atomic number outside the model's elements ({1, 6, 7, 8, 9, 16,
+                             17} for ANI-2x, {1, 6, 7, 8} for ANI-1x) */
   NNP_ERR_CHARGE = 3,     /* total charge != 0: the model handles neutral molecules only */
   NNP_ERR_ALLOC = 4,      /* device or host allocation failed */
   NNP_ERR_CUDA = 5,       /* a CUDA call failed; see nnp_last_error */
@@ -80,16 +81,33 @@ typedef enum {
   NNP_FP16 = 2  /* tensor cores (tcgen05), FP16 operands, FP32 accumulation */
 } nnp_precision;
 
+/* The two ANI models (Sec. 1; Sec. 3 "Extensibility with other NNPs" runs
+ * ANI-1x beside ANI-2x).  Both: radial features of 16 shifts per element,
+ * angular features of 32 per unordered element pair, layout [radial,
+ * element-major | angular, pair blocks of the row-major upper triangle, each
+ * distance-shift-major]; networks of three CELU (alpha 0.1) hidden layers and
+ * one output per element.
+ *   ANI-2x: H, C, N, O, F, S, Cl; cutoffs 5.1 / 3.5 A; 8 distance x 4 angle
+ *           shifts; 1008 features; widths H 256-192-160, C 224-192-160, N and
+ *           O 192-160-128, F, S and Cl 160-128-96.
+ *   ANI-1x: H, C, N, O; cutoffs 5.2 / 3.5 A; 4 distance x 8 angle shifts; 384
+ *           features; widths H 160-128-96, C 144-112-96, N and O 128-112-96. */
+typedef enum {
+  NNP_MODEL_ANI2X = 0,
+  NNP_MODEL_ANI1X = 1
+} nnp_model;
+
 typedef struct {
-  int32_t n_models;       /* ensemble size M >= 1 (8 for ANI-2x) */
+  int32_t n_models;       /* ensemble size M >= 1 (8 for ANI-2x and ANI-1x) */
   int32_t precision;      /* nnp_precision */
   const float* weights;   /* HOST pointer, FP32, copied at create time.  Packed
-                             [model][element H,C,N,O,F,S,Cl][W1 b1 W2 b2 W3 b3 w4 b4],
+                             [model][element, in the model's order][W1 b1 W2 b2 W3 b3 w4 b4],
                              each W row-major [out][in] */
   int64_t n_weights;      /* number of floats in weights; must equal
-                             n_models * nnp_weights_per_model() */
+                             n_models * nnp_weights_per_model_of(model) */
   double box[3];          /* 0,0,0: non-periodic; else orthorhombic periodic box edges
-                             in Angstrom (each > 2 * 5.1), minimum-image convention */
+                             in Angstrom (each more than twice the radial cutoff),
+                             minimum-image convention */
   int32_t total_charge;   /* must be 0 */
   int32_t max_neighbors;  /* radial neighbour capacity per atom; 0 = automatic */
   int32_t max_angular;    /* angular (3.5 A) neighbour capacity per atom; 0 = automatic */
@@ -103,21 +121,27 @@ typedef struct {
                              layer (default; see nnp_precision), 1 = one product */
   int32_t recompute_aev;  /* 1: the features live only between the featurizer and the first
                              layer, in the buffer that later holds dE/dG (one fewer
-                             [rows][1024]-sized buffer); the reverse pass recomputes every
+                             [rows][features]-sized buffer); the reverse pass recomputes every
                              geometric quantity from the positions either way.
                              nnp_get_features then needs an energy-only nnp_compute
                              (forces_out NULL) before it, else NNP_ERR_UNSUPPORTED */
   int32_t test_abort;     /* tests only, else 0: 1 = every tensor-core kernel starts as if
                              one of its bounded waits had given up, before it issues any
                              copy or product, so the step ends with NNP_ERR_TIMEOUT */
-  int32_t reserved[4];    /* must be zero */
+  int32_t model;          /* nnp_model (0 = ANI-2x, the zero-initialised default) */
+  int32_t reserved[3];    /* must be zero */
 } nnp_params;
 
-/* Number of FP32 parameters of one ensemble member (1,713,223). */
+/* Number of FP32 parameters of one ANI-2x ensemble member (1,713,223). */
 int64_t nnp_weights_per_model(void);
 
-/* Number of features per atom (1008). */
+/* Number of features per atom of ANI-2x (1008). */
 int32_t nnp_num_features(void);
+
+/* The same for a given nnp_model (ANI-1x: 326,660 parameters, 384 features);
+ * -1 for an unknown model. */
+int64_t nnp_weights_per_model_of(int32_t model);
+int32_t nnp_num_features_of(int32_t model);
 
 /*
  * Create a handle for one molecule / NNP region of n_atoms atoms with atomic
@@ -193,7 +217,8 @@ nnp_status nnp_get_capacity(nnp_handle h, int32_t* max_radial, int32_t* max_angu
 nnp_status nnp_get_neighbors(nnp_handle h, int32_t kind, int32_t* counts_dev, int32_t* lists_dev,
                              int32_t cap, void* stream);
 
-/* Features as the networks consumed them, widened to FP32: DEVICE [N][1008]. */
+/* Features as the networks consumed them, widened to FP32: DEVICE [N][F], F =
+ * nnp_num_features_of(the handle's model). */
 nnp_status nnp_get_features(nnp_handle h, float* features_dev, void* stream);
 
 /* Per-atom ensemble-mean energies: DEVICE FP64 [N]. */

@@ -214,7 +214,6 @@ __host__ __device__ constexpr int aev_fwd_warp_floats(int cap_r, int cap_a) {
   return 12 * kBufStride + kMeta + (3 * cap_r > 6 * cap_a ? 3 * cap_r : 6 * cap_a);
 }
 
-constexpr float kLog2e = 1.4426950408889634f;
 
 // The SFU base-2 exponential and logarithm, denormals flushed to zero (values
 // below 2^-126 only ever multiply other factors here).
@@ -229,23 +228,46 @@ __device__ __forceinline__ float lg2_ftz(float x) {
   return y;
 }
 
-// Species pair (s, t), s <= t, of each of the 28 blocks, row-major upper triangle.
-__constant__ unsigned char kBlkS[kPairBlocks] = {0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 2,
-                                                 2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 5, 5, 6};
-__constant__ unsigned char kBlkT[kPairBlocks] = {0, 1, 2, 3, 4, 5, 6, 1, 2, 3, 4, 5, 6, 2,
-                                                 3, 4, 5, 6, 3, 4, 5, 6, 4, 5, 6, 5, 6, 6};
+// b^N for a compile-time N >= 0 by repeated squaring (ceil(log2 N) squarings
+// and a multiplication per set bit).  Each rounding is unbiased, and the
+// relative error stays near N times that of b.
+template <int N> __device__ __forceinline__ float powi(float b) {
+  if constexpr (N == 0) {
+    return 1.f;
+  } else if constexpr (N == 1) {
+    return b;
+  } else {
+    const float h = powi<N / 2>(b);
+    return (N & 1) ? h * h * b : h * h;
+  }
+}
 
-// Index of the unordered species pair {s, t} in the row-major upper triangle.
-__device__ __forceinline__ int pair_block(int s, int t) {
+// Species pair (s, t), s <= t, of each block, row-major upper triangle: the
+// 28 blocks of seven elements, then the 10 of four.
+__constant__ unsigned char kBlkS[kPairBlocks + 10] = {0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 3,
+                                                      3, 3, 3, 4, 4, 4, 5, 5, 6, 0, 0, 0, 0, 1, 1, 1, 2, 2, 3};
+__constant__ unsigned char kBlkT[kPairBlocks + 10] = {0, 1, 2, 3, 4, 5, 6, 1, 2, 3, 4, 5, 6, 2, 3, 4, 5, 6, 3,
+                                                      4, 5, 6, 4, 5, 6, 5, 6, 6, 0, 1, 2, 3, 1, 2, 3, 2, 3, 3};
+template <int NS> __device__ __forceinline__ int blk_s(int b) {
+  static_assert(NS == 7 || NS == 4, "tables of seven and of four elements");
+  return kBlkS[(NS == 7 ? 0 : kPairBlocks) + b];
+}
+template <int NS> __device__ __forceinline__ int blk_t(int b) {
+  return kBlkT[(NS == 7 ? 0 : kPairBlocks) + b];
+}
+
+// Index of the unordered species pair {s, t} in the row-major upper triangle
+// of NS elements.
+template <int NS> __device__ __forceinline__ int pair_block(int s, int t) {
   const int a = min(s, t), b = max(s, t);
-  return a * kSpecies - (a * (a - 1)) / 2 + (b - a);
+  return a * NS - (a * (a - 1)) / 2 + (b - a);
 }
 
 // Element groups of an element-sorted angular neighbour list and the prefix
 // of the block-major pair enumeration, each block padded to a multiple of 4
-// pairs (the padding pairs contribute zero).  cnt_s: on lanes 0..6 the size
-// of element group s.  Writes gs[7] (group starts), gn[7] (sizes), bpre[29]
-// (first pair of each block, bpre[28] = padded number of pairs) and for each
+// pairs (the padding pairs contribute zero).  cnt_s: on lanes 0..NS-1 the size
+// of element group s.  Writes gs[NS] (group starts), gn[NS] (sizes), bpre[NP+1]
+// (first pair of each block, bpre[NP] = padded number of pairs) and for each
 // block its decode record: bm[b] = (row width W, first list position of the
 // j group, of the k group, pairs), be[b] = (n for a same-element block, else
 // 0; bits of 1/W).  A block of two elements is a rectangle: pair l is (row
@@ -254,8 +276,10 @@ __device__ __forceinline__ int pair_block(int s, int t) {
 // row a holds the n-1-a pairs (a, a+1..) followed by the pairs of row
 // n-1-a (n even) or n-2-a (n odd), so that every row has W pairs.  Call with
 // the whole warp, then __syncwarp before reading.
+template <int NS>
 __device__ __forceinline__ void angular_blocks(int cnt_s, int lane, int* gs, int* gn, int* bpre,
                                                int4* bm, int2* be) {
+  constexpr int NP = NS * (NS + 1) / 2;
   const unsigned FULL = 0xffffffffu;
   int start = cnt_s;
 #pragma unroll
@@ -264,15 +288,15 @@ __device__ __forceinline__ void angular_blocks(int cnt_s, int lane, int* gs, int
     if (lane >= o) start += v;
   }
   start -= cnt_s;
-  if (lane < kSpecies) {
+  if (lane < NS) {
     gs[lane] = start;
     gn[lane] = cnt_s;
   }
-  const int bs = lane < kPairBlocks ? kBlkS[lane] : 0, bt = lane < kPairBlocks ? kBlkT[lane] : 0;
+  const int bs = lane < NP ? blk_s<NS>(lane) : 0, bt = lane < NP ? blk_t<NS>(lane) : 0;
   const int ns = __shfl_sync(FULL, cnt_s, bs), nt = __shfl_sync(FULL, cnt_s, bt);
   const int gss = __shfl_sync(FULL, start, bs), gst = __shfl_sync(FULL, start, bt);
-  const int size = lane < kPairBlocks ? (bs == bt ? ns * (ns - 1) / 2 : ns * nt) : 0;
-  if (lane < kPairBlocks) {
+  const int size = lane < NP ? (bs == bt ? ns * (ns - 1) / 2 : ns * nt) : 0;
+  if (lane < NP) {
     const int w = bs == bt ? ((ns & 1) ? ns : ns - 1) : nt;
     const int wd = w > 0 ? w : 1;
     bm[lane] = make_int4(wd, gss, gst, size);
@@ -284,7 +308,7 @@ __device__ __forceinline__ void angular_blocks(int cnt_s, int lane, int* gs, int
     const int v = __shfl_up_sync(FULL, incl, o);
     if (lane >= o) incl += v;
   }
-  if (lane < kPairBlocks) bpre[lane + 1] = incl;
+  if (lane < NP) bpre[lane + 1] = incl;
   if (lane == 0) bpre[0] = 0;
 }
 
@@ -292,12 +316,13 @@ __device__ __forceinline__ void angular_blocks(int cnt_s, int lane, int* gs, int
 // positions j < k of its two neighbours, or j = -1 for a padding pair.
 // b0: the block holding the warp's first pair of this iteration, base: that
 // pair (the iteration covers base .. base + 31).
+template <int NP>
 __device__ __forceinline__ int decode_block_pair(int P, int b0, int base, const int* bpre, const int4* bm,
                                                  const int2* be, int& j, int& k) {
   // the last block starting at or before P among those starting in the
   // iteration's window (a uniform walk over the window's few block starts)
   int b = b0;
-  for (int bb = b0 + 1; bb < kPairBlocks && bpre[bb] < base + 32; ++bb) b = bpre[bb] <= P ? bb : b;
+  for (int bb = b0 + 1; bb < NP && bpre[bb] < base + 32; ++bb) b = bpre[bb] <= P ? bb : b;
   const int l = P - bpre[b];
   const int4 m = bm[b];  // W, j-group start, k-group start, pairs
   const int2 e = be[b];  // n (same-element block) or 0, 1/W
@@ -336,10 +361,14 @@ __device__ __forceinline__ int decode_block_pair(int P, int b0, int base, const 
 // contiguous run of pairs, accumulated once and written once; padded to a
 // multiple of 4 pairs, every run starts 16-byte aligned in the factor rows.
 // With kSplit each feature v is written as hi = round(v) in the row's first
-// 1024 columns and lo = round(v - hi) in the next 1024 (16-bit outputs).
-template <typename TOut, bool kSplit = false>
+// kPad columns and lo = round(v - hi) in the next kPad (16-bit outputs).
+// Shape: the model's elements and angular grid (NA distance x NZ angle
+// shifts, NA x NZ = 32 features per block).
+template <typename TOut, bool kSplit, typename Shape>
 __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __restrict__ row_of_int,
                       TOut* __restrict__ out) {
+  constexpr int NS = Shape::NS, NA = Shape::NA, NZ = Shape::NZ, NP = Shape::kNP;
+  constexpr int kRad = Shape::kRad, kFeat = Shape::kFeat, kPad = Shape::kPad;
   extern __shared__ __align__(16) float smem[];
   const unsigned FULL = 0xffffffffu;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -350,7 +379,7 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
   asm volatile("griddepcontrol.wait;" ::: "memory");  // neighbour lists of the kernel before
   if (q >= g.n_atoms) return;  // warp-uniform; no block-level barriers below
   float* buf = smem + (size_t)warp * aev_fwd_warp_floats(nl.cap_r, nl.cap_a);  // [12][36]
-  float* R2 = buf;                                       // [2][112], radial phase only
+  float* R2 = buf;                                       // [2][kRad], radial phase only
   int* bpre = reinterpret_cast<int*>(buf + 12 * kBufStride);  // [29] block prefix
   int4* bm = reinterpret_cast<int4*>(bpre + 32);         // [28] block decode records
   int2* be = reinterpret_cast<int2*>(bm + kPairBlocks);  // [28]
@@ -363,14 +392,14 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
   float4* avec = reinterpret_cast<float4*>(U);
   float* afc = reinterpret_cast<float*>(avec + nl.cap_a);
   int* asp = reinterpret_cast<int*>(afc + nl.cap_a);
-  TOut* dst = out + (size_t)row_of_int[q] * (kSplit ? 2 : 1) * kFeaturesPad;
+  TOut* dst = out + (size_t)row_of_int[q] * (kSplit ? 2 : 1) * kPad;
   auto put = [&](int f, float v) {
     const TOut hi = cvt_out<TOut>(v);
     dst[f] = hi;
-    if (kSplit) dst[kFeaturesPad + f] = cvt_out<TOut>(v - to_float(hi));
+    if (kSplit) dst[kPad + f] = cvt_out<TOut>(v - to_float(hi));
   };
 
-  for (int f = lane; f < 2 * kRadial; f += 32) R2[f] = 0.f;
+  for (int f = lane; f < 2 * kRad; f += 32) R2[f] = 0.f;
   const float4 xi = g.pos[q];
 
   // ---- radial: stage the neighbours (lane-parallel loads), then lane =
@@ -390,20 +419,21 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
   __syncwarp();
   {
     const int half = lane >> 4, k = lane & 15;
-    const float shs = c.ShfRs[k];
-    float* acc = R2 + half * kRadial;
+    const float shs = c.ShfRs[k], shsl = c.ShfRsl[k];
+    float* acc = R2 + half * kRad;
     for (int t = half; t < nr; t += 2) {
-      const float y = fmaf(rd[t], c.sqEtaR, -shs);  // exp(-EtaR (r - ShfR)^2) = 2^(-y^2)
+      // exp(-EtaR (r - ShfR)^2) = 2^(-y^2), constants as hi + lo pairs
+      const float y = fmaf(rd[t], c.sqEtaR, -shs) + fmaf(rd[t], c.sqEtaRl, -shsl);
       acc[rsp[t] * kShfR + k] += ex2_ftz(-y * y) * rfc[t];
     }
   }
   __syncwarp();
-  for (int f = lane; f < kRadial; f += 32) put(f, R2[f] + R2[kRadial + f]);
+  for (int f = lane; f < kRad; f += 32) put(f, R2[f] + R2[kRad + f]);
   __syncwarp();  // R2 and the radial staging are dead from here on
 
   // ---- angular staging and the element groups of the list ----
   const int na = min(nl.cnt_a[q], nl.cap_a);
-  int cnt_s = 0;  // lane s < 7: size of element group s
+  int cnt_s = 0;  // lane s < NS: size of element group s
   {
     const int* la = nl.nbr_a + (size_t)q * nl.cap_a;
     for (int base = 0; base < na; base += 32) {
@@ -419,30 +449,30 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
         asp[t] = sp;
       }
 #pragma unroll
-      for (int e = 0; e < kSpecies; ++e) {
+      for (int e = 0; e < NS; ++e) {
         const int n_e = __popc(__ballot_sync(FULL, sp == e));
         if (lane == e) cnt_s += n_e;
       }
     }
   }
-  angular_blocks(cnt_s, lane, gs, gn, bpre, bm, be);
+  angular_blocks<NS>(cnt_s, lane, gs, gn, bpre, bm, be);
   __syncwarp();
-  const int T = bpre[kPairBlocks];
+  const int T = bpre[NP];
 
   // ---- angular, 32 neighbour pairs at a time ----
-  const int fa = lane >> 2, fz = lane & 3;
+  const int fa = lane / NZ, fz = lane % NZ;
   float acc = 0.f;
   int pcur = -1;  // block being accumulated; blocks before it are written
   int b0 = 0;  // block holding the iteration's first pair
   for (int base = 0; base < T; base += 32) {
-    while (bpre[b0 + 1] <= base) ++b0;  // uniform; bpre[28] = T > base
+    while (bpre[b0 + 1] <= base) ++b0;  // uniform; bpre[NP] = T > base
     const int P = base + lane;
     const bool valid = P < T;
     int pl = -1;
     if (valid) {
-      // phase 1: this lane's pair -> 8 distance factors, 4 angle factors
+      // phase 1: this lane's pair -> NA distance factors, NZ angle factors
       int j, k;
-      const int b = decode_block_pair(P, b0, base, bpre, bm, be, j, k);
+      const int b = decode_block_pair<NP>(P, b0, base, bpre, bm, be, j, k);
       if (j >= 0) {
         const float4 rj = avec[j], rk = avec[k];
         const float cost = __fdividef(rj.x * rk.x + rj.y * rk.y + rj.z * rk.z, rj.w * rk.w);
@@ -451,24 +481,29 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
         const float fcjk = 2.f * afc[j] * afc[k];
         const float u = 0.5f * (rj.w + rk.w);
 #pragma unroll
-        for (int a = 0; a < kShfA; ++a) {
-          const float y = fmaf(u, c.sqEtaA, -c.ShfAs[a]);  // 2^(-y^2) = exp(-EtaA (u - ShfA)^2)
+        for (int a = 0; a < NA; ++a) {
+          // 2^(-y^2) = exp(-EtaA (u - ShfA)^2)
+          const float y = fmaf(u, c.sqEtaA, -c.ShfAs[a]) + fmaf(u, c.sqEtaAl, -c.ShfAsl[a]);
           buf[a * kBufStride + lane] = ex2_ftz(-y * y);
         }
 #pragma unroll
-        for (int z = 0; z < kShfZ; ++z) {
-          // t = 1 + cos(theta' - ThetaS): ((1 + cos) / 2)^Zeta = 2^(Zeta (lg2 t - 1))
+        for (int z = 0; z < NZ; ++z) {
+          // t = 1 + cos(theta' - ThetaS): ((1 + cos) / 2)^Zeta = 2^(Zeta (lg2 t - 1)),
+          // or (t / 2)^Zeta by multiplication for an integer Zeta
           const float t = fmaxf(fmaf(sp, c.sinZ[z], fmaf(cp, c.cosZ[z], 1.f)), 0.f);
-          buf[(kShfA + z) * kBufStride + lane] = ex2_ftz(fmaf(c.Zeta, lg2_ftz(t), -c.Zeta)) * fcjk;
+          float A;
+          if constexpr (Shape::kZetaInt > 0) A = powi<Shape::kZetaInt>(0.5f * t);
+          else A = ex2_ftz(fmaf(c.Zeta, lg2_ftz(t), -c.Zeta));
+          buf[(NA + z) * kBufStride + lane] = A * fcjk;
         }
       } else {  // padding pair: zero factors
 #pragma unroll
-        for (int f = 0; f < kShfA + kShfZ; ++f) buf[f * kBufStride + lane] = 0.f;
+        for (int f = 0; f < NA + NZ; ++f) buf[f * kBufStride + lane] = 0.f;
       }
       pl = b;
     } else {  // past the last pair: zero factors, so phase 2 can walk all 8 groups
 #pragma unroll
-      for (int f = 0; f < kShfA + kShfZ; ++f) buf[f * kBufStride + lane] = 0.f;
+      for (int f = 0; f < NA + NZ; ++f) buf[f * kBufStride + lane] = 0.f;
     }
     // phase 2: lane = feature (a, z).  Blocks are padded to multiples of 4
     // pairs, so each group of 4 pairs lies in one block: walk the 8 groups
@@ -478,14 +513,14 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
     const unsigned starts = __ballot_sync(FULL, valid && (lane == 0 || prev != pl));
     __syncwarp();
     const float4* ra4 = reinterpret_cast<const float4*>(buf + fa * kBufStride);
-    const float4* za4 = reinterpret_cast<const float4*>(buf + (kShfA + fz) * kBufStride);
+    const float4* za4 = reinterpret_cast<const float4*>(buf + (NA + fz) * kBufStride);
 #pragma unroll
     for (int gi = 0; gi < 8; ++gi) {
       if ((starts >> (4 * gi)) & 1u) {
         const int p = __shfl_sync(FULL, pl, 4 * gi);
         if (p != pcur) {  // block pcur is complete: write it, and zeros for empty blocks
-          if (pcur >= 0) put(kRadial + pcur * kAngPerBlock + lane, acc);
-          for (int e = pcur + 1; e < p; ++e) put(kRadial + e * kAngPerBlock + lane, 0.f);
+          if (pcur >= 0) put(kRad + pcur * 32 + lane, acc);
+          for (int e = pcur + 1; e < p; ++e) put(kRad + e * 32 + lane, 0.f);
           acc = 0.f;
           pcur = p;
         }
@@ -498,9 +533,9 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
     }
     __syncwarp();
   }
-  if (pcur >= 0) put(kRadial + pcur * kAngPerBlock + lane, acc);
-  for (int e = pcur + 1; e < kPairBlocks; ++e) put(kRadial + e * kAngPerBlock + lane, 0.f);
-  if (lane < kFeaturesPad - kFeatures) put(kFeatures + lane, 0.f);
+  if (pcur >= 0) put(kRad + pcur * 32 + lane, acc);
+  for (int e = pcur + 1; e < NP; ++e) put(kRad + e * 32 + lane, 0.f);
+  if (lane < kPad - kFeat) put(kFeat + lane, 0.f);
 }
 
 // ---------------------------------------------------------------------------
@@ -552,11 +587,15 @@ constexpr int kAdjStage = 64;
 // accumulators in shared memory
 // (the lanes of a chunk that share the first neighbour are reduced by a
 // segmented scan first), then to the warp's FP64 accumulator of the molecule.
+template <typename Shape>
 __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborLists nl, AevConst c,
                               const int* __restrict__ row_of_int, const float* __restrict__ dG,
                               const int4* __restrict__ work, const int* __restrict__ orig,
                               double* __restrict__ F, int smem_atoms_max, int stage_cap,
                               int* __restrict__ ovf, int pass) {
+  constexpr int NS = Shape::NS, NA = Shape::NA, NZ = Shape::NZ;
+  constexpr int kRad = Shape::kRad, kFeat = Shape::kFeat, kPad = Shape::kPad;
+  static_assert(kFeat / 4 <= 8 * 32, "dE/dG row: at most 8 float4 per lane");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const unsigned FULL = 0xffffffffu;
   const int nwarps = blockDim.x >> 5;
@@ -567,7 +606,7 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
   double* accm = reinterpret_cast<double*>(smem_raw);  // [nwarps][smem_atoms_max][3]
   float* gR = reinterpret_cast<float*>(accm + (size_t)nwarps * smem_atoms_max * 3) +
               (size_t)warp * adj_warp_floats(nl.cap_r, stage_cap);
-  float* gA = gR + kSpecies * kGRStride;  // [28][36]
+  float* gA = gR + kSpecies * kGRStride;  // [NP <= 28][36]
   float4* nb = reinterpret_cast<float4*>(gA + kPairBlocks * kGAStride);  // [stage_cap][2]
   float* sg = reinterpret_cast<float*>(nb + 2 * stage_cap);                // [stage_cap][3]
   double* acc_w = smem_acc ? accm + (size_t)warp * smem_atoms_max * 3 : nullptr;
@@ -600,22 +639,24 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
       continue;
     }
     {
-      // dE/dG row: 252 float4 (1008 floats), 8 per lane, loads issued together
-      const float4* grow = reinterpret_cast<const float4*>(dG + (size_t)row_of_int[q] * kFeaturesPad);
+      // dE/dG row: kFeat / 4 float4 (252 of ANI-2x, 96 of ANI-1x), up to 8
+      // per lane, loads issued together
+      const float4* grow = reinterpret_cast<const float4*>(dG + (size_t)row_of_int[q] * kPad);
       float4 v[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int f4 = lane + 32 * i;
-        if (f4 < kFeatures / 4) v[i] = __ldg(grow + f4);
+        if (f4 < kFeat / 4) v[i] = __ldg(grow + f4);
       }
-      // 16-byte stores: radial float4 f4 < 28 is (species f4 / 4, shifts 4 (f4 % 4) ..),
-      // angular float4 f4 is (block (f4 - 28) / 8, features 4 ((f4 - 28) % 8) ..)
+      // 16-byte stores: radial float4 f4 < kRad / 4 is (species f4 / 4, shifts
+      // 4 (f4 % 4) ..), angular float4 f4 is (block (f4 - kRad / 4) / 8,
+      // features 4 ((f4 - kRad / 4) % 8) ..)
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int f4 = lane + 32 * i;
-        if (f4 >= kFeatures / 4) continue;
-        float* d = f4 < kRadial / 4 ? gR + (f4 >> 2) * kGRStride + 4 * (f4 & 3)
-                                    : gA + ((f4 - kRadial / 4) >> 3) * kGAStride + 4 * ((f4 - kRadial / 4) & 7);
+        if (f4 >= kFeat / 4) continue;
+        float* d = f4 < kRad / 4 ? gR + (f4 >> 2) * kGRStride + 4 * (f4 & 3)
+                                 : gA + ((f4 - kRad / 4) >> 3) * kGAStride + 4 * ((f4 - kRad / 4) & 7);
         *reinterpret_cast<float4*>(d) = v[i];
       }
     }
@@ -660,7 +701,7 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
           const float gk[4] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
           for (int h = 0; h < 4; ++h) {
-            const float y = fmaf(r, c.sqEtaR, -c.ShfRs[4 * k4 + h]);
+            const float y = fmaf(r, c.sqEtaR, -c.ShfRs[4 * k4 + h]) + fmaf(r, c.sqEtaRl, -c.ShfRsl[4 * k4 + h]);
             const float e = ex2_ftz(-y * y);  // exp(-EtaR (r - ShfR)^2)
             dEdr = fmaf(gk[h] * e, fmaf(afc, y, dfc), dEdr);
           }
@@ -687,7 +728,7 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
         fold_pair(P, na, fw, inv_fw, j, k);
         const float4 uj = nb[2 * j], uk = nb[2 * k];  // unit vectors, distances
         const float4 pj = nb[2 * j + 1], pk = nb[2 * k + 1];  // fc, dfc/dr, 1 / r, species
-        const int b = pair_block(__float_as_int(pj.w), __float_as_int(pk.w));
+        const int b = pair_block<NS>(__float_as_int(pj.w), __float_as_int(pk.w));
         const float cost = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
         const float cp = 0.95f * cost;
         const float sp = sqrtf(fmaxf(1.f - cp * cp, 1e-12f));
@@ -698,30 +739,37 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
         // V = sum_a R_a sum_z g[a][z] A_z with R_a = exp(-EtaA (u - ShfA[a])^2)
         // = 2^(-y_a^2), y_a = sqEtaA (u - ShfA[a]), u = rjk / 2: the distance sums first,
         // GR[z] = sum_a R_a g[a][z] and GY[z] = sum_a y_a R_a g[a][z]
-        float GR[kShfZ] = {0.f, 0.f, 0.f, 0.f}, GY[kShfZ] = {0.f, 0.f, 0.f, 0.f};
+        float GR[NZ], GY[NZ];
 #pragma unroll
-        for (int a = 0; a < kShfA; ++a) {
-          const float y = fmaf(rjk, c.hsqEtaA, -c.ShfAs[a]);
+        for (int z = 0; z < NZ; ++z) GR[z] = GY[z] = 0.f;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+          const float y = fmaf(rjk, c.hsqEtaA, -c.ShfAs[a]) + fmaf(rjk, c.hsqEtaAl, -c.ShfAsl[a]);
           const float R = ex2_ftz(-y * y);
           const float yR = y * R;
-          const float4 g4 = gp[a];  // g[a][0..3]
-          GR[0] = fmaf(R, g4.x, GR[0]);
-          GR[1] = fmaf(R, g4.y, GR[1]);
-          GR[2] = fmaf(R, g4.z, GR[2]);
-          GR[3] = fmaf(R, g4.w, GR[3]);
-          GY[0] = fmaf(yR, g4.x, GY[0]);
-          GY[1] = fmaf(yR, g4.y, GY[1]);
-          GY[2] = fmaf(yR, g4.z, GY[2]);
-          GY[3] = fmaf(yR, g4.w, GY[3]);
+#pragma unroll
+          for (int z4 = 0; z4 < NZ / 4; ++z4) {
+            const float4 g4 = gp[a * (NZ / 4) + z4];  // g[a][4 z4 .. 4 z4 + 3]
+            GR[4 * z4 + 0] = fmaf(R, g4.x, GR[4 * z4 + 0]);
+            GR[4 * z4 + 1] = fmaf(R, g4.y, GR[4 * z4 + 1]);
+            GR[4 * z4 + 2] = fmaf(R, g4.z, GR[4 * z4 + 2]);
+            GR[4 * z4 + 3] = fmaf(R, g4.w, GR[4 * z4 + 3]);
+            GY[4 * z4 + 0] = fmaf(yR, g4.x, GY[4 * z4 + 0]);
+            GY[4 * z4 + 1] = fmaf(yR, g4.y, GY[4 * z4 + 1]);
+            GY[4 * z4 + 2] = fmaf(yR, g4.z, GY[4 * z4 + 2]);
+            GY[4 * z4 + 3] = fmaf(yR, g4.w, GY[4 * z4 + 3]);
+          }
         }
         // angle factors, t = 2b = 1 + cp cosZ + sp sinZ: A = 2 b^Zeta = t pz
         // with pz = b^(Zeta-1) = 2^((Zeta-1)(lg2 t - 1)); dA/dcp = Zeta pz
         // (cosZ - cp/sp sinZ), Zeta applied once below
         float V = 0.f, dVdc = 0.f, dVdu = 0.f;
 #pragma unroll
-        for (int z = 0; z < kShfZ; ++z) {
+        for (int z = 0; z < NZ; ++z) {
           const float t = fmaxf(fmaf(sp, c.sinZ[z], fmaf(cp, c.cosZ[z], 1.f)), 0.f);
-          const float pz = ex2_ftz(fmaf(c.Zeta - 1.f, lg2_ftz(t), 1.f - c.Zeta));
+          float pz;
+          if constexpr (Shape::kZetaInt > 0) pz = powi<Shape::kZetaInt - 1>(0.5f * t);
+          else pz = ex2_ftz(fmaf(c.Zeta - 1.f, lg2_ftz(t), 1.f - c.Zeta));
           const float A = t * pz;
           V = fmaf(GR[z], A, V);
           dVdu = fmaf(GY[z], A, dVdu);  // dV/du = gradA x this
@@ -836,30 +884,43 @@ size_t aev_adj_smem_bytes(int cap_r, int cap_a, int warps, int mol_atoms_smem_ma
          (size_t)warps * adj_warp_floats(cap_r, cap_a) * sizeof(float);
 }
 
-void launch_aev(const Geometry& g, const NeighborLists& nl, const AevConst& c,
-                const int* row_of_int, void* out, Prec prec, int warps, cudaStream_t s, bool split) {
-  if (g.n_atoms <= 0) return;
+namespace {
+template <typename Shape>
+void launch_aev_shape(const Geometry& g, const NeighborLists& nl, const AevConst& c, const int* row_of_int,
+                      void* out, Prec prec, int warps, cudaStream_t s, bool split) {
   const int blocks = (g.n_atoms + warps - 1) / warps;
   const size_t smem = aev_fwd_smem_bytes(nl.cap_r, nl.cap_a, warps);
   switch (prec) {
     case Prec::F32:
-      launch_pdl(k_aev<float>, blocks, warps * 32, smem, s, g, nl, c, row_of_int, (float*)out);
+      launch_pdl(k_aev<float, false, Shape>, blocks, warps * 32, smem, s, g, nl, c, row_of_int, (float*)out);
       break;
     case Prec::BF16:
       if (split)
-        launch_pdl(k_aev<__nv_bfloat16, true>, blocks, warps * 32, smem, s, g, nl, c, row_of_int,
+        launch_pdl(k_aev<__nv_bfloat16, true, Shape>, blocks, warps * 32, smem, s, g, nl, c, row_of_int,
                    (__nv_bfloat16*)out);
       else
-        launch_pdl(k_aev<__nv_bfloat16>, blocks, warps * 32, smem, s, g, nl, c, row_of_int,
+        launch_pdl(k_aev<__nv_bfloat16, false, Shape>, blocks, warps * 32, smem, s, g, nl, c, row_of_int,
                    (__nv_bfloat16*)out);
       break;
     case Prec::F16:
       if (split)
-        launch_pdl(k_aev<__half, true>, blocks, warps * 32, smem, s, g, nl, c, row_of_int, (__half*)out);
+        launch_pdl(k_aev<__half, true, Shape>, blocks, warps * 32, smem, s, g, nl, c, row_of_int,
+                   (__half*)out);
       else
-        launch_pdl(k_aev<__half>, blocks, warps * 32, smem, s, g, nl, c, row_of_int, (__half*)out);
+        launch_pdl(k_aev<__half, false, Shape>, blocks, warps * 32, smem, s, g, nl, c, row_of_int,
+                   (__half*)out);
       break;
   }
+}
+}  // namespace
+
+void launch_aev(const Geometry& g, const NeighborLists& nl, const AevConst& c,
+                const int* row_of_int, void* out, Prec prec, int warps, cudaStream_t s, bool split) {
+  if (g.n_atoms <= 0) return;
+  if (c.model == 1)
+    launch_aev_shape<ShapeANI1x>(g, nl, c, row_of_int, out, prec, warps, s, split);
+  else
+    launch_aev_shape<ShapeANI2x>(g, nl, c, row_of_int, out, prec, warps, s, split);
 }
 
 int aev_adj_stage_cap(int cap_a) { return cap_a < kAdjStage ? cap_a : kAdjStage; }
@@ -879,7 +940,8 @@ void launch_aev_adjoint(const Geometry& g, const NeighborLists& nl, const AevCon
   if (n_work <= 0) return;
   const int stage = aev_adj_stage_cap(nl.cap_a);
   // ovf[0] was zeroed at the start of the step
-  launch_pdl(k_aev_adjoint, n_work, warps * 32, aev_adj_smem_bytes(nl.cap_r, stage, warps, mol_atoms_smem_max),
+  auto kern = c.model == 1 ? k_aev_adjoint<ShapeANI1x> : k_aev_adjoint<ShapeANI2x>;
+  launch_pdl(kern, n_work, warps * 32, aev_adj_smem_bytes(nl.cap_r, stage, warps, mol_atoms_smem_max),
              s, g, nl, c, row_of_int, dG, work, orig, F, mol_atoms_smem_max, stage, ovf, 0);
   if (stage < nl.cap_a) {  // two CTAs per SM: dense systems defer most centres; an empty pass is cheap
     static int sms = 0;
@@ -889,7 +951,7 @@ void launch_aev_adjoint(const Geometry& g, const NeighborLists& nl, const AevCon
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (sms <= 0) sms = 152;
     }
-    k_aev_adjoint<<<2 * sms, warps * 32, aev_adj_smem_bytes(nl.cap_r, nl.cap_a, warps, 0), s>>>(
+    kern<<<2 * sms, warps * 32, aev_adj_smem_bytes(nl.cap_r, nl.cap_a, warps, 0), s>>>(
         g, nl, c, row_of_int, dG, work, orig, F, 0, nl.cap_a, ovf, 1);
   }
 }
@@ -904,21 +966,25 @@ cudaError_t aev_set_smem_limits(size_t fwd_bytes, size_t adj_bytes) {
   std::lock_guard<std::mutex> lock(mu);
   fwd_bytes = fwd_max = fwd_bytes > fwd_max ? fwd_bytes : fwd_max;
   adj_bytes = adj_max = adj_bytes > adj_max ? adj_bytes : adj_max;
-  cudaError_t e;
-  e = cudaFuncSetAttribute(k_aev<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_bytes);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_aev<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)fwd_bytes);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_aev<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_bytes);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_aev<__nv_bfloat16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)fwd_bytes);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_aev<__half, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_aev_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)adj_bytes);
+  const void* fwd[] = {(const void*)k_aev<float, false, ShapeANI2x>,
+                       (const void*)k_aev<__nv_bfloat16, false, ShapeANI2x>,
+                       (const void*)k_aev<__half, false, ShapeANI2x>,
+                       (const void*)k_aev<__nv_bfloat16, true, ShapeANI2x>,
+                       (const void*)k_aev<__half, true, ShapeANI2x>,
+                       (const void*)k_aev<float, false, ShapeANI1x>,
+                       (const void*)k_aev<__nv_bfloat16, false, ShapeANI1x>,
+                       (const void*)k_aev<__half, false, ShapeANI1x>,
+                       (const void*)k_aev<__nv_bfloat16, true, ShapeANI1x>,
+                       (const void*)k_aev<__half, true, ShapeANI1x>};
+  for (const void* f : fwd) {
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_bytes);
+    if (e != cudaSuccess) return e;
+  }
+  for (const void* f : {(const void*)k_aev_adjoint<ShapeANI2x>, (const void*)k_aev_adjoint<ShapeANI1x>}) {
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace nnp

@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(256) k_gemm_simt(const GemmProblem* __restrict
       switch (P.epi) {
         case (int)Epi::BiasCelu: {
           const float z = v + P.bias[n];
-          const float h = z > 0.f ? z : 0.1f * (expf(fminf(z, 0.f) * 10.f) - 1.f);
+          // alpha expm1(z / alpha): exp(z / alpha) - 1 would cancel for small |z|
+          const float h = z > 0.f ? z : 0.1f * expm1f(fminf(z, 0.f) * 10.f);
           st_f(static_cast<T*>(P.D) + (size_t)m * P.ldd + n, h);
           break;
         }

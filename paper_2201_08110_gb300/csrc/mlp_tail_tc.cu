@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int k = 2 * i + h;
                 const float z = v[k] + b3[k];
                 const float ex = celu01_exp(z);  // celu'(z): 1 above zero
-                yacc = fmaf(w4[k], fmaxf(z, fmaf(0.1f, ex, -0.1f)), yacc);
+                yacc = fmaf(w4[k], celu01_fast(z), yacc);
                 dv[h] = w4[k] * P.inv_m * ex;
               }
               o[i] = Pack<T>::two(dv[0], dv[1]);

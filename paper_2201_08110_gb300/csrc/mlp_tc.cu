@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int i = 0; i < 16; ++i) {
                 const float z = v[i] + b[i];
                 const float ex = celu01_exp(z);  // celu'(z): 1 above zero
-                yp = fmaf(w[i], fmaxf(z, fmaf(0.1f, ex, -0.1f)), yp);
+                yp = fmaf(w[i], celu01_fast(z), yp);
                 v[i] = w[i] * P.inv_m * ex;
               }
 #pragma unroll
@@ -277,51 +277,93 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (half == 0 && row < P.M) P.y[(size_t)row * P.ldy] = yp + ypart[r] + P.b4;
         epi_sync();  // ypart is free for the next tile
       } else {
-        const bool f32 = P.epi == (int)Epi::Store;  // else bias + CELU into T
-        const int bw = f32 ? 32 : 64;               // box columns
-        const int nbox = (n_tile + bw - 1) / bw;
-        const int nparts = (!f32 && P.d_lo > 0) ? 2 : 1;  // hi, then lo = round(v - hi)
-        for (int bx = half; bx < nbox; bx += 2)
-          for (int part = 0; part < nparts; ++part) {
+        if (P.epi == (int)Epi::Store) {
+          // dE/dG, FP32: 32-column boxes, one TMEM load each (columns past the
+          // problem's stored as zeros)
+          const int nbox = (n_tile + 31) / 32;
+          for (int bx = half; bx < nbox; bx += 2) {
             if (leader && in_flight) bulk_wait_read();  // the previous store has read stg
             half_sync();
-            for (int cc = 0; cc < bw; cc += 16) {
-              const int c = bx * bw + cc;  // column in the tile
-              float v[16];
-              if (c < n_tile) {
-                tmem_ld16(tbase + (uint32_t)c, v);
-              } else {  // past the problem's columns: zeros
+            const int c = bx * 32;
+            float v[32];
+            tmem_ld32(tbase + (uint32_t)c, v);  // c + 32 <= 256: inside the accumulator
 #pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = 0.f;
-              }
-              if (f32) {
-                put16_f32(stg, r, cc, v);
-              } else {
-                float b[16];
-                if (c < n_tile) {
-                  ldg16(P.bias + tl.n0 + c, b);
-#pragma unroll
-                  for (int i = 0; i < 16; ++i) v[i] = celu01_fast(v[i] + b[i]);
-                }
-                uint32_t o[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                  o[i] = Pack<T>::two(v[2 * i], v[2 * i + 1]);
-                  if (part)  // the rounding residual, exact in FP32
-                    o[i] = Pack<T>::two(v[2 * i] - Pack<T>::lo(o[i]), v[2 * i + 1] - Pack<T>::hi(o[i]));
-                }
-                *reinterpret_cast<uint4*>(stg + sw128_offset(r, cc)) = make_uint4(o[0], o[1], o[2], o[3]);
-                *reinterpret_cast<uint4*>(stg + sw128_offset(r, cc + 8)) = make_uint4(o[4], o[5], o[6], o[7]);
-              }
-            }
+            for (int i = 16; i < 32; ++i)
+              if (c + 16 >= n_tile) v[i] = 0.f;
+            put16_f32(stg, r, 0, *reinterpret_cast<const float(*)[16]>(v));
+            put16_f32(stg, r, 16, *reinterpret_cast<const float(*)[16]>(v + 16));
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             half_sync();
             if (leader) {
-              tma_store_2d(&maps.d, stg, P.d_col0 + tl.n0 + bx * bw + (part ? P.d_lo : 0), P.a_row0 + tl.m0);
+              tma_store_2d(&maps.d, stg, P.d_col0 + tl.n0 + c, P.a_row0 + tl.m0);
               bulk_commit();
               in_flight = true;
             }
           }
+        } else {
+          // bias + CELU into T, 64-column boxes.  With a split output (d_lo >
+          // 0) each value is computed once: hi = round(v) goes to the box, and
+          // lo = round(v - hi) (exact in FP32 before its rounding) waits in
+          // registers until the hi box has been read, then goes out as a second
+          // box d_lo columns to the right.
+          const int nbox = (n_tile + 63) / 64;
+          const bool two = P.d_lo > 0;
+          for (int bx = half; bx < nbox; bx += 2) {
+            if (leader && in_flight) bulk_wait_read();  // the previous store has read stg
+            half_sync();
+            uint32_t lo[32];
+#pragma unroll
+            for (int h32 = 0; h32 < 2; ++h32) {
+              const int c = bx * 64 + h32 * 32;  // column in the tile
+              float v[32];
+              if (c < n_tile) tmem_ld32(tbase + (uint32_t)c, v);  // warp-uniform; c + 32 <= 256
+#pragma unroll
+              for (int q = 0; q < 2; ++q) {
+                const int cq = c + 16 * q;
+                float b[16];
+                if (cq < n_tile) {  // bias only for the problem's columns (no read past it)
+                  ldg16(P.bias + tl.n0 + cq, b);
+#pragma unroll
+                  for (int i = 0; i < 16; ++i) v[16 * q + i] = celu01_fast(v[16 * q + i] + b[i]);
+                } else {  // past the problem's columns: zeros
+#pragma unroll
+                  for (int i = 0; i < 16; ++i) v[16 * q + i] = 0.f;
+                }
+              }
+              uint32_t o[16];
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                o[i] = Pack<T>::two(v[2 * i], v[2 * i + 1]);
+                lo[16 * h32 + i] = Pack<T>::two(v[2 * i] - Pack<T>::lo(o[i]), v[2 * i + 1] - Pack<T>::hi(o[i]));
+              }
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                *reinterpret_cast<uint4*>(stg + sw128_offset(r, h32 * 32 + 8 * k)) =
+                    make_uint4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            half_sync();
+            if (leader) {
+              tma_store_2d(&maps.d, stg, P.d_col0 + tl.n0 + bx * 64, P.a_row0 + tl.m0);
+              bulk_commit();
+              in_flight = true;
+            }
+            if (two) {
+              if (leader) bulk_wait_read();  // the hi box has been read
+              half_sync();
+#pragma unroll
+              for (int k = 0; k < 8; ++k)
+                *reinterpret_cast<uint4*>(stg + sw128_offset(r, 8 * k)) =
+                    make_uint4(lo[4 * k], lo[4 * k + 1], lo[4 * k + 2], lo[4 * k + 3]);
+              asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+              half_sync();
+              if (leader) {
+                tma_store_2d(&maps.d, stg, P.d_col0 + tl.n0 + bx * 64 + P.d_lo, P.a_row0 + tl.m0);
+                bulk_commit();
+              }
+            }
+          }
+        }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();

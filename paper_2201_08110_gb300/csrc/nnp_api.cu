@@ -87,6 +87,7 @@ struct nnp_ctx {
   int aev_aliased = 0;     // the features share their buffer with dE/dG
   bool features_overwritten = false;  // the last step's reverse pass wrote over the features
   int test_abort = 0;
+  ModelDesc md{};  // the model: elements, feature layout, network widths
   AevConst aevc{};
   int elem_count[kSpecies] = {0};
   int elem_row0[kSpecies + 1] = {0};
@@ -191,38 +192,63 @@ cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
 }
 
-void init_aev_const(AevConst& c, const double box[3]) {
+// ANI-2x (model 0): cutoffs 5.1 / 3.5 A, EtaR 19.7, EtaA 12.5, Zeta 14.1, shift
+// grids as closed linspaces (radial 0.8 .. 4.9 A in 16, angular distance
+// 0.8 .. 3.1 A in 8, angle 0.39 .. 2.75 rad in 4).  ANI-1x (model 1): 5.2 /
+// 3.5 A, EtaR 16, EtaA 8, Zeta 32, radial shifts 0.9 + 0.26875 k A (16),
+// angular distance shifts 0.9 + 0.65 a A (4), angle shifts pi/16 + z pi/8 (8).
+// Both: the featurizer functions of Sec. 1 (ANI's modified Behler-Parrinello
+// symmetry functions).
+void init_aev_const(AevConst& c, const double box[3], int model) {
   std::memset(&c, 0, sizeof(c));
-  c.Rcr = 5.1f;
+  const bool x1 = model == 1;
+  const int ns = x1 ? 4 : kSpecies, na = x1 ? 4 : 8, nz = x1 ? 8 : 4;
+  c.model = x1 ? 1 : 0;
+  c.Rcr = x1 ? 5.2f : 5.1f;
   c.Rca = 3.5f;
   c.Rcr2 = c.Rcr * c.Rcr;
   c.Rca2 = c.Rca * c.Rca;
   c.Rcr2d = (double)c.Rcr * (double)c.Rcr;
   c.Rca2d = (double)c.Rca * (double)c.Rca;
-  c.EtaR = 19.7f;
-  c.EtaA = 12.5f;
-  c.Zeta = 14.1f;
-  for (int k = 0; k < kShfR; ++k) c.ShfR[k] = (float)(0.8 + (4.9 - 0.8) * k / (kShfR - 1));
-  for (int k = 0; k < kShfA; ++k) c.ShfA[k] = (float)(0.8 + (3.1 - 0.8) * k / (kShfA - 1));
-  for (int k = 0; k < kShfZ; ++k) {
-    const double z = 0.39 + (2.75 - 0.39) * k / (kShfZ - 1);
+  c.EtaR = x1 ? 16.f : 19.7f;
+  c.EtaA = x1 ? 8.f : 12.5f;
+  c.Zeta = x1 ? (float)ShapeANI1x::kZetaInt : 14.1f;  // the ANI-1x kernels raise to 32 by multiplication
+  const double pi = 3.14159265358979323846;
+  double shr[kShfR], sha[kMaxShfA];
+  for (int k = 0; k < kShfR; ++k) shr[k] = x1 ? 0.9 + 0.26875 * k : 0.8 + (4.9 - 0.8) * k / (kShfR - 1);
+  for (int k = 0; k < na; ++k) sha[k] = x1 ? 0.9 + 0.65 * k : 0.8 + (3.1 - 0.8) * k / (na - 1);
+  for (int k = 0; k < kShfR; ++k) c.ShfR[k] = (float)shr[k];
+  for (int k = 0; k < na; ++k) c.ShfA[k] = (float)sha[k];
+  for (int k = 0; k < nz; ++k) {
+    const double z = x1 ? pi / 16.0 + k * pi / 8.0 : 0.39 + (2.75 - 0.39) * k / (nz - 1);
     c.cosZ[k] = (float)std::cos(z);
     c.sinZ[k] = (float)std::sin(z);
   }
   const double log2e = 1.4426950408889634;
   const double sqR = std::sqrt((double)c.EtaR * log2e), sqA = std::sqrt((double)c.EtaA * log2e);
-  c.sqEtaR = (float)sqR;
-  c.sqEtaA = (float)sqA;
-  for (int k = 0; k < kShfR; ++k) c.ShfRs[k] = (float)(sqR * (double)c.ShfR[k]);
-  for (int k = 0; k < kShfA; ++k) c.ShfAs[k] = (float)(sqA * (double)c.ShfA[k]);
+  auto hi = [](double v) { return (float)v; };
+  auto lo = [](double v) { return (float)(v - (double)(float)v); };
+  c.sqEtaR = hi(sqR);
+  c.sqEtaRl = lo(sqR);
+  c.sqEtaA = hi(sqA);
+  c.sqEtaAl = lo(sqA);
+  for (int k = 0; k < kShfR; ++k) {
+    c.ShfRs[k] = hi(sqR * shr[k]);
+    c.ShfRsl[k] = lo(sqR * shr[k]);
+  }
+  for (int k = 0; k < na; ++k) {
+    c.ShfAs[k] = hi(sqA * sha[k]);
+    c.ShfAsl[k] = lo(sqA * sha[k]);
+  }
   c.gradR = (float)(-2.0 * (double)c.EtaR / sqR);
   c.gradA = (float)(-2.0 * (double)c.EtaA / sqA);
-  c.hsqEtaA = (float)(0.5 * sqA);
+  c.hsqEtaA = 0.5f * c.sqEtaA;  // exact halving of the pair
+  c.hsqEtaAl = 0.5f * c.sqEtaAl;
   c.hgradA = (float)(-(double)c.EtaA / sqA);
   c.dcosA = (float)(0.95 * (double)c.Zeta);
   int p = 0;
-  for (int s = 0; s < kSpecies; ++s)
-    for (int t = s; t < kSpecies; ++t) {
+  for (int s = 0; s < ns; ++s)
+    for (int t = s; t < ns; ++t) {
       c.pair_index[s][t] = p;
       c.pair_index[t][s] = p;
       ++p;
@@ -234,14 +260,16 @@ void init_aev_const(AevConst& c, const double box[3]) {
   }
 }
 
-long element_params(int e) {
-  const long n0 = kFeatures, n1 = kHidden[e][0], n2 = kHidden[e][1], n3 = kHidden[e][2];
+// Parameters of one element's network in the caller's weight layout: W1
+// [h1][nfeat], b1, W2 [h2][h1], b2, W3 [h3][h2], b3, w4 [h3], b4.
+long element_params(const ModelDesc& md, int e) {
+  const long n0 = md.nfeat, n1 = md.hidden[e][0], n2 = md.hidden[e][1], n3 = md.hidden[e][2];
   return n1 * n0 + n1 + n2 * n1 + n2 + n3 * n2 + n3 + n3 + 1;
 }
 
-long model_params() {
+long model_params(const ModelDesc& md) {
   long s = 0;
-  for (int e = 0; e < kSpecies; ++e) s += element_params(e);
+  for (int e = 0; e < md.ns; ++e) s += element_params(md, e);
   return s;
 }
 
@@ -331,7 +359,36 @@ void add_tiles(Layer& L, int bm, int bn) {
 
 namespace nnp {
 // The featurizer constants, for other translation units of the library.
-void aev_constants(AevConst& c, const double box[3]) { init_aev_const(c, box); }
+void aev_constants(AevConst& c, const double box[3], int model) { init_aev_const(c, box, model); }
+
+// ANI-2x: H, C, N, O, F, S, Cl; widths H 256-192-160, C 224-192-160, N and O
+// 192-160-128, F, S and Cl 160-128-96.  ANI-1x: H, C, N, O; widths H
+// 160-128-96, C 144-112-96, N and O 128-112-96 (device widths C 160-128-96,
+// N and O 128-128-96).
+bool model_desc(int id, ModelDesc& md) {
+  std::memset(&md, 0, sizeof(md));
+  static const int z7[7] = {1, 6, 7, 8, 9, 16, 17};
+  static const int h2x[7][3] = {{256, 192, 160}, {224, 192, 160}, {192, 160, 128}, {192, 160, 128},
+                                {160, 128, 96},  {160, 128, 96},  {160, 128, 96}};
+  static const int h1x[4][3] = {{160, 128, 96}, {144, 112, 96}, {128, 112, 96}, {128, 112, 96}};
+  if (id != 0 && id != 1) return false;
+  md.id = id;
+  md.ns = id == 1 ? 4 : 7;
+  md.na = id == 1 ? 4 : 8;
+  md.nz = 32 / md.na;
+  md.nfeat = id == 1 ? ShapeANI1x::kFeat : ShapeANI2x::kFeat;
+  md.kpad = id == 1 ? ShapeANI1x::kPad : ShapeANI2x::kPad;
+  md.Rcr = id == 1 ? 5.2f : 5.1f;
+  md.Rca = 3.5f;
+  for (int e = 0; e < md.ns; ++e) {
+    md.z[e] = z7[e];
+    for (int l = 0; l < 3; ++l) {
+      md.hidden[e][l] = id == 1 ? h1x[e][l] : h2x[e][l];
+      md.hpad[e][l] = (md.hidden[e][l] + 31) / 32 * 32;
+    }
+  }
+  return true;
+}
 }  // namespace nnp
 
 namespace {
@@ -442,8 +499,18 @@ nnp_status set_l1_tiles(nnp_ctx* h, int bn) {
 
 extern "C" {
 
-int64_t nnp_weights_per_model(void) { return model_params(); }
-int32_t nnp_num_features(void) { return kFeatures; }
+int64_t nnp_weights_per_model(void) { return nnp_weights_per_model_of(NNP_MODEL_ANI2X); }
+int32_t nnp_num_features(void) { return nnp_num_features_of(NNP_MODEL_ANI2X); }
+
+int64_t nnp_weights_per_model_of(int32_t model) {
+  ModelDesc md;
+  return model_desc(model, md) ? model_params(md) : -1;
+}
+
+int32_t nnp_num_features_of(int32_t model) {
+  ModelDesc md;
+  return model_desc(model, md) ? md.nfeat : -1;
+}
 
 const char* nnp_last_error(nnp_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
@@ -498,9 +565,11 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   if (params->n_models < 1 || params->n_models > kMaxModels)
     return fail(nullptr, NNP_ERR_ARG, "n_models must be in [1, 16]");
   if (params->precision < 0 || params->precision > 2) return fail(nullptr, NNP_ERR_ARG, "bad precision");
-  if (!params->weights || params->n_weights != model_params() * params->n_models)
-    return fail(nullptr, NNP_ERR_ARG, "weights: expected n_models * nnp_weights_per_model() floats");
-  for (int r = 0; r < 4; ++r)
+  ModelDesc md;
+  if (!model_desc(params->model, md)) return fail(nullptr, NNP_ERR_ARG, "model must be 0 (ANI-2x) or 1 (ANI-1x)");
+  if (!params->weights || params->n_weights != model_params(md) * params->n_models)
+    return fail(nullptr, NNP_ERR_ARG, "weights: expected n_models * nnp_weights_per_model_of(model) floats");
+  for (int r = 0; r < 3; ++r)
     if (params->reserved[r] != 0) return fail(nullptr, NNP_ERR_ARG, "reserved fields must be zero");
   if ((params->single_pass | params->recompute_aev | params->test_abort) & ~1)
     return fail(nullptr, NNP_ERR_ARG, "single_pass, recompute_aev and test_abort must be 0 or 1");
@@ -508,14 +577,17 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
     return fail(nullptr, NNP_ERR_ARG, "neighbor_mode must be 0, 1 or 2");
   for (int i = 0; i < N; ++i) {
     const int z = Z[i];
-    if (!(z == 1 || z == 6 || z == 7 || z == 8 || z == 9 || z == 16 || z == 17))
+    bool known = false;
+    for (int e = 0; e < md.ns; ++e) known = known || md.z[e] == z;
+    if (!known)
       return fail(nullptr, NNP_ERR_SPECIES, "unsupported atomic number " + std::to_string(z) +
-                                                 " at atom " + std::to_string(i));
+                                                 " at atom " + std::to_string(i) + " for this model");
   }
   const bool periodic = params->box[0] != 0.0 || params->box[1] != 0.0 || params->box[2] != 0.0;
   if (periodic)
     for (int k = 0; k < 3; ++k)
-      if (!(params->box[k] > 2.0 * 5.1)) return fail(nullptr, NNP_ERR_ARG, "box edge must exceed 2 * 5.1 A");
+      if (!(params->box[k] > 2.0 * (double)md.Rcr))
+        return fail(nullptr, NNP_ERR_ARG, "box edge must exceed twice the radial cutoff");
   if (params->max_neighbors < 0 || params->max_angular < 0)
     return fail(nullptr, NNP_ERR_ARG, "negative capacity");
 
@@ -544,7 +616,8 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   h->split = (h->prec != Prec::F32 && !params->single_pass) ? 1 : 0;
   h->aev_aliased = params->recompute_aev;
   h->test_abort = params->test_abort;
-  init_aev_const(h->aevc, params->box);
+  h->md = md;
+  init_aev_const(h->aevc, params->box, md.id);
   for (int m = 0; m < n_mols; ++m) h->max_mol = std::max(h->max_mol, mol_offsets[m + 1] - mol_offsets[m]);
   if (h->prec != Prec::F32 && !tc_available())
     return fail(h, NNP_ERR_UNSUPPORTED, "tensor-core path needs an sm_103a device");
@@ -690,15 +763,16 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   h->ldh2 = (long)M * kH2Max;
   h->ldz3 = (long)M * kH3Max;
   const size_t R = h->n_rows;
-  // dE/dG [R][1024] FP32; with recompute_aev the features (at most as large:
-  // [R][1024] FP32 or [R][2 x 1024] 16-bit) live in the same buffer
-  CK(dalloc(&h->d_dG, R * kFeaturesPad));
-  CK(cudaMemset(h->d_dG, 0, R * kFeaturesPad * sizeof(float)));
+  // dE/dG [R][kpad] FP32; with recompute_aev the features (at most as large:
+  // [R][kpad] FP32 or [R][2 x kpad] 16-bit) live in the same buffer
+  const size_t kpad = (size_t)md.kpad;
+  CK(dalloc(&h->d_dG, R * kpad));
+  CK(cudaMemset(h->d_dG, 0, R * kpad * sizeof(float)));
   if (h->aev_aliased) {
     h->d_aev = h->d_dG;
   } else {
-    CK(cudaMalloc(&h->d_aev, R * kFeaturesPad * sp * es));
-    CK(cudaMemset(h->d_aev, 0, R * kFeaturesPad * sp * es));
+    CK(cudaMalloc(&h->d_aev, R * kpad * sp * es));
+    CK(cudaMemset(h->d_aev, 0, R * kpad * sp * es));
   }
   CK(cudaMalloc(&h->d_h1, R * h->ldh1 * es));
   CK(cudaMemset(h->d_h1, 0, R * h->ldh1 * es));
@@ -723,29 +797,33 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   CK(dalloc(&h->d_F, (size_t)N * 3));
 
   // ---- weights: pack into the product layouts ----
-  // W1  [e]: rows m*h1+o, 1024 cols         W2  [e][m]: rows o, 256 cols
+  // W1  [e]: rows m*h1+o, kpad cols         W2  [e][m]: rows o, 256 cols
   // W3  [e][m]: rows o, 192 cols            W3T [e][m]: rows (h2 index), 160 cols
-  // W2T [e][m]: rows (h1 index), 192 cols   W1T [e]: rows 1024 (feature), M*256 cols
+  // W2T [e][m]: rows (h1 index), 192 cols   W1T [e]: rows kpad (feature), M*256 cols
+  // Device widths hp (multiples of 32) may exceed the caller's widths: the
+  // extra rows and columns stay zero.
   const float* W = params->weights;
-  const long per_model = model_params();
+  const long per_model = model_params(md);
+  const int NE = md.ns;
+  const auto& hp = md.hpad;
   long eoff[kSpecies];
   {
     long a = 0;
-    for (int e = 0; e < kSpecies; ++e) {
+    for (int e = 0; e < NE; ++e) {
       eoff[e] = a;
-      a += element_params(e);
+      a += element_params(md, e);
     }
   }
   size_t rows_w1 = 0, rows_w2 = 0, rows_w3 = 0, rows_w3t = 0, rows_w2t = 0;
-  for (int e = 0; e < kSpecies; ++e) {
-    rows_w1 += (size_t)M * kHidden[e][0];
-    rows_w2 += (size_t)M * kHidden[e][1];
-    rows_w3 += (size_t)M * kHidden[e][2];
-    rows_w3t += (size_t)M * kHidden[e][1];
-    rows_w2t += (size_t)M * kHidden[e][0];
+  for (int e = 0; e < NE; ++e) {
+    rows_w1 += (size_t)M * hp[e][0];
+    rows_w2 += (size_t)M * hp[e][1];
+    rows_w3 += (size_t)M * hp[e][2];
+    rows_w3t += (size_t)M * hp[e][1];
+    rows_w2t += (size_t)M * hp[e][0];
   }
   // the forward weights of the split path hold hi | lo side by side
-  const size_t ld_w1 = (size_t)sp * kFeaturesPad, ld_w2 = (size_t)sp * kH1Max,
+  const size_t ld_w1 = (size_t)sp * kpad, ld_w2 = (size_t)sp * kH1Max,
                ld_w3 = (size_t)sp * kH2Max, ld_w3t = kH3Max, ld_w2t = kH2Max,
                ld_w1t = (size_t)M * kH1Max;
   h->w_off[0] = 0;
@@ -754,7 +832,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   h->w_off[3] = h->w_off[2] + rows_w3 * ld_w3;
   h->w_off[4] = h->w_off[3] + rows_w3t * ld_w3t;
   h->w_off[5] = h->w_off[4] + rows_w2t * ld_w2t;
-  const size_t w_total = h->w_off[5] + (size_t)kSpecies * kFeaturesPad * ld_w1t;
+  const size_t w_total = h->w_off[5] + (size_t)NE * kpad * ld_w1t;
   Packer pk{h->prec};
   pk.resize(w_total);
   size_t b1_total = rows_w1, b2_total = rows_w2, b3_total = rows_w3;
@@ -765,34 +843,36 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
       r2t[kSpecies][kMaxModels];
   {
     size_t a1 = 0, a2 = 0, a3 = 0, a3t = 0, a2t = 0;
-    for (int e = 0; e < kSpecies; ++e) {
+    for (int e = 0; e < NE; ++e) {
       r1[e] = a1;
-      a1 += (size_t)M * kHidden[e][0];
+      a1 += (size_t)M * hp[e][0];
       for (int m = 0; m < M; ++m) {
         r2[e][m] = a2;
-        a2 += kHidden[e][1];
+        a2 += hp[e][1];
         r3[e][m] = a3;
-        a3 += kHidden[e][2];
+        a3 += hp[e][2];
         r3t[e][m] = a3t;
-        a3t += kHidden[e][1];
+        a3t += hp[e][1];
         r2t[e][m] = a2t;
-        a2t += kHidden[e][0];
+        a2t += hp[e][0];
       }
     }
   }
-  for (int e = 0; e < kSpecies; ++e) {
-    const int n1 = kHidden[e][0], n2 = kHidden[e][1], n3 = kHidden[e][2];
+  const int nfeat = md.nfeat;
+  for (int e = 0; e < NE; ++e) {
+    // caller's widths n1..n3 (weight layout), device widths p1 (row stride of W1 per member)
+    const int n1 = md.hidden[e][0], n2 = md.hidden[e][1], n3 = md.hidden[e][2], p1 = hp[e][0];
     for (int m = 0; m < M; ++m) {
       const float* p = W + (size_t)m * per_model + eoff[e];
-      const float *W1 = p, *b1 = W1 + (size_t)n1 * kFeatures, *W2 = b1 + n1, *b2 = W2 + (size_t)n2 * n1,
+      const float *W1 = p, *b1 = W1 + (size_t)n1 * nfeat, *W2 = b1 + n1, *b2 = W2 + (size_t)n2 * n1,
                   *W3 = b2 + n2, *b3 = W3 + (size_t)n3 * n2, *w4p = b3 + n3, *b4p = w4p + n3;
       for (int o = 0; o < n1; ++o) {
-        for (int k = 0; k < kFeatures; ++k) {
-          const float v = W1[(size_t)o * kFeatures + k];
-          pk.set_fwd(h->w_off[0] + (r1[e] + (size_t)m * n1 + o) * ld_w1 + k, kFeaturesPad, v, h->split);
-          pk.set(h->w_off[5] + ((size_t)e * kFeaturesPad + k) * ld_w1t + (size_t)m * n1 + o, v);
+        for (int k = 0; k < nfeat; ++k) {
+          const float v = W1[(size_t)o * nfeat + k];
+          pk.set_fwd(h->w_off[0] + (r1[e] + (size_t)m * p1 + o) * ld_w1 + k, kpad, v, h->split);
+          pk.set(h->w_off[5] + ((size_t)e * kpad + k) * ld_w1t + (size_t)m * p1 + o, v);
         }
-        bias[r1[e] + (size_t)m * n1 + o] = b1[o];
+        bias[r1[e] + (size_t)m * p1 + o] = b1[o];
       }
       for (int o = 0; o < n2; ++o) {
         for (int k = 0; k < n1; ++k) {
@@ -832,23 +912,23 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   char* D3 = static_cast<char*>(h->d_d3);
   const bool tc = h->prec != Prec::F32;
   const int bm = tc ? 128 : 64;
-  for (int e = 0; e < kSpecies; ++e) {
+  for (int e = 0; e < NE; ++e) {
     const int Me = h->elem_count[e];
     if (Me == 0) continue;
-    const int n1 = kHidden[e][0], n2 = kHidden[e][1], n3 = kHidden[e][2];
+    const int n1 = hp[e][0], n2 = hp[e][1], n3 = hp[e][2];
     const size_t row0 = h->elem_row0[e];
     {  // layer 1 forward
       GemmProblem P{};
-      P.A = aev + row0 * kFeaturesPad * es; P.lda = kFeaturesPad;
+      P.A = aev + row0 * kpad * sp * es; P.lda = (long)(kpad * sp);
       P.B = wb + (h->w_off[0] + r1[e] * ld_w1) * es; P.ldb = ld_w1;
       P.D = H1 + row0 * h->ldh1 * es; P.ldd = h->ldh1;
       P.bias = h->d_b + r1[e];
-      P.M = Me; P.N = M * n1; P.K = tc ? kFeaturesPad : kFeatures; P.epi = (int)Epi::BiasCelu;
+      P.M = Me; P.N = M * n1; P.K = tc ? (int)kpad : nfeat; P.epi = (int)Epi::BiasCelu;
       P.a_row0 = (int)row0; P.b_row0 = (int)r1[e]; P.elem = e; P.model = -1;
       if (h->split) {  // features, W1 and h1 as hi | lo
         P.split = 1;
-        P.a_lo = kFeaturesPad;
-        P.b_lo = kFeaturesPad;
+        P.a_lo = (int)kpad;
+        P.b_lo = (int)kpad;
         P.d_lo = M * kH1Max;
       }
       h->L[0].probs.push_back(P);
@@ -857,10 +937,10 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
     {  // layer 1 reverse: dE/dG = sum_m delta1_m W1_m
       GemmProblem P{};
       P.A = H1 + row0 * h->ldh1 * es; P.lda = h->ldh1;
-      P.B = wb + (h->w_off[5] + (size_t)e * kFeaturesPad * ld_w1t) * es; P.ldb = ld_w1t;
-      P.D = h->d_dG + row0 * kFeaturesPad; P.ldd = kFeaturesPad;
-      P.M = Me; P.N = tc ? kFeaturesPad : kFeatures; P.K = M * n1; P.epi = (int)Epi::Store;
-      P.a_row0 = (int)row0; P.b_row0 = e * kFeaturesPad; P.elem = e; P.model = -1;
+      P.B = wb + (h->w_off[5] + (size_t)e * kpad * ld_w1t) * es; P.ldb = ld_w1t;
+      P.D = h->d_dG + row0 * kpad; P.ldd = (long)kpad;
+      P.M = Me; P.N = tc ? (int)kpad : nfeat; P.K = M * n1; P.epi = (int)Epi::Store;
+      P.a_row0 = (int)row0; P.b_row0 = e * (int)kpad; P.elem = e; P.model = -1;
       h->L[5].probs.push_back(P);
       add_tiles(h->L[5], bm, tc ? 256 : 64);
     }
@@ -966,7 +1046,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
       const void* base;
       uint64_t rows, cols;
     };
-    const MapSpec A[6] = {{h->d_aev, R64, (uint64_t)kFeaturesPad * sp},
+    const MapSpec A[6] = {{h->d_aev, R64, (uint64_t)kpad * sp},
                           {h->d_h1, R64, (uint64_t)h->ldh1},
                           {h->d_h2s, R64, (uint64_t)2 * M * kH2Max},
                           {h->d_d3, R64, (uint64_t)h->ldz3},
@@ -977,7 +1057,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
                           {wb + h->w_off[2] * es, rows_w3, ld_w3},
                           {wb + h->w_off[3] * es, rows_w3t, ld_w3t},
                           {wb + h->w_off[4] * es, rows_w2t, ld_w2t},
-                          {wb + h->w_off[5] * es, (uint64_t)kSpecies * kFeaturesPad, ld_w1t}};
+                          {wb + h->w_off[5] * es, (uint64_t)NE * kpad, ld_w1t}};
     h->l1_b_base[0] = B[0].base;
     h->l1_b_rows[0] = B[0].rows;
     h->l1_b_cols[0] = B[0].cols;
@@ -996,8 +1076,8 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
     // outputs of the two first-layer products, stored by TMA: h1 (16-bit, 64-column
     // boxes) and dE/dG (FP32, 32-column boxes)
     if (!tc_make_map(h->tc_maps[0] + 256, h->d_h1, h->prec, R64, (uint64_t)h->ldh1, (uint64_t)h->ldh1, 128) ||
-        !tc_make_map(h->tc_maps[5] + 256, h->d_dG, Prec::F32, R64, (uint64_t)kFeaturesPad,
-                     (uint64_t)kFeaturesPad, 128, 32))
+        !tc_make_map(h->tc_maps[5] + 256, h->d_dG, Prec::F32, R64, (uint64_t)kpad,
+                     (uint64_t)kpad, 128, 32))
       return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for a first-layer output");
     if (h->split) {  // layer 2's output h2 (hi | lo), layer 3's d3
       if (!tc_make_map(h->tc_maps[1] + 256, h->d_h2s, h->prec, R64, (uint64_t)2 * M * kH2Max,
@@ -1016,16 +1096,16 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
     }
     CK(tc_set_smem());
     // fused tail: one problem per (element, member), tiles of 128 rows
-    for (int e = 0; e < kSpecies; ++e) {
+    for (int e = 0; e < NE; ++e) {
       const int Me = h->elem_count[e];
       if (Me == 0) continue;
       for (int m = 0; m < M; ++m) {
         TailProblem T{};
         T.Me = Me;
         T.row0 = h->elem_row0[e];
-        T.h1 = kHidden[e][0];
-        T.h2 = kHidden[e][1];
-        T.h3 = kHidden[e][2];
+        T.h1 = hp[e][0];
+        T.h2 = hp[e][1];
+        T.h3 = hp[e][2];
         T.a_col0 = m * T.h1;
         T.w2_row0 = (int)r2[e][m];
         T.w3_row0 = (int)r3[e][m];
@@ -1218,8 +1298,10 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
     gemm(1);
     mark(4);
     gemm(2);
+    int h3[kSpecies] = {0};
+    for (int e = 0; e < h->md.ns; ++e) h3[e] = h->md.hpad[e][2];
     launch_head(h->d_z3, h->ldz3, h->prec, h->d_row_elem, h->d_w4, h->d_b4, h->d_d3, h->d_y,
-                h->n_rows, h->n_models, s);
+                h->n_rows, h->n_models, h3, s);
     ++kernels;
     mark(5);
     launch_energy(h->d_y, h->n_models, h->d_row_of_int, h->d_mol_off, h->n_mols, E, h->d_atom_e, s);
@@ -1524,8 +1606,8 @@ nnp_status nnp_get_features(nnp_handle h, float* out, void* stream) {
   if (h->features_overwritten)
     return fail(h, NNP_ERR_UNSUPPORTED,
                 "recompute_aev: the last step's reverse pass reused the features' buffer");
-  launch_export_features(h->d_aev, h->prec, h->d_row_of_int, h->d_orig, h->n_atoms, out,
-                         static_cast<cudaStream_t>(stream), h->split != 0);
+  launch_export_features(h->d_aev, h->prec, h->d_row_of_int, h->d_orig, h->n_atoms, h->md.nfeat,
+                         h->md.kpad, out, static_cast<cudaStream_t>(stream), h->split != 0);
   CK(cudaGetLastError());
   return NNP_OK;
 }

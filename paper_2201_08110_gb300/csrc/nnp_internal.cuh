@@ -23,16 +23,57 @@ struct nnp_ctx;
 
 namespace nnp {
 
+// Two models share the library: ANI-2x (model 0: H, C, N, O, F, S, Cl; 8
+// distance x 4 angle shifts per angular block) and ANI-1x (model 1: H, C, N,
+// O; 4 x 8).  Both have 16 radial shifts and 32 features per angular block;
+// each model's features are stored in its own layout (radial species-major,
+// then the species-pair blocks of the row-major upper triangle).  The sizes
+// below are those of ANI-2x, the larger model: they bound both.
 constexpr int kSpecies = 7;
 constexpr int kShfR = 16;
 constexpr int kShfA = 8;
 constexpr int kShfZ = 4;
+constexpr int kMaxShfA = 8, kMaxShfZ = 8;               // angular shift grids of either model
 constexpr int kRadial = kSpecies * kShfR;               // 112
 constexpr int kPairBlocks = kSpecies * (kSpecies + 1) / 2;  // 28
 constexpr int kAngPerBlock = kShfA * kShfZ;             // 32
 constexpr int kAngular = kPairBlocks * kAngPerBlock;    // 896
 constexpr int kFeatures = kRadial + kAngular;           // 1008
 constexpr int kFeaturesPad = 1024;                      // K of the first layer, padded
+constexpr int kModels = 2;
+
+// Shape of one model's featurizer output: NS elements, NA distance shifts and
+// 32 / NA angle shifts per angular block; the feature row of the first
+// layer's product holds kPad >= kFeat columns (a multiple of 64, the
+// tensor-core K box).  kZetaInt: the angular exponent Zeta when it is an
+// integer the kernels raise to by repeated multiplication (ANI-1x: 32), else
+// 0 (ANI-2x: Zeta = 14.1, taken through log2 and exp2).
+template <int NS_, int NA_, int ZI_> struct AevShape {
+  static constexpr int NS = NS_, NA = NA_, NZ = 32 / NA_, kZetaInt = ZI_;
+  static constexpr int kRad = NS * kShfR;
+  static constexpr int kNP = NS * (NS + 1) / 2;
+  static constexpr int kFeat = kRad + kNP * 32;
+  static constexpr int kPad = (kFeat + 63) / 64 * 64;
+};
+using ShapeANI2x = AevShape<7, 8, 0>;   // 1008 features, rows of 1024
+using ShapeANI1x = AevShape<4, 4, 32>;  // 384 features
+static_assert(ShapeANI2x::kFeat == kFeatures && ShapeANI2x::kPad == kFeaturesPad, "ANI-2x layout");
+static_assert(ShapeANI1x::kFeat == 384 && ShapeANI1x::kPad == 384, "ANI-1x layout");
+
+// Host description of a model: elements, widths of the caller's weights, the
+// widths the device networks use (rounded up to multiples of 32 with zero
+// weights and biases: a padded unit is celu(0) = 0 and feeds nothing, so the
+// energy and forces are unchanged), feature counts.
+struct ModelDesc {
+  int id;
+  int ns, na, nz;
+  int nfeat, kpad;
+  int z[kSpecies];
+  int hidden[kSpecies][3];  // caller's widths
+  int hpad[kSpecies][3];    // device widths
+  float Rcr, Rca;
+};
+bool model_desc(int id, ModelDesc& md);
 constexpr int kMaxModels = 16;
 constexpr int kRowAlign = 128;                          // row padding of every element block
 
@@ -48,29 +89,28 @@ constexpr int kHidden[kSpecies][3] = {{256, 192, 160}, {224, 192, 160}, {192, 16
                                       {160, 128, 96}};
 constexpr int kH1Max = 256, kH2Max = 192, kH3Max = 160;
 
-// kHidden for device code: width of hidden layer l (0..2) of element e.
-__host__ __device__ __forceinline__ int hidden_width(int e, int l) {
-  constexpr int w[3][4] = {{256, 224, 192, 160}, {192, 192, 160, 128}, {160, 160, 128, 96}};
-  const int g = e <= 1 ? e : (e <= 3 ? 2 : 3);  // H, C, {N, O}, {F, S, Cl}
-  return w[l][g];
-}
-
 // Featurizer constants in FP32, as the kernels use them.
 struct AevConst {
   float Rcr, Rca, Rcr2, Rca2;  // cutoffs and squares (FP32)
   double Rcr2d, Rca2d;         // FP64 squares of the FP32 cutoffs (exact predicate)
   float EtaR, EtaA, Zeta;
-  float ShfR[kShfR], ShfA[kShfA], cosZ[kShfZ], sinZ[kShfZ];
+  float ShfR[kShfR], ShfA[kMaxShfA], cosZ[kMaxShfZ], sinZ[kMaxShfZ];
   // exp(-Eta (r - Shf)^2) = 2^(-y^2) with y = sqEta r - ShfS = sqEta (r - Shf),
-  // sqEta = sqrt(Eta log2(e)); gradX = -2 Eta / sqEta turns y into d/dr
-  float sqEtaR, sqEtaA, ShfRs[kShfR], ShfAs[kShfA], gradR, gradA;
+  // sqEta = sqrt(Eta log2(e)); gradX = -2 Eta / sqEta turns y into d/dr.
+  // sqEta and ShfS are held as FP32 pairs hi + lo (the *l members), y =
+  // fma(r, sqEta, -ShfS) + fma(r, sqEtal, -ShfSl): rounding them to single
+  // FP32 values would shift y by up to 3e-6 for every pair alike, a bias of
+  // up to 1e-5 on the features in a Gaussian's flank.
+  float sqEtaR, sqEtaA, ShfRs[kShfR], ShfAs[kMaxShfA], gradR, gradA;
+  float sqEtaRl, sqEtaAl, ShfRsl[kShfR], ShfAsl[kMaxShfA];
   // the same halved (the angular distance is (r_j + r_k) / 2), and
   // 0.95 Zeta (d cos' / d cos times the exponent)
-  float hsqEtaA, hgradA, dcosA;
+  float hsqEtaA, hgradA, dcosA, hsqEtaAl;
   int pair_index[kSpecies][kSpecies];
   float box[3];
   double boxd[3];
   int periodic;
+  int model;  // 0 ANI-2x, 1 ANI-1x: selects the featurizer's shape
 };
 
 // Geometry of one step: what the featurizer and its reverse pass read.
@@ -222,9 +262,10 @@ int aev_adj_stage_cap(int cap_a);  // main launch's per-warp staging capacity
 int aev_adj_launches(int cap_a);   // kernels per reverse pass
 // dynamic shared memory to allow for both launches of the reverse pass
 size_t aev_adj_launch_smem(int cap_r, int cap_a, int warps, int mol_atoms_smem_max);
+// h3: width of the last hidden layer of each element (device networks)
 void launch_head(const float* z3, long ldz, Prec prec, const int* row_elem, const float* w4,
                  const float* b4, void* delta3, float* y, int n_rows, int n_models,
-                 cudaStream_t s);
+                 const int h3[kSpecies], cudaStream_t s);
 void launch_energy(const float* y, int n_models, const int* row_of_int, const int* mol_off,
                    int n_mols, double* energy_out, double* atom_energy_row, cudaStream_t s);
 void launch_gemm_simt(const GemmProblem* d_problems, const GemmTile* d_tiles, int n_tiles,
@@ -238,10 +279,11 @@ cudaError_t aev_set_smem_limits(size_t fwd_bytes, size_t adj_bytes);
 // Inspection helpers.
 void launch_export_neighbors(const NeighborLists& nl, int kind, const int* orig_of_int, int n,
                              int* counts_out, int* lists_out, int cap_out, cudaStream_t s);
-// split: rows of hi | lo (2 x 1024 columns), exported as hi + lo
+// rows of kpad columns (split: hi | lo, 2 x kpad columns, exported as hi +
+// lo); the first nfeat columns are exported
 void launch_export_features(const void* aev, Prec prec, const int* row_of_int,
-                            const int* orig_of_int, int n, float* out, cudaStream_t s,
-                            bool split = false);
+                            const int* orig_of_int, int n, int nfeat, int kpad, float* out,
+                            cudaStream_t s, bool split = false);
 void launch_export_atomic_energies(const double* atom_energy_row, const int* row_of_int,
                                    const int* orig_of_int, int n, double* out, cudaStream_t s);
 
@@ -256,8 +298,9 @@ void launch_mlp_tail(const TailProblem* probs, const GemmTile* tiles, const int*
                      Prec p, const void* maps, int reverse, unsigned* status, const int* abort_req,
                      cudaStream_t s);
 
-// Featurizer constants (cutoffs, shift grids, species-pair table, box).
-void aev_constants(AevConst& c, const double box[3]);
+// Featurizer constants (cutoffs, shift grids, species-pair table, box) of a
+// model (0 ANI-2x, 1 ANI-1x).
+void aev_constants(AevConst& c, const double box[3], int model = 0);
 
 // For the MD loop (md.cu): one evaluation of a handle enqueued on s as direct
 // launches (captured by the caller's graph); returns the number of kernels,

@@ -117,11 +117,15 @@ template <> __device__ __forceinline__ __half from_f<__half>(float v) { return _
 // (FP32, bias included), h3 = celu(z3), y = w4 . h3 + b4, and the start of
 // the reverse pass delta3 = (1/M) w4 * celu'(z3) in the products' element
 // type.  One warp per (row, model).
+struct ElemWidths {
+  int h3[kSpecies];
+};
+
 template <typename T>
 __global__ void k_head(const float* __restrict__ z3, long ldz, const int* __restrict__ row_elem,
                        const float* __restrict__ w4, const float* __restrict__ b4,
                        T* __restrict__ d3, float* __restrict__ y, int n_rows, int n_models,
-                       float inv_m) {
+                       float inv_m, ElemWidths wid) {
   const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= (long)n_rows * n_models) return;
@@ -131,7 +135,7 @@ __global__ void k_head(const float* __restrict__ z3, long ldz, const int* __rest
     if (lane == 0) y[(size_t)row * n_models + m] = 0.f;
     return;
   }
-  const int h3 = hidden_width(e, 2);
+  const int h3 = wid.h3[e];
   const float* zr = z3 + (size_t)row * ldz + (size_t)m * h3;
   T* dr = d3 + (size_t)row * ldz + (size_t)m * h3;
   const float* w = w4 + ((size_t)e * kMaxModels + m) * kH3Max;
@@ -139,7 +143,7 @@ __global__ void k_head(const float* __restrict__ z3, long ldz, const int* __rest
   for (int c = lane; c < h3; c += 32) {
     const float z = zr[c];
     const float ex = expf(fminf(z, 0.f) * 10.f);  // exp(z / alpha), alpha = 0.1
-    const float h = z > 0.f ? z : 0.1f * (ex - 1.f);
+    const float h = z > 0.f ? z : 0.1f * expm1f(fminf(z, 0.f) * 10.f);  // no cancellation near 0
     const float dh = z > 0.f ? 1.f : ex;
     acc = fmaf(w[c], h, acc);
     dr[c] = from_f<T>(w[c] * dh * inv_m);
@@ -195,14 +199,14 @@ __global__ void k_export_neighbors(const int* __restrict__ cnt, const int* __res
 
 template <typename T>
 __global__ void k_export_features(const T* __restrict__ aev, const int* __restrict__ row_of_int,
-                                  const int* __restrict__ orig, int n, float* __restrict__ out,
-                                  int split) {
+                                  const int* __restrict__ orig, int n, int nfeat, int kpad,
+                                  float* __restrict__ out, int split) {
   const int q = blockIdx.x;
   if (q >= n) return;
-  const T* src = aev + (size_t)row_of_int[q] * (split ? 2 : 1) * kFeaturesPad;
-  float* dst = out + (size_t)orig[q] * kFeatures;
-  for (int f = threadIdx.x; f < kFeatures; f += blockDim.x)
-    dst[f] = split ? to_f(src[f]) + to_f(src[kFeaturesPad + f]) : to_f(src[f]);
+  const T* src = aev + (size_t)row_of_int[q] * (split ? 2 : 1) * kpad;
+  float* dst = out + (size_t)orig[q] * nfeat;
+  for (int f = threadIdx.x; f < nfeat; f += blockDim.x)
+    dst[f] = split ? to_f(src[f]) + to_f(src[kpad + f]) : to_f(src[f]);
 }
 
 __global__ void k_export_atomic(const double* __restrict__ e_row, const int* __restrict__ row_of_int,
@@ -237,25 +241,28 @@ void launch_gather_positions(const float* pos, const int* orig, float4* out, int
 }
 
 void launch_head(const float* z3, long ldz, Prec prec, const int* row_elem, const float* w4,
-                 const float* b4, void* d3, float* y, int n_rows, int n_models, cudaStream_t s) {
+                 const float* b4, void* d3, float* y, int n_rows, int n_models, const int h3[kSpecies],
+                 cudaStream_t s) {
   const long warps = (long)n_rows * n_models;
   if (warps == 0) return;
   const int threads = 256;
   const long blocks = (warps * 32 + threads - 1) / threads;
   const float inv_m = 1.0f / (float)n_models;
+  ElemWidths wid;
+  for (int e = 0; e < kSpecies; ++e) wid.h3[e] = h3[e];
   switch (prec) {
     case Prec::F32:
       k_head<float><<<blocks, threads, 0, s>>>(z3, ldz, row_elem, w4, b4, (float*)d3, y, n_rows,
-                                               n_models, inv_m);
+                                               n_models, inv_m, wid);
       break;
     case Prec::BF16:
       k_head<__nv_bfloat16><<<blocks, threads, 0, s>>>(z3, ldz, row_elem, w4, b4,
                                                        (__nv_bfloat16*)d3, y, n_rows, n_models,
-                                                       inv_m);
+                                                       inv_m, wid);
       break;
     case Prec::F16:
       k_head<__half><<<blocks, threads, 0, s>>>(z3, ldz, row_elem, w4, b4, (__half*)d3, y, n_rows,
-                                                n_models, inv_m);
+                                                n_models, inv_m, wid);
       break;
   }
 }
@@ -278,19 +285,20 @@ void launch_export_neighbors(const NeighborLists& nl, int kind, const int* orig,
 }
 
 void launch_export_features(const void* aev, Prec prec, const int* row_of_int, const int* orig,
-                            int n, float* out, cudaStream_t s, bool split) {
+                            int n, int nfeat, int kpad, float* out, cudaStream_t s, bool split) {
   if (n <= 0) return;
   const int sp = split ? 1 : 0;
   switch (prec) {
     case Prec::F32:
-      k_export_features<float><<<n, 256, 0, s>>>((const float*)aev, row_of_int, orig, n, out, 0);
+      k_export_features<float><<<n, 256, 0, s>>>((const float*)aev, row_of_int, orig, n, nfeat, kpad, out, 0);
       break;
     case Prec::BF16:
-      k_export_features<__nv_bfloat16>
-          <<<n, 256, 0, s>>>((const __nv_bfloat16*)aev, row_of_int, orig, n, out, sp);
+      k_export_features<__nv_bfloat16><<<n, 256, 0, s>>>((const __nv_bfloat16*)aev, row_of_int, orig, n,
+                                                         nfeat, kpad, out, sp);
       break;
     case Prec::F16:
-      k_export_features<__half><<<n, 256, 0, s>>>((const __half*)aev, row_of_int, orig, n, out, sp);
+      k_export_features<__half><<<n, 256, 0, s>>>((const __half*)aev, row_of_int, orig, n, nfeat, kpad,
+                                                  out, sp);
       break;
   }
 }

@@ -19,12 +19,15 @@ LIB_PATH = os.path.join(_HERE, "_build", "libnnp.so")
 
 FP32, BF16, FP16 = 0, 1, 2
 _PREC = {"fp32": FP32, "bf16": BF16, "fp16": FP16}
+ANI2X, ANI1X = 0, 1
+_MODEL = {"ani2x": ANI2X, "ani1x": ANI1X}
 STATUS = {0: "NNP_OK", 1: "NNP_ERR_ARG", 2: "NNP_ERR_SPECIES", 3: "NNP_ERR_CHARGE",
           4: "NNP_ERR_ALLOC", 5: "NNP_ERR_CUDA", 6: "NNP_ERR_CAPACITY", 7: "NNP_ERR_NONFINITE",
           8: "NNP_ERR_TIMEOUT", 9: "NNP_ERR_UNSUPPORTED", 10: "NNP_ERR_TOO_LARGE"}
 
 # Every entry point declared in include/nnp.h.
-EXPORTS = ("nnp_weights_per_model", "nnp_num_features", "nnp_create", "nnp_create_batch",
+EXPORTS = ("nnp_weights_per_model", "nnp_num_features", "nnp_weights_per_model_of",
+           "nnp_num_features_of", "nnp_create", "nnp_create_batch",
            "nnp_compute", "nnp_compute_host", "nnp_get_status", "nnp_last_error", "nnp_destroy",
            "nnp_get_capacity", "nnp_get_neighbors", "nnp_get_features",
            "nnp_get_atomic_energies", "nnp_compute_timed", "nnp_kernels_per_step",
@@ -50,7 +53,8 @@ class Params(ctypes.Structure):
                 ("max_neighbors", ctypes.c_int32), ("max_angular", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("neighbor_mode", ctypes.c_int32),
                 ("single_pass", ctypes.c_int32), ("recompute_aev", ctypes.c_int32),
-                ("test_abort", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("test_abort", ctypes.c_int32), ("model", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class MDParams(ctypes.Structure):
@@ -78,6 +82,10 @@ def load_library(path: str = LIB_PATH):
     P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
     lib.nnp_weights_per_model.restype = I64
     lib.nnp_num_features.restype = I32
+    lib.nnp_weights_per_model_of.argtypes = [I32]
+    lib.nnp_weights_per_model_of.restype = I64
+    lib.nnp_num_features_of.argtypes = [I32]
+    lib.nnp_num_features_of.restype = I32
     lib.nnp_create.argtypes = [P, I32, P, P]
     lib.nnp_create.restype = ctypes.c_int
     lib.nnp_create_batch.argtypes = [P, P, I32, P, P]
@@ -124,8 +132,16 @@ def load_library(path: str = LIB_PATH):
     return lib
 
 
-def weights_per_model() -> int:
-    return int(load_library().nnp_weights_per_model())
+def _model_id(model) -> int:
+    return _MODEL[model] if isinstance(model, str) else int(model)
+
+
+def weights_per_model(model="ani2x") -> int:
+    return int(load_library().nnp_weights_per_model_of(_model_id(model)))
+
+
+def num_features(model="ani2x") -> int:
+    return int(load_library().nnp_num_features_of(_model_id(model)))
 
 
 def _stream_ptr(stream) -> int:
@@ -146,7 +162,8 @@ class NNP:
     def __init__(self, Z, weights, n_models: int, mol_off=None, precision: str = "fp32",
                  box=None, max_neighbors: int = 0, max_angular: int = 0,
                  use_graph: bool = False, total_charge: int = 0, neighbor_mode: int = 0,
-                 single_pass: bool = False, recompute_aev: bool = False, test_abort: bool = False):
+                 single_pass: bool = False, recompute_aev: bool = False, test_abort: bool = False,
+                 model="ani2x"):
         self._lib = load_library()
         Z = np.ascontiguousarray(Z, dtype=np.int32)
         if mol_off is None:
@@ -169,6 +186,7 @@ class NNP:
         p.single_pass = 1 if single_pass else 0
         p.recompute_aev = 1 if recompute_aev else 0
         p.test_abort = 1 if test_abort else 0
+        p.model = _model_id(model)
         h = ctypes.c_void_p()
         rc = self._lib.nnp_create_batch(Z.ctypes.data, mol_off.ctypes.data, mol_off.shape[0] - 1,
                                         ctypes.byref(p), ctypes.byref(h))
@@ -181,6 +199,8 @@ class NNP:
         self.precision = precision
         self.mol_off = mol_off
         self.box = b
+        self.model = p.model
+        self.n_features = num_features(p.model)
 
     # -- lifetime --
     def close(self):
@@ -274,7 +294,7 @@ class NNP:
 
     def features(self, stream=None):
         import torch
-        out = torch.empty(self.n_atoms, 1008, dtype=torch.float32, device="cuda")
+        out = torch.empty(self.n_atoms, self.n_features, dtype=torch.float32, device="cuda")
         self._check(self._lib.nnp_get_features(self._h, _ptr(out), _stream_ptr(stream)))
         return out
 

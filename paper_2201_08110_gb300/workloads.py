@@ -140,10 +140,10 @@ def batch(seed: int, sizes, model: str = "ani2x") -> Batch:
     return Batch(Z.astype(np.int32), P.astype(np.float32), np.asarray(off, dtype=np.int32))
 
 
-def pocket(seed: int, n: int = 1500, edge: float = 24.7) -> Batch:
+def pocket(seed: int, n: int = 1500, edge: float = 24.7, model: str = "ani2x") -> Batch:
     """One periodic region of n atoms in a cubic box."""
     g = rng(seed)
-    Z = species_iid(g, n)
+    Z = species_iid(g, n, model)
     pos = geometry(g, n, edge=edge, periodic=True)
     return Batch(Z, pos, np.array([0, n], dtype=np.int32), np.full(3, edge))
 
@@ -213,6 +213,13 @@ def config3_sizes(n_mols: int = 512) -> np.ndarray:
 def config3(n_mols: int = 512) -> tuple[Batch, np.ndarray, int]:
     s = workload_seed(3)
     return batch(s, config3_sizes(n_mols)), weights(s + 1, 8), 8
+
+
+def config3_ani1x(n_mols: int = 512) -> tuple[Batch, np.ndarray, int]:
+    """The 512-molecule batch's sizes with H, C, N, O molecules and an
+    8-network ANI-1x ensemble (the second model of Sec. 3)."""
+    s = workload_seed(3) + 10
+    return batch(s, config3_sizes(n_mols), model="ani1x"), weights(s + 1, 8, model="ani1x"), 8
 
 
 def config5_sizes(n_mols: int = 4096) -> np.ndarray:

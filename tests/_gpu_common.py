@@ -40,22 +40,23 @@ def split_mode(prec):
     return (prec[:-7], True) if prec.endswith("-single") else (prec, False)
 
 
-def oracle_batch(b, w, M, mols=None, aev=False):
+def oracle_batch(b, w, M, mols=None, aev=False, model="ani2x"):
     """Oracle energies/forces (and per-atom energies) for the given molecules
     of a batch (all by default); returns per-molecule dicts."""
     mols = range(b.n_mols) if mols is None else mols
     out = {}
     for m in mols:
         sub = b.molecule(m)
-        r = oracle.compute(sub.Z, sub.pos, sub.mol_off, w, M, box=b.box, aev=aev, atom_energies=True)
+        r = oracle.compute(sub.Z, sub.pos, sub.mol_off, w, M, box=b.box, aev=aev, atom_energies=True,
+                           model=model)
         out[m] = r
     return out
 
 
-def oracle_whole_batch(b, w, M):
+def oracle_whole_batch(b, w, M, model="ani2x"):
     """The same per-molecule dicts from one oracle call over the whole batch
     (the oracle spreads molecules over the host cores)."""
-    r = oracle.compute(b.Z, b.pos, b.mol_off, w, M, box=b.box, atom_energies=True)
+    r = oracle.compute(b.Z, b.pos, b.mol_off, w, M, box=b.box, atom_energies=True, model=model)
     out = {}
     for m in range(b.n_mols):
         a0, a1 = int(b.mol_off[m]), int(b.mol_off[m + 1])

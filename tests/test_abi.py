@@ -41,6 +41,46 @@ def test_host_only_queries(lib):
     assert lib.nnp_num_features() == 1008
 
 
+def test_model_queries(lib):
+    """Sizes per model: ANI-2x as above, ANI-1x 384 features and the oracle's
+    parameter count; an unknown model is -1."""
+    import oracle
+    from paper_2201_08110_gb300 import nnp
+    assert lib.nnp_weights_per_model_of(0) == 1713223
+    assert lib.nnp_num_features_of(0) == 1008
+    assert lib.nnp_num_features_of(1) == 384 == oracle.MODEL_FEATURES["ani1x"]
+    assert lib.nnp_weights_per_model_of(1) == oracle.weights_per_model(model="ani1x") == 326660
+    assert lib.nnp_weights_per_model_of(2) == -1 and lib.nnp_num_features_of(-1) == -1
+    assert nnp.weights_per_model("ani1x") == 326660 and nnp.num_features("ani1x") == 384
+
+
+def test_create_checks_the_model_before_touching_the_device(lib):
+    """ANI-1x has no F, S or Cl, needs its own weight count and a box edge
+    above 2 x 5.2 A; an unknown model id is NNP_ERR_ARG."""
+    from paper_2201_08110_gb300 import nnp
+    import numpy as np
+    p = nnp.Params()
+    p.n_models = 1
+    p.model = 1
+    w = np.zeros(nnp.weights_per_model("ani1x"), np.float32)
+    p.weights = w.ctypes.data
+    p.n_weights = w.size
+    h = ctypes.c_void_p()
+    Z = np.array([6, 9], np.int32)
+    assert lib.nnp_create(Z.ctypes.data, 2, ctypes.byref(p), ctypes.byref(h)) == 2  # F
+    assert b"atomic number 9" in lib.nnp_last_error(None)
+    Z = np.array([6, 1], np.int32)
+    p.box[0] = p.box[1] = p.box[2] = 10.3  # above 2 x 5.1, below 2 x 5.2
+    assert lib.nnp_create(Z.ctypes.data, 2, ctypes.byref(p), ctypes.byref(h)) == 1
+    p.box[0] = p.box[1] = p.box[2] = 0.0
+    p.model = 0  # ANI-2x with ANI-1x's weight count
+    assert lib.nnp_create(Z.ctypes.data, 2, ctypes.byref(p), ctypes.byref(h)) == 1
+    p.model = 2
+    assert lib.nnp_create(Z.ctypes.data, 2, ctypes.byref(p), ctypes.byref(h)) == 1
+    assert b"model" in lib.nnp_last_error(None)
+    assert not h.value
+
+
 def test_create_rejects_bad_arguments_before_touching_the_device(lib):
     """Argument, species and charge errors are returned synchronously."""
     from paper_2201_08110_gb300 import nnp
