@@ -409,6 +409,45 @@ def measure_coupling(steps: int, flush, stream, fp32_peak: float, with_oracle: b
            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                         "frac": achieved / fp32_peak, "work": FLOP_COUPLING_PAIR * pairs,
                         "peak_note": "derived FP32 FMA peak: 152 SMs x 128 lanes x 2 x max SM clock"}}
+    # the fixed cost of one call: the same call on fewer MM atoms (a line fit
+    # of time against pairs gives the intercept) and a one-element kernel
+    # timed the same way (the floor of any single launch on this stream)
+    def timed(fn, n=steps):
+        t = []
+        for _ in range(n):
+            flush.zero_()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            fn()
+            a1.record(stream)
+            a1.synchronize()
+            t.append(a0.elapsed_time(a1))
+        return statistics.median(t)
+    sizes = [n for n in (2000, 6000, 20000) if n < env.n_mm] + [env.n_mm]
+    per_size = {}
+    for n in sizes[:-1]:
+        sub = [ins[0], ins[1], ins[2], ins[3], ins[4][:n].contiguous(), ins[5][:n].contiguous(),
+               ins[6][:n].contiguous(), ins[7][:n].contiguous()]
+        fm_n = torch.zeros(n, 3, dtype=torch.float64, device="cuda")
+        f = lambda: nnp.mm_coupling(*sub, W.COULOMB_KCAL, energy=e, nnp_forces=fn, mm_forces=fm_n,
+                                    stream=stream)
+        for _ in range(3):
+            f()
+        per_size[n] = timed(f)
+    per_size[env.n_mm] = ms
+    x = np.array([b.n_atoms * n for n in per_size], dtype=np.float64)
+    y = np.array(list(per_size.values()), dtype=np.float64)
+    slope, intercept = np.polyfit(x, y, 1)
+    one = torch.zeros(1, dtype=torch.float32, device="cuda")
+    floor_ms = timed(lambda: one.zero_())
+    out["fixed_cost"] = {
+        "ms_by_mm_atoms": {str(k): v for k, v in per_size.items()},
+        "fit_intercept_ms": float(intercept), "fit_ms_per_mpair": float(slope * 1e6),
+        "one_element_kernel_ms": floor_ms,
+        "note": "intercept of a line through the call times at the MM sizes shown: the part of a "
+                "call that does not grow with the pairs; one_element_kernel_ms: a 1-float fill "
+                "timed the same way (events around one launch, L2 flushed before), the floor of "
+                "any launch on this stream"}
     if with_oracle:
         import oracle
         t0 = time.perf_counter()
