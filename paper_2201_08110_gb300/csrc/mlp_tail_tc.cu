@@ -279,9 +279,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    {
       // ---- MMA issuer: phases alternate between the two accumulators; a
-      // phase's K block b waits only for block b of its A operand ----
+      // phase's K block b waits only for block b of its A operand.  The whole
+      // warp walks the loop (its values stay warp-uniform) and one elected
+      // lane issues each tcgen05 instruction ----
       uint32_t it = 0, tcount = 0;
       uint32_t used[2] = {0, 0};       // phases issued per accumulator
       uint32_t blk_waits[4] = {0, 0, 0, 0};
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       auto phase = [&](int x, const unsigned char* a_base, int k, int n, uint64_t* blk_free,
                        uint64_t* a_ready, uint32_t* a_waits) {
         if (!ok) return;
-        if (used[x] > 0 && !mbar_wait(&acc_free[x], (used[x] - 1) & 1, abort_flag)) {
+        if (used[x] > 0 && !mbar_wait_warp(&acc_free[x], (used[x] - 1) & 1, abort_flag)) {
           ok = false;
           return;
         }
@@ -304,13 +306,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t d = tmem + (uint32_t)(x * kTmemCols / 2);
         const int n_kb = nblocks(k);
         for (int kb = 0; kb < n_kb; ++kb, ++it) {
-          if (!mbar_wait(&a_ready[kb], a_waits[kb] & 1, abort_flag)) {
+          if (!mbar_wait_warp(&a_ready[kb], a_waits[kb] & 1, abort_flag)) {
             ok = false;
             return;
           }
           ++a_waits[kb];
           const int s = it % kRing;
-          if (!mbar_wait(&full[s], (it / kRing) & 1, abort_flag)) {
+          if (!mbar_wait_warp(&full[s], (it / kRing) & 1, abort_flag)) {
             ok = false;
             return;
           }
@@ -319,18 +321,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint64_t db = smem_desc_sw128(ring + (size_t)s * kRingBytes);
           const int ksteps = min(kBK, k - kb * kBK) / 16;
           for (int j = 0; j < ksteps; ++j)
-            mma_f16(d, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc, (kb > 0 || j > 0) ? 1u : 0u);
-          mma_commit(&empty[s]);
-          if (blk_free) mma_commit(&blk_free[kb]);
+            mma_f16_elect(d, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc, (kb > 0 || j > 0) ? 1u : 0u);
+          mma_commit_elect(&empty[s]);
+          if (blk_free) mma_commit_elect(&blk_free[kb]);
         }
-        mma_commit(&acc_ready[x]);
+        mma_commit_elect(&acc_ready[x]);
         ++used[x];
       };
       // L2 forward: A = h1, taken block by block in the order the producer
       // loads it (the blocks the previous tile freed first, first)
       auto phase1 = [&](const TailProblem& P, int first) {
         if (!ok) return;
-        if (used[0] > 0 && !mbar_wait(&acc_free[0], (used[0] - 1) & 1, abort_flag)) {
+        if (used[0] > 0 && !mbar_wait_warp(&acc_free[0], (used[0] - 1) & 1, abort_flag)) {
           ok = false;
           return;
         }
@@ -341,13 +343,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool acc = false;
         for (int i = 0; i < kA1Blocks; ++i) {
           const int kb = (first + i) % kA1Blocks;
-          if (!mbar_wait(&a1_full[kb], tcount & 1, abort_flag)) {
+          if (!mbar_wait_warp(&a1_full[kb], tcount & 1, abort_flag)) {
             ok = false;
             return;
           }
           if (kb >= nb1) continue;
           const int s = it % kRing;
-          if (!mbar_wait(&full[s], (it / kRing) & 1, abort_flag)) {
+          if (!mbar_wait_warp(&full[s], (it / kRing) & 1, abort_flag)) {
             ok = false;
             return;
           }
@@ -356,16 +358,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint64_t db = smem_desc_sw128(ring + (size_t)s * kRingBytes);
           const int ksteps = min(kBK, P.h1 - kb * kBK) / 16;
           for (int j = 0; j < ksteps; ++j) {
-            mma_f16(d, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc, acc ? 1u : 0u);
+            mma_f16_elect(d, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc, acc ? 1u : 0u);
             acc = true;
           }
-          mma_commit(&empty[s]);
+          mma_commit_elect(&empty[s]);
           ++it;
         }
-        mma_commit(&acc_ready[0]);
+        mma_commit_elect(&acc_ready[0]);
         ++used[0];
         // A1 blocks past h2 are not read again in this tile
-        for (int kb = nblocks(P.h2); kb < kA1Blocks; ++kb) mma_commit(&a1_free[kb]);
+        for (int kb = nblocks(P.h2); kb < kA1Blocks; ++kb) mma_commit_elect(&a1_free[kb]);
       };
       int first = 0;
       for (int tile = tile_begin; ok && tile < tile_end; ++tile, ++tcount) {
@@ -373,7 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const TailProblem P = probs[tl.problem];
         if (rev_only) {
           phase(0, A2, P.h3, P.h2, nullptr, a2_full, a2_waits);  // L3 reverse, d3 loaded by TMA
-          if (ok) mma_commit(a2_free);                            // A2 may take phase 4's h1
+          if (ok) mma_commit_elect(a2_free);                            // A2 may take phase 4's h1
           phase(1, A1, P.h2, P.h1, a1_free, blk_done, blk_waits);  // L2 reverse, d2 over h2
           continue;
         }
@@ -384,10 +386,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         phase(1, A1, P.h2, P.h3, reverse ? nullptr : a1_free, blk_done, blk_waits);
         if (!reverse) continue;
         phase(0, A2, P.h3, P.h2, nullptr, blk_done, blk_waits);  // L3 reverse, block by block of d3
-        if (ok) mma_commit(a2_free);        // d3 consumed: A2 may take phase 4's h1
+        if (ok) mma_commit_elect(a2_free);        // d3 consumed: A2 may take phase 4's h1
         phase(1, A1, P.h2, P.h1, a1_free, blk_done, blk_waits);  // L2 reverse, block by block of d2 (over h2)
       }
-      if (!ok) {
+      if (!ok && lane == 0) {
         atomicOr(status, kStatTimeout);
         atomicExch(abort_flag, 1);
       }

@@ -18,6 +18,10 @@ namespace nnp {
 void launch_gemm_tc(const GemmProblem* probs, const GemmTile* tiles, const int* cta_off, int n_ctas,
                     Prec p, int b_box_rows, const void* maps, unsigned* status, const int* abort_req,
                     cudaStream_t s);
+void launch_gemm_tc2(const GemmProblem* probs, const GemmTile* tiles, const int* pair_off, int n_pairs,
+                     Prec p, int b_half_rows, const void* maps, unsigned* status, const int* abort_req,
+                     cudaStream_t s);
+int tc2_max_pairs(int sms);
 bool tc_available();
 size_t tc_maps_bytes();
 // box_cols x box_rows boxes of a [rows][cols] 16-bit matrix; 128-byte swizzle
@@ -137,6 +141,8 @@ struct nnp_ctx {
   int n_work = 0;
   int fwd_warps = 4, adj_warps = 4, adj_chunk = 0, adj_shared_acc = 1, smem_atoms_max = 0;
   int l1_bn = 256;                  // N tile of the first layer's products (tensor cores)
+  bool l1_pairs = true;             // the first layer's products on CTA pairs (256-row tiles)
+  int l1_max_pairs = 0;             // CTA pairs that fit on the GPU at once
   int tc_box[6] = {256, kH2Max, kH3Max, kH2Max, kH1Max, 256};  // weight-box rows per layer
   std::vector<int> mol_off_h;
   const void* l1_b_base[2] = {nullptr, nullptr};  // W1, W1T (tensor-core maps of layers 0, 5)
@@ -435,23 +441,28 @@ nnp_status build_work_list(nnp_ctx* h, int warps, int chunk, int shared_acc = 1)
 }
 
 // Tiles (and, on tensor cores, the weight maps) of the first layer's two
-// products for an N tile of bn columns.
+// products for an N tile of bn columns.  On CTA pairs (h->l1_pairs) a tile
+// has 256 rows and the units that share out the tiles are the SM pairs; each
+// CTA's B box holds half the tile's columns.
 nnp_status set_l1_tiles(nnp_ctx* h, int bn) {
+  const int bm = h->l1_pairs ? 256 : 128;
   for (int layer : {0, 5}) {
     Layer& L = h->L[layer];
     L.tiles.clear();
     std::vector<double> cost;
     for (int pi = 0; pi < (int)L.probs.size(); ++pi) {
       const GemmProblem& P = L.probs[pi];
-      for (int m0 = 0; m0 < P.M; m0 += 128)
+      for (int m0 = 0; m0 < P.M; m0 += bm)
         for (int n0 = 0; n0 < P.N; n0 += bn) {
           L.tiles.push_back(GemmTile{pi, m0, n0, 0});
           cost.push_back((double)P.K * std::min(bn, P.N - n0));
         }
     }
     // the last, partly filled wave: split its cheapest tiles into 2 or 4
-    // column pieces (at least 64 columns) so they spread over more CTAs
-    const int S = h->sms, r = (int)L.tiles.size() % S;
+    // column pieces so they spread over more CTAs.  A piece is a whole number
+    // of 64-column output boxes: the epilogue stores whole boxes (zeros past
+    // a tile's columns), which past a piece would land in its neighbour's
+    const int S = h->l1_pairs ? h->l1_max_pairs : h->sms, r = (int)L.tiles.size() % S;
     const int k = (r > 0 && 4 * r <= S) ? 4 : (r > 0 && 2 * r <= S) ? 2 : 1;
     if (k > 1 && bn / k >= 64) {
       std::vector<int> order(L.tiles.size());
@@ -463,7 +474,7 @@ nnp_status set_l1_tiles(nnp_ctx* h, int bn) {
         const int i = order[q];
         GemmTile& t = L.tiles[i];
         const int w = std::min(bn, L.probs[t.problem].N - t.n0);
-        if (w < 64 * k || w % (16 * k)) continue;
+        if (w % (64 * k)) continue;
         const int pw = w / k;
         for (int piece = 1; piece < k; ++piece) {
           extra.push_back(GemmTile{t.problem, t.m0, t.n0 + piece * pw, pw});
@@ -486,10 +497,11 @@ nnp_status set_l1_tiles(nnp_ctx* h, int bn) {
       CK(cudaMemcpy(L.d_tiles, L.tiles.data(), sizeof(GemmTile) * L.tiles.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(L.d_cta_off, L.cta_off.data(), sizeof(int) * L.cta_off.size(), cudaMemcpyHostToDevice));
     const int i = layer == 0 ? 0 : 1;
+    const int box_rows = h->l1_pairs ? bn / 2 : bn;
     if (!tc_make_map(h->tc_maps[layer] + 128, h->l1_b_base[i], h->prec, h->l1_b_rows[i],
-                     h->l1_b_cols[i], h->l1_b_cols[i], (uint32_t)bn))
+                     h->l1_b_cols[i], h->l1_b_cols[i], (uint32_t)box_rows))
       return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the first layer");
-    h->tc_box[layer] = bn;
+    h->tc_box[layer] = box_rows;
   }
   h->l1_bn = bn;
   return NNP_OK;
@@ -1176,7 +1188,9 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
       CK(cudaMemcpy(L.d_tiles, L.tiles.data(), sizeof(GemmTile) * L.tiles.size(), cudaMemcpyHostToDevice));
   }
 
-  if (h->prec != Prec::F32) {  // first-layer tiles balanced over the SMs
+  if (h->prec != Prec::F32) {  // first-layer tiles balanced over the SMs (or SM pairs)
+    h->l1_max_pairs = std::min(tc2_max_pairs(h->sms), h->sms / 2);
+    h->l1_pairs = h->l1_max_pairs > 0;
     const nnp_status st = set_l1_tiles(h, h->l1_bn);
     if (st != NNP_OK) return st;
   }
@@ -1202,6 +1216,9 @@ void run_gemm(nnp_ctx* h, int layer, cudaStream_t s) {
   if (L.tiles.empty()) return;
   if (h->prec == Prec::F32)
     launch_gemm_simt(L.d_probs, L.d_tiles, (int)L.tiles.size(), s);
+  else if ((layer == 0 || layer == 5) && h->l1_pairs)
+    launch_gemm_tc2(L.d_probs, L.d_tiles, L.d_cta_off, (int)L.cta_off.size() - 1, h->prec,
+                    h->tc_box[layer], h->tc_maps[layer], h->d_status, h->d_abort, s);
   else
     launch_gemm_tc(L.d_probs, L.d_tiles, L.d_cta_off, (int)L.cta_off.size() - 1, h->prec,
                    h->tc_box[layer], h->tc_maps[layer], h->d_status, h->d_abort, s);

@@ -326,6 +326,28 @@ def test_pocket_and_dense_molecules(lib, prec):
     assert int(ca.max()) > 64
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_repeated_steps_give_identical_energies(lib, prec):
+    """Twenty steps of one handle on the same positions: the energies are
+    bit-identical (every sum on their path has a fixed order) and the forces
+    agree to FP64 rounding (their global accumulation order may vary).  A
+    race between CTAs (an output box written by two of them, a read before a
+    write) shows here even where the values it produces stay plausible.  The
+    periodic region with 2 networks has first-layer tiles split into column
+    pieces; the batch has 8 networks."""
+    cases = [(W.pocket(W.workload_seed(5) + 2), W.weights(99, 2), 2), (small_batch(), W.weights(6, 8), 8)]
+    for b, w, M in cases:
+        model = lib.NNP(b.Z, w, M, mol_off=b.mol_off, precision=prec, box=b.box, use_graph=True)
+        pos = torch.tensor(b.pos, device="cuda")
+        E0, F0 = (t.cpu().numpy().copy() for t in model.compute(pos))
+        for _ in range(19):
+            E, F = model.compute(pos)
+        torch.cuda.synchronize()
+        model.status()
+        np.testing.assert_array_equal(E.cpu().numpy(), E0)
+        np.testing.assert_allclose(F.cpu().numpy(), F0, rtol=1e-12, atol=1e-12)
+
+
 def test_autotuner_keeps_results_and_picks_valid_schedule(lib):
     b, w, M = small_batch(), W.weights(6, 8), 8
     for prec in ("fp32", "fp16"):
