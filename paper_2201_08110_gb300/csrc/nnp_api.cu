@@ -1053,6 +1053,12 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   }
   if (tc) {
     if (tc_maps_bytes() > sizeof(h->tc_maps[0])) return fail(h, NNP_ERR_UNSUPPORTED, "tensor map size");
+    CK(tc_set_smem());
+    // CTA pairs for the first layer's two products (layers 2 and 3 of the
+    // split forward, K <= 3 x 256 and N <= 192, ran slower on pairs: fewer,
+    // longer tiles for the same work)
+    h->l1_max_pairs = std::min(tc2_max_pairs(h->sms), h->sms / 2);
+    h->l1_pairs = h->l1_max_pairs > 0;
     const uint64_t R64 = (uint64_t)h->n_rows;
     struct MapSpec {
       const void* base;
@@ -1106,7 +1112,6 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         CK(cudaMemcpy(L.d_cta_off, L.cta_off.data(), sizeof(int) * L.cta_off.size(), cudaMemcpyHostToDevice));
       }
     }
-    CK(tc_set_smem());
     // fused tail: one problem per (element, member), tiles of 128 rows
     for (int e = 0; e < NE; ++e) {
       const int Me = h->elem_count[e];
@@ -1189,8 +1194,6 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   }
 
   if (h->prec != Prec::F32) {  // first-layer tiles balanced over the SMs (or SM pairs)
-    h->l1_max_pairs = std::min(tc2_max_pairs(h->sms), h->sms / 2);
-    h->l1_pairs = h->l1_max_pairs > 0;
     const nnp_status st = set_l1_tiles(h, h->l1_bn);
     if (st != NNP_OK) return st;
   }
@@ -1216,7 +1219,7 @@ void run_gemm(nnp_ctx* h, int layer, cudaStream_t s) {
   if (L.tiles.empty()) return;
   if (h->prec == Prec::F32)
     launch_gemm_simt(L.d_probs, L.d_tiles, (int)L.tiles.size(), s);
-  else if ((layer == 0 || layer == 5) && h->l1_pairs)
+  else if (h->l1_pairs && (layer == 0 || layer == 5))
     launch_gemm_tc2(L.d_probs, L.d_tiles, L.d_cta_off, (int)L.cta_off.size() - 1, h->prec,
                     h->tc_box[layer], h->tc_maps[layer], h->d_status, h->d_abort, s);
   else
