@@ -296,6 +296,8 @@ NCU_TRAFFIC = {
     ("adjoint", "1dd06ca99192"): 4604.8,  # ncu --set full, 512-molecule batch, FP16
     ("features", "1dd06ca99192"): 807.2,  # ncu --set full, 512-molecule batch, FP16
     ("tail", "b875ce9262f5"): 6404.4,  # ncu --set full, 512-molecule batch, FP16
+    ("l1_fwd", "2951e46a4e75"): 12059.4,  # ncu --set full, 512-molecule batch, BF16 split, CTA pairs
+    ("l1_rev", "2951e46a4e75"): 7297.1,  # the same capture, first-layer reverse
 }
 
 
