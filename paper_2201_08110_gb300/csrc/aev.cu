@@ -936,24 +936,35 @@ int aev_adj_launches(int cap_a) { return cap_a > kAdjStage ? 2 : 1; }
 void launch_aev_adjoint(const Geometry& g, const NeighborLists& nl, const AevConst& c,
                         const int* row_of_int, const float* dG, const int4* work, int n_work,
                         const int* orig, double* F, int warps, int mol_atoms_smem_max, int* ovf,
-                        cudaStream_t s) {
+                        int ovf_ctas, cudaStream_t s) {
   if (n_work <= 0) return;
   const int stage = aev_adj_stage_cap(nl.cap_a);
   // ovf[0] was zeroed at the start of the step
   auto kern = c.model == 1 ? k_aev_adjoint<ShapeANI1x> : k_aev_adjoint<ShapeANI2x>;
   launch_pdl(kern, n_work, warps * 32, aev_adj_smem_bytes(nl.cap_r, stage, warps, mol_atoms_smem_max),
              s, g, nl, c, row_of_int, dG, work, orig, F, mol_atoms_smem_max, stage, ovf, 0);
-  if (stage < nl.cap_a) {  // two CTAs per SM: dense systems defer most centres; an empty pass is cheap
-    static int sms = 0;
-    if (!sms) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (sms <= 0) sms = 152;
-    }
-    kern<<<2 * sms, warps * 32, aev_adj_smem_bytes(nl.cap_r, nl.cap_a, warps, 0), s>>>(
+  if (stage < nl.cap_a) {
+    // as many CTAs as the SMs hold at once (ovf_ctas, from aev_adj_overflow_ctas):
+    // dense systems defer most centres to this launch, and their CTAs leave at
+    // once when the list is short
+    kern<<<ovf_ctas, warps * 32, aev_adj_smem_bytes(nl.cap_r, nl.cap_a, warps, 0), s>>>(
         g, nl, c, row_of_int, dG, work, orig, F, 0, nl.cap_a, ovf, 1);
   }
+}
+
+int aev_adj_overflow_ctas(int cap_r, int cap_a, int warps, int model) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 152;
+  const size_t smem = aev_adj_smem_bytes(cap_r, cap_a, warps, 0);
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, model == 1 ? k_aev_adjoint<ShapeANI1x> : k_aev_adjoint<ShapeANI2x>, warps * 32, smem);
+  if (e != cudaSuccess || per_sm <= 0) {
+    cudaGetLastError();
+    per_sm = 2;
+  }
+  return sms * per_sm;
 }
 
 // Raises (never lowers) the dynamic shared-memory limits of the featurizer

@@ -140,6 +140,7 @@ struct nnp_ctx {
   int n_nbr_work = 0;
   int n_work = 0;
   int fwd_warps = 4, adj_warps = 4, adj_chunk = 0, adj_shared_acc = 1, smem_atoms_max = 0;
+  int adj_ovf_ctas = 304;  // CTAs of the reverse pass's overflow launch
   int l1_bn = 256;                  // N tile of the first layer's products (tensor cores)
   bool l1_pairs = true;             // the first layer's products on CTA pairs (256-row tiles)
   int l1_max_pairs = 0;             // CTA pairs that fit on the GPU at once
@@ -437,6 +438,7 @@ nnp_status build_work_list(nnp_ctx* h, int warps, int chunk, int shared_acc = 1)
   h->adj_warps = warps;
   h->adj_chunk = chunk;
   CK(aev_set_smem_limits(0, aev_adj_launch_smem(h->nl.cap_r, h->nl.cap_a, warps, smax)));
+  h->adj_ovf_ctas = aev_adj_overflow_ctas(h->nl.cap_r, h->nl.cap_a, warps, h->md.id);
   return NNP_OK;
 }
 
@@ -1336,7 +1338,7 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
   gemm(5);
   mark(9);
   launch_aev_adjoint(g, h->nl, h->aevc, h->d_row_of_int, h->d_dG, h->d_work, h->n_work, h->d_orig,
-                     F, h->adj_warps, h->smem_atoms_max, h->d_ovf, s);
+                     F, h->adj_warps, h->smem_atoms_max, h->d_ovf, h->adj_ovf_ctas, s);
   kernels += aev_adj_launches(h->nl.cap_a);
   if (fork) cudaStreamWaitEvent(s, h->ev_join, 0);
   mark(10);

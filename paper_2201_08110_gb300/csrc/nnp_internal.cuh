@@ -257,8 +257,11 @@ void launch_aev(const Geometry& g, const NeighborLists& nl, const AevConst& c,
 void launch_aev_adjoint(const Geometry& g, const NeighborLists& nl, const AevConst& c,
                         const int* row_of_int, const float* dG, const int4* work, int n_work,
                         const int* orig, double* F, int warps, int mol_atoms_smem_max, int* ovf,
-                        cudaStream_t s);
+                        int ovf_ctas, cudaStream_t s);
 int aev_adj_stage_cap(int cap_a);  // main launch's per-warp staging capacity
+// CTAs of the overflow launch: as many as the SMs hold at once (the launch's
+// shared memory must already be allowed: aev_set_smem_limits)
+int aev_adj_overflow_ctas(int cap_r, int cap_a, int warps, int model);
 int aev_adj_launches(int cap_a);   // kernels per reverse pass
 // dynamic shared memory to allow for both launches of the reverse pass
 size_t aev_adj_launch_smem(int cap_r, int cap_a, int warps, int mol_atoms_smem_max);
