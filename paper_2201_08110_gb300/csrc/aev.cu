@@ -409,11 +409,12 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
     const int* lr = nl.nbr_r + (size_t)q * nl.cap_r;
     for (int t = lane; t < nr; t += 32) {
       const int j = lr[t];
-      const float3 d = disp(xi, g.pos[j], c);
+      const float4 xj = g.pos[j];  // w: the element index
+      const float3 d = disp(xi, xj, c);
       const float r = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
       rd[t] = r;
       rfc[t] = 0.125f * cospif(r / c.Rcr) + 0.125f;  // fc / 4 (the radial prefactor)
-      rsp[t] = g.species[j];
+      rsp[t] = __float_as_int(xj.w);
     }
   }
   __syncwarp();
@@ -441,11 +442,12 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
       int sp = -1;
       if (t < na) {
         const int j = la[t];
-        const float3 d = disp(xi, g.pos[j], c);
+        const float4 xj = g.pos[j];
+        const float3 d = disp(xi, xj, c);
         const float r = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
         avec[t] = make_float4(d.x, d.y, d.z, r);
         afc[t] = 0.5f * cospif(r / c.Rca) + 0.5f;
-        sp = g.species[j];
+        sp = __float_as_int(xj.w);
         asp[t] = sp;
       }
 #pragma unroll
@@ -667,13 +669,14 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
     const int* la = nl.nbr_a + (size_t)q * nl.cap_a;
     for (int t = lane; t < na; t += 32) {
       const int j = la[t];
-      const float3 d = disp(xi, g.pos[j], c);
+      const float4 xj = g.pos[j];
+      const float3 d = disp(xi, xj, c);
       const float ir = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
       const float r = (d.x * d.x + d.y * d.y + d.z * d.z) * ir;
       nb[2 * t] = make_float4(d.x * ir, d.y * ir, d.z * ir, r);
       float sn, cs;
       sincospif(r * inv_rca, &sn, &cs);
-      nb[2 * t + 1] = make_float4(0.5f * cs + 0.5f, dfc_a * sn, ir, __int_as_float(g.species[j]));
+      nb[2 * t + 1] = make_float4(0.5f * cs + 0.5f, dfc_a * sn, ir, xj.w);  // w: element index bits
       sg[3 * t] = sg[3 * t + 1] = sg[3 * t + 2] = 0.f;
     }
     __syncwarp();
@@ -684,7 +687,8 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
       const int* lr = nl.nbr_r + (size_t)q * nl.cap_r;
       for (int t = lane; t < nr; t += 32) {
         const int j = lr[t];
-        const float3 d = disp(xi, g.pos[j], c);
+        const float4 xj = g.pos[j];
+        const float3 d = disp(xi, xj, c);
         const float ir = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
         const float r = (d.x * d.x + d.y * d.y + d.z * d.z) * ir;
         float sn, cs;
@@ -693,7 +697,7 @@ __global__ void __launch_bounds__(128, 7) k_aev_adjoint(Geometry g, NeighborList
         const float dfc = dfc_r * sn;
         // d(e fc)/dr / e = -2 EtaR (r - ShfR) fc + dfc = afc y + dfc, y = sqEtaR (r - ShfR)
         const float afc = c.gradR * fc;
-        const float4* gsp = reinterpret_cast<const float4*>(gR + g.species[j] * kGRStride);
+        const float4* gsp = reinterpret_cast<const float4*>(gR + __float_as_int(xj.w) * kGRStride);
         float dEdr = 0.f;
 #pragma unroll
         for (int k4 = 0; k4 < kShfR / 4; ++k4) {

@@ -1266,7 +1266,8 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
   };
   mark(0);
   // with forces, the gather also zeroes them and the reverse pass's overflow count
-  launch_gather_positions(pos, h->d_orig, h->d_pos, h->n_atoms, h->d_status, F, F ? h->d_ovf : nullptr, s);
+  launch_gather_positions(pos, h->d_orig, h->d_species_int, h->d_pos, h->n_atoms, h->d_status, F,
+                          F ? h->d_ovf : nullptr, s);
   if (h->use_cells) {
     launch_neighbors_cells(g, h->nl, h->aevc, h->cells, h->cellbuf, h->n_atoms, h->d_status, s);
     kernels += 5;  // gather, bin count, scan, fill, neighbours

@@ -115,7 +115,7 @@ struct AevConst {
 
 // Geometry of one step: what the featurizer and its reverse pass read.
 struct Geometry {
-  const float4* pos;      // [N] internal order
+  const float4* pos;      // [N] internal order; w holds the element index (int bits)
   const int* mol_start;   // [N] first internal index of the atom's molecule
   const int* mol_end;     // [N] one past the last
   const int* species;     // [N] element index of internal atom
@@ -233,8 +233,10 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, siz
 
 // F_zero / ovf_zero (or null): forces and the reverse pass's overflow count
 // to zero in the same launch.
-void launch_gather_positions(const float* pos_caller, const int* orig_of_int, float4* pos_int,
-                             int n, unsigned* status, double* F_zero, int* ovf_zero, cudaStream_t s);
+// pos_int[q] = (x, y, z, element index of q as int bits)
+void launch_gather_positions(const float* pos_caller, const int* orig_of_int, const int* species_int,
+                             float4* pos_int, int n, unsigned* status, double* F_zero, int* ovf_zero,
+                             cudaStream_t s);
 // Neighbour search by work items (a0, molecule atoms, first centre, end centre),
 // chunks of nbr_chunk() centres of one molecule, one CTA each.
 int nbr_chunk();

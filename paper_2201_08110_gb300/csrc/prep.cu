@@ -84,8 +84,9 @@ __global__ void k_species_place(const int* __restrict__ species, const int* __re
 // non-finite input; when forces follow, also zeroes the forces (caller order,
 // FP64) and the reverse pass's overflow count.
 __global__ void k_gather_positions(const float* __restrict__ pos, const int* __restrict__ orig,
-                                   float4* __restrict__ out, int n, unsigned* __restrict__ status,
-                                   double* __restrict__ F, int* __restrict__ ovf) {
+                                   const int* __restrict__ species, float4* __restrict__ out, int n,
+                                   unsigned* __restrict__ status, double* __restrict__ F,
+                                   int* __restrict__ ovf) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q == 0 && ovf) *ovf = 0;
   if (q >= n) return;
@@ -97,7 +98,7 @@ __global__ void k_gather_positions(const float* __restrict__ pos, const int* __r
   }
   const float x = pos[3 * (size_t)a], y = pos[3 * (size_t)a + 1], z = pos[3 * (size_t)a + 2];
   if (!(isfinite(x) && isfinite(y) && isfinite(z))) atomicOr(status, kStatNonFinite);
-  out[q] = make_float4(x, y, z, 0.f);
+  out[q] = make_float4(x, y, z, __int_as_float(species[q]));  // the featurizers read the element here
 }
 
 template <typename T> __device__ __forceinline__ float to_f(T v);
@@ -234,10 +235,11 @@ void launch_species_place(const int* species, const int* mol_off, int n_mols,
                                              species_int, mol_start, mol_end, row_elem);
 }
 
-void launch_gather_positions(const float* pos, const int* orig, float4* out, int n, unsigned* status,
-                             double* F_zero, int* ovf_zero, cudaStream_t s) {
+void launch_gather_positions(const float* pos, const int* orig, const int* species, float4* out, int n,
+                             unsigned* status, double* F_zero, int* ovf_zero, cudaStream_t s) {
   if (n > 0)
-    k_gather_positions<<<(n + 255) / 256, 256, 0, s>>>(pos, orig, out, n, status, F_zero, ovf_zero);
+    k_gather_positions<<<(n + 255) / 256, 256, 0, s>>>(pos, orig, species, out, n, status, F_zero,
+                                                       ovf_zero);
 }
 
 void launch_head(const float* z3, long ldz, Prec prec, const int* row_elem, const float* w4,

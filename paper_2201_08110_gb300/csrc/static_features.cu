@@ -89,7 +89,7 @@ __global__ void k_static_prepare(const int* __restrict__ Z, const float* __restr
     const int ej = elem[j];
     slot += (ej < e) || (ej == e && j < i);
   }
-  s->pos[slot] = make_float4(x, y, z, 0.f);
+  s->pos[slot] = make_float4(x, y, z, __int_as_float(e));  // w: the element index, as the featurizer reads it
   s->species[slot] = e;
   s->mol_start[slot] = 0;
   s->mol_end[slot] = n;
