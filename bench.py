@@ -233,9 +233,10 @@ def stage_work(Z, M: int, n_pairs: float, n_triples: float, n_tests: float, prec
         work.update({"l2_fwd": ("tensor", l2, l2, None), "l3_fwd": ("tensor", l3 + out, l3 + out, None),
                      "l3_rev": ("tensor", l3, l3, None), "l2_rev": ("tensor", l2, l2, None)})
     elif split:
-        work.update({"l2_fwd": ("tensor", l2, 3 * l2, None), "l3_fwd": ("tensor", l3 + out, 3 * l3 + out, None),
-                     # the reverse tail: both hidden layers reverse, after its own forward
-                     "tail_rev": ("tensor", l2 + l3, 2 * l2 + 2 * l3 + out, None)})
+        # layer 2 forward, then the tail: layer 3 forward (three products) with
+        # the output layer, and both hidden layers reverse
+        work.update({"l2_fwd": ("tensor", l2, 3 * l2, None),
+                     "tail": ("tensor", l3 + out + l3 + l2, 3 * l3 + out + l3 + l2, None)})
     else:
         # the fused tail: both hidden layers forward, the output layer and both reverse
         work["tail"] = ("tensor", 2 * l2 + 2 * l3 + out, 2 * l2 + 2 * l3 + out, None)
@@ -244,12 +245,13 @@ def stage_work(Z, M: int, n_pairs: float, n_triples: float, n_tests: float, prec
 
 def shown_stages(stages: dict, prec: str, split: bool) -> dict:
     """Stage times under the names of the kernels that ran (nnp_compute_timed's
-    slots: the fused tail in l2_fwd; with split operands the reverse tail in l3_rev)."""
+    slots: the fused tail in l2_fwd; with split operands the tail from layer 3 on
+    in l3_fwd)."""
     if prec == "fp32":
         return dict(stages)
     out = {k: v for k, v in stages.items() if k not in ("l2_fwd", "l3_fwd", "l3_rev", "l2_rev")}
     if split:
-        out["l2_fwd"], out["l3_fwd"], out["tail_rev"] = stages["l2_fwd"], stages["l3_fwd"], stages["l3_rev"]
+        out["l2_fwd"], out["tail"] = stages["l2_fwd"], stages["l3_fwd"]
     else:
         out["tail"] = stages["l2_fwd"]
     return out

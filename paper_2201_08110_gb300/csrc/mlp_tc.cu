@@ -45,15 +45,14 @@ constexpr uint32_t kBBytes = kBNMax * kBK * 2;   // 32 KB (room for 256 B rows)
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
 constexpr uint32_t kStgBytes = 128 * 128;        // one output box: 128 rows x 128 bytes
 constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes + 2 * kStgBytes + 1024 /*align*/ +
-                              256 /*barriers*/ + 128 * sizeof(float) /*row sums*/;
+                              256 /*barriers*/;
 
 // CTA pairs (first layer): each CTA stages its 128 rows of A and half of
 // B's rows, so a stage is 32 KB and six fit.
 constexpr int kStages2 = 6;
 constexpr uint32_t kBHalfBytes = (kBNMax / 2) * kBK * 2;  // 16 KB
 constexpr uint32_t kStageBytes2 = kABytes + kBHalfBytes;
-constexpr size_t kSmemBytes2 = (size_t)kStages2 * kStageBytes2 + 2 * kStgBytes + 1024 /*align*/ + 256 /*barriers*/ +
-                               128 * sizeof(float) /*row sums*/;
+constexpr size_t kSmemBytes2 = (size_t)kStages2 * kStageBytes2 + 2 * kStgBytes + 1024 /*align*/ + 256 /*barriers*/;
 
 struct TcMaps {
   CUtensorMap a;
@@ -170,72 +169,6 @@ __device__ __forceinline__ void epi_store_tile(const GemmProblem& P, int n0, int
   }
 }
 
-// The output-layer epilogue (Epi::Energy) of one tile: this thread's share
-// of w4 . celu(acc + bias) over the columns of its half's boxes; half 1 posts
-// it, half 0 adds and stores y for row m_first + r of the element block.
-// With an output (P.D), each box's start of the reverse pass, d3 = (1/M) w4
-// celu'(z), is stored too (16-bit, zeros past N).  Every epilogue warp of the
-// CTA calls it (named barrier 4 over all of them; ypart: [128] floats).
-template <typename T>
-__device__ __forceinline__ void epi_energy_tile(const GemmProblem& P, int n0, int n_tile, uint32_t tbase,
-                                                unsigned char* stg, int r, int half, bool leader,
-                                                bool& in_flight, const CUtensorMap* dmap, int m_first,
-                                                float* ypart) {
-  auto half_sync = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(2 + half) : "memory"); };
-  auto epi_sync = [&]() { asm volatile("bar.sync 4, %0;" ::"r"(32 * kEpiWarps) : "memory"); };
-  float yp = 0.f;
-  const bool d3_out = P.D != nullptr;
-  for (int c = half * 64; c < n_tile; c += 128) {
-    if (d3_out) {
-      if (leader && in_flight) bulk_wait_read();  // the previous store has read stg
-      half_sync();
-    }
-#pragma unroll
-    for (int h32 = 0; h32 < 2; ++h32) {
-      const int cc = h32 * 32;
-      float v[32];
-      if (c + cc < n_tile) tmem_ld32(tbase + (uint32_t)(c + cc), v);  // warp-uniform; inside the accumulator
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        uint32_t o[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-        const int cq = c + cc + 16 * q;
-        if (cq < n_tile) {
-          float b[16], w[16];
-          ldg16(P.bias + n0 + cq, b);
-          ldg16(P.w4 + n0 + cq, w);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const float z = v[16 * q + i] + b[i];
-            const float ex = celu01_exp(z);  // celu'(z): 1 above zero
-            yp = fmaf(w[i], celu01_fast(z), yp);
-            v[16 * q + i] = w[i] * P.inv_m * ex;
-          }
-#pragma unroll
-          for (int i = 0; i < 8; ++i) o[i] = Pack<T>::two(v[16 * q + 2 * i], v[16 * q + 2 * i + 1]);
-        }
-        if (d3_out) {
-          *reinterpret_cast<uint4*>(stg + sw128_offset(r, cc + 16 * q)) = make_uint4(o[0], o[1], o[2], o[3]);
-          *reinterpret_cast<uint4*>(stg + sw128_offset(r, cc + 16 * q + 8)) = make_uint4(o[4], o[5], o[6], o[7]);
-        }
-      }
-    }
-    if (d3_out) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      half_sync();
-      if (leader) {
-        tma_store_2d(dmap, stg, P.d_col0 + n0 + c, P.a_row0 + m_first);
-        bulk_commit();
-        in_flight = true;
-      }
-    }
-  }
-  if (half == 1) ypart[r] = yp;
-  epi_sync();
-  const int row = m_first + r;
-  if (half == 0 && row < P.M) P.y[(size_t)row * P.ldy] = yp + ypart[r] + P.b4;
-  epi_sync();  // ypart is free for the next tile
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ TcMaps maps, const GemmProblem* __restrict__ probs,
@@ -252,7 +185,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* tempty = tfull + 2;       // [2] accumulator drained
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
-  float* ypart = reinterpret_cast<float*>(full) + 64;  // [128] Epi::Energy: half 1's row sums
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t stage_tx = kABytes + (uint32_t)b_box_rows * kBK * 2;
@@ -405,12 +337,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (epi_any(!got)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t tbase = tmem + acc * kBNMax + ((uint32_t)(quarter * 32) << 16);
-      if (P.epi == (int)Epi::Energy) {
-        epi_energy_tile<T>(P, tl.n0, n_tile, tbase, stg, r, half, leader, in_flight, &maps.d, tl.m0, ypart);
-      } else {
-        epi_store_tile<T>(P, tl.n0, n_tile, tbase, stg, r, half, leader, in_flight, &maps.d,
-                          P.a_row0 + tl.m0);
-      }
+      epi_store_tile<T>(P, tl.n0, n_tile, tbase, stg, r, half, leader, in_flight, &maps.d, P.a_row0 + tl.m0);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
@@ -458,7 +385,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   uint64_t* tempty = tfull + 2;        // [2] accumulator drained (first CTA's, both CTAs arrive)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
-  float* ypart = reinterpret_cast<float*>(full) + 64;  // [128] Epi::Energy: half 1's row sums
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_ctarank();
@@ -607,13 +533,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t tbase = tmem + acc * kBNMax + ((uint32_t)(quarter * 32) << 16);
       const int m_cta = tl.m0 + (int)rank * kBM;  // this CTA's first row in the element block
-      if (m_cta < P.M) {  // uniform over the CTA: rows past the element's atoms are not stored
-        if (P.epi == (int)Epi::Energy)
-          epi_energy_tile<T>(P, tl.n0, n_tile, tbase, stg, r, half, leader, in_flight, &maps.d, m_cta, ypart);
-        else
-          epi_store_tile<T>(P, tl.n0, n_tile, tbase, stg, r, half, leader, in_flight, &maps.d,
-                            P.a_row0 + m_cta);
-      }
+      if (m_cta < P.M)  // uniform over the CTA: rows past the element's atoms are not stored
+        epi_store_tile<T>(P, tl.n0, n_tile, tbase, stg, r, half, leader, in_flight, &maps.d, P.a_row0 + m_cta);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(mapa_rank(&tempty[acc], 0));

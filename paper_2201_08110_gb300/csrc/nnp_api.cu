@@ -107,7 +107,6 @@ struct nnp_ctx {
   // device: activations
   void *d_aev = nullptr, *d_h1 = nullptr, *d_h2 = nullptr, *d_d3 = nullptr;
   void* d_h2s = nullptr;  // split forward: second hidden layer (hi | lo) [rows][2 M 192]
-  void* d_d3s = nullptr;  // split forward: start of the reverse pass d3 [rows][M 192]
   float* d_z3 = nullptr;  // third-layer pre-activation, FP32 (not a product operand)
   float *d_y = nullptr, *d_dG = nullptr;
   double* d_atom_e = nullptr;
@@ -125,7 +124,7 @@ struct nnp_ctx {
   CellGrid cells{};
   CellBuffers cellbuf{};
   alignas(64) unsigned char tc_maps[6][384];  // tensor-core path: {A, B, D} TMA descriptors per layer
-  alignas(64) unsigned char tail_maps[8 * 128];  // fused tail: h1, w2, w3, w3t, w2t, h1 (32-col boxes), h2, d3
+  alignas(64) unsigned char tail_maps[7 * 128];  // fused tail: h1, w2, w3, w3t, w2t, h1 (32-col boxes), h2
   std::vector<TailProblem> tail_probs;
   std::vector<GemmTile> tail_tiles;
   std::vector<int> tail_off;  // CTA c runs tail tiles tail_off[c] .. tail_off[c + 1]
@@ -539,7 +538,7 @@ void nnp_destroy(nnp_handle h) {
   if (h->aev_aliased) h->d_aev = nullptr;  // the dE/dG buffer
   void* ptrs[] = {h->d_Z, h->d_mol_off, h->d_orig, h->d_row_of_int, h->d_species_int,
                   h->d_mol_start, h->d_mol_end, h->d_row_elem, h->d_pos, h->nl.cnt_r,
-                  h->nl.nbr_r, h->nl.cnt_a, h->nl.nbr_a, h->d_aev, h->d_h1, h->d_h2s, h->d_d3s,
+                  h->nl.nbr_r, h->nl.cnt_a, h->nl.nbr_a, h->d_aev, h->d_h1, h->d_h2s,
                   h->d_h2, h->d_z3, h->d_d3, h->d_y, h->d_dG, h->d_atom_e, h->d_status, h->d_abort, h->d_w, h->d_b,
                   h->d_w4, h->d_b4, h->d_maps, h->d_work, h->d_ovf, h->d_nbr_work, h->d_pos_in, h->d_E, h->d_F};
   for (void* p : ptrs)
@@ -798,11 +797,9 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
     CK(cudaMalloc(&h->d_d3, R * h->ldz3 * es));
     CK(cudaMemset(h->d_d3, 0, R * h->ldz3 * es));
   }
-  if (h->split) {  // the split forward's second hidden layer (hi | lo) and d3
+  if (h->split) {  // the split forward's second hidden layer (hi | lo)
     CK(cudaMalloc(&h->d_h2s, R * 2 * M * kH2Max * es));
     CK(cudaMemset(h->d_h2s, 0, R * 2 * M * kH2Max * es));
-    CK(cudaMalloc(&h->d_d3s, R * M * kH2Max * es));
-    CK(cudaMemset(h->d_d3s, 0, R * M * kH2Max * es));
   }
   CK(dalloc(&h->d_y, R * M));
   CK(dalloc(&h->d_atom_e, R));
@@ -972,22 +969,12 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         h->L[1].probs.push_back(P);
         add_tiles(h->L[1], bm, tc ? 256 : 64);
       }
-      {  // layer 3 forward; on tensor cores with the output layer fused (the
-         // tile holds the whole row), else the FP32 pre-activation for k_head
+      {  // layer 3 forward: the FP32 pre-activation for k_head
         GemmProblem P{};
         P.A = H2 + (row0 * h->ldh2 + (size_t)m * n2) * es; P.lda = h->ldh2;
         P.B = wb + (h->w_off[2] + r3[e][m] * ld_w3) * es; P.ldb = ld_w3;
-        if (tc) {
-          P.D = D3 + (row0 * h->ldz3 + (size_t)m * n3) * es; P.ldd = h->ldz3;
-          P.epi = (int)Epi::Head;
-          P.w4 = h->d_w4 + ((size_t)e * kMaxModels + m) * kH3Max;
-          P.y = h->d_y + row0 * M + m; P.ldy = M;
-          P.b4 = b4[(size_t)e * kMaxModels + m];
-          P.inv_m = 1.0f / (float)M;
-        } else {
-          P.D = Z3 + (row0 * h->ldz3 + (size_t)m * n3); P.ldd = h->ldz3;
-          P.epi = (int)Epi::Bias;
-        }
+        P.D = Z3 + (row0 * h->ldz3 + (size_t)m * n3); P.ldd = h->ldz3;
+        P.epi = (int)Epi::Bias;
         P.bias = h->d_b + b1_total + b2_total + r3[e][m];
         P.M = Me; P.N = n3; P.K = n2;
         P.a_row0 = (int)row0; P.a_col0 = m * n2; P.b_row0 = (int)r3[e][m]; P.elem = e; P.model = m;
@@ -1015,10 +1002,10 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         add_tiles(h->L[4], bm, tc ? 256 : 64);
       }
     }
-    // split forward (tensor cores): layers 2 and 3 as grouped products on
-    // (hi, lo) operands; h2 of member m at column m * 192 (the last 64-column
-    // box of a narrower layer stays inside the member's columns), its lo half
-    // M * 192 columns to the right
+    // split forward (tensor cores): layer 2 as a grouped product on (hi, lo)
+    // operands (the fused tail starts at layer 3); h2 of member m at column
+    // m * 192 (the last 64-column box of a narrower layer stays inside the
+    // member's columns), its lo half M * 192 columns to the right
     for (int m = 0; m < (h->split ? M : 0); ++m) {
       {  // layer 2 forward: h2 = celu(W2 h1 + b2)
         GemmProblem P{};
@@ -1032,24 +1019,6 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         P.elem = e; P.model = m;
         h->L[1].probs.push_back(P);
         add_tiles(h->L[1], bm, kH2Max);
-      }
-      {  // layer 3 forward + output layer: y = w4 . celu(W3 h2 + b3) + b4, and
-         // d3 = (1/M) w4 celu'(z3) for the reverse pass (member m at column m * 192)
-        GemmProblem P{};
-        P.M = Me; P.N = n3; P.K = n2; P.epi = (int)Epi::Energy;
-        P.D = h->d_d3s; P.d_col0 = m * kH2Max;
-        P.a_row0 = (int)row0; P.a_col0 = m * kH2Max; P.b_row0 = (int)r3[e][m];
-        P.bias = h->d_b + b1_total + b2_total + r3[e][m];
-        P.w4 = h->d_w4 + ((size_t)e * kMaxModels + m) * kH3Max;
-        P.y = h->d_y + row0 * M + m; P.ldy = M;
-        P.b4 = b4[(size_t)e * kMaxModels + m];
-        P.inv_m = 1.0f / (float)M;
-        P.split = 1;
-        P.a_lo = M * kH2Max;
-        P.b_lo = kH2Max;
-        P.elem = e; P.model = m;
-        h->L[2].probs.push_back(P);
-        add_tiles(h->L[2], bm, kH3Max);
       }
     }
   }
@@ -1085,9 +1054,9 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
     h->l1_b_rows[1] = B[5].rows;
     h->l1_b_cols[1] = B[5].cols;
     // the two first-layer products (layers 1-4 run in the fused tail), and with
-    // the split forward the forward products of layers 2 and 3
-    for (int l : {0, 5, 1, 2}) {
-      if ((l == 1 || l == 2) && !h->split) continue;
+    // the split forward the forward product of layer 2
+    for (int l : {0, 5, 1}) {
+      if (l == 1 && !h->split) continue;
       if (!tc_make_map(h->tc_maps[l], A[l].base, h->prec, A[l].rows, A[l].cols, A[l].cols, 128) ||
           !tc_make_map(h->tc_maps[l] + 128, B[l].base, h->prec, B[l].rows, B[l].cols, B[l].cols,
                        (uint32_t)h->tc_box[l]))
@@ -1099,14 +1068,12 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         !tc_make_map(h->tc_maps[5] + 256, h->d_dG, Prec::F32, R64, (uint64_t)kpad,
                      (uint64_t)kpad, 128, 32))
       return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for a first-layer output");
-    if (h->split) {  // layer 2's output h2 (hi | lo), layer 3's d3
+    if (h->split) {  // layer 2's output h2 (hi | lo)
       if (!tc_make_map(h->tc_maps[1] + 256, h->d_h2s, h->prec, R64, (uint64_t)2 * M * kH2Max,
-                       (uint64_t)2 * M * kH2Max, 128) ||
-          !tc_make_map(h->tc_maps[2] + 256, h->d_d3s, h->prec, R64, (uint64_t)M * kH2Max,
-                       (uint64_t)M * kH2Max, 128))
+                       (uint64_t)2 * M * kH2Max, 128))
         return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the split forward");
-      for (int l : {1, 2}) {  // tiles balanced over the SMs by K x N
-        Layer& L = h->L[l];
+      {  // tiles balanced over the SMs by K x N
+        Layer& L = h->L[1];
         std::vector<double> cost;
         for (const GemmTile& t : L.tiles) cost.push_back((double)L.probs[t.problem].K * L.probs[t.problem].N);
         balance_tiles(L.tiles, cost, h->sms, L.cta_off);
@@ -1135,10 +1102,11 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         T.w4 = h->d_w4 + ((size_t)e * kMaxModels + m) * kH3Max;
         T.b4 = b4[(size_t)e * kMaxModels + m];
         T.inv_m = 1.0f / (float)M;
-        // the split forward's layer-3 product writes y; the tail then only
-        // runs the reverse pass (recomputing its own forward for it)
-        T.y = h->split ? nullptr : h->d_y + (size_t)T.row0 * M + m;
+        // with split operands the tail starts at layer 3 (h2 from the layer-2
+        // product, hi | lo) and writes y too
+        T.y = h->d_y + (size_t)T.row0 * M + m;
         T.h2_col0 = m * kH2Max;
+        T.h2_lo = M * kH2Max;
         T.ldy = M;
         const int pi = (int)h->tail_probs.size();
         h->tail_probs.push_back(T);
@@ -1156,14 +1124,11 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
     if (!tc_make_map(h->tail_maps + 5 * 128, h->d_h1, h->prec, R64, (uint64_t)h->ldh1, (uint64_t)h->ldh1,
                      128, 32, true))
       return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the fused tail");
-    // reverse-only mode (split forward): h2 and d3 as the forward products stored
-    // them; without the split forward, valid maps that the kernel does not use
+    // split mode: h2 (hi | lo) as the layer-2 product stored it; without the
+    // split forward, a valid map that the kernel does not use
     const void* h2_base = h->split ? h->d_h2s : h->d_h1;
-    const void* d3_base = h->split ? h->d_d3s : h->d_h1;
     const uint64_t h2_cols = h->split ? (uint64_t)2 * M * kH2Max : (uint64_t)h->ldh1;
-    const uint64_t d3_cols = h->split ? (uint64_t)M * kH2Max : (uint64_t)h->ldh1;
-    if (!tc_make_map(h->tail_maps + 6 * 128, h2_base, h->prec, R64, h2_cols, h2_cols, 128) ||
-        !tc_make_map(h->tail_maps + 7 * 128, d3_base, h->prec, R64, d3_cols, d3_cols, 128))
+    if (!tc_make_map(h->tail_maps + 6 * 128, h2_base, h->prec, R64, h2_cols, h2_cols, 128))
       return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the fused tail");
     CK(tail_set_smem());
     {  // balance the tail's tiles by network size (two products per layer and direction)
@@ -1290,10 +1255,11 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
       ++kernels;
     };
     if (h->split) {
-      // split forward: layer 2, then layer 3 with the output layer (y)
+      // split forward: layer 2, then the tail from layer 3 on (layer 3 forward
+      // with the output layer and, with forces, both reverse phases)
       gemm(1);
       mark(4);
-      gemm(2);
+      tail(F ? 2 : 3);
     } else {
       // tensor cores: L2 fwd, L3 fwd + output layer, L3 rev, L2 rev in one kernel
       tail(F ? 1 : 0);
@@ -1314,7 +1280,6 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
     ++kernels;
     mark(6);
     if (!F) return kernels;
-    if (h->split) tail(2);  // the reverse pass of layers 3 and 2 from the stored h2 and d3
     mark(7);
     mark(8);
   } else {
@@ -1459,9 +1424,9 @@ int32_t nnp_kernels_per_step(nnp_handle h, int32_t with_forces) {
     for (int l = 1; l < 3; ++l) k += h->L[l].tiles.empty() ? 0 : 1;
     if (with_forces)
       for (int l = 3; l < 5; ++l) k += h->L[l].tiles.empty() ? 0 : 1;
-  } else if (h->split) {
-    for (int l = 1; l < 3; ++l) k += h->L[l].tiles.empty() ? 0 : 1;
-    if (with_forces) k += h->tail_tiles.empty() ? 0 : 1;
+  } else if (h->split) {  // layer 2, then the tail from layer 3 on
+    k += h->L[1].tiles.empty() ? 0 : 1;
+    k += h->tail_tiles.empty() ? 0 : 1;
   } else {
     k += h->tail_tiles.empty() ? 0 : 1;
   }

@@ -158,12 +158,7 @@ enum class Epi : int {
   BiasCelu = 0,   // D = celu(acc + bias[n])           (forward hidden layer)
   Bias = 1,       // D = acc + bias[n], FP32 output     (pre-activation of the last hidden layer)
   DCelu = 2,      // D = acc * celu'(D_in-place)       (reverse through a hidden layer)
-  Store = 3,      // D = acc (FP32 output)              (dE/dG)
-  Head = 4,       // last hidden layer + output layer: z = acc + bias, y[row] = w4 . celu(z) + b4,
-                  // D = (1/M) w4 * celu'(z)  (needs the whole row in one tile)
-  Energy = 5      // last hidden layer + output layer, tensor-core path: y[row] = w4 . celu(acc + bias)
-                  // + b4 in FP32 and, if D is given, D = (1/M) w4 * celu'(acc + bias) (16-bit);
-                  // needs the whole row in one tile
+  Store = 3       // D = acc (FP32 output)              (dE/dG)
 };
 
 struct GemmProblem {
@@ -180,11 +175,6 @@ struct GemmProblem {
   // right of the hi halves in the same arrays; with d_lo > 0 a 16-bit output
   // is stored as hi = round(v) and lo = round(v - hi), lo d_lo columns right.
   int split, a_lo, b_lo, d_lo;
-  // Epi::Head / Epi::Energy only
-  const float* w4;  // [N] output weights of this (element, member)
-  float* y;         // per-row output, stride ldy
-  long ldy;
-  float b4, inv_m;
 };
 
 // The fused tail of one (element, ensemble member): second and third hidden
@@ -201,7 +191,8 @@ struct TailProblem {
   float b4, inv_m;
   float* y;     // y + row0 * M + member, stride ldy
   long ldy;
-  int h2_col0;  // reverse-only mode: first column of this member in h2 and d3 (member * 192)
+  int h2_col0;  // split mode: first column of this member in h2 (member * 192)
+  int h2_lo;    // split mode: columns from h2_hi to h2_lo (M * 192)
 };
 
 // A tile of the flattened problem list.
