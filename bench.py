@@ -295,11 +295,12 @@ def src_hash(*names):
 # scaled to the bench workload by atoms.  A kernel changed since its capture
 # finds no entry and reports null.
 NCU_TRAFFIC = {
-    ("adjoint", "1dd06ca99192"): 4604.8,  # ncu --set full, 512-molecule batch, FP16
-    ("features", "1dd06ca99192"): 807.2,  # ncu --set full, 512-molecule batch, FP16
-    ("tail", "b875ce9262f5"): 6404.4,  # ncu --set full, 512-molecule batch, FP16
-    ("l1_fwd", "2951e46a4e75"): 12059.4,  # ncu --set full, 512-molecule batch, BF16 split, CTA pairs
-    ("l1_rev", "2951e46a4e75"): 7297.1,  # the same capture, first-layer reverse
+    # ncu --set full, 512-molecule batch, split BF16 step (first launch of each kernel)
+    ("features", "ae4a540c8f1f"): 2846.7,
+    ("l1_fwd", "4a5c20e5b515"): 12052.9,  # first layer forward, CTA pairs
+    ("l1_rev", "4a5c20e5b515"): 7293.4,   # the same kernel's second launch, first-layer reverse
+    ("l2_fwd", "4a5c20e5b515"): 12597.3,  # layer 2 forward (k_gemm_tc)
+    ("tail", "eeafe1138397"): 13143.9,    # the tail from layer 3 on
 }
 
 
