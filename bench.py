@@ -233,27 +233,22 @@ def stage_work(Z, M: int, n_pairs: float, n_triples: float, n_tests: float, prec
         work.update({"l2_fwd": ("tensor", l2, l2, None), "l3_fwd": ("tensor", l3 + out, l3 + out, None),
                      "l3_rev": ("tensor", l3, l3, None), "l2_rev": ("tensor", l2, l2, None)})
     elif split:
-        # layer 2 forward, then the tail: layer 3 forward (three products) with
-        # the output layer, and both hidden layers reverse
-        work.update({"l2_fwd": ("tensor", l2, 3 * l2, None),
-                     "tail": ("tensor", l3 + out + l3 + l2, 3 * l3 + out + l3 + l2, None)})
+        # the tail: layers 2 and 3 forward (three products each) with the
+        # output layer, and both hidden layers reverse
+        work["tail"] = ("tensor", 2 * l2 + 2 * l3 + out, 4 * l2 + 4 * l3 + out, None)
     else:
         # the fused tail: both hidden layers forward, the output layer and both reverse
         work["tail"] = ("tensor", 2 * l2 + 2 * l3 + out, 2 * l2 + 2 * l3 + out, None)
     return work
 
 
-def shown_stages(stages: dict, prec: str, split: bool) -> dict:
+def shown_stages(stages: dict, prec: str) -> dict:
     """Stage times under the names of the kernels that ran (nnp_compute_timed's
-    slots: the fused tail in l2_fwd; with split operands the tail from layer 3 on
-    in l3_fwd)."""
+    slots: the fused tail in l2_fwd)."""
     if prec == "fp32":
         return dict(stages)
     out = {k: v for k, v in stages.items() if k not in ("l2_fwd", "l3_fwd", "l3_rev", "l2_rev")}
-    if split:
-        out["l2_fwd"], out["tail"] = stages["l2_fwd"], stages["l3_fwd"]
-    else:
-        out["tail"] = stages["l2_fwd"]
+    out["tail"] = stages["l2_fwd"]
     return out
 
 
@@ -299,8 +294,6 @@ NCU_TRAFFIC = {
     ("features", "ae4a540c8f1f"): 2846.7,
     ("l1_fwd", "4a5c20e5b515"): 12052.9,  # first layer forward, CTA pairs
     ("l1_rev", "4a5c20e5b515"): 7293.4,   # the same kernel's second launch, first-layer reverse
-    ("l2_fwd", "4a5c20e5b515"): 12597.3,  # layer 2 forward (k_gemm_tc)
-    ("tail", "eeafe1138397"): 13143.9,    # the tail from layer 3 on
 }
 
 
@@ -850,7 +843,7 @@ def run_ours(args):
     hbm, bf16, bf16_sus, peak_kind, sm_max = peaks()
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 lanes x 2 x max SM clock, TFLOP/s
     tensor_path = args.precision != "fp32"
-    shown = shown_stages(stages, args.precision, split)
+    shown = shown_stages(stages, args.precision)
     rooflines = rooflines_of(shown, work, tensor_path, hbm, bf16, peak_kind, fp32_peak)
     dom = max(rooflines, key=lambda k: rooflines[k]["ms"])
     kernel_src = {"features": "aev.cu", "adjoint": "aev.cu", "neighbors": "aev.cu",

@@ -27,15 +27,15 @@
 //   warps 2-17: epilogue, 64 columns at a time (TMEM lane quarter = warp % 4,
 //     16 columns per warp), signalling each finished block.
 // Split mode (reverse = 2, or 3 without the reverse pass; split-operand
-// forward products): layer 2 ran elsewhere and stored h2 as hi and lo 16-bit
-// halves; the producer loads h2_hi into A1 and h2_lo into A2 by TMA (h2_lo
-// once the previous tile is done with A2: its d1 store has read the staging
-// memory over A2, or without the reverse pass its last product has read
-// h2_lo), and the tile starts at L3 forward: the three products h2_hi W3_hi,
-// h2_hi W3_lo (which need only A1, so they overlap the previous tile's last
-// epilogue) and h2_lo W3_hi, with the output layer (and d3) in its epilogue,
-// then the two reverse phases.  One or three phases a tile: accumulator x of
-// tile t's first phase alternates with t, the next ones x^1, x.
+// forward products): the first layer stored h1 as hi and lo 16-bit halves;
+// the producer loads h1_hi into A1 and h1_lo into the second buffer and the
+// block after it by TMA (h1_lo once the previous tile is done there: its d1
+// store has read the staging memory, or without the reverse pass its last
+// product has read h2_lo).  Each forward layer is three products, the two on
+// the hi half of the activations first (for layer 2 they need only A1, so
+// they overlap the previous tile's last epilogue), then lo x W_hi; phase 1's
+// epilogue writes h2 as hi into A1 and lo into A2, phase 2's output layer
+// then writes d3 over h2_lo.
 // Waits are bounded: one that gives up sets the timeout status bit, the CTA
 // stops, frees its tensor memory and returns.
 #include <cstring>
@@ -54,7 +54,7 @@ constexpr int kRing = 3;
 constexpr uint32_t kBlk = 128 * kBK * 2;     // one [128][64] 16-bit block: 16 KB
 constexpr uint32_t kRingBytes = 256 * kBK * 2;  // a weight block of up to 256 rows
 constexpr int kA1Blocks = 4;                 // h1 (<= 256 columns), then h2 and d2 over it
-constexpr int kA2Blocks = 3;                 // d3 (<= 160 columns); in split mode h2_lo (<= 192) first
+constexpr int kA2Blocks = 3;                 // d3 (<= 160 columns); in split mode h1_lo, h2_lo first
 constexpr int kEpiWarps = 16;  // four per TMEM lane quarter, 16 of every 64 columns each
 constexpr int kThreads = 64 + 32 * kEpiWarps + 32;  // + the phase-4 staging loader
 constexpr int kTmemCols = 512;  // two accumulators of 256 columns
@@ -63,6 +63,7 @@ constexpr int kTmemCols = 512;  // two accumulators of 256 columns
 constexpr uint32_t kP4Box = 128 * 32 * 2;
 constexpr int kP4Boxes = kH1Max / 32;
 static_assert((size_t)kP4Boxes * kP4Box <= (size_t)(kA2Blocks + 1) * kBlk, "phase-4 staging");
+static_assert(kA1Blocks <= kA2Blocks + 1, "split mode: h1_lo over the second buffer and the block after it");
 constexpr size_t kSmemBytes = (size_t)(kA1Blocks + kA2Blocks + 1) * kBlk + (size_t)kRing * kRingBytes +
                               1024 + 256 + 3 * 128 * sizeof(float);
 
@@ -73,7 +74,6 @@ struct TailMaps {
   CUtensorMap w3t;  // [sum h2 rows][160], box 64 x 192
   CUtensorMap w2t;  // [sum h1 rows][192], box 64 x 256
   CUtensorMap h1s;  // activations again, box 32 x 128, 64-byte swizzle (phase 4 in and out)
-  CUtensorMap h2;   // split mode: second hidden layer, hi | lo [rows][2*M*192], box 64 x 128
 };
 constexpr int kBoxW2 = kH2Max, kBoxW3 = kH3Max, kBoxW3T = kH2Max, kBoxW2T = kH1Max;
 
@@ -164,8 +164,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* blk_done = acc_free + 2;   // [4] epilogue -> MMA: 64-column block of the next A written
   uint64_t* p4_full = blk_done + 4;    // producer -> epilogue: the tile's h1 is in P4
   uint64_t* a2_free = p4_full + 1;     // MMA -> P4 loader: phase-3 MMAs are done with d3 (A2)
-  uint64_t* a2_full = a2_free + 1;     // [3] split mode: producer -> MMA, block b of h2_lo loaded
-  uint64_t* p4_drained = a2_full + kA2Blocks;  // split mode: epilogue -> producer, d1 store read P4
+  uint64_t* lo_full = a2_free + 1;     // [4] split mode: producer -> MMA, block b of h1_lo loaded
+  uint64_t* p4_drained = lo_full + kA1Blocks;  // split mode: epilogue -> producer, d1 store read P4
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(p4_drained + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   // [3][128]: the output-layer dot of each row over the column groups 1-3
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int b = 0; b < 4; ++b) mbar_init(&blk_done[b], kEpiWarps);
     mbar_init(p4_full, 1);
     mbar_init(a2_free, 1);
-    for (int b = 0; b < kA2Blocks; ++b) mbar_init(&a2_full[b], 1);
+    for (int b = 0; b < kA1Blocks; ++b) mbar_init(&lo_full[b], 1);
     mbar_init(p4_drained, 1);
     *abort_flag = *abort_req;  // nonzero only in tests of the abort path
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -221,36 +221,47 @@ __global__ void __launch_bounds__(kThreads, 1)
       // an abort requested at the start: nothing is loaded (the other roles'
       // first waits give up on the flag)
       bool ok = *(volatile int*)abort_flag == 0;
-      uint32_t a1_uses[kA1Blocks] = {0, 0, 0, 0};  // split mode: loads of each A1 block
       for (int tile = tile_begin; ok && tile < tile_end; ++tile, ++tcount) {
         const GemmTile tl = tiles[tile];
         const TailProblem P = probs[tl.problem];
         if (split) {
-          const int nb2 = nblocks(P.h2);
-          // h2_hi into A1, block by block as the previous tile's L2-reverse MMAs free it
-          for (int kb = 0; ok && kb < nb2; ++kb) {
-            if (a1_uses[kb] > 0 && !mbar_wait(&a1_free[kb], (a1_uses[kb] - 1) & 1, abort_flag)) {
+          const int nb1 = nblocks(P.h1), nb2 = nblocks(P.h2);
+          // h1_hi into A1 as the previous tile frees each block (blocks past
+          // h1 get a plain arrival: every block completes once a tile)
+          for (int kb = 0; ok && kb < kA1Blocks; ++kb) {
+            if (tcount > 0 && !mbar_wait(&a1_free[kb], (tcount - 1) & 1, abort_flag)) {
               ok = false;
               break;
             }
-            ++a1_uses[kb];
+            if (kb >= nb1) {
+              mbar_arrive(&a1_full[kb]);
+              continue;
+            }
             mbar_expect_tx(&a1_full[kb], kBlk);
-            tma_load_2d(A1 + (size_t)kb * kBlk, &maps.h2, P.h2_col0 + kb * kBK, P.row0 + tl.m0, &a1_full[kb]);
+            tma_load_2d(A1 + (size_t)kb * kBlk, &maps.h1, P.a_col0 + kb * kBK, P.row0 + tl.m0, &a1_full[kb]);
           }
-          // W3_hi and W3_lo for the two products on h2_hi, which need nothing else
+          // W2_hi and W2_lo for the two products on h1_hi, which need nothing else
           ok = ok &&
-               produce_weights(&maps.w3, P.w3_row0, nb2, kBoxW3, ring, full, empty, it, abort_flag) &&
-               produce_weights(&maps.w3, P.w3_row0, nb2, kBoxW3, ring, full, empty, it, abort_flag, kH2Max);
-          // h2_lo into A2 once the previous tile is done with A2: its d1 store
-          // has read P4 (over A2), or its last product has read h2_lo
+               produce_weights(&maps.w2, P.w2_row0, nb1, kBoxW2, ring, full, empty, it, abort_flag) &&
+               produce_weights(&maps.w2, P.w2_row0, nb1, kBoxW2, ring, full, empty, it, abort_flag, kH1Max);
+          // h1_lo into the second buffer and the block after it (four blocks)
+          // once the previous tile is done there: its d1 store has read P4,
+          // or (without the reverse pass) its last product has read h2_lo
           if (ok && tcount > 0 && !mbar_wait(with_rev ? p4_drained : a2_free, (tcount - 1) & 1, abort_flag))
             ok = false;
-          for (int kb = 0; ok && kb < nb2; ++kb) {
-            mbar_expect_tx(&a2_full[kb], kBlk);
-            tma_load_2d(A2 + (size_t)kb * kBlk, &maps.h2, P.h2_lo + P.h2_col0 + kb * kBK, P.row0 + tl.m0,
-                        &a2_full[kb]);
+          for (int kb = 0; ok && kb < kA1Blocks; ++kb) {
+            if (kb >= nb1) {
+              mbar_arrive(&lo_full[kb]);
+              continue;
+            }
+            mbar_expect_tx(&lo_full[kb], kBlk);
+            tma_load_2d(A2 + (size_t)kb * kBlk, &maps.h1, P.h1_lo + P.a_col0 + kb * kBK, P.row0 + tl.m0,
+                        &lo_full[kb]);
           }
-          ok = ok && produce_weights(&maps.w3, P.w3_row0, nb2, kBoxW3, ring, full, empty, it, abort_flag);
+          ok = ok && produce_weights(&maps.w2, P.w2_row0, nb1, kBoxW2, ring, full, empty, it, abort_flag) &&
+               produce_weights(&maps.w3, P.w3_row0, nb2, kBoxW3, ring, full, empty, it, abort_flag) &&
+               produce_weights(&maps.w3, P.w3_row0, nb2, kBoxW3, ring, full, empty, it, abort_flag, kH2Max) &&
+               produce_weights(&maps.w3, P.w3_row0, nb2, kBoxW3, ring, full, empty, it, abort_flag);
           if (ok && with_rev)
             ok = produce_weights(&maps.w3t, P.w3t_row0, nblocks(P.h3), kBoxW3T, ring, full, empty, it, abort_flag) &&
                  produce_weights(&maps.w2t, P.w2t_row0, nb2, kBoxW2T, ring, full, empty, it, abort_flag);
@@ -306,9 +317,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       // phases 2-4: K block b waits for block b of the A operand from the
       // epilogue; blk_free: commit each K block's completion there (the
       // last reader of that block of A1)
-      // split mode: waits for the TMA loads of h2_lo (A2) and h2_hi (A1)
-      uint32_t a2_waits[kA2Blocks] = {0, 0, 0};
+      // split mode: waits for the TMA loads of h1_hi (A1) and h1_lo
       uint32_t a1_waits[kA1Blocks] = {0, 0, 0, 0};
+      uint32_t lo_waits[kA1Blocks] = {0, 0, 0, 0};
       // a_ready / a_waits: the barriers (and the waits so far) that block b of
       // the A operand completes (the epilogue's blk_done)
       auto phase = [&](int x, const unsigned char* a_base, int k, int n, uint64_t* blk_free,
@@ -386,30 +397,36 @@ __global__ void __launch_bounds__(kThreads, 1)
         // A1 blocks past h2 are not read again in this tile
         for (int kb = nblocks(P.h2); kb < kA1Blocks; ++kb) mma_commit_elect(&a1_free[kb]);
       };
-      // split mode, L3 forward: h2_hi W3_hi, h2_hi W3_lo (A1, loaded by TMA),
-      // then h2_lo W3_hi (A2, loaded by TMA), in the producer's ring order
-      auto phase_l3_split = [&](int x, const TailProblem& P) {
+      // split mode, a forward layer (K = k, N = n) as three products in the
+      // producer's ring order: A_hi B_hi and A_hi B_lo (A_hi in A1), then
+      // A_lo B_hi (A_lo in the second buffer).  Before its first use, K block
+      // b of A_hi waits on hi_ready[b] and of A_lo on lo_ready[b] (null: no
+      // wait), for b < n_wait (blocks past k complete their barrier but issue
+      // nothing); after the A_hi products, A1 blocks from keep_a1 on are free.
+      auto phase_split = [&](int x, int k, int n, int n_wait, uint64_t* hi_ready, uint32_t* hi_waits,
+                             uint64_t* lo_ready, uint32_t* lo_waits, int keep_a1) {
         if (!ok) return;
         if (used[x] > 0 && !mbar_wait_warp(&acc_free[x], (used[x] - 1) & 1, abort_flag)) {
           ok = false;
           return;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t idesc = instr_desc(fmt, (uint32_t)P.h3);
+        const uint32_t idesc = instr_desc(fmt, (uint32_t)n);
         const uint32_t d = tmem + (uint32_t)(x * kTmemCols / 2);
-        const int n_kb = nblocks(P.h2);
+        const int n_kb = nblocks(k);
         bool acc = false;
-        for (int seg = 0; seg < 3; ++seg)
-          for (int kb = 0; kb < n_kb; ++kb, ++it) {
-            uint64_t* a_ready = seg == 0 ? &a1_full[kb] : seg == 2 ? &a2_full[kb] : nullptr;
-            uint32_t* a_wait = seg == 0 ? &a1_waits[kb] : seg == 2 ? &a2_waits[kb] : nullptr;
-            if (a_ready) {
-              if (!mbar_wait_warp(a_ready, *a_wait & 1, abort_flag)) {
+        for (int seg = 0; seg < 3; ++seg) {
+          uint64_t* ready = seg == 0 ? hi_ready : seg == 2 ? lo_ready : nullptr;
+          uint32_t* waits = seg == 0 ? hi_waits : lo_waits;
+          for (int kb = 0; kb < (ready ? n_wait : n_kb); ++kb) {
+            if (ready) {
+              if (!mbar_wait_warp(&ready[kb], waits[kb] & 1, abort_flag)) {
                 ok = false;
                 return;
               }
-              ++*a_wait;
+              ++waits[kb];
             }
+            if (kb >= n_kb) continue;
             const int s = it % kRing;
             if (!mbar_wait_warp(&full[s], (it / kRing) & 1, abort_flag)) {
               ok = false;
@@ -418,13 +435,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint64_t da = smem_desc_sw128((seg == 2 ? A2 : A1) + (size_t)kb * kBlk);
             const uint64_t db = smem_desc_sw128(ring + (size_t)s * kRingBytes);
-            const int ksteps = min(kBK, P.h2 - kb * kBK) / 16;
+            const int ksteps = min(kBK, k - kb * kBK) / 16;
             for (int j = 0; j < ksteps; ++j) {
               mma_f16_elect(d, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc, acc ? 1u : 0u);
               acc = true;
             }
             mma_commit_elect(&empty[s]);
+            ++it;
           }
+          if (seg == 1)
+            for (int kb = keep_a1; kb < kA1Blocks; ++kb) mma_commit_elect(&a1_free[kb]);
+        }
         mma_commit_elect(&acc_ready[x]);
         ++used[x];
       };
@@ -433,16 +454,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         const GemmTile tl = tiles[tile];
         const TailProblem P = probs[tl.problem];
         if (split) {
-          const int x = (int)(tcount & 1);  // one or three phases a tile: accumulators x, x^1, x
-          phase_l3_split(x, P);             // L3 forward, y (and d3 -> A2)
+          const int nb2 = nblocks(P.h2);
+          // L2 forward: h1_hi (A1) and h1_lo (second buffer) loaded by TMA;
+          // A1 blocks past h2 are free after the products on h1_hi
+          phase_split(0, P.h1, P.h2, kA1Blocks, a1_full, a1_waits, lo_full, lo_waits, nb2);
+          // L3 forward: h2_hi (A1) and h2_lo (A2) from the epilogue, block b
+          // of both announced by one blk_done arrival
+          phase_split(1, P.h2, P.h3, nb2, blk_done, blk_waits, nullptr, nullptr, kA1Blocks);
           if (!with_rev) {  // the last readers of A1 and A2 in this tile
-            for (int kb = 0; ok && kb < nblocks(P.h2); ++kb) mma_commit_elect(&a1_free[kb]);
+            for (int kb = 0; ok && kb < nb2; ++kb) mma_commit_elect(&a1_free[kb]);
             if (ok) mma_commit_elect(a2_free);
             continue;
           }
-          phase(x ^ 1, A2, P.h3, P.h2, nullptr, blk_done, blk_waits);  // L3 reverse, block by block of d3
-          if (ok) mma_commit_elect(a2_free);                          // A2 may take phase 4's h1
-          phase(x, A1, P.h2, P.h1, a1_free, blk_done, blk_waits);     // L2 reverse, d2 over h2_hi
+          phase(0, A2, P.h3, P.h2, nullptr, blk_done, blk_waits);  // L3 reverse, block by block of d3
+          if (ok) mma_commit_elect(a2_free);                      // A2 may take phase 4's h1
+          phase(1, A1, P.h2, P.h1, a1_free, blk_done, blk_waits);  // L2 reverse, d2 over h2_hi
           continue;
         }
         phase1(P, first);                 // L2 forward
@@ -491,7 +517,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int r = quarter * 32 + lane;  // tile row = TMEM lane
     const uint32_t tq = (uint32_t)(quarter * 32) << 16;
     uint32_t ready_waits[2] = {0, 0}, p4_waits = 0;
-    uint32_t a1_waits[kA1Blocks] = {0, 0, 0, 0};  // split mode: h2_hi block loads waited for
     bool ok = true;
     auto wait_acc = [&](int x) -> uint32_t {  // TMEM address of accumulator x for this warp
       if (ok && !mbar_wait(&acc_ready[x], ready_waits[x] & 1, abort_flag)) {
@@ -542,9 +567,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       const TailProblem P = probs[tl.problem];
       const int row = tl.m0 + r;
       const bool row_ok = row < P.Me;
-      // accumulators of phases 2, 3, 4: 1, 0, 1 after phase 1 in accumulator 0;
-      // in split mode (no phase 1) x, x^1, x with x alternating by tile
-      const int xa = split ? (int)((tile - tile_begin) & 1) : 1;
       // the barrier ends the previous tile's readers of ypart
       if (epi_stop()) break;
       {  // warm the L1 with this tile's b2, b3 and w4 (128-byte lines, one per thread)
@@ -556,8 +578,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
 
       // phase 1, L2 forward (accumulator 0): h2 = celu(acc + b2) -> A1 (its
-      // MMAs, the last readers of h1 there, are complete), block by block
-      if (!split) {
+      // MMAs, the last readers of h1 there, are complete), block by block; in
+      // split mode as hi = round(h2) into A1 and lo = round(h2 - hi) into A2
+      {
         const uint32_t t = wait_acc(0);
         for (int b = 0; b < nblocks(P.h2); ++b) {
           int c0, c1;
@@ -566,21 +589,25 @@ __global__ void __launch_bounds__(kThreads, 1)
             float bias[16], v[16];
             ldg16(P.b2 + c, bias);  // in flight during the TMEM load
             tmem_ld16(t + (uint32_t)c, v);
-            uint32_t o[8];
+            uint32_t o[8], lo[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-              o[i] = Pack<T>::two(celu01_fast(v[2 * i] + bias[2 * i]),
-                                  celu01_fast(v[2 * i + 1] + bias[2 * i + 1]));
+            for (int i = 0; i < 8; ++i) {
+              const float h0 = celu01_fast(v[2 * i] + bias[2 * i]);
+              const float h1 = celu01_fast(v[2 * i + 1] + bias[2 * i + 1]);
+              o[i] = Pack<T>::two(h0, h1);
+              lo[i] = Pack<T>::two(h0 - Pack<T>::lo(o[i]), h1 - Pack<T>::hi(o[i]));
+            }
             put16(A1, r, c, o);
+            if (split) put16(A2, r, c, lo);
           }
           arrive(&blk_done[b]);
         }
         release(&acc_free[0]);
       }
 
-      // phase 2, L3 forward + output layer (accumulator xa): y, d3 -> A2
+      // phase 2, L3 forward + output layer (accumulator 1): y, d3 -> A2
       {
-        const uint32_t t = wait_acc(xa);
+        const uint32_t t = wait_acc(1);
         if (with_rev) {  // the previous tile's d1 store has read P4 (over A2)
           if (et == 0) bulk_wait_read();
           epi_sync();
@@ -616,23 +643,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         quad_sync();
         if (ok && !grp && row_ok)
           P.y[(size_t)row * P.ldy] = yacc + ypart[r] + ypart[128 + r] + ypart[256 + r] + P.b4;
-        release(&acc_free[xa]);
+        release(&acc_free[1]);
       }
       if (!with_rev) continue;
 
-      // phase 3, L3 reverse (accumulator xa^1): d2 = acc * celu'(h2), in place in A1
+      // phase 3, L3 reverse (accumulator 0): d2 = acc * celu'(h2), in place in A1
       {
-        const uint32_t t = wait_acc(xa ^ 1);
+        const uint32_t t = wait_acc(0);
         for (int b = 0; b < nblocks(P.h2); ++b) {
-          if (split) {  // block b of h2_hi, loaded by TMA
-            if (ok && !mbar_wait(&a1_full[b], a1_waits[b] & 1, abort_flag)) {
-              atomicOr(status, kStatTimeout);
-              atomicExch(abort_flag, 1);
-              ok = false;
-            }
-            ok = __all_sync(0xffffffffu, ok);
-            ++a1_waits[b];
-          }
           int c0, c1;
           my_cols(b, P.h2, c0, c1);
           for (int c = c0; ok && c < c1; c += 16) {
@@ -648,14 +666,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           arrive(&blk_done[b]);
         }
-        release(&acc_free[xa ^ 1]);
+        release(&acc_free[0]);
       }
 
-      // phase 4, L2 reverse (accumulator xa): d1 = acc * celu'(h1), h1 staged in
+      // phase 4, L2 reverse (accumulator 1): d1 = acc * celu'(h1), h1 staged in
       // P4 by TMA and overwritten there by d1, which one thread then stores
       // with TMA (this warp: every fourth 16-column chunk of its 32 rows)
       {
-        const uint32_t t = wait_acc(xa);
+        const uint32_t t = wait_acc(1);
         if (ok && !mbar_wait(p4_full, p4_waits & 1, abort_flag)) {
           atomicOr(status, kStatTimeout);
           atomicExch(abort_flag, 1);
@@ -674,14 +692,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 v[2 * k + 1] * dcelu_from_act(Pack<T>::hi(hin[k])));
           put16_p4(P4, r, c, o);
         }
-        release(&acc_free[xa]);
+        release(&acc_free[1]);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         epi_sync();
         if (et == 0 && ok) {
           for (int j = 0; j < P.h1 / 32; ++j)
             tma_store_2d(&maps.h1s, P4 + (size_t)j * kP4Box, P.a_col0 + 32 * j, P.row0 + tl.m0);
           bulk_commit();
-          if (split) {  // the producer's next h2_lo load goes over P4
+          if (split) {  // the producer's next h1_lo load goes over P4
             bulk_wait_read();
             mbar_arrive(p4_drained);
           }

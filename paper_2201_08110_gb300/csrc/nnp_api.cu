@@ -106,7 +106,6 @@ struct nnp_ctx {
   NeighborLists nl{};
   // device: activations
   void *d_aev = nullptr, *d_h1 = nullptr, *d_h2 = nullptr, *d_d3 = nullptr;
-  void* d_h2s = nullptr;  // split forward: second hidden layer (hi | lo) [rows][2 M 192]
   float* d_z3 = nullptr;  // third-layer pre-activation, FP32 (not a product operand)
   float *d_y = nullptr, *d_dG = nullptr;
   double* d_atom_e = nullptr;
@@ -124,7 +123,7 @@ struct nnp_ctx {
   CellGrid cells{};
   CellBuffers cellbuf{};
   alignas(64) unsigned char tc_maps[6][384];  // tensor-core path: {A, B, D} TMA descriptors per layer
-  alignas(64) unsigned char tail_maps[7 * 128];  // fused tail: h1, w2, w3, w3t, w2t, h1 (32-col boxes), h2
+  alignas(64) unsigned char tail_maps[6 * 128];  // fused tail: h1, w2, w3, w3t, w2t, h1 (32-col boxes)
   std::vector<TailProblem> tail_probs;
   std::vector<GemmTile> tail_tiles;
   std::vector<int> tail_off;  // CTA c runs tail tiles tail_off[c] .. tail_off[c + 1]
@@ -538,7 +537,7 @@ void nnp_destroy(nnp_handle h) {
   if (h->aev_aliased) h->d_aev = nullptr;  // the dE/dG buffer
   void* ptrs[] = {h->d_Z, h->d_mol_off, h->d_orig, h->d_row_of_int, h->d_species_int,
                   h->d_mol_start, h->d_mol_end, h->d_row_elem, h->d_pos, h->nl.cnt_r,
-                  h->nl.nbr_r, h->nl.cnt_a, h->nl.nbr_a, h->d_aev, h->d_h1, h->d_h2s,
+                  h->nl.nbr_r, h->nl.cnt_a, h->nl.nbr_a, h->d_aev, h->d_h1,
                   h->d_h2, h->d_z3, h->d_d3, h->d_y, h->d_dG, h->d_atom_e, h->d_status, h->d_abort, h->d_w, h->d_b,
                   h->d_w4, h->d_b4, h->d_maps, h->d_work, h->d_ovf, h->d_nbr_work, h->d_pos_in, h->d_E, h->d_F};
   for (void* p : ptrs)
@@ -797,10 +796,6 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
     CK(cudaMalloc(&h->d_d3, R * h->ldz3 * es));
     CK(cudaMemset(h->d_d3, 0, R * h->ldz3 * es));
   }
-  if (h->split) {  // the split forward's second hidden layer (hi | lo)
-    CK(cudaMalloc(&h->d_h2s, R * 2 * M * kH2Max * es));
-    CK(cudaMemset(h->d_h2s, 0, R * 2 * M * kH2Max * es));
-  }
   CK(dalloc(&h->d_y, R * M));
   CK(dalloc(&h->d_atom_e, R));
   CK(dalloc(&h->d_pos_in, (size_t)N * 3));
@@ -1002,32 +997,13 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         add_tiles(h->L[4], bm, tc ? 256 : 64);
       }
     }
-    // split forward (tensor cores): layer 2 as a grouped product on (hi, lo)
-    // operands (the fused tail starts at layer 3); h2 of member m at column
-    // m * 192 (the last 64-column box of a narrower layer stays inside the
-    // member's columns), its lo half M * 192 columns to the right
-    for (int m = 0; m < (h->split ? M : 0); ++m) {
-      {  // layer 2 forward: h2 = celu(W2 h1 + b2)
-        GemmProblem P{};
-        P.M = Me; P.N = n2; P.K = n1; P.epi = (int)Epi::BiasCelu;
-        P.a_row0 = (int)row0; P.a_col0 = m * n1; P.b_row0 = (int)r2[e][m]; P.d_col0 = m * kH2Max;
-        P.bias = h->d_b + b1_total + r2[e][m];
-        P.split = 1;
-        P.a_lo = M * kH1Max;
-        P.b_lo = kH1Max;
-        P.d_lo = M * kH2Max;
-        P.elem = e; P.model = m;
-        h->L[1].probs.push_back(P);
-        add_tiles(h->L[1], bm, kH2Max);
-      }
-    }
   }
   if (tc) {
     if (tc_maps_bytes() > sizeof(h->tc_maps[0])) return fail(h, NNP_ERR_UNSUPPORTED, "tensor map size");
     CK(tc_set_smem());
-    // CTA pairs for the first layer's two products (layers 2 and 3 of the
-    // split forward, K <= 3 x 256 and N <= 192, ran slower on pairs: fewer,
-    // longer tiles for the same work)
+    // CTA pairs for the first layer's two products (grouped products of
+    // layers 2 and 3 with K <= 3 x 256 and N <= 192 ran slower on pairs:
+    // fewer, longer tiles for the same work)
     h->l1_max_pairs = std::min(tc2_max_pairs(h->sms), h->sms / 2);
     h->l1_pairs = h->l1_max_pairs > 0;
     const uint64_t R64 = (uint64_t)h->n_rows;
@@ -1037,7 +1013,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
     };
     const MapSpec A[6] = {{h->d_aev, R64, (uint64_t)kpad * sp},
                           {h->d_h1, R64, (uint64_t)h->ldh1},
-                          {h->d_h2s, R64, (uint64_t)2 * M * kH2Max},
+                          {h->d_h1, R64, (uint64_t)h->ldh1},
                           {h->d_d3, R64, (uint64_t)h->ldz3},
                           {h->d_h2, R64, (uint64_t)h->ldh2},
                           {h->d_h1, R64, (uint64_t)h->ldh1}};
@@ -1053,10 +1029,8 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
     h->l1_b_base[1] = B[5].base;
     h->l1_b_rows[1] = B[5].rows;
     h->l1_b_cols[1] = B[5].cols;
-    // the two first-layer products (layers 1-4 run in the fused tail), and with
-    // the split forward the forward product of layer 2
-    for (int l : {0, 5, 1}) {
-      if (l == 1 && !h->split) continue;
+    // the two first-layer products (layers 2 and 3 run in the fused tail)
+    for (int l : {0, 5}) {
       if (!tc_make_map(h->tc_maps[l], A[l].base, h->prec, A[l].rows, A[l].cols, A[l].cols, 128) ||
           !tc_make_map(h->tc_maps[l] + 128, B[l].base, h->prec, B[l].rows, B[l].cols, B[l].cols,
                        (uint32_t)h->tc_box[l]))
@@ -1068,19 +1042,6 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         !tc_make_map(h->tc_maps[5] + 256, h->d_dG, Prec::F32, R64, (uint64_t)kpad,
                      (uint64_t)kpad, 128, 32))
       return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for a first-layer output");
-    if (h->split) {  // layer 2's output h2 (hi | lo)
-      if (!tc_make_map(h->tc_maps[1] + 256, h->d_h2s, h->prec, R64, (uint64_t)2 * M * kH2Max,
-                       (uint64_t)2 * M * kH2Max, 128))
-        return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the split forward");
-      {  // tiles balanced over the SMs by K x N
-        Layer& L = h->L[1];
-        std::vector<double> cost;
-        for (const GemmTile& t : L.tiles) cost.push_back((double)L.probs[t.problem].K * L.probs[t.problem].N);
-        balance_tiles(L.tiles, cost, h->sms, L.cta_off);
-        CK(dalloc(&L.d_cta_off, L.cta_off.size()));
-        CK(cudaMemcpy(L.d_cta_off, L.cta_off.data(), sizeof(int) * L.cta_off.size(), cudaMemcpyHostToDevice));
-      }
-    }
     // fused tail: one problem per (element, member), tiles of 128 rows
     for (int e = 0; e < NE; ++e) {
       const int Me = h->elem_count[e];
@@ -1102,11 +1063,8 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         T.w4 = h->d_w4 + ((size_t)e * kMaxModels + m) * kH3Max;
         T.b4 = b4[(size_t)e * kMaxModels + m];
         T.inv_m = 1.0f / (float)M;
-        // with split operands the tail starts at layer 3 (h2 from the layer-2
-        // product, hi | lo) and writes y too
         T.y = h->d_y + (size_t)T.row0 * M + m;
-        T.h2_col0 = m * kH2Max;
-        T.h2_lo = M * kH2Max;
+        T.h1_lo = M * kH1Max;
         T.ldy = M;
         const int pi = (int)h->tail_probs.size();
         h->tail_probs.push_back(T);
@@ -1123,12 +1081,6 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the fused tail");
     if (!tc_make_map(h->tail_maps + 5 * 128, h->d_h1, h->prec, R64, (uint64_t)h->ldh1, (uint64_t)h->ldh1,
                      128, 32, true))
-      return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the fused tail");
-    // split mode: h2 (hi | lo) as the layer-2 product stored it; without the
-    // split forward, a valid map that the kernel does not use
-    const void* h2_base = h->split ? h->d_h2s : h->d_h1;
-    const uint64_t h2_cols = h->split ? (uint64_t)2 * M * kH2Max : (uint64_t)h->ldh1;
-    if (!tc_make_map(h->tail_maps + 6 * 128, h2_base, h->prec, R64, h2_cols, h2_cols, 128))
       return fail(h, NNP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the fused tail");
     CK(tail_set_smem());
     {  // balance the tail's tiles by network size (two products per layer and direction)
@@ -1254,17 +1206,11 @@ int enqueue_step(nnp_ctx* h, const float* pos, double* E, double* F, cudaStream_
                       h->tail_maps, reverse, h->d_status, h->d_abort, s);
       ++kernels;
     };
-    if (h->split) {
-      // split forward: layer 2, then the tail from layer 3 on (layer 3 forward
-      // with the output layer and, with forces, both reverse phases)
-      gemm(1);
-      mark(4);
-      tail(F ? 2 : 3);
-    } else {
-      // tensor cores: L2 fwd, L3 fwd + output layer, L3 rev, L2 rev in one kernel
-      tail(F ? 1 : 0);
-      mark(4);
-    }
+    // tensor cores: L2 fwd, L3 fwd + output layer, L3 rev, L2 rev in one
+    // kernel (without forces, the forward phases); with split operands each
+    // forward product as three
+    tail(h->split ? (F ? 2 : 3) : (F ? 1 : 0));
+    mark(4);
     mark(5);
     // with forces (and no per-stage events) the energy reduction runs on a
     // side stream, concurrently with the reverse pass, joined at the end
@@ -1424,9 +1370,6 @@ int32_t nnp_kernels_per_step(nnp_handle h, int32_t with_forces) {
     for (int l = 1; l < 3; ++l) k += h->L[l].tiles.empty() ? 0 : 1;
     if (with_forces)
       for (int l = 3; l < 5; ++l) k += h->L[l].tiles.empty() ? 0 : 1;
-  } else if (h->split) {  // layer 2, then the tail from layer 3 on
-    k += h->L[1].tiles.empty() ? 0 : 1;
-    k += h->tail_tiles.empty() ? 0 : 1;
   } else {
     k += h->tail_tiles.empty() ? 0 : 1;
   }

@@ -191,8 +191,7 @@ struct TailProblem {
   float b4, inv_m;
   float* y;     // y + row0 * M + member, stride ldy
   long ldy;
-  int h2_col0;  // split mode: first column of this member in h2 (member * 192)
-  int h2_lo;    // split mode: columns from h2_hi to h2_lo (M * 192)
+  int h1_lo;    // split mode: columns from h1_hi to h1_lo (M * 256)
 };
 
 // A tile of the flattened problem list.
