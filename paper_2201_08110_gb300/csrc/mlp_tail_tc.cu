@@ -258,10 +258,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             tma_load_2d(A2 + (size_t)kb * kBlk, &maps.h1, P.h1_lo + P.a_col0 + kb * kBK, P.row0 + tl.m0,
                         &lo_full[kb]);
           }
-          ok = ok && produce_weights(&maps.w2, P.w2_row0, nb1, kBoxW2, ring, full, empty, it, abort_flag) &&
-               produce_weights(&maps.w3, P.w3_row0, nb2, kBoxW3, ring, full, empty, it, abort_flag) &&
-               produce_weights(&maps.w3, P.w3_row0, nb2, kBoxW3, ring, full, empty, it, abort_flag, kH2Max) &&
-               produce_weights(&maps.w3, P.w3_row0, nb2, kBoxW3, ring, full, empty, it, abort_flag);
+          ok = ok && produce_weights(&maps.w2, P.w2_row0, nb1, kBoxW2, ring, full, empty, it, abort_flag);
+          // W3 block by block, in the order of layer 3's products: hi, lo, hi
+          for (int kb = 0; ok && kb < nb2; ++kb)
+            ok = produce_weights(&maps.w3, P.w3_row0, 1, kBoxW3, ring, full, empty, it, abort_flag, kb * kBK) &&
+                 produce_weights(&maps.w3, P.w3_row0, 1, kBoxW3, ring, full, empty, it, abort_flag,
+                                 kH2Max + kb * kBK) &&
+                 produce_weights(&maps.w3, P.w3_row0, 1, kBoxW3, ring, full, empty, it, abort_flag, kb * kBK);
           if (ok && with_rev)
             ok = produce_weights(&maps.w3t, P.w3t_row0, nblocks(P.h3), kBoxW3T, ring, full, empty, it, abort_flag) &&
                  produce_weights(&maps.w2t, P.w2t_row0, nb2, kBoxW2T, ring, full, empty, it, abort_flag);
@@ -399,12 +402,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       };
       // split mode, a forward layer (K = k, N = n) as three products in the
       // producer's ring order: A_hi B_hi and A_hi B_lo (A_hi in A1), then
-      // A_lo B_hi (A_lo in the second buffer).  Before its first use, K block
-      // b of A_hi waits on hi_ready[b] and of A_lo on lo_ready[b] (null: no
-      // wait), for b < n_wait (blocks past k complete their barrier but issue
-      // nothing); after the A_hi products, A1 blocks from keep_a1 on are free.
+      // A_lo B_hi (A_lo in the second buffer), each over all K blocks; or,
+      // with by_block, the three products of K block b as soon as block b is
+      // ready (A_hi and A_lo of a block announced together on hi_ready).
+      // Before its first use, K block b of A_hi waits on hi_ready[b] and of
+      // A_lo on lo_ready[b] (null: no wait), for b < n_wait (blocks past k
+      // complete their barrier but issue nothing); after the A_hi products, A1
+      // blocks from keep_a1 on are free.
       auto phase_split = [&](int x, int k, int n, int n_wait, uint64_t* hi_ready, uint32_t* hi_waits,
-                             uint64_t* lo_ready, uint32_t* lo_waits, int keep_a1) {
+                             uint64_t* lo_ready, uint32_t* lo_waits, int keep_a1, bool by_block) {
         if (!ok) return;
         if (used[x] > 0 && !mbar_wait_warp(&acc_free[x], (used[x] - 1) & 1, abort_flag)) {
           ok = false;
@@ -415,36 +421,46 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t d = tmem + (uint32_t)(x * kTmemCols / 2);
         const int n_kb = nblocks(k);
         bool acc = false;
-        for (int seg = 0; seg < 3; ++seg) {
-          uint64_t* ready = seg == 0 ? hi_ready : seg == 2 ? lo_ready : nullptr;
-          uint32_t* waits = seg == 0 ? hi_waits : lo_waits;
-          for (int kb = 0; kb < (ready ? n_wait : n_kb); ++kb) {
-            if (ready) {
-              if (!mbar_wait_warp(&ready[kb], waits[kb] & 1, abort_flag)) {
-                ok = false;
-                return;
-              }
-              ++waits[kb];
-            }
-            if (kb >= n_kb) continue;
-            const int s = it % kRing;
-            if (!mbar_wait_warp(&full[s], (it / kRing) & 1, abort_flag)) {
+        auto wait_ready = [&](uint64_t* ready, uint32_t* waits, int kb) -> bool {
+          if (!ready) return true;
+          if (!mbar_wait_warp(&ready[kb], waits[kb] & 1, abort_flag)) return false;
+          ++waits[kb];
+          return true;
+        };
+        // one ring block: K block kb of A_hi (A1) or A_lo (second buffer)
+        auto issue = [&](bool lo_half, int kb) -> bool {
+          const int s = it % kRing;
+          if (!mbar_wait_warp(&full[s], (it / kRing) & 1, abort_flag)) return false;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t da = smem_desc_sw128((lo_half ? A2 : A1) + (size_t)kb * kBlk);
+          const uint64_t db = smem_desc_sw128(ring + (size_t)s * kRingBytes);
+          const int ksteps = min(kBK, k - kb * kBK) / 16;
+          for (int j = 0; j < ksteps; ++j) {
+            mma_f16_elect(d, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc, acc ? 1u : 0u);
+            acc = true;
+          }
+          mma_commit_elect(&empty[s]);
+          ++it;
+          return true;
+        };
+        if (by_block) {
+          for (int kb = 0; kb < n_kb; ++kb)
+            if (!wait_ready(hi_ready, hi_waits, kb) || !issue(false, kb) || !issue(false, kb) || !issue(true, kb)) {
               ok = false;
               return;
             }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint64_t da = smem_desc_sw128((seg == 2 ? A2 : A1) + (size_t)kb * kBlk);
-            const uint64_t db = smem_desc_sw128(ring + (size_t)s * kRingBytes);
-            const int ksteps = min(kBK, k - kb * kBK) / 16;
-            for (int j = 0; j < ksteps; ++j) {
-              mma_f16_elect(d, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc, acc ? 1u : 0u);
-              acc = true;
-            }
-            mma_commit_elect(&empty[s]);
-            ++it;
+        } else {
+          for (int seg = 0; seg < 3; ++seg) {
+            uint64_t* ready = seg == 0 ? hi_ready : seg == 2 ? lo_ready : nullptr;
+            uint32_t* waits = seg == 0 ? hi_waits : lo_waits;
+            for (int kb = 0; kb < (ready ? n_wait : n_kb); ++kb)
+              if (!wait_ready(ready, waits, kb) || (kb < n_kb && !issue(seg == 2, kb))) {
+                ok = false;
+                return;
+              }
+            if (seg == 1)
+              for (int kb = keep_a1; kb < kA1Blocks; ++kb) mma_commit_elect(&a1_free[kb]);
           }
-          if (seg == 1)
-            for (int kb = keep_a1; kb < kA1Blocks; ++kb) mma_commit_elect(&a1_free[kb]);
         }
         mma_commit_elect(&acc_ready[x]);
         ++used[x];
@@ -457,10 +473,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int nb2 = nblocks(P.h2);
           // L2 forward: h1_hi (A1) and h1_lo (second buffer) loaded by TMA;
           // A1 blocks past h2 are free after the products on h1_hi
-          phase_split(0, P.h1, P.h2, kA1Blocks, a1_full, a1_waits, lo_full, lo_waits, nb2);
+          phase_split(0, P.h1, P.h2, kA1Blocks, a1_full, a1_waits, lo_full, lo_waits, nb2, false);
           // L3 forward: h2_hi (A1) and h2_lo (A2) from the epilogue, block b
-          // of both announced by one blk_done arrival
-          phase_split(1, P.h2, P.h3, nb2, blk_done, blk_waits, nullptr, nullptr, kA1Blocks);
+          // of both announced by one blk_done arrival, its three products
+          // issued as soon as it is written
+          phase_split(1, P.h2, P.h3, nb2, blk_done, blk_waits, nullptr, nullptr, kA1Blocks, true);
           if (!with_rev) {  // the last readers of A1 and A2 in this tile
             for (int kb = 0; ok && kb < nb2; ++kb) mma_commit_elect(&a1_free[kb]);
             if (ok) mma_commit_elect(a2_free);
