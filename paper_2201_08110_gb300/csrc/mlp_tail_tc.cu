@@ -117,9 +117,13 @@ __device__ __forceinline__ void get16(const unsigned char* blocks, int r, int c,
   o[4] = y.x; o[5] = y.y; o[6] = y.z; o[7] = y.w;
 }
 
-// celu'(z) from h = celu(z), alpha = 0.1: 1 + h / alpha for z <= 0, where it
-// is at most 1, and 1 for z > 0, where 1 + h / alpha exceeds 1.
-__device__ __forceinline__ float dcelu_from_act(float h) { return fminf(fmaf(10.f, h, 1.f), 1.f); }
+// d * celu'(z) for two values, celu'(z) from h = celu(z), alpha = 0.1:
+// 1 + h / alpha for z <= 0, where it is at most 1, and 1 for z > 0, where
+// 1 + h / alpha exceeds 1 (packed FP32 arithmetic).
+__device__ __forceinline__ float2 times_dcelu(float2 d, float2 h) {
+  const float2 g = __ffma2_rn(f2(10.f), h, f2(1.f));
+  return __fmul2_rn(d, make_float2(fminf(g.x, 1.f), fminf(g.y, 1.f)));
+}
 
 // Row r, columns c..c+15 (c a multiple of 16) of the phase-4 tile: box c / 32,
 // 64-byte rows whose 16-byte chunk k sits at position k ^ ((r / 2) % 4), the
@@ -609,10 +613,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t o[8], lo[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              const float h0 = celu01_fast(v[2 * i] + bias[2 * i]);
-              const float h1 = celu01_fast(v[2 * i + 1] + bias[2 * i + 1]);
-              o[i] = Pack<T>::two(h0, h1);
-              lo[i] = Pack<T>::two(h0 - Pack<T>::lo(o[i]), h1 - Pack<T>::hi(o[i]));
+              float2 h, e;
+              celu01_pair(__fadd2_rn(make_float2(v[2 * i], v[2 * i + 1]), make_float2(bias[2 * i], bias[2 * i + 1])),
+                          h, e);
+              o[i] = Pack<T>::two(h.x, h.y);
+              lo[i] = Pack<T>::two(h.x - Pack<T>::lo(o[i]), h.y - Pack<T>::hi(o[i]));
             }
             put16(A1, r, c, o);
             if (split) put16(A2, r, c, lo);
@@ -629,7 +634,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (et == 0) bulk_wait_read();
           epi_sync();
         }
-        float yacc = 0.f;
+        float2 yacc2 = f2(0.f);  // even and odd columns
         for (int b = 0; b < nblocks(P.h3); ++b) {
           int c0, c1;
           my_cols(b, P.h3, c0, c1);
@@ -641,21 +646,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t o[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              float dv[2];
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const int k = 2 * i + h;
-                const float z = v[k] + b3[k];
-                const float ex = celu01_exp(z);  // celu'(z): 1 above zero
-                yacc = fmaf(w4[k], celu01_fast(z), yacc);
-                dv[h] = w4[k] * P.inv_m * ex;
-              }
-              o[i] = Pack<T>::two(dv[0], dv[1]);
+              const float2 w = make_float2(w4[2 * i], w4[2 * i + 1]);
+              float2 h, ex;  // celu(z) and celu'(z)
+              celu01_pair(__fadd2_rn(make_float2(v[2 * i], v[2 * i + 1]), make_float2(b3[2 * i], b3[2 * i + 1])),
+                          h, ex);
+              yacc2 = __ffma2_rn(w, h, yacc2);
+              const float2 dv = __fmul2_rn(__fmul2_rn(w, f2(P.inv_m)), ex);
+              o[i] = Pack<T>::two(dv.x, dv.y);
             }
             if (with_rev) put16(A2, r, c, o);
           }
           if (with_rev) arrive(&blk_done[b]);
         }
+        const float yacc = yacc2.x + yacc2.y;
         if (grp) ypart[(grp - 1) * 128 + r] = yacc;
         quad_sync();
         if (ok && !grp && row_ok)
@@ -676,9 +679,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t hin[8], o[8];
             get16(A1, r, c, hin);
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-              o[i] = Pack<T>::two(v[2 * i] * dcelu_from_act(Pack<T>::lo(hin[i])),
-                                  v[2 * i + 1] * dcelu_from_act(Pack<T>::hi(hin[i])));
+            for (int i = 0; i < 8; ++i) {
+              const float2 d = times_dcelu(make_float2(v[2 * i], v[2 * i + 1]),
+                                           make_float2(Pack<T>::lo(hin[i]), Pack<T>::hi(hin[i])));
+              o[i] = Pack<T>::two(d.x, d.y);
+            }
             put16(A1, r, c, o);
           }
           arrive(&blk_done[b]);
@@ -704,9 +709,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint32_t hin[8], o[8];
           get16_p4(P4, r, c, hin);
 #pragma unroll
-          for (int k = 0; k < 8; ++k)
-            o[k] = Pack<T>::two(v[2 * k] * dcelu_from_act(Pack<T>::lo(hin[k])),
-                                v[2 * k + 1] * dcelu_from_act(Pack<T>::hi(hin[k])));
+          for (int k = 0; k < 8; ++k) {
+            const float2 d = times_dcelu(make_float2(v[2 * k], v[2 * k + 1]),
+                                         make_float2(Pack<T>::lo(hin[k]), Pack<T>::hi(hin[k])));
+            o[k] = Pack<T>::two(d.x, d.y);
+          }
           put16_p4(P4, r, c, o);
         }
         release(&acc_free[1]);

@@ -328,6 +328,25 @@ __device__ __forceinline__ float celu01_fast(float z) {
   return fmaxf(z, neg);
 }
 
+// celu01_fast of two values with packed FP32 arithmetic (per component the
+// same roundings, so the same results), and e = exp(min(z, 0) / alpha), which
+// is celu'(z) (1 above zero): the epilogues that need both share the
+// exponential.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ void celu01_pair(float2 z, float2& c, float2& e) {
+  const float2 zn = make_float2(fminf(z.x, 0.f), fminf(z.y, 0.f));
+  float2 p = __ffma2_rn(zn, f2(125.f / 3.f), f2(50.f / 3.f));
+  p = __ffma2_rn(zn, p, f2(5.f));
+  p = __ffma2_rn(zn, p, f2(1.f));
+  p = __fmul2_rn(p, zn);
+  const float2 u = __fmul2_rn(zn, f2(14.426950408889634f));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.x) : "f"(u.x));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.y) : "f"(u.y));
+  const float2 q = __ffma2_rn(f2(0.1f), e, f2(-0.1f));
+  c.x = fmaxf(z.x, zn.x > -0.0125f ? p.x : q.x);
+  c.y = fmaxf(z.y, zn.y > -0.0125f ? p.y : q.y);
+}
+
 // Programmatic dependent launch: let the next kernel in the stream start its
 // prologue, and wait until the kernels this one depends on have completed
 // (with their memory visible).  Both are no-ops in a launch without the
