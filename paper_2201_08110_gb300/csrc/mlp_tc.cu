@@ -127,7 +127,13 @@ __device__ __forceinline__ void epi_store_tile(const GemmProblem& P, int n0, int
           if (cq < n_tile) {  // bias only for the problem's columns (no read past it)
             ldg16(P.bias + n0 + cq, b);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[16 * q + i] = celu01_fast(v[16 * q + i] + b[i]);
+            for (int i = 0; i < 16; i += 2) {  // two values per packed FP32 instruction
+              float2 h, e;
+              celu01_pair(__fadd2_rn(make_float2(v[16 * q + i], v[16 * q + i + 1]), make_float2(b[i], b[i + 1])), h,
+                          e);
+              v[16 * q + i] = h.x;
+              v[16 * q + i + 1] = h.y;
+            }
           } else {  // past the problem's columns: zeros
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[16 * q + i] = 0.f;

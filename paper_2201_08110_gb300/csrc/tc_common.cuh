@@ -299,40 +299,21 @@ __device__ __forceinline__ void ldg16(const float* p, float (&v)[16]) {
   }
 }
 
-// exp(min(z, 0) / alpha), alpha = 0.1, on the SFU base-2 exponential with
-// denormals flushed to zero (relative error near 2^-22, far below the 16-bit
-// rounding of every value it feeds).  It is CELU's slope for z <= 0 and 1
-// for z > 0.
-__device__ __forceinline__ float celu01_exp(float z) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(fminf(z, 0.f) * 14.426950408889634f));
-  return y;
-}
-
-// CELU (alpha = 0.1): max(z, alpha expm1(min(z, 0) / alpha)).  For z > 0 the
-// second term is 0; for z <= 0, alpha expm1(z / alpha) >= z since exp(u) >=
-// 1 + u.  For -1/80 < z <= 0 the Taylor polynomial of degree 4 of alpha
-// expm1(z / alpha) = z + 5 z^2 + (50/3) z^3 + (125/3) z^4 + ... (truncation at
-// most (250/3) |z|^5, 2.2e-6 of the value), so that small activations keep
-// their relative precision (alpha (exp(z / alpha) - 1) would cancel: the
-// exponential's error, near 2^-22 of 1, is an absolute error on values that
-// may be far smaller); below, |alpha expm1(z / alpha)| >= 0.0117, so the same
-// error is at most 1.8e-6 of it.  Both stay under the 2^-17 relative
-// precision of a split (hi, lo) 16-bit activation.
-__device__ __forceinline__ float celu01_fast(float z) {
-  const float zn = fminf(z, 0.f);
-  float p = fmaf(zn, 125.f / 3.f, 50.f / 3.f);
-  p = fmaf(zn, p, 5.f);
-  p = fmaf(zn, p, 1.f);
-  const float neg = zn > -0.0125f ? p * zn : fmaf(0.1f, celu01_exp(z), -0.1f);
-  return fmaxf(z, neg);
-}
-
-// celu01_fast of two values with packed FP32 arithmetic (per component the
-// same roundings, so the same results), and e = exp(min(z, 0) / alpha), which
-// is celu'(z) (1 above zero): the epilogues that need both share the
-// exponential.
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// CELU (alpha = 0.1) of two values, c = max(z, alpha expm1(min(z, 0) / alpha)),
+// and its slope e = exp(min(z, 0) / alpha) (1 for z > 0), in packed FP32
+// arithmetic (two values per instruction, per component the roundings of the
+// scalar operations).  For z > 0 the second term of the max is 0; for z <= 0,
+// alpha expm1(z / alpha) >= z since exp(u) >= 1 + u.  For -1/80 < z <= 0 the
+// Taylor polynomial of degree 4 of alpha expm1(z / alpha) = z + 5 z^2 +
+// (50/3) z^3 + (125/3) z^4 + ... (truncation at most (250/3) |z|^5, 2.2e-6 of
+// the value) keeps small activations' relative precision (alpha (exp(z /
+// alpha) - 1) would cancel: the exponential's error, near 2^-22 of 1, is an
+// absolute error on values that may be far smaller); below, |alpha expm1(z /
+// alpha)| >= 0.0117, so the same error is at most 1.8e-6 of it.  Both stay
+// under the 2^-17 relative precision of a split (hi, lo) 16-bit activation.
+// The exponential is the SFU base-2 one with denormals flushed to zero.
 __device__ __forceinline__ void celu01_pair(float2 z, float2& c, float2& e) {
   const float2 zn = make_float2(fminf(z.x, 0.f), fminf(z.y, 0.f));
   float2 p = __ffma2_rn(zn, f2(125.f / 3.f), f2(50.f / 3.f));
