@@ -242,6 +242,31 @@ template <int N> __device__ __forceinline__ float powi(float b) {
   }
 }
 
+// Packed FP32 arithmetic: two values per instruction, per component the
+// roundings of the scalar operation (so the same results as the scalar code).
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 ex2_ftz2(float2 x) { return make_float2(ex2_ftz(x.x), ex2_ftz(x.y)); }
+__device__ __forceinline__ float2 lg2_ftz2(float2 x) { return make_float2(lg2_ftz(x.x), lg2_ftz(x.y)); }
+template <int N> __device__ __forceinline__ float2 powi2(float2 b) {
+  if constexpr (N == 0) {
+    return f2(1.f);
+  } else if constexpr (N == 1) {
+    return b;
+  } else {
+    const float2 h = powi2<N / 2>(b);
+    return (N & 1) ? mul2(mul2(h, h), b) : mul2(h, h);
+  }
+}
+// 2^(-y^2) of two Gaussian arguments y = fma(r, c_hi, -s_hi) + fma(r, c_lo, -s_lo)
+__device__ __forceinline__ float2 gauss2(float r, float c_hi, float c_lo, float s_hi0, float s_hi1,
+                                         float s_lo0, float s_lo1, float2& y) {
+  y = add2(fma2(f2(r), f2(c_hi), make_float2(-s_hi0, -s_hi1)), fma2(f2(r), f2(c_lo), make_float2(-s_lo0, -s_lo1)));
+  return ex2_ftz2(mul2(make_float2(-y.x, -y.y), y));
+}
+
 // Species pair (s, t), s <= t, of each block, row-major upper triangle: the
 // 28 blocks of seven elements, then the 10 of four.
 __constant__ unsigned char kBlkS[kPairBlocks + 10] = {0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 3,
@@ -483,20 +508,26 @@ __global__ void k_aev(Geometry g, NeighborLists nl, AevConst c, const int* __res
         const float fcjk = 2.f * afc[j] * afc[k];
         const float u = 0.5f * (rj.w + rk.w);
 #pragma unroll
-        for (int a = 0; a < NA; ++a) {
-          // 2^(-y^2) = exp(-EtaA (u - ShfA)^2)
-          const float y = fmaf(u, c.sqEtaA, -c.ShfAs[a]) + fmaf(u, c.sqEtaAl, -c.ShfAsl[a]);
-          buf[a * kBufStride + lane] = ex2_ftz(-y * y);
+        for (int a = 0; a < NA; a += 2) {
+          // 2^(-y^2) = exp(-EtaA (u - ShfA)^2), two shifts at a time
+          float2 y;
+          const float2 R = gauss2(u, c.sqEtaA, c.sqEtaAl, c.ShfAs[a], c.ShfAs[a + 1], c.ShfAsl[a], c.ShfAsl[a + 1], y);
+          buf[a * kBufStride + lane] = R.x;
+          buf[(a + 1) * kBufStride + lane] = R.y;
         }
 #pragma unroll
-        for (int z = 0; z < NZ; ++z) {
+        for (int z = 0; z < NZ; z += 2) {
           // t = 1 + cos(theta' - ThetaS): ((1 + cos) / 2)^Zeta = 2^(Zeta (lg2 t - 1)),
           // or (t / 2)^Zeta by multiplication for an integer Zeta
-          const float t = fmaxf(fmaf(sp, c.sinZ[z], fmaf(cp, c.cosZ[z], 1.f)), 0.f);
-          float A;
-          if constexpr (Shape::kZetaInt > 0) A = powi<Shape::kZetaInt>(0.5f * t);
-          else A = ex2_ftz(fmaf(c.Zeta, lg2_ftz(t), -c.Zeta));
-          buf[(NA + z) * kBufStride + lane] = A * fcjk;
+          const float2 t0 = fma2(f2(sp), make_float2(c.sinZ[z], c.sinZ[z + 1]),
+                                 fma2(f2(cp), make_float2(c.cosZ[z], c.cosZ[z + 1]), f2(1.f)));
+          const float2 t = make_float2(fmaxf(t0.x, 0.f), fmaxf(t0.y, 0.f));
+          float2 A;
+          if constexpr (Shape::kZetaInt > 0) A = powi2<Shape::kZetaInt>(mul2(f2(0.5f), t));
+          else A = ex2_ftz2(fma2(f2(c.Zeta), lg2_ftz2(t), f2(-c.Zeta)));
+          const float2 Af = mul2(A, f2(fcjk));
+          buf[(NA + z) * kBufStride + lane] = Af.x;
+          buf[(NA + z + 1) * kBufStride + lane] = Af.y;
         }
       } else {  // padding pair: zero factors
 #pragma unroll
