@@ -290,10 +290,12 @@ def src_hash(*names):
 # scaled to the bench workload by atoms.  A kernel changed since its capture
 # finds no entry and reports null.
 NCU_TRAFFIC = {
-    # ncu --set full, 512-molecule batch, split BF16 step (first launch of each kernel)
-    ("features", "ae4a540c8f1f"): 2846.7,
-    ("l1_fwd", "4a5c20e5b515"): 12052.9,  # first layer forward, CTA pairs
-    ("l1_rev", "4a5c20e5b515"): 7293.4,   # the same kernel's second launch, first-layer reverse
+    # ncu --set full, 512-molecule batch, split BF16 step (first launches of each kernel)
+    ("features", "9212797d998e"): 2849.1,
+    ("adjoint", "9212797d998e"): 4585.2,  # main launch (the overflow launch moves ~1 KB)
+    ("l1_fwd", "8c4a8808f271"): 12052.4,  # first layer forward, CTA pairs
+    ("l1_rev", "8c4a8808f271"): 7296.0,   # the same kernel's second launch, first-layer reverse
+    ("tail", "a3a9d71014bf"): 11044.0,    # layers 2 and 3 forward and reverse
 }
 
 
