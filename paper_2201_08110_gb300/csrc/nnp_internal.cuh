@@ -285,8 +285,9 @@ void launch_export_atomic_energies(const double* atom_energy_row, const int* row
 size_t tail_maps_bytes();
 int tail_weight_box(int which);  // box rows of the w2, w3, w3t, w2t maps
 cudaError_t tail_set_smem();
-// reverse: 0 forward only, 1 forward and reverse, 2 reverse only (h2 and d3
-// stored by the split forward products).  abort_req: DEVICE int read at
+// reverse: 0 forward only, 1 forward and reverse (one product per layer);
+// with split operands (h1 stored as hi | lo, three products per forward
+// layer) 2 forward and reverse, 3 forward only.  abort_req: DEVICE int read at
 // kernel start; nonzero makes the kernel stop before it issues any copy or
 // product, as after a bounded wait that gave up
 void launch_mlp_tail(const TailProblem* probs, const GemmTile* tiles, const int* cta_off, int n_ctas,
