@@ -129,7 +129,10 @@ typedef struct {
                              one of its bounded waits had given up, before it issues any
                              copy or product, so the step ends with NNP_ERR_TIMEOUT */
   int32_t model;          /* nnp_model (0 = ANI-2x, the zero-initialised default) */
-  int32_t reserved[3];    /* must be zero */
+  int32_t single_cta;     /* 1: the first layer's tensor-core products on single CTAs
+                             (128-row tiles), the path taken when the device cannot hold
+                             CTA pairs; 0 = pairs where possible (default) */
+  int32_t reserved[2];    /* must be zero */
 } nnp_params;
 
 /* Number of FP32 parameters of one ANI-2x ensemble member (1,713,223). */

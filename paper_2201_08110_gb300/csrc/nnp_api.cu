@@ -91,6 +91,7 @@ struct nnp_ctx {
   int aev_aliased = 0;     // the features share their buffer with dE/dG
   bool features_overwritten = false;  // the last step's reverse pass wrote over the features
   int test_abort = 0;
+  int single_cta = 0;  // the first layer on single CTAs even where pairs fit
   ModelDesc md{};  // the model: elements, feature layout, network widths
   AevConst aevc{};
   int elem_count[kSpecies] = {0};
@@ -581,10 +582,10 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   if (!model_desc(params->model, md)) return fail(nullptr, NNP_ERR_ARG, "model must be 0 (ANI-2x) or 1 (ANI-1x)");
   if (!params->weights || params->n_weights != model_params(md) * params->n_models)
     return fail(nullptr, NNP_ERR_ARG, "weights: expected n_models * nnp_weights_per_model_of(model) floats");
-  for (int r = 0; r < 3; ++r)
+  for (int r = 0; r < 2; ++r)
     if (params->reserved[r] != 0) return fail(nullptr, NNP_ERR_ARG, "reserved fields must be zero");
-  if ((params->single_pass | params->recompute_aev | params->test_abort) & ~1)
-    return fail(nullptr, NNP_ERR_ARG, "single_pass, recompute_aev and test_abort must be 0 or 1");
+  if ((params->single_pass | params->recompute_aev | params->test_abort | params->single_cta) & ~1)
+    return fail(nullptr, NNP_ERR_ARG, "single_pass, recompute_aev, test_abort and single_cta must be 0 or 1");
   if (params->neighbor_mode < 0 || params->neighbor_mode > 2)
     return fail(nullptr, NNP_ERR_ARG, "neighbor_mode must be 0, 1 or 2");
   for (int i = 0; i < N; ++i) {
@@ -628,6 +629,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   h->split = (h->prec != Prec::F32 && !params->single_pass) ? 1 : 0;
   h->aev_aliased = params->recompute_aev;
   h->test_abort = params->test_abort;
+  h->single_cta = params->single_cta;
   h->md = md;
   init_aev_const(h->aevc, params->box, md.id);
   for (int m = 0; m < n_mols; ++m) h->max_mol = std::max(h->max_mol, mol_offsets[m + 1] - mol_offsets[m]);
@@ -1004,7 +1006,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
     // CTA pairs for the first layer's two products (grouped products of
     // layers 2 and 3 with K <= 3 x 256 and N <= 192 ran slower on pairs:
     // fewer, longer tiles for the same work)
-    h->l1_max_pairs = std::min(tc2_max_pairs(h->sms), h->sms / 2);
+    h->l1_max_pairs = h->single_cta ? 0 : std::min(tc2_max_pairs(h->sms), h->sms / 2);
     h->l1_pairs = h->l1_max_pairs > 0;
     const uint64_t R64 = (uint64_t)h->n_rows;
     struct MapSpec {

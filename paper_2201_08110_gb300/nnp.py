@@ -54,7 +54,7 @@ class Params(ctypes.Structure):
                 ("use_graph", ctypes.c_int32), ("neighbor_mode", ctypes.c_int32),
                 ("single_pass", ctypes.c_int32), ("recompute_aev", ctypes.c_int32),
                 ("test_abort", ctypes.c_int32), ("model", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("single_cta", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class MDParams(ctypes.Structure):
@@ -163,7 +163,7 @@ class NNP:
                  box=None, max_neighbors: int = 0, max_angular: int = 0,
                  use_graph: bool = False, total_charge: int = 0, neighbor_mode: int = 0,
                  single_pass: bool = False, recompute_aev: bool = False, test_abort: bool = False,
-                 model="ani2x"):
+                 model="ani2x", single_cta: bool = False):
         self._lib = load_library()
         Z = np.ascontiguousarray(Z, dtype=np.int32)
         if mol_off is None:
@@ -187,6 +187,7 @@ class NNP:
         p.recompute_aev = 1 if recompute_aev else 0
         p.test_abort = 1 if test_abort else 0
         p.model = _model_id(model)
+        p.single_cta = 1 if single_cta else 0
         h = ctypes.c_void_p()
         rc = self._lib.nnp_create_batch(Z.ctypes.data, mol_off.ctypes.data, mol_off.shape[0] - 1,
                                         ctypes.byref(p), ctypes.byref(h))

@@ -103,6 +103,12 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
     p.n_weights = w.size
     p.box[0] = p.box[1] = p.box[2] = 9.0
     assert lib.nnp_create(Z.ctypes.data, 2, ctypes.byref(p), ctypes.byref(h)) == 1  # box < 2 Rc
+    p.box[0] = p.box[1] = p.box[2] = 0.0
+    p.single_cta = 2
+    assert lib.nnp_create(Z.ctypes.data, 2, ctypes.byref(p), ctypes.byref(h)) == 1  # flag not 0 / 1
+    p.single_cta = 0
+    p.reserved[1] = 1
+    assert lib.nnp_create(Z.ctypes.data, 2, ctypes.byref(p), ctypes.byref(h)) == 1  # reserved field
     assert not h.value
 
 

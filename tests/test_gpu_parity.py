@@ -326,6 +326,25 @@ def test_pocket_and_dense_molecules(lib, prec):
     assert int(ca.max()) > 64
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16-single"])
+def test_single_cta_first_layer_matches_oracle(lib, prec):
+    """The first layer's products on single CTAs (128-row tiles, the path for
+    a device that cannot hold CTA pairs): the batch with biases and the
+    periodic region (2 networks, first-layer tiles split into column pieces)
+    against the oracle, with repeated steps bit-identical."""
+    cases = [(small_batch(), W.weights(6, 8, bias_std=0.1), 8), (W.pocket(9, n=250, edge=14.0), W.weights(7, 2), 2)]
+    for b, w, M in cases:
+        model, E, F = run(lib, b, w, M, prec, single_cta=True, use_graph=True)
+        worst = check_batch(prec, E, F, b, oracle_batch(b, w, M))
+        print(f"single-CTA {prec}: worst errors {worst}")
+        pos = torch.tensor(b.pos, device="cuda")
+        for _ in range(5):
+            E2, _ = model.compute(pos)
+        torch.cuda.synchronize()
+        model.status()
+        np.testing.assert_array_equal(E2.cpu().numpy(), E)
+
+
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 def test_repeated_steps_give_identical_energies(lib, prec):
     """Twenty steps of one handle on the same positions: the energies are
