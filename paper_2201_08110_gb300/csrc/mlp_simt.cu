@@ -1,100 +1,123 @@
 // mlp_simt.cu -- grouped matrix products of the atomic networks on the FP32
 // SIMT pipes (the plain FP32 path), with the networks' epilogues fused.
 //
-// Every product is D[M, N] = A[M, K] * B[N, K]^T with A and B K-major; the
-// problem list covers all elements and ensemble members of one layer, and a
-// tile table flattens their output tiles into one launch.  Tiles are 64 x 64,
-// 256 threads, 4 x 4 outputs per thread, K in steps of 16 staged through
-// shared memory.
+// Every product is D[M, N] = A[M, K] * B[N, K]^T with A and B K-major (rows
+// and leading dimensions 16-byte aligned, K a multiple of 4); the problem
+// list covers all elements and ensemble members of one layer, and a tile
+// table flattens their output tiles (simt_tile_m() x simt_tile_n()) into one
+// launch.
 #include "nnp_internal.cuh"
 
 namespace nnp {
 
 namespace {
 
-template <typename T> __device__ __forceinline__ float ld_f(const T* p);
-template <> __device__ __forceinline__ float ld_f<float>(const float* p) { return *p; }
-template <> __device__ __forceinline__ float ld_f<__nv_bfloat16>(const __nv_bfloat16* p) {
-  return __bfloat162float(*p);
-}
-template <> __device__ __forceinline__ float ld_f<__half>(const __half* p) { return __half2float(*p); }
-template <typename T> __device__ __forceinline__ void st_f(T* p, float v);
-template <> __device__ __forceinline__ void st_f<float>(float* p, float v) { *p = v; }
-template <> __device__ __forceinline__ void st_f<__nv_bfloat16>(__nv_bfloat16* p, float v) {
-  *p = __float2bfloat16_rn(v);
-}
-template <> __device__ __forceinline__ void st_f<__half>(__half* p, float v) { *p = __float2half_rn(v); }
+// Tiles of BM x BN outputs, 256 threads as 16 x 16, each thread TM x TN
+// outputs (rows ty * TM.., columns tx * TN..); K in steps of BK staged
+// through shared memory (transposed, k-major, rows padded so the 16-byte
+// reads stay aligned), the next step's operands fetched into registers while
+// the current one is multiplied (one barrier per step).
+constexpr int TM = 8, TN = 4, BK = 16;
+constexpr int BM = 16 * TM, BN = 16 * TN;
+constexpr int kPadM = BM + 4, kPadN = BN + 4;
 
-constexpr int BM = 64, BN = 64, BK = 16;
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_gemm_simt(const GemmProblem* __restrict__ probs,
+__global__ void __launch_bounds__(256, 3) k_gemm_simt(const GemmProblem* __restrict__ probs,
                                                    const GemmTile* __restrict__ tiles) {
-  __shared__ __align__(16) float As[BK][BM + 4];
-  __shared__ __align__(16) float Bs[BK][BN + 4];
+  __shared__ __align__(16) float As[2][BK][kPadM];
+  __shared__ __align__(16) float Bs[2][BK][kPadN];
   const GemmTile tl = tiles[blockIdx.x];
   const GemmProblem P = probs[tl.problem];
-  const T* __restrict__ A = static_cast<const T*>(P.A);
-  const T* __restrict__ B = static_cast<const T*>(P.B);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float acc[4][4];
+  const float* __restrict__ A = static_cast<const float*>(P.A);
+  const float* __restrict__ B = static_cast<const float*>(P.B);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // loader: float4 k4 (of BK / 4) of A rows lr and lr + 64, of B row lr
+  const int lr = tid >> 2, k4 = (tid & 3) * 4;
+  float4 ra[2], rb;
+  auto fetch = [&](int k0) {
+    const int gk = k0 + k4;
+    const bool kin = gk < P.K;  // K is a multiple of 4
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-
-  for (int k0 = 0; k0 < P.K; k0 += BK) {
-#pragma unroll
-    for (int it = 0; it < (BM * BK) / 256; ++it) {
-      const int idx = threadIdx.x + it * 256;
-      const int r = idx / BK, kk = idx % BK;
-      const int gm = tl.m0 + r, gk = k0 + kk;
-      As[kk][r] = (gm < P.M && gk < P.K) ? ld_f(A + (size_t)gm * P.lda + gk) : 0.f;
-      const int gn = tl.n0 + r;
-      Bs[kk][r] = (gn < P.N && gk < P.K) ? ld_f(B + (size_t)gn * P.ldb + gk) : 0.f;
+    for (int i = 0; i < 2; ++i) {
+      const int gm = tl.m0 + lr + 64 * i;
+      ra[i] = (kin && gm < P.M) ? __ldg(reinterpret_cast<const float4*>(A + (size_t)gm * P.lda + gk))
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    __syncthreads();
+    const int gn = tl.n0 + lr;
+    rb = (kin && gn < P.N) ? __ldg(reinterpret_cast<const float4*>(B + (size_t)gn * P.ldb + gk))
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  auto stage = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      As[buf][k4 + 0][lr + 64 * i] = ra[i].x;
+      As[buf][k4 + 1][lr + 64 * i] = ra[i].y;
+      As[buf][k4 + 2][lr + 64 * i] = ra[i].z;
+      As[buf][k4 + 3][lr + 64 * i] = ra[i].w;
+    }
+    Bs[buf][k4 + 0][lr] = rb.x;
+    Bs[buf][k4 + 1][lr] = rb.y;
+    Bs[buf][k4 + 2][lr] = rb.z;
+    Bs[buf][k4 + 3][lr] = rb.w;
+  };
+  float acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+
+  fetch(0);
+  stage(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < P.K; k0 += BK) {
+    const bool more = k0 + BK < P.K;
+    if (more) fetch(k0 + BK);  // in flight during this step's products
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      const float4 a = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-      const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * TM]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * TM + 4]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * TN]);
+      const float av[TM] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[TN] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
-    __syncthreads();
+    if (more) {
+      stage(buf ^ 1);  // the other buffer: its readers finished before the last barrier
+      __syncthreads();
+      buf ^= 1;
+    }
   }
 
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int m = tl.m0 + ty * 4 + i;
+  for (int i = 0; i < TM; ++i) {
+    const int m = tl.m0 + ty * TM + i;
     if (m >= P.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int n = tl.n0 + tx * 4 + j;
+    for (int j = 0; j < TN; ++j) {
+      const int n = tl.n0 + tx * TN + j;
       if (n >= P.N) continue;
       const float v = acc[i][j];
+      float* d = static_cast<float*>(P.D) + (size_t)m * P.ldd + n;
       switch (P.epi) {
         case (int)Epi::BiasCelu: {
           const float z = v + P.bias[n];
           // alpha expm1(z / alpha): exp(z / alpha) - 1 would cancel for small |z|
-          const float h = z > 0.f ? z : 0.1f * expm1f(fminf(z, 0.f) * 10.f);
-          st_f(static_cast<T*>(P.D) + (size_t)m * P.ldd + n, h);
+          *d = z > 0.f ? z : 0.1f * expm1f(fminf(z, 0.f) * 10.f);
           break;
         }
         case (int)Epi::Bias:
-          static_cast<float*>(P.D)[(size_t)m * P.ldd + n] = v + P.bias[n];
+          *d = v + P.bias[n];
           break;
         case (int)Epi::DCelu: {
-          T* d = static_cast<T*>(P.D) + (size_t)m * P.ldd + n;
-          const float h = ld_f(d);
-          st_f(d, v * (h > 0.f ? 1.f : fmaf(10.f, h, 1.f)));
+          const float h = *d;
+          *d = v * (h > 0.f ? 1.f : fmaf(10.f, h, 1.f));
           break;
         }
         default:
-          static_cast<float*>(P.D)[(size_t)m * P.ldd + n] = v;
+          *d = v;
           break;
       }
     }
@@ -103,18 +126,12 @@ __global__ void __launch_bounds__(256) k_gemm_simt(const GemmProblem* __restrict
 
 }  // namespace
 
-void launch_gemm_simt_typed(const GemmProblem* probs, const GemmTile* tiles, int n_tiles, Prec p,
-                            cudaStream_t s) {
-  if (n_tiles <= 0) return;
-  switch (p) {
-    case Prec::F32: k_gemm_simt<float><<<n_tiles, 256, 0, s>>>(probs, tiles); break;
-    case Prec::BF16: k_gemm_simt<__nv_bfloat16><<<n_tiles, 256, 0, s>>>(probs, tiles); break;
-    case Prec::F16: k_gemm_simt<__half><<<n_tiles, 256, 0, s>>>(probs, tiles); break;
-  }
-}
+int simt_tile_m() { return BM; }
+int simt_tile_n() { return BN; }
 
 void launch_gemm_simt(const GemmProblem* probs, const GemmTile* tiles, int n_tiles, cudaStream_t s) {
-  launch_gemm_simt_typed(probs, tiles, n_tiles, Prec::F32, s);
+  if (n_tiles <= 0) return;
+  k_gemm_simt<<<n_tiles, 256, 0, s>>>(probs, tiles);
 }
 
 }  // namespace nnp

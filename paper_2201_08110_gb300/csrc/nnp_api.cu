@@ -919,7 +919,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
   float* Z3 = h->d_z3;
   char* D3 = static_cast<char*>(h->d_d3);
   const bool tc = h->prec != Prec::F32;
-  const int bm = tc ? 128 : 64;
+  const int bm = tc ? 128 : simt_tile_m(), bn_simt = simt_tile_n();
   for (int e = 0; e < NE; ++e) {
     const int Me = h->elem_count[e];
     if (Me == 0) continue;
@@ -940,7 +940,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         P.d_lo = M * kH1Max;
       }
       h->L[0].probs.push_back(P);
-      add_tiles(h->L[0], bm, tc ? 256 : 64);  // first layer forward
+      add_tiles(h->L[0], bm, tc ? 256 : bn_simt);  // first layer forward
     }
     {  // layer 1 reverse: dE/dG = sum_m delta1_m W1_m
       GemmProblem P{};
@@ -950,7 +950,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
       P.M = Me; P.N = tc ? (int)kpad : nfeat; P.K = M * n1; P.epi = (int)Epi::Store;
       P.a_row0 = (int)row0; P.b_row0 = e * (int)kpad; P.elem = e; P.model = -1;
       h->L[5].probs.push_back(P);
-      add_tiles(h->L[5], bm, tc ? 256 : 64);
+      add_tiles(h->L[5], bm, tc ? 256 : bn_simt);
     }
     // layers 2 and 3 and their reverse as grouped products: the FP32 path only
     // (on tensor cores the fused tail keeps h2, d3 and d2 on chip)
@@ -964,7 +964,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         P.M = Me; P.N = n2; P.K = n1; P.epi = (int)Epi::BiasCelu;
         P.a_row0 = (int)row0; P.a_col0 = m * n1; P.b_row0 = (int)r2[e][m]; P.elem = e; P.model = m;
         h->L[1].probs.push_back(P);
-        add_tiles(h->L[1], bm, tc ? 256 : 64);
+        add_tiles(h->L[1], bm, tc ? 256 : bn_simt);
       }
       {  // layer 3 forward: the FP32 pre-activation for k_head
         GemmProblem P{};
@@ -976,7 +976,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         P.M = Me; P.N = n3; P.K = n2;
         P.a_row0 = (int)row0; P.a_col0 = m * n2; P.b_row0 = (int)r3[e][m]; P.elem = e; P.model = m;
         h->L[2].probs.push_back(P);
-        add_tiles(h->L[2], bm, tc ? 256 : 64);
+        add_tiles(h->L[2], bm, tc ? 256 : bn_simt);
       }
       {  // layer 3 reverse: delta2 = (delta3 W3) * celu'(h2), in place over h2
         GemmProblem P{};
@@ -986,7 +986,7 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         P.M = Me; P.N = n2; P.K = n3; P.epi = (int)Epi::DCelu;
         P.a_row0 = (int)row0; P.a_col0 = m * n3; P.b_row0 = (int)r3t[e][m]; P.elem = e; P.model = m;
         h->L[3].probs.push_back(P);
-        add_tiles(h->L[3], bm, tc ? 256 : 64);
+        add_tiles(h->L[3], bm, tc ? 256 : bn_simt);
       }
       {  // layer 2 reverse: delta1 = (delta2 W2) * celu'(h1), in place over h1
         GemmProblem P{};
@@ -996,10 +996,16 @@ nnp_status nnp_create_batch(const int32_t* Z, const int32_t* mol_offsets, int32_
         P.M = Me; P.N = n1; P.K = n2; P.epi = (int)Epi::DCelu;
         P.a_row0 = (int)row0; P.a_col0 = m * n2; P.b_row0 = (int)r2t[e][m]; P.elem = e; P.model = m;
         h->L[4].probs.push_back(P);
-        add_tiles(h->L[4], bm, tc ? 256 : 64);
+        add_tiles(h->L[4], bm, tc ? 256 : bn_simt);
       }
     }
   }
+  if (!tc)  // the SIMT products read 16-byte vectors along K
+    for (const Layer& L : h->L)
+      for (const GemmProblem& P : L.probs)
+        if (((reinterpret_cast<uintptr_t>(P.A) | reinterpret_cast<uintptr_t>(P.B)) & 15) || (P.lda | P.ldb) % 4 ||
+            P.K % 4)
+          return fail(h, NNP_ERR_UNSUPPORTED, "FP32 product operands not 16-byte aligned");
   if (tc) {
     if (tc_maps_bytes() > sizeof(h->tc_maps[0])) return fail(h, NNP_ERR_UNSUPPORTED, "tensor map size");
     CK(tc_set_smem());

@@ -263,10 +263,12 @@ void launch_head(const float* z3, long ldz, Prec prec, const int* row_elem, cons
                  const int h3[kSpecies], cudaStream_t s);
 void launch_energy(const float* y, int n_models, const int* row_of_int, const int* mol_off,
                    int n_mols, double* energy_out, double* atom_energy_row, cudaStream_t s);
+// FP32 grouped products on the SIMT pipes; tiles of simt_tile_m() x
+// simt_tile_n() outputs.
 void launch_gemm_simt(const GemmProblem* d_problems, const GemmTile* d_tiles, int n_tiles,
                       cudaStream_t s);
-void launch_gemm_simt_typed(const GemmProblem* d_problems, const GemmTile* d_tiles, int n_tiles,
-                            Prec p, cudaStream_t s);
+int simt_tile_m();
+int simt_tile_n();
 size_t aev_fwd_smem_bytes(int cap_r, int cap_a, int warps);
 size_t aev_adj_smem_bytes(int cap_r, int cap_a, int warps, int mol_atoms_smem_max);
 cudaError_t aev_set_smem_limits(size_t fwd_bytes, size_t adj_bytes);
