@@ -59,11 +59,11 @@ __global__ void __launch_bounds__(256, 3) k_gemm_simt(const GemmProblem* __restr
     Bs[buf][k4 + 2][lr] = rb.z;
     Bs[buf][k4 + 3][lr] = rb.w;
   };
-  float acc[TM][TN];
+  float2 acc[TM][TN / 2];  // columns (2j, 2j + 1) as a pair: packed FP32 products
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < TN / 2; ++j) acc[i][j] = make_float2(0.f, 0.f);
 
   fetch(0);
   stage(0);
@@ -78,11 +78,11 @@ __global__ void __launch_bounds__(256, 3) k_gemm_simt(const GemmProblem* __restr
       const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * TM + 4]);
       const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * TN]);
       const float av[TM] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float bv[TN] = {b.x, b.y, b.z, b.w};
+      const float2 bv[TN / 2] = {make_float2(b.x, b.y), make_float2(b.z, b.w)};
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        for (int j = 0; j < TN / 2; ++j) acc[i][j] = __ffma2_rn(make_float2(av[i], av[i]), bv[j], acc[i][j]);
     }
     if (more) {
       stage(buf ^ 1);  // the other buffer: its readers finished before the last barrier
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256, 3) k_gemm_simt(const GemmProblem* __restr
     for (int j = 0; j < TN; ++j) {
       const int n = tl.n0 + tx * TN + j;
       if (n >= P.N) continue;
-      const float v = acc[i][j];
+      const float v = (j & 1) ? acc[i][j >> 1].y : acc[i][j >> 1].x;
       float* d = static_cast<float*>(P.D) + (size_t)m * P.ldd + n;
       switch (P.epi) {
         case (int)Epi::BiasCelu: {
