@@ -334,7 +334,7 @@ NCU_TRAFFIC = {
     ("adjoint", "9212797d998e"): 4585.2,  # main launch (the overflow launch moves ~1 KB)
     ("l1_fwd", "8c4a8808f271"): 12052.4,  # first layer forward, CTA pairs
     ("l1_rev", "8c4a8808f271"): 7296.0,   # the same kernel's second launch, first-layer reverse
-    ("tail", "a3a9d71014bf"): 11044.0,    # layers 2 and 3 forward and reverse
+    ("tail", "d55967cc02da"): 11044.0,    # layers 2 and 3 forward and reverse
 }
 
 

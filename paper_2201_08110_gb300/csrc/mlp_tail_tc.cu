@@ -20,7 +20,8 @@
 //     as soon as the previous tile's MMAs are done with that block of A1;
 //     then the W3, W3^T, W2^T blocks);
 //   warp 18, one lane: TMA loads of phase 4's staged h1 tile;
-//   warp 1, one lane: tcgen05.mma issuer; the four phases of a tile alternate
+//   warp 1: tcgen05.mma issuer (the whole warp walks the loop, an elected
+//     lane issues each instruction); the four phases of a tile alternate
 //     between two 256-column accumulators, and K block b of a phase waits
 //     only until the epilogue has written block b of its A operand, so a
 //     phase's MMAs overlap the previous phase's epilogue;
@@ -31,11 +32,11 @@
 // the producer loads h1_hi into A1 and h1_lo into the second buffer and the
 // block after it by TMA (h1_lo once the previous tile is done there: its d1
 // store has read the staging memory, or without the reverse pass its last
-// product has read h2_lo).  Each forward layer is three products, the two on
-// the hi half of the activations first (for layer 2 they need only A1, so
-// they overlap the previous tile's last epilogue), then lo x W_hi; phase 1's
-// epilogue writes h2 as hi into A1 and lo into A2, phase 2's output layer
-// then writes d3 over h2_lo.
+// product has read h2_lo).  Each forward layer is three products: for layer
+// 2 the two on h1_hi first (they need only A1, so they overlap the previous
+// tile's last epilogue), then h1_lo x W2_hi; for layer 3 the three of each
+// 64-column block as soon as phase 1's epilogue has written it (h2 as hi
+// into A1 and lo into A2); phase 2's output layer then writes d3 over h2_lo.
 // Waits are bounded: one that gives up sets the timeout status bit, the CTA
 // stops, frees its tensor memory and returns.
 #include <cstring>
