@@ -356,8 +356,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint64_t da = smem_desc_sw128(a_base + (size_t)kb * kBlk);
           const uint64_t db = smem_desc_sw128(ring + (size_t)s * kRingBytes);
           const int ksteps = min(kBK, k - kb * kBK) / 16;
-          for (int j = 0; j < ksteps; ++j)
-            mma_f16_elect(d, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc, (kb > 0 || j > 0) ? 1u : 0u);
+          if (ksteps == 4) {
+            mma_f16_elect4(d, da, db, idesc, kb > 0 ? 1u : 0u);
+          } else {
+            for (int j = 0; j < ksteps; ++j)
+              mma_f16_elect(d, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc, (kb > 0 || j > 0) ? 1u : 0u);
+          }
           mma_commit_elect(&empty[s]);
           if (blk_free) mma_commit_elect(&blk_free[kb]);
         }
@@ -393,9 +397,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint64_t da = smem_desc_sw128(A1 + (size_t)kb * kBlk);
           const uint64_t db = smem_desc_sw128(ring + (size_t)s * kRingBytes);
           const int ksteps = min(kBK, P.h1 - kb * kBK) / 16;
-          for (int j = 0; j < ksteps; ++j) {
-            mma_f16_elect(d, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc, acc ? 1u : 0u);
+          if (ksteps == 4) {
+            mma_f16_elect4(d, da, db, idesc, acc ? 1u : 0u);
             acc = true;
+          } else {
+            for (int j = 0; j < ksteps; ++j) {
+              mma_f16_elect(d, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc, acc ? 1u : 0u);
+              acc = true;
+            }
           }
           mma_commit_elect(&empty[s]);
           ++it;
@@ -440,9 +449,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint64_t da = smem_desc_sw128((lo_half ? A2 : A1) + (size_t)kb * kBlk);
           const uint64_t db = smem_desc_sw128(ring + (size_t)s * kRingBytes);
           const int ksteps = min(kBK, k - kb * kBK) / 16;
-          for (int j = 0; j < ksteps; ++j) {
-            mma_f16_elect(d, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc, acc ? 1u : 0u);
+          if (ksteps == 4) {
+            mma_f16_elect4(d, da, db, idesc, acc ? 1u : 0u);
             acc = true;
+          } else {
+            for (int j = 0; j < ksteps; ++j) {
+              mma_f16_elect(d, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), idesc, acc ? 1u : 0u);
+              acc = true;
+            }
           }
           mma_commit_elect(&empty[s]);
           ++it;

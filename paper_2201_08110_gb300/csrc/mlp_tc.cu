@@ -286,10 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const unsigned char* sa = smem + s * kStageBytes;
         const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sa + kABytes);
         if (kb * kBK + kBK <= P.K) {  // a whole K block: four K = 16 steps, +32 bytes each
-          mma_f16_elect(dtm, da, db, idesc, kt > 0 ? 1u : 0u);
-          mma_f16_elect(dtm, da + 2, db + 2, idesc, 1u);
-          mma_f16_elect(dtm, da + 4, db + 4, idesc, 1u);
-          mma_f16_elect(dtm, da + 6, db + 6, idesc, 1u);
+          mma_f16_elect4(dtm, da, db, idesc, kt > 0 ? 1u : 0u);
         } else {
           const int ksteps = (P.K - kb * kBK) / 16;
           for (int j = 0; j < ksteps; ++j)
@@ -485,10 +482,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           const unsigned char* sa = smem + s * kStageBytes2;
           const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sa + kABytes);
           if (kb * kBK + kBK <= P.K) {
-            mma_f16_pair_elect(dtm, da, db, idesc, kt > 0 ? 1u : 0u);
-            mma_f16_pair_elect(dtm, da + 2, db + 2, idesc, 1u);
-            mma_f16_pair_elect(dtm, da + 4, db + 4, idesc, 1u);
-            mma_f16_pair_elect(dtm, da + 6, db + 6, idesc, 1u);
+            mma_f16_pair_elect4(dtm, da, db, idesc, kt > 0 ? 1u : 0u);
           } else {
             const int ksteps = (P.K - kb * kBK) / 16;
             for (int j = 0; j < ksteps; ++j)

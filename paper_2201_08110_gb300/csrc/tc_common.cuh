@@ -194,6 +194,38 @@ __device__ __forceinline__ void mma_f16_pair_elect(uint32_t tmem_d, uint64_t a, 
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
+// The four K = 16 steps of a 64-column K block under one election: the
+// descriptors advance by 32 bytes (2 in their 16-byte address units) a step;
+// accumulate applies to the first step, the others accumulate.
+__device__ __forceinline__ void mma_f16_elect4(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                               uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p, q, e;\n\t"
+      "elect.sync _|e, 0xffffffff;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "setp.eq.b32 q, %4, %4;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %6, %3, q;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %7, %8, %3, q;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %9, %10, %3, q;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate), "l"(a + 2), "l"(b + 2), "l"(a + 4), "l"(b + 4), "l"(a + 6),
+      "l"(b + 6));
+}
+__device__ __forceinline__ void mma_f16_pair_elect4(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                                    uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p, q, e;\n\t"
+      "elect.sync _|e, 0xffffffff;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "setp.eq.b32 q, %4, %4;\n\t"
+      "@e tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t"
+      "@e tcgen05.mma.cta_group::2.kind::f16 [%0], %5, %6, %3, q;\n\t"
+      "@e tcgen05.mma.cta_group::2.kind::f16 [%0], %7, %8, %3, q;\n\t"
+      "@e tcgen05.mma.cta_group::2.kind::f16 [%0], %9, %10, %3, q;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate), "l"(a + 2), "l"(b + 2), "l"(a + 4), "l"(b + 4), "l"(a + 6),
+      "l"(b + 6));
+}
+
 __device__ __forceinline__ void mma_commit_elect(uint64_t* bar) {
   asm volatile(
       "{\n\t.reg .pred e;\n\t"
