@@ -332,9 +332,9 @@ NCU_TRAFFIC = {
     # ncu --set full, 512-molecule batch, split BF16 step (first launches of each kernel)
     ("features", "9212797d998e"): 2849.1,
     ("adjoint", "9212797d998e"): 4585.2,  # main launch (the overflow launch moves ~1 KB)
-    ("l1_fwd", "8c4a8808f271"): 12052.4,  # first layer forward, CTA pairs
-    ("l1_rev", "8c4a8808f271"): 7296.0,   # the same kernel's second launch, first-layer reverse
-    ("tail", "d55967cc02da"): 11044.0,    # layers 2 and 3 forward and reverse
+    ("l1_fwd", "4baba2fdbf12"): 12062.0,  # first layer forward, CTA pairs
+    ("l1_rev", "4baba2fdbf12"): 7299.3,   # the same kernel's second launch, first-layer reverse
+    ("tail", "2a9bf57dcfbd"): 11042.4,    # layers 2 and 3 forward and reverse
 }
 
 
