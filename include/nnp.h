@@ -230,10 +230,9 @@ nnp_status nnp_get_atomic_energies(nnp_handle h, double* energies_dev, void* str
 /* ---- measurement -------------------------------------------------------------- */
 
 /* Stages of one evaluation, in launch order.  Fused kernels report in the
- * slot of their first stage: with 16-bit networks in one product per layer,
- * layers 2 and 3 forward and reverse in NNP_STAGE_L2_FWD; with split operands
- * and forces, layer 3 forward, the output layer and layers 3 and 2 reverse in
- * NNP_STAGE_L3_FWD. */
+ * slot of their first stage: with 16-bit networks, layers 2 and 3 forward,
+ * the output layer and (with forces) layers 3 and 2 reverse run in one kernel
+ * and report in NNP_STAGE_L2_FWD. */
 typedef enum {
   NNP_STAGE_NEIGHBORS = 0, /* position gather + neighbour lists */
   NNP_STAGE_FEATURES = 1,  /* radial + angular features */
